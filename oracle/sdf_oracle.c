@@ -1,0 +1,981 @@
+/*
+ * sdf_oracle.c -- plain FP64 CPU oracle of the online-spectral-deflation
+ * active-set solver (arXiv 2606.17971).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load this library.  It shares
+ * no code, header, table or helper with the CUDA path and is written for
+ * legibility, not speed: explicit CSR assembly, explicit sub-matrix
+ * extraction, Householder QR, Jacobi eigenvalues, plain loops.  Where OpenMP
+ * is used it only splits independent rows / independent dot products, so the
+ * result does not depend on the thread count.
+ *
+ * What each function follows (sections / equations / algorithms of the paper):
+ *   orc_create           -- Sec. 2.1.2 Eq. (schur): S = M + alpha K^T M^-1 K
+ *                           (= alpha A^T A + I when M = I, K = A);
+ *                           App. A Eq. (fd_lap) 5/7-point -Laplacian,
+ *                           Eq. (harmonic) harmonic face averaging,
+ *                           App. B.3 explicit CSR assembly of S.
+ *   orc_desired_state    -- the Gaussian desired state of the benchmark
+ *                           workloads, y_d = a exp(-|x-c|^2 / (2 s^2)).
+ *   orc_solve            -- App. B.1 Algorithm (pdas): primal active-set loop,
+ *                           Eq. (reduced) restricted system, and
+ *                           Algorithm (online_deflation) lines 5-18: restrict
+ *                           + QR, E = Z^T S_II Z, cond(E) > tau_cond guard.
+ *   pcg_core             -- App. B.2 Jacobi-PCG, stop on ||r|| < eps ||b||.
+ *   adef2_core           -- Sec. 2.2.1 Algorithm (adef2), read as the standard
+ *                           A-DEF2 of Tang et al. / Gaul et al. that the paper
+ *                           cites: x0 <- x0 + Q(b - S x0); preconditioned
+ *                           residual z = D^-1 r; search direction
+ *                           p = P z + beta p with P = I - Z E^-1 Z^T S_II;
+ *                           unprojected residual recurrence, stop on
+ *                           ||r|| < eps ||b|| (App. B.2).
+ *
+ * Readings where the paper is silent or garbled are listed in the design doc of
+ * the repository; the ones that change arithmetic are repeated at the
+ * function that implements them.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_ERR_ARG 1
+#define ORC_ERR_NOMEM 2
+#define ORC_ERR_CG_MAXIT 5
+#define ORC_ERR_OUTER_MAXIT 6
+#define ORC_ERR_BREAKDOWN 7
+#define ORC_ERR_NONFINITE 8
+
+typedef struct {
+  int n;      /* rows */
+  int *rp;    /* n+1 */
+  int *ci;    /* nnz */
+  double *v;  /* nnz */
+} csr_t;
+
+typedef struct {
+  int dim, nx, ny, nz, N;
+  double h[3];
+  double alpha, mass, kscale;
+  csr_t A; /* state operator A_h (K = kscale * A_h)              */
+  csr_t S; /* S = mass I + (alpha kscale^2 / mass) A^T A         */
+} orc_problem;
+
+/* Per-solve statistics, filled by orc_solve (layout mirrored in oracle.py). */
+#define ORC_MAX_OUTER 64
+typedef struct {
+  int32_t status;
+  int32_t outer_iters;
+  int32_t cg_iters[ORC_MAX_OUTER];
+  int32_t n_active[ORC_MAX_OUTER]; /* |A| in force during outer iteration j */
+  int32_t fallback[ORC_MAX_OUTER]; /* 1 = plain PCG used (guard fired)      */
+  double cond_E[ORC_MAX_OUTER];
+  double relres[ORC_MAX_OUTER];    /* recurrence ||r||/||b|| at exit        */
+  double true_relres;              /* ||b - S_II x||/||b||, last solve      */
+  double min_margin;               /* min over I of |y_i - (psi_i - tau)|   */
+  double min_lambda_active;        /* min of lambda over the final A        */
+} orc_stats;
+
+typedef struct {
+  double rtol;      /* CG tolerance on ||r||/||b||                          */
+  double tau;       /* active-set tolerance (App. B.1: 1e-10)               */
+  double tau_cond;  /* solve-time guard (Remark tau_cond: 1e10)             */
+  int32_t max_outer;/* maximum number of inner solves                       */
+  int32_t max_cg;   /* CG iteration cap                                     */
+  int32_t deflate;  /* 1: A-DEF2 with the given modes, 0: plain Jacobi-PCG  */
+  int32_t rule;     /* 0: primal rule (paper), 1: full PDAS rule (test only) */
+  double pdas_c;    /* c of the PDAS rule lambda_i + c (y_i - psi_i) > 0    */
+} orc_opts;
+
+/* ------------------------------------------------------------------------ */
+/* small helpers                                                            */
+
+static void csr_free(csr_t *m) {
+  free(m->rp);
+  free(m->ci);
+  free(m->v);
+  m->rp = NULL;
+  m->ci = NULL;
+  m->v = NULL;
+}
+
+static double dot(int n, const double *a, const double *b) {
+  double s = 0.0;
+  for (int i = 0; i < n; ++i) s += a[i] * b[i];
+  return s;
+}
+
+static double nrm2(int n, const double *a) { return sqrt(dot(n, a, a)); }
+
+static void csr_mv(const csr_t *m, const double *x, double *y) {
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < m->n; ++i) {
+    double s = 0.0;
+    for (int p = m->rp[i]; p < m->rp[i + 1]; ++p) s += m->v[p] * x[m->ci[p]];
+    y[i] = s;
+  }
+}
+
+static int node_index(const orc_problem *P, int i, int j, int l) {
+  return i + P->nx * (j + P->ny * l);
+}
+
+/* Harmonic face average, Eq. (harmonic). */
+static double harmonic(double a, double b) { return 2.0 * a * b / (a + b); }
+
+/* ------------------------------------------------------------------------ */
+/* Assembly of A_h (App. A) and S (Sec. 2.1.2, App. B.3).                   */
+
+/*
+ * A_h y at node p:
+ *   diff_scale * sum over the 2d faces f of kappa_f (y_p - y_nb(f)) / h_d^2
+ *   + first-order upwind convection  b_d (y_p - y_{p-e_d}) / h_d  (b_d > 0)
+ *                                    b_d (y_{p+e_d} - y_p) / h_d  (b_d < 0)
+ * with homogeneous Dirichlet data (neighbours outside the grid are 0).
+ * kappa_f is the harmonic mean of the two node values; a face towards the
+ * boundary takes the interior node's value.
+ */
+static int assemble_A(orc_problem *P, const double *kappa, double diff_scale,
+                      const double *bvec) {
+  int N = P->N, dim = P->dim;
+  int maxnz = N * (2 * dim + 1);
+  csr_t *A = &P->A;
+  A->n = N;
+  A->rp = (int *)malloc(sizeof(int) * (N + 1));
+  A->ci = (int *)malloc(sizeof(int) * maxnz);
+  A->v = (double *)malloc(sizeof(double) * maxnz);
+  if (!A->rp || !A->ci || !A->v) return ORC_ERR_NOMEM;
+  int n[3] = {P->nx, P->ny, P->nz};
+  int nnz = 0;
+  A->rp[0] = 0;
+  for (int l = 0; l < (dim == 3 ? P->nz : 1); ++l)
+    for (int j = 0; j < P->ny; ++j)
+      for (int i = 0; i < P->nx; ++i) {
+        int p = node_index(P, i, j, l);
+        int c[3] = {i, j, l};
+        double kp = kappa ? kappa[p] : 1.0;
+        double diag = 0.0;
+        double off[3][2] = {{0, 0}, {0, 0}, {0, 0}}; /* [dir][side -,+] */
+        int has[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+        for (int d = 0; d < dim; ++d) {
+          double ih2 = 1.0 / (P->h[d] * P->h[d]);
+          for (int s = 0; s < 2; ++s) {
+            int cc[3] = {c[0], c[1], c[2]};
+            cc[d] += (s == 0) ? -1 : 1;
+            int inside = cc[d] >= 0 && cc[d] < n[d];
+            double kf;
+            if (inside) {
+              int q = node_index(P, cc[0], cc[1], cc[2]);
+              double kq = kappa ? kappa[q] : 1.0;
+              kf = harmonic(kp, kq);
+              has[d][s] = 1;
+              off[d][s] -= diff_scale * kf * ih2;
+            } else {
+              kf = kp;
+            }
+            diag += diff_scale * kf * ih2;
+          }
+          double bd = bvec ? bvec[d] : 0.0;
+          if (bd > 0.0) {
+            diag += bd / P->h[d];
+            if (c[d] - 1 >= 0) {
+              has[d][0] = 1;
+              off[d][0] -= bd / P->h[d];
+            }
+          } else if (bd < 0.0) {
+            diag -= bd / P->h[d];
+            if (c[d] + 1 < n[d]) {
+              has[d][1] = 1;
+              off[d][1] += bd / P->h[d];
+            }
+          }
+        }
+        /* emit in increasing column index: -z, -y, -x, 0, +x, +y, +z */
+        for (int d = dim - 1; d >= 0; --d)
+          if (has[d][0]) {
+            int cc[3] = {c[0], c[1], c[2]};
+            cc[d] -= 1;
+            A->ci[nnz] = node_index(P, cc[0], cc[1], cc[2]);
+            A->v[nnz++] = off[d][0];
+          }
+        A->ci[nnz] = p;
+        A->v[nnz++] = diag;
+        for (int d = 0; d < dim; ++d)
+          if (has[d][1]) {
+            int cc[3] = {c[0], c[1], c[2]};
+            cc[d] += 1;
+            A->ci[nnz] = node_index(P, cc[0], cc[1], cc[2]);
+            A->v[nnz++] = off[d][1];
+          }
+        A->rp[p + 1] = nnz;
+      }
+  return ORC_OK;
+}
+
+static int csr_transpose(const csr_t *m, csr_t *t) {
+  int n = m->n, nnz = m->rp[n];
+  t->n = n;
+  t->rp = (int *)calloc(n + 1, sizeof(int));
+  t->ci = (int *)malloc(sizeof(int) * (nnz > 0 ? nnz : 1));
+  t->v = (double *)malloc(sizeof(double) * (nnz > 0 ? nnz : 1));
+  if (!t->rp || !t->ci || !t->v) return ORC_ERR_NOMEM;
+  for (int p = 0; p < nnz; ++p) t->rp[m->ci[p] + 1]++;
+  for (int i = 0; i < n; ++i) t->rp[i + 1] += t->rp[i];
+  int *fill = (int *)malloc(sizeof(int) * (n > 0 ? n : 1));
+  if (!fill) return ORC_ERR_NOMEM;
+  memcpy(fill, t->rp, sizeof(int) * n);
+  for (int i = 0; i < n; ++i)
+    for (int p = m->rp[i]; p < m->rp[i + 1]; ++p) {
+      int q = fill[m->ci[p]]++;
+      t->ci[q] = i;
+      t->v[q] = m->v[p];
+    }
+  free(fill);
+  return ORC_OK;
+}
+
+/* S = mass I + w A^T A, w = alpha kscale^2 / mass; row p of A^T A is the sum
+ * over the rows l of A that hold column p of A_lp * (row l of A). */
+static int assemble_S(orc_problem *P) {
+  csr_t At;
+  int rc = csr_transpose(&P->A, &At);
+  if (rc) return rc;
+  int N = P->N;
+  double w = P->alpha * P->kscale * P->kscale / P->mass;
+  int *mark = (int *)malloc(sizeof(int) * N);
+  double *acc = (double *)calloc(N, sizeof(double));
+  int *list = (int *)malloc(sizeof(int) * 64);
+  csr_t *S = &P->S;
+  S->n = N;
+  S->rp = (int *)malloc(sizeof(int) * (N + 1));
+  if (!mark || !acc || !list || !S->rp) return ORC_ERR_NOMEM;
+  /* first pass: count the pattern */
+  for (int i = 0; i < N; ++i) mark[i] = -1;
+  S->rp[0] = 0;
+  for (int p = 0; p < N; ++p) {
+    int cnt = 1;
+    mark[p] = p;
+    for (int a = At.rp[p]; a < At.rp[p + 1]; ++a) {
+      int l = At.ci[a];
+      for (int b = P->A.rp[l]; b < P->A.rp[l + 1]; ++b) {
+        int q = P->A.ci[b];
+        if (mark[q] != p) {
+          mark[q] = p;
+          cnt++;
+        }
+      }
+    }
+    S->rp[p + 1] = S->rp[p] + cnt;
+  }
+  int nnz = S->rp[N];
+  S->ci = (int *)malloc(sizeof(int) * nnz);
+  S->v = (double *)malloc(sizeof(double) * nnz);
+  if (!S->ci || !S->v) return ORC_ERR_NOMEM;
+  /* second pass: values */
+  for (int i = 0; i < N; ++i) mark[i] = -1;
+  for (int p = 0; p < N; ++p) {
+    int cnt = 0;
+    list[cnt++] = p;
+    mark[p] = p;
+    acc[p] = 0.0;
+    for (int a = At.rp[p]; a < At.rp[p + 1]; ++a) {
+      int l = At.ci[a];
+      double alp = At.v[a]; /* = A_lp */
+      for (int b = P->A.rp[l]; b < P->A.rp[l + 1]; ++b) {
+        int q = P->A.ci[b];
+        if (mark[q] != p) {
+          mark[q] = p;
+          acc[q] = 0.0;
+          list[cnt++] = q;
+        }
+        acc[q] += alp * P->A.v[b];
+      }
+    }
+    /* insertion sort of the (at most 25) column indices */
+    for (int x = 1; x < cnt; ++x) {
+      int key = list[x], y = x - 1;
+      while (y >= 0 && list[y] > key) {
+        list[y + 1] = list[y];
+        --y;
+      }
+      list[y + 1] = key;
+    }
+    int base = S->rp[p];
+    for (int x = 0; x < cnt; ++x) {
+      int q = list[x];
+      S->ci[base + x] = q;
+      S->v[base + x] = w * acc[q] + (q == p ? P->mass : 0.0);
+    }
+  }
+  free(mark);
+  free(acc);
+  free(list);
+  csr_free(&At);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Public: problem life cycle and accessors                                  */
+
+void orc_destroy(void *h) {
+  orc_problem *P = (orc_problem *)h;
+  if (!P) return;
+  csr_free(&P->A);
+  csr_free(&P->S);
+  free(P);
+}
+
+/* dim 2 or 3; n_d interior nodes per direction, h_d = 1/(n_d+1).
+ * kappa: node diffusivity (N values) or NULL for kappa = 1.
+ * bvec: convection velocity (dim values) or NULL.
+ * K = kscale * A_h, M = mass * I. */
+void *orc_create(int dim, int nx, int ny, int nz, const double *kappa,
+                 double diff_scale, const double *bvec, double kscale,
+                 double mass, double alpha) {
+  if (dim != 2 && dim != 3) return NULL;
+  if (nx < 1 || ny < 1 || (dim == 3 && nz < 1)) return NULL;
+  if (!(mass > 0.0) || !(alpha > 0.0)) return NULL;
+  orc_problem *P = (orc_problem *)calloc(1, sizeof(orc_problem));
+  if (!P) return NULL;
+  P->dim = dim;
+  P->nx = nx;
+  P->ny = ny;
+  P->nz = dim == 3 ? nz : 1;
+  P->N = P->nx * P->ny * P->nz;
+  P->h[0] = 1.0 / (nx + 1);
+  P->h[1] = 1.0 / (ny + 1);
+  P->h[2] = dim == 3 ? 1.0 / (nz + 1) : 1.0;
+  P->alpha = alpha;
+  P->mass = mass;
+  P->kscale = kscale;
+  if (assemble_A(P, kappa, diff_scale, bvec) || assemble_S(P)) {
+    orc_destroy(P);
+    return NULL;
+  }
+  return P;
+}
+
+int orc_size(void *h) { return ((orc_problem *)h)->N; }
+int orc_nnz_A(void *h) { return ((orc_problem *)h)->A.rp[((orc_problem *)h)->N]; }
+int orc_nnz_S(void *h) { return ((orc_problem *)h)->S.rp[((orc_problem *)h)->N]; }
+
+static void copy_csr(const csr_t *m, int *rp, int *ci, double *v) {
+  memcpy(rp, m->rp, sizeof(int) * (m->n + 1));
+  memcpy(ci, m->ci, sizeof(int) * m->rp[m->n]);
+  memcpy(v, m->v, sizeof(double) * m->rp[m->n]);
+}
+void orc_get_A(void *h, int *rp, int *ci, double *v) { copy_csr(&((orc_problem *)h)->A, rp, ci, v); }
+void orc_get_S(void *h, int *rp, int *ci, double *v) { copy_csr(&((orc_problem *)h)->S, rp, ci, v); }
+
+/* y = S x (full grid) */
+void orc_apply_S(void *h, const double *x, double *y) { csr_mv(&((orc_problem *)h)->S, x, y); }
+
+/* y = S x on selected rows only: out[t] = (S x)_{rows[t]} */
+void orc_apply_S_rows(void *h, const double *x, const int *rows, int nrows, double *out) {
+  const csr_t *S = &((orc_problem *)h)->S;
+  for (int t = 0; t < nrows; ++t) {
+    int i = rows[t];
+    double s = 0.0;
+    for (int p = S->rp[i]; p < S->rp[i + 1]; ++p) s += S->v[p] * x[S->ci[p]];
+    out[t] = s;
+  }
+}
+
+/* Desired state y_d(x) = a exp(-|x - c|^2 / (2 sigma^2)) at the interior
+ * nodes x_d = (i_d + 1) h_d, and rhs = M y_d = mass * y_d. */
+void orc_desired_state(void *h, double a, const double *c, double sigma,
+                       double *yd, double *rhs) {
+  orc_problem *P = (orc_problem *)h;
+  for (int l = 0; l < P->nz; ++l)
+    for (int j = 0; j < P->ny; ++j)
+      for (int i = 0; i < P->nx; ++i) {
+        double x0 = (i + 1) * P->h[0] - c[0];
+        double x1 = (j + 1) * P->h[1] - c[1];
+        double r2 = x0 * x0 + x1 * x1;
+        if (P->dim == 3) {
+          double x2 = (l + 1) * P->h[2] - c[2];
+          r2 += x2 * x2;
+        }
+        int p = node_index(P, i, j, l);
+        yd[p] = a * exp(-r2 / (2.0 * sigma * sigma));
+        if (rhs) rhs[p] = P->mass * yd[p];
+      }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Restriction to the inactive set: S_II by sub-matrix indexing (App. B.3). */
+
+typedef struct {
+  int nI;
+  int *idx;   /* nI global indices of I, increasing        */
+  int *loc;   /* N: local index in I, or -1 if active      */
+  csr_t SII;
+} restr_t;
+
+static int restrict_build(const orc_problem *P, const unsigned char *active,
+                          restr_t *R) {
+  int N = P->N;
+  R->loc = (int *)malloc(sizeof(int) * (N > 0 ? N : 1));
+  R->idx = (int *)malloc(sizeof(int) * (N > 0 ? N : 1));
+  if (!R->loc || !R->idx) return ORC_ERR_NOMEM;
+  R->nI = 0;
+  for (int i = 0; i < N; ++i) {
+    if (!active[i]) {
+      R->loc[i] = R->nI;
+      R->idx[R->nI++] = i;
+    } else {
+      R->loc[i] = -1;
+    }
+  }
+  int nI = R->nI;
+  const csr_t *S = &P->S;
+  R->SII.n = nI;
+  R->SII.rp = (int *)malloc(sizeof(int) * (nI + 1));
+  int cnt = 0;
+  for (int a = 0; a < nI; ++a) {
+    int i = R->idx[a];
+    for (int p = S->rp[i]; p < S->rp[i + 1]; ++p)
+      if (R->loc[S->ci[p]] >= 0) cnt++;
+  }
+  R->SII.ci = (int *)malloc(sizeof(int) * (cnt > 0 ? cnt : 1));
+  R->SII.v = (double *)malloc(sizeof(double) * (cnt > 0 ? cnt : 1));
+  if (!R->SII.rp || !R->SII.ci || !R->SII.v) return ORC_ERR_NOMEM;
+  cnt = 0;
+  R->SII.rp[0] = 0;
+  for (int a = 0; a < nI; ++a) {
+    int i = R->idx[a];
+    for (int p = S->rp[i]; p < S->rp[i + 1]; ++p) {
+      int lj = R->loc[S->ci[p]];
+      if (lj >= 0) {
+        R->SII.ci[cnt] = lj;
+        R->SII.v[cnt++] = S->v[p];
+      }
+    }
+    R->SII.rp[a + 1] = cnt;
+  }
+  return ORC_OK;
+}
+
+static void restrict_free(restr_t *R) {
+  free(R->idx);
+  free(R->loc);
+  csr_free(&R->SII);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Dense helpers for the k x k coarse problem.                              */
+
+/* Cholesky E = L L^T (lower, column-major k x k, in place).  Returns 0 on
+ * success, 1 if a pivot is not positive. */
+static int cholesky(int k, double *L) {
+  for (int j = 0; j < k; ++j) {
+    double d = L[j + j * k];
+    for (int m = 0; m < j; ++m) d -= L[j + m * k] * L[j + m * k];
+    if (!(d > 0.0)) return 1;
+    d = sqrt(d);
+    L[j + j * k] = d;
+    for (int i = j + 1; i < k; ++i) {
+      double s = L[i + j * k];
+      for (int m = 0; m < j; ++m) s -= L[i + m * k] * L[j + m * k];
+      L[i + j * k] = s / d;
+    }
+    for (int i = 0; i < j; ++i) L[i + j * k] = 0.0;
+  }
+  return 0;
+}
+
+/* solve (L L^T) x = b in place */
+static void chol_solve(int k, const double *L, double *b) {
+  for (int i = 0; i < k; ++i) {
+    double s = b[i];
+    for (int m = 0; m < i; ++m) s -= L[i + m * k] * b[m];
+    b[i] = s / L[i + i * k];
+  }
+  for (int i = k - 1; i >= 0; --i) {
+    double s = b[i];
+    for (int m = i + 1; m < k; ++m) s -= L[m + i * k] * b[m];
+    b[i] = s / L[i + i * k];
+  }
+}
+
+/* Eigenvalues of a symmetric k x k matrix by the cyclic Jacobi method
+ * (textbook rotation form); ev receives the diagonal after convergence. */
+static void jacobi_eigenvalues(int k, const double *Ain, double *ev) {
+  double *A = (double *)malloc(sizeof(double) * k * k);
+  memcpy(A, Ain, sizeof(double) * k * k);
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int j = 0; j < k; ++j)
+      for (int i = 0; i < k; ++i) {
+        tot += A[i + j * k] * A[i + j * k];
+        if (i != j) off += A[i + j * k] * A[i + j * k];
+      }
+    if (off <= 1e-30 * tot) break;
+    for (int p = 0; p < k - 1; ++p)
+      for (int q = p + 1; q < k; ++q) {
+        double apq = A[p + q * k];
+        if (apq == 0.0) continue;
+        double app = A[p + p * k], aqq = A[q + q * k];
+        double theta = (aqq - app) / (2.0 * apq);
+        double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        for (int r = 0; r < k; ++r) { /* columns p, q */
+          double arp = A[r + p * k], arq = A[r + q * k];
+          A[r + p * k] = c * arp - s * arq;
+          A[r + q * k] = s * arp + c * arq;
+        }
+        for (int r = 0; r < k; ++r) { /* rows p, q */
+          double apr = A[p + r * k], aqr = A[q + r * k];
+          A[p + r * k] = c * apr - s * aqr;
+          A[q + r * k] = s * apr + c * aqr;
+        }
+      }
+  }
+  for (int i = 0; i < k; ++i) ev[i] = A[i + i * k];
+  free(A);
+}
+
+/* Householder QR of the n x k column-major matrix X (n >= k): on return Q
+ * (n x k, orthonormal columns) overwrites X and rdiag holds |R_jj|. */
+static int householder_qr(int n, int k, double *X, double *rdiag) {
+  double *V = (double *)malloc(sizeof(double) * (size_t)n * k);
+  double *beta = (double *)malloc(sizeof(double) * k);
+  if (!V || !beta) return ORC_ERR_NOMEM;
+  for (int j = 0; j < k; ++j) {
+    double *x = X + (size_t)j * n;
+    double nx2 = 0.0;
+    for (int i = j; i < n; ++i) nx2 += x[i] * x[i];
+    double nx = sqrt(nx2);
+    double *v = V + (size_t)j * n;
+    for (int i = 0; i < n; ++i) v[i] = 0.0;
+    if (nx == 0.0) {
+      beta[j] = 0.0;
+      rdiag[j] = 0.0;
+      continue;
+    }
+    double alpha = x[j] >= 0 ? -nx : nx;
+    for (int i = j; i < n; ++i) v[i] = x[i];
+    v[j] -= alpha;
+    double vv = 0.0;
+    for (int i = j; i < n; ++i) vv += v[i] * v[i];
+    beta[j] = vv > 0 ? 2.0 / vv : 0.0;
+    rdiag[j] = fabs(alpha);
+    /* apply H_j = I - beta v v^T to columns j..k-1 */
+    for (int c = j; c < k; ++c) {
+      double *y = X + (size_t)c * n;
+      double s = 0.0;
+      for (int i = j; i < n; ++i) s += v[i] * y[i];
+      s *= beta[j];
+      for (int i = j; i < n; ++i) y[i] -= s * v[i];
+    }
+  }
+  /* form Q e_c = H_0 ... H_c e_c (H_j, j > c, leaves e_c unchanged) */
+  for (int c = 0; c < k; ++c) {
+    double *y = X + (size_t)c * n;
+    for (int i = 0; i < n; ++i) y[i] = (i == c) ? 1.0 : 0.0;
+    for (int j = c; j >= 0; --j) {
+      const double *v = V + (size_t)j * n;
+      double s = 0.0;
+      for (int i = j; i < n; ++i) s += v[i] * y[i];
+      s *= beta[j];
+      for (int i = j; i < n; ++i) y[i] -= s * v[i];
+    }
+  }
+  free(V);
+  free(beta);
+  return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Inner solvers on S_II (compressed inactive numbering).                   */
+
+static void diag_of(const csr_t *S, double *d) {
+  for (int i = 0; i < S->n; ++i)
+    for (int a = S->rp[i]; a < S->rp[i + 1]; ++a)
+      if (S->ci[a] == i) d[i] = S->v[a];
+}
+
+/* Jacobi-PCG (App. B.2).  x holds x0 on entry.  Returns status; *iters is
+ * the number of CG iterations, *relres the final recurrence ||r||/||b||. */
+static int pcg_core(const csr_t *S, const double *b, double *x, double rtol,
+                    int maxit, int *iters, double *relres) {
+  int n = S->n;
+  double *r = (double *)malloc(sizeof(double) * (n + 1));
+  double *z = (double *)malloc(sizeof(double) * (n + 1));
+  double *p = (double *)malloc(sizeof(double) * (n + 1));
+  double *q = (double *)malloc(sizeof(double) * (n + 1));
+  double *d = (double *)malloc(sizeof(double) * (n + 1));
+  if (!r || !z || !p || !q || !d) return ORC_ERR_NOMEM;
+  diag_of(S, d);
+  csr_mv(S, x, q);
+  for (int i = 0; i < n; ++i) {
+    r[i] = b[i] - q[i];
+    z[i] = r[i] / d[i];
+    p[i] = z[i];
+  }
+  double rho = dot(n, r, z);
+  double bn = nrm2(n, b);
+  int it = 0, st = ORC_OK;
+  double rn = nrm2(n, r);
+  while (rn > rtol * bn) {
+    if (it >= maxit) {
+      st = ORC_ERR_CG_MAXIT;
+      break;
+    }
+    csr_mv(S, p, q);
+    double pq = dot(n, p, q);
+    if (!(pq > 0.0)) {
+      st = isfinite(pq) ? ORC_ERR_BREAKDOWN : ORC_ERR_NONFINITE;
+      break;
+    }
+    double a = rho / pq;
+    for (int i = 0; i < n; ++i) {
+      x[i] += a * p[i];
+      r[i] -= a * q[i];
+      z[i] = r[i] / d[i];
+    }
+    double rho_new = dot(n, r, z);
+    double beta = rho_new / rho;
+    rho = rho_new;
+    for (int i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
+    rn = nrm2(n, r);
+    ++it;
+  }
+  *iters = it;
+  *relres = bn > 0 ? rn / bn : 0.0;
+  free(r);
+  free(z);
+  free(p);
+  free(q);
+  free(d);
+  return st;
+}
+
+/*
+ * A-DEF2 deflated Jacobi-PCG (Sec. 2.2.1, Algorithm adef2, read as the
+ * standard A-DEF2 of the cited Tang et al. / Gaul et al. framework):
+ *   Z = QR(Phi|_I)                      (Sec. 2.2.2, simple restriction)
+ *   E = Z^T S_II Z, Q = Z E^-1 Z^T      (Eq. coarse)
+ *   P = I - Z E^-1 Z^T S_II             (Eq. proj)
+ *   x = x0 + Q (b - S_II x0)            (coarse-corrected start)
+ *   r = b - S_II x, z = D^-1 r, p = P z
+ *   loop: q = S_II p, a = (r,z)/(p,q), x += a p, r -= a q,
+ *         z = D^-1 r, beta = (r,z)_new/(r,z)_old, p = P z + beta p
+ *   until ||r|| <= eps ||b||  (unprojected recurrence residual, App. B.2).
+ * The printed listing applies P^T to the residual and leaves the search
+ * direction unprojected; that combination does not reach the unprojected
+ * stopping test, so the cited standard form is used.
+ * Guard (Algorithm online_deflation, Remark tau_cond): cond(E) > tau_cond, or
+ * a restricted basis that QR finds numerically rank deficient
+ * (min R_jj <= 1e-7 max R_jj), falls back to plain Jacobi-PCG.
+ */
+static int adef2_core(const csr_t *S, const double *b, double *x,
+                      const double *ZI /* nI x k, orthonormal */, int k,
+                      double rtol, int maxit, int *iters, double *relres,
+                      double *condE, int *fallback, double tau_cond,
+                      int rank_deficient) {
+  int n = S->n;
+  *fallback = 0;
+  *condE = 0.0;
+  if (k == 0 || rank_deficient) {
+    *fallback = 1;
+    *condE = INFINITY;
+    return pcg_core(S, b, x, rtol, maxit, iters, relres);
+  }
+  double *SZ = (double *)malloc(sizeof(double) * (size_t)n * k);
+  double *E = (double *)malloc(sizeof(double) * k * k);
+  double *L = (double *)malloc(sizeof(double) * k * k);
+  double *ev = (double *)malloc(sizeof(double) * k);
+  double *c = (double *)malloc(sizeof(double) * k);
+  if (!SZ || !E || !L || !ev || !c) return ORC_ERR_NOMEM;
+  for (int j = 0; j < k; ++j) csr_mv(S, ZI + (size_t)j * n, SZ + (size_t)j * n);
+#pragma omp parallel for schedule(static)
+  for (int jj = 0; jj < k * k; ++jj) {
+    int i = jj % k, j = jj / k;
+    E[i + j * k] = dot(n, ZI + (size_t)i * n, SZ + (size_t)j * n);
+  }
+  /* symmetrise the rounding of the Galerkin matrix */
+  for (int j = 0; j < k; ++j)
+    for (int i = 0; i < j; ++i) {
+      double s = 0.5 * (E[i + j * k] + E[j + i * k]);
+      E[i + j * k] = s;
+      E[j + i * k] = s;
+    }
+  jacobi_eigenvalues(k, E, ev);
+  double emin = ev[0], emax = ev[0];
+  for (int i = 1; i < k; ++i) {
+    if (ev[i] < emin) emin = ev[i];
+    if (ev[i] > emax) emax = ev[i];
+  }
+  *condE = emin > 0 ? emax / emin : INFINITY;
+  memcpy(L, E, sizeof(double) * k * k);
+  if (!(*condE <= tau_cond) || cholesky(k, L)) {
+    *fallback = 1;
+    free(SZ);
+    free(E);
+    free(L);
+    free(ev);
+    free(c);
+    return pcg_core(S, b, x, rtol, maxit, iters, relres);
+  }
+  double *r = (double *)malloc(sizeof(double) * (n + 1));
+  double *z = (double *)malloc(sizeof(double) * (n + 1));
+  double *p = (double *)malloc(sizeof(double) * (n + 1));
+  double *q = (double *)malloc(sizeof(double) * (n + 1));
+  double *d = (double *)malloc(sizeof(double) * (n + 1));
+  if (!r || !z || !p || !q || !d) return ORC_ERR_NOMEM;
+  diag_of(S, d);
+  /* x = x0 + Z E^-1 Z^T (b - S x0) */
+  csr_mv(S, x, q);
+  for (int i = 0; i < n; ++i) r[i] = b[i] - q[i];
+#pragma omp parallel for schedule(static)
+  for (int j = 0; j < k; ++j) c[j] = dot(n, ZI + (size_t)j * n, r);
+  chol_solve(k, L, c);
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < k; ++j) s += ZI[(size_t)j * n + i] * c[j];
+    x[i] += s;
+  }
+  csr_mv(S, x, q);
+  for (int i = 0; i < n; ++i) {
+    r[i] = b[i] - q[i];
+    z[i] = r[i] / d[i];
+  }
+  double rho = dot(n, r, z);
+  /* p = P z = z - Z E^-1 (S Z)^T z */
+#pragma omp parallel for schedule(static)
+  for (int j = 0; j < k; ++j) c[j] = dot(n, SZ + (size_t)j * n, z);
+  chol_solve(k, L, c);
+#pragma omp parallel for schedule(static)
+  for (int i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < k; ++j) s += ZI[(size_t)j * n + i] * c[j];
+    p[i] = z[i] - s;
+  }
+  double bn = nrm2(n, b);
+  double rn = nrm2(n, r);
+  int it = 0, st = ORC_OK;
+  while (rn > rtol * bn) {
+    if (it >= maxit) {
+      st = ORC_ERR_CG_MAXIT;
+      break;
+    }
+    csr_mv(S, p, q);
+    double pq = dot(n, p, q);
+    if (!(pq > 0.0)) {
+      st = isfinite(pq) ? ORC_ERR_BREAKDOWN : ORC_ERR_NONFINITE;
+      break;
+    }
+    double a = rho / pq;
+    for (int i = 0; i < n; ++i) {
+      x[i] += a * p[i];
+      r[i] -= a * q[i];
+      z[i] = r[i] / d[i];
+    }
+    double rho_new = dot(n, r, z);
+    double beta = rho_new / rho;
+    rho = rho_new;
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < k; ++j) c[j] = dot(n, SZ + (size_t)j * n, z);
+    chol_solve(k, L, c);
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < n; ++i) {
+      double s = 0.0;
+      for (int j = 0; j < k; ++j) s += ZI[(size_t)j * n + i] * c[j];
+      p[i] = (z[i] - s) + beta * p[i];
+    }
+    rn = nrm2(n, r);
+    ++it;
+  }
+  *iters = it;
+  *relres = bn > 0 ? rn / bn : 0.0;
+  free(SZ);
+  free(E);
+  free(L);
+  free(ev);
+  free(c);
+  free(r);
+  free(z);
+  free(p);
+  free(q);
+  free(d);
+  return st;
+}
+
+/* Restrict Phi (N x k, column-major, leading dimension ld) to I and
+ * orthonormalise by Householder QR.  Sets *rank_def when the restriction is
+ * numerically rank deficient. */
+static double *restrict_modes(const restr_t *R, const double *Phi, int k,
+                              int ld, int *rank_def) {
+  int nI = R->nI;
+  *rank_def = 0;
+  if (k == 0) return NULL;
+  if (nI < k) {
+    *rank_def = 1;
+    return NULL;
+  }
+  double *Z = (double *)malloc(sizeof(double) * (size_t)nI * k);
+  double *rd = (double *)malloc(sizeof(double) * k);
+  for (int j = 0; j < k; ++j)
+    for (int a = 0; a < nI; ++a) Z[(size_t)j * nI + a] = Phi[(size_t)j * ld + R->idx[a]];
+  householder_qr(nI, k, Z, rd);
+  double rmax = 0.0, rmin = INFINITY;
+  for (int j = 0; j < k; ++j) {
+    if (rd[j] > rmax) rmax = rd[j];
+    if (rd[j] < rmin) rmin = rd[j];
+  }
+  if (!(rmin > 1e-7 * rmax)) *rank_def = 1;
+  free(rd);
+  return Z;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Public inner solve on a given active set (used by the unit pins).        */
+
+/* Solve S_II x_I = b_I, b = rhs_I - S_IA psi_A (Eq. reduced) with
+ * plain Jacobi-PCG (deflate = 0) or A-DEF2 (deflate = 1).  x: N values, on
+ * entry x0 on I (values on A ignored); on exit x_I on I and psi on A. */
+int orc_inner_solve(void *h, const unsigned char *active, const double *rhs,
+                    const double *psi, const double *Phi, int k, int ld,
+                    int deflate, double rtol, int maxit, double tau_cond,
+                    double *x, int *iters, double *relres, double *condE,
+                    int *fallback) {
+  orc_problem *P = (orc_problem *)h;
+  int N = P->N;
+  restr_t R;
+  memset(&R, 0, sizeof(R));
+  if (restrict_build(P, active, &R)) return ORC_ERR_NOMEM;
+  int nI = R.nI;
+  double *b = (double *)malloc(sizeof(double) * (nI + 1));
+  double *xi = (double *)malloc(sizeof(double) * (nI + 1));
+  /* b = rhs_I - S_IA psi_A */
+  for (int a = 0; a < nI; ++a) {
+    int i = R.idx[a];
+    double s = rhs[i];
+    for (int p = P->S.rp[i]; p < P->S.rp[i + 1]; ++p)
+      if (active[P->S.ci[p]]) s -= P->S.v[p] * psi[P->S.ci[p]];
+    b[a] = s;
+    xi[a] = x[i];
+  }
+  int st = ORC_OK;
+  *fallback = 0;
+  *condE = 0.0;
+  *iters = 0;
+  *relres = 0.0;
+  if (nI > 0) {
+    if (deflate) {
+      int rd = 0;
+      double *Z = restrict_modes(&R, Phi, k, ld, &rd);
+      st = adef2_core(&R.SII, b, xi, Z, Z ? k : 0, rtol, maxit, iters, relres,
+                      condE, fallback, tau_cond, rd);
+      free(Z);
+    } else {
+      st = pcg_core(&R.SII, b, xi, rtol, maxit, iters, relres);
+    }
+  }
+  for (int i = 0; i < N; ++i) x[i] = active[i] ? psi[i] : xi[R.loc[i]];
+  free(b);
+  free(xi);
+  restrict_free(&R);
+  return st;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Outer primal active-set loop (App. B.1 Algorithm pdas) around the inner  */
+/* solve of Algorithm online_deflation (lines 5-18).                        */
+
+int orc_solve(void *h, const double *rhs, const double *psi, const double *Phi,
+              int k, int ld, const orc_opts *o, const double *x0 /* N or NULL */,
+              double *y, double *lambda, unsigned char *active, orc_stats *st) {
+  orc_problem *P = (orc_problem *)h;
+  int N = P->N;
+  memset(st, 0, sizeof(*st));
+  int maxo = o->max_outer < ORC_MAX_OUTER ? o->max_outer : ORC_MAX_OUTER;
+  unsigned char *anew = (unsigned char *)malloc(N > 0 ? N : 1);
+  unsigned char *aused = (unsigned char *)malloc(N > 0 ? N : 1);
+  double *x = (double *)malloc(sizeof(double) * (N > 0 ? N : 1));
+  if (!anew || !aused || !x) return ORC_ERR_NOMEM;
+  /* cold start: y = 0, A = empty */
+  for (int i = 0; i < N; ++i) {
+    active[i] = 0;
+    y[i] = 0.0;
+  }
+  int status = ORC_ERR_OUTER_MAXIT;
+  for (int it = 0; it < maxo; ++it) {
+    int nA = 0;
+    for (int i = 0; i < N; ++i) nA += active[i];
+    memcpy(aused, active, N);
+    for (int i = 0; i < N; ++i) x[i] = active[i] ? psi[i] : (x0 ? x0[i] : 0.0);
+    int cg = 0, fb = 0;
+    double rr = 0.0, ce = 0.0;
+    int s = orc_inner_solve(h, active, rhs, psi, Phi, k, ld, o->deflate, o->rtol,
+                            o->max_cg, o->tau_cond, x, &cg, &rr, &ce, &fb);
+    st->cg_iters[it] = cg;
+    st->n_active[it] = nA;
+    st->fallback[it] = fb;
+    st->cond_E[it] = ce;
+    st->relres[it] = rr;
+    st->outer_iters = it + 1;
+    memcpy(y, x, sizeof(double) * N);
+    if (s != ORC_OK) {
+      status = s;
+      break;
+    }
+    /* active-set update */
+    if (o->rule == 0) {
+      for (int i = 0; i < N; ++i) anew[i] = y[i] > psi[i] - o->tau;
+    } else {
+      /* full PDAS rule lambda_i + c (y_i - psi_i) > 0, lambda = rhs - S y */
+      orc_apply_S(h, y, lambda);
+      for (int i = 0; i < N; ++i) {
+        double lam = rhs[i] - lambda[i];
+        anew[i] = lam + o->pdas_c * (y[i] - psi[i]) > 0.0;
+      }
+    }
+    int changed = 0;
+    for (int i = 0; i < N; ++i) changed += anew[i] != active[i];
+    if (!changed) {
+      status = ORC_OK;
+      break;
+    }
+    memcpy(active, anew, N);
+  }
+  /* multiplier lambda = rhs - S y (Eq. schur) and diagnostics */
+  orc_apply_S(h, y, lambda);
+  for (int i = 0; i < N; ++i) lambda[i] = rhs[i] - lambda[i];
+  double mm = INFINITY, ml = INFINITY;
+  for (int i = 0; i < N; ++i) {
+    if (!aused[i]) {
+      double g = fabs(y[i] - (psi[i] - o->tau));
+      if (g < mm) mm = g;
+    } else if (lambda[i] < ml) {
+      ml = lambda[i];
+    }
+  }
+  st->min_margin = mm;
+  st->min_lambda_active = ml;
+  /* true residual of the last restricted solve (its own active set) */
+  {
+    double num = 0.0, den = 0.0;
+    for (int i = 0; i < N; ++i)
+      if (!aused[i]) {
+        double b = rhs[i], sy = 0.0;
+        for (int p = P->S.rp[i]; p < P->S.rp[i + 1]; ++p) {
+          int j = P->S.ci[p];
+          if (aused[j]) b -= P->S.v[p] * psi[j];
+          else sy += P->S.v[p] * y[j];
+        }
+        num += (b - sy) * (b - sy);
+        den += b * b;
+      }
+    st->true_relres = den > 0 ? sqrt(num / den) : 0.0;
+  }
+  st->status = status;
+  free(anew);
+  free(aused);
+  free(x);
+  return status;
+}
