@@ -1,0 +1,216 @@
+/*
+ * sdf.h -- C ABI of the B300-native (sm_103a) spectral-deflation active-set
+ * solver for state-constrained optimal control (arXiv 2606.17971).
+ *
+ * The method (paper references are sections / equations / algorithms):
+ *   S = M + alpha K^T M^-1 K with M = mass*I, K = kscale*A_h      (Sec. 2.1.2 Eq. schur)
+ *   primal active-set loop: A <- {i : y_i > psi_i - tau}            (App. B.1 Alg. pdas)
+ *   restricted system S_II y_I = rhs_I - S_IA psi_A                  (Sec. 2.1.2 Eq. reduced)
+ *   inner solve: A-DEF2 deflated Jacobi-PCG with Z = Phi|_I          (Sec. 2.2.1 Alg. adef2,
+ *                (orthonormalised), E = Z^T S_II Z, guard             Sec. 2.2.2, Alg.
+ *                cond(E) > tau_cond -> plain Jacobi-PCG               online_deflation l. 5-18)
+ *   stop on the unprojected residual ||r|| <= rtol ||b||            (App. B.2 Eq. cg_stop)
+ *   A_h: 5-point (2D) / 7-point (3D) -diff_scale div(kappa grad)     (App. A Eq. fd_lap,
+ *        with harmonic face means, plus optional per-instance          Eq. harmonic)
+ *        first-order upwind convection b . grad
+ *
+ * Conventions for every entry point:
+ *   - Grids are interior nodes of the unit box, n_d per direction,
+ *     h_d = 1/(n_d+1), node index i + n_x (j + n_y l) (x fastest).
+ *   - "device" pointers are CUDA global-memory addresses on the current device;
+ *     "host" pointers are ordinary CPU memory.  The library never allocates
+ *     device memory: the caller passes every device buffer (problem buffer,
+ *     workspace, inputs, outputs) and keeps it alive for the duration of the
+ *     calls that use it.  All work is enqueued on the caller's stream
+ *     (a cudaStream_t passed as void*, NULL = legacy default stream).
+ *   - Every function returns an sdf_status; no exception or abort crosses the
+ *     ABI.  On a non-OK status sdf_last_error(handle) holds a one-line reason.
+ *     A sticky CUDA error is reported as SDF_ERR_CUDA with CUDA's text.
+ *   - A handle is not thread-safe: calls on one handle must not run
+ *     concurrently from several host threads.
+ */
+#ifndef SDF_H_
+#define SDF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SDF_OK = 0,
+  SDF_ERR_INVALID_ARG = 1, /* bad size, NULL pointer, misaligned buffer       */
+  SDF_ERR_WORKSPACE = 2,   /* buffer smaller than the size query returned     */
+  SDF_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed     */
+  SDF_ERR_NOT_SPD = 4,     /* reserved: a coarse matrix was not SPD           */
+  SDF_ERR_CG_MAXIT = 5,    /* CG hit max_cg without meeting rtol              */
+  SDF_ERR_OUTER_MAXIT = 6, /* active set still changing after max_outer       */
+  SDF_ERR_BREAKDOWN = 7,   /* CG breakdown: p^T S p <= 0                      */
+  SDF_ERR_NONFINITE = 8,   /* NaN / Inf met in a reduction                    */
+  SDF_ERR_TIMEOUT = 9,     /* host watchdog: solve exceeded its launch budget */
+  SDF_ERR_UNSUPPORTED = 10 /* combination not built (e.g. k > SDF_MAX_K)      */
+} sdf_status;
+
+typedef enum { SDF_F64 = 0, SDF_F32 = 1, SDF_BF16 = 2 } sdf_dtype;
+
+/* Maximum deflation rank and outer iterations recorded per instance. */
+#define SDF_MAX_K 128
+#define SDF_MAX_OUTER 32
+/* Instance parameters: 7 doubles per instance, in this order. */
+#define SDF_INSTANCE_DOUBLES 7 /* a, c_x, c_y, c_z, b_x, b_y, b_z */
+
+typedef struct sdf_problem sdf_problem;
+
+/* Problem description (host struct, copied by sdf_problem_create).
+ *   dim          2 or 3
+ *   n[3]         interior nodes per direction (n[2] ignored for dim 2)
+ *   alpha        Tikhonov weight (> 0)
+ *   mass         M = mass * I (> 0); the paper's form is mass = 1
+ *   kscale       K = kscale * A_h; the paper's form is kscale = 1
+ *   diff_scale   A_h = diff_scale * (-div(kappa grad)) + b . grad
+ *   has_kappa    1: node diffusivity given to sdf_problem_create, 0: kappa = 1
+ *   convection   1: each instance carries its upwind convection velocity b
+ *   yd_sigma     width of the Gaussian desired state
+ *                y_d(x) = a exp(-|x - c|^2 / (2 yd_sigma^2)), rhs = mass y_d */
+typedef struct {
+  int32_t dim;
+  int32_t n[3];
+  double alpha;
+  double mass;
+  double kscale;
+  double diff_scale;
+  int32_t has_kappa;
+  int32_t convection;
+  double yd_sigma;
+} sdf_problem_desc;
+
+/* Solve options (defaults from sdf_default_opts).
+ *   rtol         CG tolerance on ||r||/||b|| (App. B.2)            [1e-8]
+ *   tau          active-set tolerance (App. B.1)                  [1e-10]
+ *   tau_cond     solve-time guard on cond(E) (Remark tau_cond)    [1e10]
+ *   max_outer    maximum inner solves per instance (<= SDF_MAX_OUTER) [30]
+ *   max_cg       CG iteration cap per inner solve                 [1000000]
+ *   deflate      1: A-DEF2 with the reference modes, 0: plain Jacobi-PCG [1]
+ *   check_every  CG iterations enqueued between two host polls of the
+ *                per-instance convergence flags                   [64]
+ *   max_launches host watchdog: total iteration launches per solve call
+ *                before SDF_ERR_TIMEOUT (0 = 4 * max_cg)          [0]        */
+typedef struct {
+  double rtol;
+  double tau;
+  double tau_cond;
+  int32_t max_outer;
+  int32_t max_cg;
+  int32_t deflate;
+  int32_t check_every;
+  int64_t max_launches;
+} sdf_opts;
+
+/* Per-instance statistics (host struct filled at the end of a solve). */
+typedef struct {
+  int32_t status;                     /* sdf_status of this instance          */
+  int32_t outer_iters;                /* inner solves performed               */
+  int32_t cg_iters[SDF_MAX_OUTER];    /* CG iterations of each inner solve    */
+  int32_t n_active[SDF_MAX_OUTER];    /* |A| in force during each solve       */
+  int32_t fallback[SDF_MAX_OUTER];    /* 1: guard fired, plain PCG used       */
+  double cond_E[SDF_MAX_OUTER];       /* estimated cond(E) (0 if plain)       */
+  double relres[SDF_MAX_OUTER];       /* recurrence ||r||/||b|| at exit       */
+} sdf_stats;
+
+void sdf_default_opts(sdf_opts *o);
+
+/* Create a host-side problem handle.
+ *   kappa_host: N node diffusivities (host, copied) when desc->has_kappa, else
+ *   ignored.  Errors: SDF_ERR_INVALID_ARG for a bad description. */
+sdf_status sdf_problem_create(const sdf_problem_desc *desc, const double *kappa_host,
+                              sdf_problem **out);
+
+/* Bytes of device memory the problem's operator data needs (face
+ * coefficients of A_h); may be 0 for constant kappa. */
+sdf_status sdf_problem_device_bytes(const sdf_problem *p, size_t *bytes);
+
+/* Bind a caller-owned device buffer of at least sdf_problem_device_bytes bytes
+ * (256-byte aligned) and fill it: kappa is copied to it and the harmonic face
+ * coefficients diff_scale * kappa_f / h_d^2 (App. A Eq. harmonic; a face
+ * towards the Dirichlet boundary takes the node value) are computed on the
+ * device.  Must precede every solve.  Enqueued on `stream`. */
+sdf_status sdf_problem_bind(sdf_problem *p, void *dev_buf, size_t bytes, void *stream);
+
+/* Register the reference modes Phi (Sec. 2.2.2 Eq. eig): device pointer to an
+ * N x k column-major array (mode j at Phi + j*ld elements), ld >= N,
+ * 1 <= k <= SDF_MAX_K, of type `dtype` (SDF_F64 for the FP64 path).  The
+ * library keeps the pointer, not a copy; the caller keeps the memory alive and
+ * unchanged while solves use it.  The base address must be 16-byte aligned. */
+sdf_status sdf_set_reference_modes(sdf_problem *p, const void *phi_dev, int k, int64_t ld,
+                                   sdf_dtype dtype);
+
+/* Closed-form reference modes for a constant-coefficient diffusion reference
+ * S_ref = mass I + w (diff_scale L_h)^2 (Sec. 2.2.7): the k smallest Kronecker
+ * sine modes, ties broken lexicographically by (i_d, ..., i_1).  Writes
+ * phi_dev (N x k column-major, ld, dtype) on the device and, if eigvals_host
+ * is not NULL, the k eigenvalues of S_ref to host memory.  Does not register
+ * the modes (call sdf_set_reference_modes). */
+sdf_status sdf_analytic_modes(sdf_problem *p, int k, void *phi_dev, int64_t ld, sdf_dtype dtype,
+                              double *eigvals_host, void *stream);
+
+/* Workspace bytes for a batch of `batch` instances under `opts`. */
+sdf_status sdf_workspace_size(const sdf_problem *p, int batch, const sdf_opts *opts,
+                              size_t *bytes);
+
+/* Solve `batch` instances (primal active-set loop around A-DEF2 or plain
+ * Jacobi-PCG), all resident on the device:
+ *   inst_dev    batch x SDF_INSTANCE_DOUBLES doubles (device)
+ *   psi_dev     N doubles: the state bound, shared by the batch (device)
+ *   ws, ws_bytes  workspace of at least sdf_workspace_size bytes (device,
+ *                 256-byte aligned); contents on entry are ignored
+ *   y_dev       batch x N doubles out: state, y_A = psi_A (device)
+ *   lambda_dev  batch x N doubles out: multiplier rhs - S y, or NULL (device)
+ *   active_dev  batch x N bytes out: 1 on the final active set (device)
+ *   stats_host  batch sdf_stats out (host), or NULL
+ * Returns the worst instance status (SDF_OK when every instance converged).
+ * The call returns after the solve has finished on `stream` (it polls
+ * convergence flags between launches). */
+sdf_status sdf_solve_batch(sdf_problem *p, const double *inst_dev, int batch,
+                           const double *psi_dev, const sdf_opts *opts, void *ws, size_t ws_bytes,
+                           void *stream, double *y_dev, double *lambda_dev, uint8_t *active_dev,
+                           sdf_stats *stats_host);
+
+/* The same solve with every input and output in HOST memory: the instance
+ * array and psi are copied to the device inside the call and y, lambda (if not
+ * NULL) and active are copied back; the workspace (device) must be at least
+ * sdf_workspace_size(...) + sdf_host_io_bytes(p, batch) bytes. */
+sdf_status sdf_host_io_bytes(const sdf_problem *p, int batch, size_t *bytes);
+sdf_status sdf_solve_batch_host(sdf_problem *p, const double *inst_host, int batch,
+                                const double *psi_host, const sdf_opts *opts, void *ws,
+                                size_t ws_bytes, void *stream, double *y_host,
+                                double *lambda_host, uint8_t *active_host,
+                                sdf_stats *stats_host);
+
+/* Building blocks, exposed for tests.
+ * sdf_apply_S: out = S_II u on I and 0 on A (mode 0), or out = S u on the
+ * whole grid (mode 1), for one instance `inst_dev` (7 doubles, device; its
+ * convection velocity is used), `active_dev` N bytes (1 = active; ignored in
+ * mode 1), u_dev and out_dev N doubles (device).  In mode 0 u must be zero on
+ * A.  Sec. 2.1.2 Eq. schur / Eq. reduced, applied matrix-free in flux form. */
+sdf_status sdf_apply_S(sdf_problem *p, const double *inst_dev, const uint8_t *active_dev,
+                       const double *u_dev, double *out_dev, int mode, void *ws, size_t ws_bytes,
+                       void *stream);
+
+/* sdf_project: out_dev[j] = sum_{i in I} Phi_j(i) v_i for the registered modes
+ * (the masked projection Phi_I^T v of Alg. adef2), k doubles (device).
+ * `active_dev` N bytes (1 = active), v_dev N doubles (device). */
+sdf_status sdf_project(sdf_problem *p, const uint8_t *active_dev, const double *v_dev,
+                       double *out_dev, void *ws, size_t ws_bytes, void *stream);
+
+/* One-line description of the last error on this handle ("" if none). */
+const char *sdf_last_error(const sdf_problem *p);
+
+/* Release the host handle (device buffers stay the caller's). */
+void sdf_problem_destroy(sdf_problem *p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SDF_H_ */

@@ -1,0 +1,1421 @@
+// sdf.cu -- sm_103a kernels and host orchestration behind include/sdf.h.
+//
+// Method (paper sections / equations / algorithms):
+//   S = mass I + w A^T A                      Sec. 2.1.2 Eq. schur (w = alpha kscale^2/mass)
+//   primal active-set loop                    App. B.1 Algorithm pdas
+//   restricted system, b = rhs_I - S_IA psi_A Sec. 2.1.2 Eq. reduced
+//   A-DEF2 deflated Jacobi-PCG                Sec. 2.2.1 Algorithm adef2 (standard
+//                                             Tang/Gaul form: p = P D^-1 r + beta p)
+//   Z = orth(Phi|_I), E = Z^T S_II Z, guard   Sec. 2.2.2, Alg. online_deflation l. 5-15
+//   stop on ||r|| <= rtol ||b||               App. B.2 Eq. cg_stop
+//
+// B300 design (what differs from the paper's CSR/cuSPARSE implementation):
+//   * S is never assembled.  S_II u is applied matrix-free in flux form on
+//     shared-memory tiles with a 2-node halo: w = A u on the halo ring, then
+//     mass u + w A^T w on the tile, masked by the active-set bytes (vectors live
+//     in full-grid layout with zeros on A, so no compaction).
+//   * Only the shared reference modes Phi are read in the loop (no per-instance
+//     N x k arrays): P z = z - Phi_I E_raw^-1 Phi_I^T S_II z, where
+//     E_raw = Phi_I^T S_II Phi_I.  This equals Z E^-1 Z^T S_II for
+//     Z = Phi_I R^-1 (Cholesky-QR, G = Phi_I^T Phi_I = R^T R); cond(E) for the
+//     guard uses the orthonormal-basis E = R^-T E_raw R^-1.
+//   * The k x k coarse operator is applied as an explicit GEMV with
+//     E_raw^-1 = (L_e^-1 L_g^-1)^T (L_e^-1 L_g^-1), computed once per outer
+//     iteration, instead of two sequential triangular solves per iteration.
+//   * Reductions are deterministic: per-block partials, summed in block order
+//     by the last block to finish (atomic ticket), no floating-point atomics.
+//   * CG runs as three kernels per iteration; per-instance convergence flags
+//     make finished instances' blocks exit at once, so the host enqueues
+//     `check_every` iterations between polls.
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sdf_device.cuh"
+
+using namespace sdf;
+
+namespace {
+
+// Per-instance solver state (device, in the workspace).
+struct InstState {
+  double rho, sigma, alpha, beta, gamma, csign;
+  double rnorm2, bnorm2;
+  int32_t phase;       // 1: the coarse-correction pass is the next K_B/K_C
+  int32_t cg_done;     // current inner solve finished (or failed)
+  int32_t outer_done;  // instance finished
+  int32_t iters;       // CG iterations of the current inner solve
+  int32_t deflate;     // A-DEF2 in force for the current inner solve
+  int32_t outer;       // index of the current inner solve
+  int32_t changes;     // active-set changes of the last update
+  int32_t pad;
+  double t[SDF_MAX_K]; // reduced projection Phi_I^T v
+  sdf_stats stats;
+};
+
+enum { CNT_SETUP = 0, CNT_SIGMA = 1, CNT_UPDATE = 2, CNT_PROJECT = 3, CNT_ACTIVE = 4, NCNT = 5 };
+
+struct Ctrl {       // grid-wide control words (device)
+  int running;      // instances still iterating in the current inner solve
+  int live;         // instances that need another outer iteration
+  int pad[62];
+};
+
+struct Layout {
+  size_t x, r, p, q, dinv, mask, W, Einv, Eraw, G, coarse, part, gpart, state, cnt, ctrl, total;
+  int gx, gxa, gxg;
+};
+
+inline size_t al(size_t v) { return (v + 255) & ~size_t(255); }
+
+// ---------------------------------------------------------------------------
+// helpers
+
+__device__ __forceinline__ void inst_cb(const OpParams &P, const double *inst, double cb[3]) {
+  for (int d = 0; d < 3; ++d) cb[d] = (P.convection && d < P.dim) ? inst[4 + d] * P.inv_h[d] : 0.0;
+}
+
+__device__ __forceinline__ double desired(const OpParams &P, const double *inst, int gx, int gy,
+                                          int gz) {
+  double dx = (gx + 1) * P.h[0] - inst[1];
+  double dy = (gy + 1) * P.h[1] - inst[2];
+  double r2 = dx * dx + dy * dy;
+  if (P.dim == 3) {
+    double dz = (gz + 1) * P.h[2] - inst[3];
+    r2 += dz * dz;
+  }
+  return inst[0] * exp(-r2 / (2.0 * P.yd_sigma * P.yd_sigma));
+}
+
+// ---------------------------------------------------------------------------
+// problem set-up: face coefficients and the shared Jacobi diagonal
+
+__global__ void k_faces(OpParams P, const double *kappa, double diff_scale, double *fx,
+                        double *fy, double *fz) {
+  long long nfx = (long long)(P.nx + 1) * P.ny * P.nz;
+  long long nfy = (long long)P.nx * (P.ny + 1) * P.nz;
+  long long nfz = P.dim == 3 ? (long long)P.nx * P.ny * (P.nz + 1) : 0;
+  auto kap = [&](int i, int j, int l) { return kappa[i + (long long)P.nx * (j + (long long)P.ny * l)]; };
+  auto hm = [](double a, double b) { return 2.0 * a * b / (a + b); };
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nfx + nfy + nfz;
+       e += (long long)gridDim.x * blockDim.x) {
+    if (e < nfx) {
+      int i = (int)(e % (P.nx + 1));
+      long long t = e / (P.nx + 1);
+      int j = (int)(t % P.ny), l = (int)(t / P.ny);
+      double kf = i == 0 ? kap(0, j, l) : i == P.nx ? kap(P.nx - 1, j, l) : hm(kap(i - 1, j, l), kap(i, j, l));
+      fx[e] = diff_scale * kf * P.inv_h[0] * P.inv_h[0];
+    } else if (e < nfx + nfy) {
+      long long f = e - nfx;
+      int i = (int)(f % P.nx);
+      long long t = f / P.nx;
+      int j = (int)(t % (P.ny + 1)), l = (int)(t / (P.ny + 1));
+      double kf = j == 0 ? kap(i, 0, l) : j == P.ny ? kap(i, P.ny - 1, l) : hm(kap(i, j - 1, l), kap(i, j, l));
+      fy[f] = diff_scale * kf * P.inv_h[1] * P.inv_h[1];
+    } else {
+      long long f = e - nfx - nfy;
+      int i = (int)(f % P.nx);
+      long long t = f / P.nx;
+      int j = (int)(t % P.ny), l = (int)(t / P.ny);
+      double kf = l == 0 ? kap(i, j, 0) : l == P.nz ? kap(i, j, P.nz - 1) : hm(kap(i, j, l - 1), kap(i, j, l));
+      fz[f] = diff_scale * kf * P.inv_h[2] * P.inv_h[2];
+    }
+  }
+}
+
+template <int DIM>
+__global__ void k_diag_shared(OpParams P, double *dinv) {
+  double cb[3] = {0, 0, 0};
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < P.N;
+       g += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(g % P.nx);
+    long long t = g / P.nx;
+    int j = (int)(t % P.ny), l = (int)(t / P.ny);
+    dinv[g] = 1.0 / diag_S<DIM>(P, cb, i, j, l);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Outer-iteration set-up (App. B.1 lines 3-5): r = b = rhs_I - S_IA psi_A,
+// x = 0, per-instance Jacobi diagonal (convection), ||b||^2, |A|.
+
+template <int DIM>
+__global__ void __launch_bounds__(NT) k_outer_setup(OpParams P, const double *inst,
+                                                    const double *psi, const uint8_t *mask,
+                                                    double *r, double *x, double *dinv,
+                                                    InstState *st, double *part, int *cnt,
+                                                    Ctrl *ctrl, int GX) {
+  __shared__ TileSmem<DIM> sm;
+  __shared__ double red[NWARP];
+  __shared__ double tot[2];
+  __shared__ int flag;
+  const int b = blockIdx.x, gblk = blockIdx.y;
+  InstState &S = st[b];
+  if (S.outer_done) return;
+  const long long N = P.N;
+  const double *ib = inst + 7 * b;
+  double cb[3];
+  inst_cb(P, ib, cb);
+  const uint8_t *mk = mask + b * N;
+  double *rb = r + b * N, *xb = x + b * N;
+  double *db = P.convection ? dinv + b * N : nullptr;
+  double bb = 0.0, na = 0.0;
+  const long long T = num_tiles<DIM>(P.nx, P.ny, P.nz);
+  for (long long t = gblk; t < T; t += GX) {
+    int ox, oy, oz;
+    tile_origin<DIM>(P, t, ox, oy, oz);
+    tile_S<DIM>(
+        P, cb, ox, oy, oz, sm,
+        [&](int, int, int, long long g) { return mk[g] ? psi[g] : 0.0; },
+        [&](int, int gx, int gy, int gz, long long g, double su) {
+          bool act = mk[g] != 0;
+          double rhs = P.mass * desired(P, ib, gx, gy, gz);
+          double bv = act ? 0.0 : rhs - su;
+          rb[g] = bv;
+          xb[g] = 0.0;
+          if (db) db[g] = act ? 0.0 : 1.0 / diag_S<DIM>(P, cb, gx, gy, gz);
+          bb += bv * bv;
+          na += act ? 1.0 : 0.0;
+        });
+  }
+  bb = block_sum(bb, red);
+  na = block_sum(na, red);
+  if (threadIdx.x == 0) {
+    part[(b * GX + gblk) * 2 + 0] = bb;
+    part[(b * GX + gblk) * 2 + 1] = na;
+  }
+  if (!last_block(cnt + b * NCNT + CNT_SETUP, GX, &flag)) return;
+  __shared__ double scratch[NT];
+  reduce_fields(part + b * GX * 2, GX, 2, 2, tot, scratch);
+  if (threadIdx.x == 0) {
+    cnt[b * NCNT + CNT_SETUP] = 0;
+    S.bnorm2 = tot[0];
+    S.stats.n_active[S.outer] = (int)tot[1];
+    S.phase = 1;
+    S.cg_done = 0;
+    S.iters = 0;
+    S.gamma = 0.0;
+    S.beta = 0.0;
+    S.csign = -1.0;
+    S.rho = 0.0;
+    S.sigma = 0.0;
+    S.alpha = 1.0;
+    for (int j = 0; j < SDF_MAX_K; ++j) S.t[j] = 0.0;
+    atomicAdd(&ctrl->running, 1);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Coarse set-up (Sec. 2.2.1 Eq. coarse, Sec. 2.2.2): W_j = S_II (mask_I Phi_j)
+// for one instance, then E_raw = Phi^T W and G = Phi^T diag(mask_I) Phi.
+
+template <int DIM, class PhiT>
+__global__ void __launch_bounds__(NT) k_modes_W(OpParams P, const double *inst, int b,
+                                                const InstState *st, const uint8_t *mask,
+                                                const PhiT *Phi, long long ld, double *W, int GX) {
+  __shared__ TileSmem<DIM> sm;
+  if (st[b].outer_done) return;
+  const int j = blockIdx.x, gblk = blockIdx.y;
+  const long long N = P.N;
+  double cb[3];
+  inst_cb(P, inst + 7 * b, cb);
+  const uint8_t *mk = mask + b * N;
+  const PhiT *ph = Phi + (long long)j * ld;
+  double *wj = W + (long long)j * N;
+  const long long T = num_tiles<DIM>(P.nx, P.ny, P.nz);
+  for (long long t = gblk; t < T; t += GX) {
+    int ox, oy, oz;
+    tile_origin<DIM>(P, t, ox, oy, oz);
+    tile_S<DIM>(
+        P, cb, ox, oy, oz, sm, [&](int, int, int, long long g) { return mk[g] ? 0.0 : (double)ph[g]; },
+        [&](int, int, int, int, long long g, double su) { wj[g] = mk[g] ? 0.0 : su; });
+  }
+}
+
+// Tall-skinny Gram C = X^T diag(m) Y (k x k, FP64) with X = Phi and Y = W
+// (which = 0) or Y = mask_I Phi (which = 1).  Per-block partials.
+template <int KMAX, class PhiT>
+__global__ void __launch_bounds__(NT) k_gram(const PhiT *Phi, long long ld, const double *W,
+                                             const uint8_t *mask, const InstState *st, int b,
+                                             long long N, int k, int which, double *gpart) {
+  constexpr int MT = KMAX / 16, CH = 16;
+  __shared__ double Xs[CH][KMAX + 1];
+  __shared__ double Ys[CH][KMAX + 1];
+  if (st[b].outer_done) return;
+  const uint8_t *mk = mask + b * N;
+  const int ti = threadIdx.x / 16, tj = threadIdx.x % 16;
+  double acc[MT][MT];
+#pragma unroll
+  for (int a = 0; a < MT; ++a)
+#pragma unroll
+    for (int c = 0; c < MT; ++c) acc[a][c] = 0.0;
+  for (long long base = (long long)blockIdx.x * CH; base < N; base += (long long)gridDim.x * CH) {
+    for (int e = threadIdx.x; e < KMAX * CH; e += NT) {
+      int c = e % CH, j = e / CH;
+      long long g = base + c;
+      double xv = 0.0, yv = 0.0;
+      if (j < k && g < N) {
+        xv = (double)Phi[(long long)j * ld + g];
+        if (which == 0) yv = W[(long long)j * N + g];
+        else yv = mk[g] ? 0.0 : xv;
+      }
+      Xs[c][j] = xv;
+      Ys[c][j] = yv;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int c = 0; c < CH; ++c) {
+      double xa[MT], yb[MT];
+#pragma unroll
+      for (int a = 0; a < MT; ++a) xa[a] = Xs[c][ti + 16 * a];
+#pragma unroll
+      for (int a = 0; a < MT; ++a) yb[a] = Ys[c][tj + 16 * a];
+#pragma unroll
+      for (int a = 0; a < MT; ++a)
+#pragma unroll
+        for (int q = 0; q < MT; ++q) acc[a][q] = fma(xa[a], yb[q], acc[a][q]);
+    }
+    __syncthreads();
+  }
+  double *out = gpart + (long long)blockIdx.x * k * k;
+#pragma unroll
+  for (int a = 0; a < MT; ++a)
+#pragma unroll
+    for (int q = 0; q < MT; ++q) {
+      int i = ti + 16 * a, j = tj + 16 * q;
+      if (i < k && j < k) out[i * k + j] = acc[a][q];
+    }
+}
+
+__global__ void k_gram_reduce(const double *gpart, int nblk, int k, const InstState *st, int b,
+                              double *out) {
+  if (st[b].outer_done) return;
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= k * k) return;
+  double s = 0.0;
+  for (int g = 0; g < nblk; ++g) s += gpart[(long long)g * k * k + e];
+  out[e] = s;
+}
+
+// k x k coarse factorisation for each instance (one block per instance):
+//   G = L_g L_g^T (Cholesky-QR of Phi_I; rank test as in the oracle),
+//   E = L_g^-1 E_raw L_g^-T  (the Galerkin matrix in the orthonormal basis),
+//   E = L_e L_e^T, Einv_raw = F^T F with F = L_e^-1 L_g^-1,
+//   cond(E) by power iteration on E and on E^-1 (guard, Remark tau_cond).
+__device__ bool dev_cholesky(double *A, int k, double *red, int *ok_s, double rank_tol) {
+  // left-looking, lower triangle of the row-major k x k matrix A (in place)
+  double dmax = 0.0;
+  for (int i = 0; i < k; ++i) dmax = fmax(dmax, A[i * k + i]);
+  __syncthreads();  // every thread has read the diagonal before it changes
+  for (int j = 0; j < k; ++j) {
+    if (threadIdx.x == 0) {
+      double d = A[j * k + j];
+      for (int m = 0; m < j; ++m) d -= A[j * k + m] * A[j * k + m];
+      *ok_s = (d > rank_tol * dmax) && isfinite(d);
+      red[0] = (*ok_s) ? sqrt(d) : 1.0;
+      A[j * k + j] = red[0];
+    }
+    __syncthreads();
+    if (!*ok_s) return false;
+    double d = red[0];
+    for (int i = j + 1 + threadIdx.x; i < k; i += NT) {
+      double s = A[i * k + j];
+      for (int m = 0; m < j; ++m) s -= A[i * k + m] * A[j * k + m];
+      A[i * k + j] = s / d;
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < k * k; e += NT)
+    if (e % k > e / k) A[e] = 0.0;  // clear the upper triangle
+  __syncthreads();
+  return true;
+}
+
+// Inverse of a lower-triangular row-major L into Li (thread per column).
+__device__ void dev_tri_inv(const double *L, double *Li, int k) {
+  for (int c = threadIdx.x; c < k; c += NT) {
+    for (int i = 0; i < k; ++i) {
+      double s = (i == c) ? 1.0 : 0.0;
+      if (i >= c)
+        for (int m = c; m < i; ++m) s -= L[i * k + m] * Li[m * k + c];
+      Li[i * k + c] = (i >= c) ? s / L[i * k + i] : 0.0;
+    }
+  }
+  __syncthreads();
+}
+
+// C = A B (row-major k x k), transA / transB select A^T / B^T.
+__device__ void dev_gemm(const double *A, const double *B, double *C, int k, bool tA, bool tB) {
+  for (int e = threadIdx.x; e < k * k; e += NT) {
+    int i = e / k, j = e % k;
+    double s = 0.0;
+    for (int m = 0; m < k; ++m) {
+      double a = tA ? A[m * k + i] : A[i * k + m];
+      double bb = tB ? B[j * k + m] : B[m * k + j];
+      s = fma(a, bb, s);
+    }
+    C[e] = s;
+  }
+  __syncthreads();
+}
+
+// largest eigenvalue of the SPD operator v -> M v (M given by up to two
+// triangular factors: op 0: M = E; op 1: M = Li^T Li), power iteration.
+__device__ double dev_power(const double *E, const double *Li, int k, int op, double *v,
+                            double *w, double *red) {
+  for (int i = threadIdx.x; i < k; i += NT) v[i] = 1.0 + 0.5 * sin((double)(i + 1));
+  __syncthreads();
+  double lam = 0.0;
+  for (int it = 0; it < 120; ++it) {
+    // w = M v
+    for (int i = threadIdx.x; i < k; i += NT) {
+      double s = 0.0;
+      if (op == 0) {
+        for (int m = 0; m < k; ++m) s = fma(E[i * k + m], v[m], s);
+      } else {
+        for (int m = 0; m <= i; ++m) s = fma(Li[i * k + m], v[m], s);  // Li v
+      }
+      w[i] = s;
+    }
+    __syncthreads();
+    if (op == 1) {  // v2 = Li^T w, stored in v
+      for (int i = threadIdx.x; i < k; i += NT) {
+        double s = 0.0;
+        for (int m = i; m < k; ++m) s = fma(Li[m * k + i], w[m], s);
+        v[i] = s;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < k; i += NT) w[i] = v[i];
+      __syncthreads();
+    }
+    double nn = 0.0;
+    for (int i = threadIdx.x; i < k; i += NT) nn += w[i] * w[i];
+    nn = block_sum(nn, red);
+    double nrm = sqrt(nn);
+    lam = nrm;  // ||M v|| with ||v|| = 1 after the first step
+    for (int i = threadIdx.x; i < k; i += NT) v[i] = nrm > 0 ? w[i] / nrm : 0.0;
+    __syncthreads();
+  }
+  return lam;
+}
+
+__global__ void __launch_bounds__(NT) k_coarse(int k, InstState *st, const double *G,
+                                               const double *Eraw, double *Einv, double *wk,
+                                               double tau_cond) {
+  __shared__ double red[NWARP];
+  __shared__ int ok;
+  __shared__ double vv[SDF_MAX_K], ww[SDF_MAX_K];
+  const int b = blockIdx.x;
+  InstState &S = st[b];
+  if (S.outer_done) return;
+  const size_t kk = (size_t)k * k;
+  double *Lg = wk + (size_t)b * 5 * kk, *Lgi = Lg + kk, *T = Lgi + kk, *E = T + kk, *Lei = E + kk;
+  const double *Gb = G + (size_t)b * kk, *Eb = Eraw + (size_t)b * kk;
+  double *Ei = Einv + (size_t)b * kk;
+  for (size_t e = threadIdx.x; e < kk; e += NT) Lg[e] = Gb[e];
+  __syncthreads();
+  bool good = dev_cholesky(Lg, k, red, &ok, 1e-14);  // rank test: R_jj^2 <= 1e-14 max R^2
+  double cond = INFINITY;
+  if (good) {
+    dev_tri_inv(Lg, Lgi, k);
+    dev_gemm(Lgi, Eb, T, k, false, false);  // T = Lg^-1 Eraw
+    dev_gemm(T, Lgi, E, k, false, true);    // E = T Lg^-T
+    for (size_t e = threadIdx.x; e < kk; e += NT) {
+      int i = (int)(e / k), j = (int)(e % k);
+      if (i < j) {
+        double s = 0.5 * (E[i * k + j] + E[j * k + i]);
+        E[i * k + j] = s;
+        E[j * k + i] = s;
+      }
+    }
+    __syncthreads();
+    double lmax = dev_power(E, nullptr, k, 0, vv, ww, red);
+    for (size_t e = threadIdx.x; e < kk; e += NT) T[e] = E[e];
+    __syncthreads();
+    good = dev_cholesky(T, k, red, &ok, 0.0);
+    if (good) {
+      dev_tri_inv(T, Lei, k);
+      double linv = dev_power(nullptr, Lei, k, 1, vv, ww, red);  // lambda_max(E^-1)
+      cond = (linv > 0 && lmax > 0) ? lmax * linv : INFINITY;
+      if (cond <= tau_cond) {
+        dev_gemm(Lei, Lgi, T, k, false, false);  // F = Le^-1 Lg^-1
+        dev_gemm(T, T, Ei, k, true, false);      // Einv_raw = F^T F
+      } else {
+        good = false;
+      }
+    }
+  }
+  if (threadIdx.x == 0) {
+    S.deflate = good ? 1 : 0;
+    S.stats.cond_E[S.outer] = cond;
+    S.stats.fallback[S.outer] = good ? 0 : 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Projection t = Phi_I^T v (initial coarse correction and sdf_project).
+
+template <int KMAX, class PhiT>
+__global__ void __launch_bounds__(NT) k_project(const PhiT *Phi, long long ld, int k, long long N,
+                                                const uint8_t *mask, const double *v,
+                                                InstState *st, double *out, double *part,
+                                                int *cnt, int GX) {
+  __shared__ double vs[512];
+  __shared__ double scratch[NT];
+  __shared__ int flag;
+  const int b = blockIdx.x, gblk = blockIdx.y;
+  if (st) {
+    const InstState &S = st[b];
+    if (S.outer_done || S.cg_done || !S.deflate) return;
+  }
+  const uint8_t *mk = mask + b * N;
+  const double *vb = v + b * N;
+  double acc[KMAX / NWARP];
+#pragma unroll
+  for (int a = 0; a < KMAX / NWARP; ++a) acc[a] = 0.0;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  for (long long base = (long long)gblk * 512; base < N; base += (long long)GX * 512) {
+    for (int e = threadIdx.x; e < 512; e += NT) {
+      long long g = base + e;
+      vs[e] = (g < N && !mk[g]) ? vb[g] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < KMAX / NWARP; ++a) {
+      int j = warp + NWARP * a;
+      if (j < k) {
+        const PhiT *ph = Phi + (long long)j * ld + base;
+        double s = 0.0;
+        for (int e = lane; e < 512; e += 32)
+          if (base + e < N) s = fma((double)ph[e], vs[e], s);
+        acc[a] += s;
+      }
+    }
+    __syncthreads();
+  }
+  const int F = KMAX;
+  double *pb = part + ((long long)b * GX + gblk) * F;
+#pragma unroll
+  for (int a = 0; a < KMAX / NWARP; ++a) {
+    double s = warp_sum(acc[a]);
+    int j = warp + NWARP * a;
+    if (lane == 0 && j < k) pb[j] = s;
+  }
+  if (!last_block(cnt + b * NCNT + CNT_PROJECT, GX, &flag)) return;
+  __shared__ double res[SDF_MAX_K];
+  reduce_fields(part + (long long)b * GX * F, GX, F, k, res, scratch);
+  if (threadIdx.x == 0) cnt[b * NCNT + CNT_PROJECT] = 0;
+  for (int j = threadIdx.x; j < k; j += NT) {
+    if (st) st[b].t[j] = res[j];
+    else out[b * k + j] = res[j];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// CG iteration, kernel A: p = mask_I (gamma D^-1 r - Phi c + beta p) with
+// c = csign E_raw^-1 t (the coarse GEMV, recomputed by every block).
+
+template <int KMAX, class PhiT>
+__global__ void __launch_bounds__(NT) k_expand(const PhiT *Phi, long long ld, int k, long long N,
+                                               const InstState *st, const double *Einv,
+                                               const uint8_t *mask, const double *r,
+                                               const double *dinv, int dinv_per_inst, double *p,
+                                               int GX) {
+  __shared__ double c[SDF_MAX_K];
+  const int b = blockIdx.x, gblk = blockIdx.y;
+  const InstState &S = st[b];
+  if (S.outer_done || S.cg_done) return;
+  const int defl = S.deflate;
+  const double gam = S.gamma, bet = S.beta;
+  if (defl) {
+    const double *Ei = Einv + (size_t)b * k * k;
+    for (int i = threadIdx.x; i < k; i += NT) {
+      double s = 0.0;
+      for (int j = 0; j < k; ++j) s = fma(Ei[i * k + j], S.t[j], s);
+      c[i] = S.csign * s;
+    }
+  }
+  __syncthreads();
+  const uint8_t *mk = mask + b * N;
+  const double *rb = r + b * N;
+  const double *db = dinv + (dinv_per_inst ? b * N : 0);
+  double *pb = p + b * N;
+  for (long long g = (long long)gblk * NT + threadIdx.x; g < N; g += (long long)GX * NT) {
+    double v = 0.0;
+    if (!mk[g]) {
+      v = gam * db[g] * rb[g] + bet * pb[g];
+      if (defl) {
+        double s0 = 0.0, s1 = 0.0;
+        int j = 0;
+        for (; j + 1 < k; j += 2) {
+          s0 = fma((double)Phi[(long long)j * ld + g], c[j], s0);
+          s1 = fma((double)Phi[(long long)(j + 1) * ld + g], c[j + 1], s1);
+        }
+        if (j < k) s0 = fma((double)Phi[(long long)j * ld + g], c[j], s0);
+        v -= s0 + s1;
+      }
+    }
+    pb[g] = v;
+  }
+}
+
+// Kernel B: q = S_II p and sigma = (p, q); the last block sets alpha.
+template <int DIM>
+__global__ void __launch_bounds__(NT) k_spmv(OpParams P, const double *inst, InstState *st,
+                                             const uint8_t *mask, const double *p, double *q,
+                                             double *part, int *cnt, Ctrl *ctrl, int GX) {
+  __shared__ TileSmem<DIM> sm;
+  __shared__ double red[NWARP];
+  __shared__ int flag;
+  const int b = blockIdx.x, gblk = blockIdx.y;
+  InstState &S = st[b];
+  if (S.outer_done || S.cg_done) return;
+  const long long N = P.N;
+  double cb[3];
+  inst_cb(P, inst + 7 * b, cb);
+  const uint8_t *mk = mask + b * N;
+  const double *pb = p + b * N;
+  double *qb = q + b * N;
+  double sg = 0.0;
+  const long long T = num_tiles<DIM>(P.nx, P.ny, P.nz);
+  for (long long t = gblk; t < T; t += GX) {
+    int ox, oy, oz;
+    tile_origin<DIM>(P, t, ox, oy, oz);
+    tile_S<DIM>(
+        P, cb, ox, oy, oz, sm, [&](int, int, int, long long g) { return pb[g]; },
+        [&](int e, int, int, int, long long g, double su) {
+          double qv = mk[g] ? 0.0 : su;
+          qb[g] = qv;
+          sg = fma(sm.u[uidx<DIM>(e % TileCfg<DIM>::TX, (e / TileCfg<DIM>::TX) % TileCfg<DIM>::TY,
+                                  e / (TileCfg<DIM>::TX * TileCfg<DIM>::TY))],
+                   qv, sg);
+        });
+  }
+  sg = block_sum(sg, red);
+  if (threadIdx.x == 0) part[b * GX + gblk] = sg;
+  if (!last_block(cnt + b * NCNT + CNT_SIGMA, GX, &flag)) return;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int g = 0; g < GX; ++g) s += __ldcg(part + b * GX + g);
+    cnt[b * NCNT + CNT_SIGMA] = 0;
+    S.sigma = s;
+    if (S.phase) {
+      S.alpha = 1.0;
+    } else if (s > 0.0 && isfinite(s)) {
+      S.alpha = S.rho / s;
+    } else {
+      S.stats.status = isfinite(s) ? SDF_ERR_BREAKDOWN : SDF_ERR_NONFINITE;
+      S.cg_done = 1;
+      S.stats.cg_iters[S.outer] = S.iters;
+      atomicSub(&ctrl->running, 1);
+    }
+  }
+}
+
+// Kernel C: x += alpha p, r -= alpha q, z = D^-1 r, v = S_II z,
+// t = Phi_I^T v, rho = (r, z), ||r||^2; the last block tests convergence
+// (App. B.2) and prepares beta for kernel A.
+template <int DIM, int KMAX, class PhiT>
+__global__ void __launch_bounds__(NT) k_update(OpParams P, const double *inst, const PhiT *Phi,
+                                               long long ld, int k, InstState *st,
+                                               const uint8_t *mask, double *r, const double *q,
+                                               const double *p, double *x, const double *dinv,
+                                               double *part, int *cnt, Ctrl *ctrl, int GX,
+                                               double rtol2, int max_cg) {
+  __shared__ TileSmem<DIM> sm;
+  __shared__ double red[NWARP];
+  __shared__ double scratch[NT];
+  __shared__ double res[SDF_MAX_K + 2];
+  __shared__ int flag;
+  using C = TileCfg<DIM>;
+  const int b = blockIdx.x, gblk = blockIdx.y;
+  InstState &S = st[b];
+  if (S.outer_done || S.cg_done) return;
+  const long long N = P.N;
+  const double alpha = S.alpha;
+  const int defl = S.deflate;
+  double cb[3];
+  inst_cb(P, inst + 7 * b, cb);
+  const uint8_t *mk = mask + b * N;
+  double *rb = r + b * N, *xb = x + b * N;
+  const double *qb = q + b * N, *pb = p + b * N;
+  const double *db = dinv + (P.convection ? b * N : 0);
+  double rho = 0.0, rr = 0.0;
+  double acc[KMAX / NWARP];
+#pragma unroll
+  for (int a = 0; a < KMAX / NWARP; ++a) acc[a] = 0.0;
+  const long long T = num_tiles<DIM>(P.nx, P.ny, P.nz);
+  for (long long t = gblk; t < T; t += GX) {
+    int ox, oy, oz;
+    tile_origin<DIM>(P, t, ox, oy, oz);
+    tile_S<DIM>(
+        P, cb, ox, oy, oz, sm,
+        [&](int, int, int, long long g) {
+          return mk[g] ? 0.0 : db[g] * (rb[g] - alpha * qb[g]);
+        },
+        [&](int e, int, int, int, long long g, double su) {
+          if (mk[g]) {
+            sm.v[e] = 0.0;
+            return;
+          }
+          double rn = rb[g] - alpha * qb[g];
+          double z = db[g] * rn;
+          xb[g] = xb[g] + alpha * pb[g];
+          rb[g] = rn;
+          rho = fma(rn, z, rho);
+          rr = fma(rn, rn, rr);
+          sm.v[e] = su;
+        });
+    if (defl) {
+      tile_project<DIM, KMAX>(P, Phi, ld, k, ox, oy, oz, sm.v, acc);
+      __syncthreads();
+    }
+  }
+  rho = block_sum(rho, red);
+  rr = block_sum(rr, red);
+  const int F = KMAX + 2;
+  double *pbk = part + ((long long)b * GX + gblk) * F;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (defl) {
+#pragma unroll
+    for (int a = 0; a < KMAX / NWARP; ++a) {
+      double s = warp_sum(acc[a]);
+      int j = warp + NWARP * a;
+      if (lane == 0 && j < k) pbk[2 + j] = s;
+    }
+  }
+  if (threadIdx.x == 0) {
+    pbk[0] = rho;
+    pbk[1] = rr;
+  }
+  if (!last_block(cnt + b * NCNT + CNT_UPDATE, GX, &flag)) return;
+  reduce_fields(part + (long long)b * GX * F, GX, F, defl ? 2 + k : 2, res, scratch);
+  if (defl)
+    for (int j = threadIdx.x; j < k; j += NT) S.t[j] = res[2 + j];
+  if (threadIdx.x == 0) {
+    cnt[b * NCNT + CNT_UPDATE] = 0;
+    double rho_new = res[0], rn2 = res[1];
+    if (!S.phase) S.iters += 1;
+    S.rnorm2 = rn2;
+    bool conv = rn2 <= rtol2 * S.bnorm2;
+    if (!isfinite(rho_new) || !isfinite(rn2)) {
+      S.stats.status = SDF_ERR_NONFINITE;
+      S.cg_done = 1;
+    } else if (conv) {
+      S.cg_done = 1;
+    } else if (S.iters >= max_cg) {
+      S.stats.status = SDF_ERR_CG_MAXIT;
+      S.cg_done = 1;
+    } else {
+      S.beta = S.phase ? 0.0 : rho_new / S.rho;
+      S.rho = rho_new;
+      S.gamma = 1.0;
+      S.csign = 1.0;
+      S.phase = 0;
+    }
+    if (S.cg_done) {
+      S.stats.cg_iters[S.outer] = S.iters;
+      S.stats.relres[S.outer] = S.bnorm2 > 0 ? sqrt(rn2 / S.bnorm2) : 0.0;
+      atomicSub(&ctrl->running, 1);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Active-set update (App. B.1 lines 7-11): y = psi on A, x on I;
+// A_new = {y > psi - tau}; count changes; stop when A_new = A.
+__global__ void __launch_bounds__(NT) k_active(long long N, const double *psi, uint8_t *mask,
+                                               const double *x, double *y, InstState *st,
+                                               double *part, int *cnt, Ctrl *ctrl, int GX,
+                                               double tau, int max_outer) {
+  __shared__ double red[NWARP];
+  __shared__ int flag;
+  const int b = blockIdx.x, gblk = blockIdx.y;
+  InstState &S = st[b];
+  if (S.outer_done) return;
+  const bool failed = S.stats.status != SDF_OK;
+  uint8_t *mk = mask + b * N;
+  const double *xb = x + b * N;
+  double *yb = y + b * N;
+  double ch = 0.0;
+  for (long long g = (long long)gblk * NT + threadIdx.x; g < N; g += (long long)GX * NT) {
+    uint8_t a = mk[g];
+    double yv = a ? psi[g] : xb[g];
+    yb[g] = yv;
+    if (!failed) {
+      uint8_t an = yv > psi[g] - tau ? 1 : 0;
+      if (an != a) {
+        ch += 1.0;
+        mk[g] = an;
+      }
+    }
+  }
+  ch = block_sum(ch, red);
+  if (threadIdx.x == 0) part[b * GX + gblk] = ch;
+  if (!last_block(cnt + b * NCNT + CNT_ACTIVE, GX, &flag)) return;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int g = 0; g < GX; ++g) s += __ldcg(part + b * GX + g);
+    cnt[b * NCNT + CNT_ACTIVE] = 0;
+    S.changes = (int)s;
+    S.stats.outer_iters = S.outer + 1;
+    if (failed) {
+      S.outer_done = 1;
+    } else if (S.changes == 0) {
+      S.outer_done = 1;
+    } else if (S.outer + 1 >= max_outer) {
+      S.outer_done = 1;
+      S.stats.status = SDF_ERR_OUTER_MAXIT;
+    } else {
+      S.outer += 1;
+      atomicAdd(&ctrl->live, 1);
+    }
+  }
+}
+
+// lambda = rhs - S y on the whole grid (Eq. schur).
+template <int DIM>
+__global__ void __launch_bounds__(NT) k_lambda(OpParams P, const double *inst, const double *y,
+                                               double *lam, int GX) {
+  __shared__ TileSmem<DIM> sm;
+  const int b = blockIdx.x, gblk = blockIdx.y;
+  const long long N = P.N;
+  const double *ib = inst + 7 * b;
+  double cb[3];
+  inst_cb(P, ib, cb);
+  const double *yb = y + b * N;
+  double *lb = lam + b * N;
+  const long long T = num_tiles<DIM>(P.nx, P.ny, P.nz);
+  for (long long t = gblk; t < T; t += GX) {
+    int ox, oy, oz;
+    tile_origin<DIM>(P, t, ox, oy, oz);
+    tile_S<DIM>(
+        P, cb, ox, oy, oz, sm, [&](int, int, int, long long g) { return yb[g]; },
+        [&](int, int gx, int gy, int gz, long long g, double su) {
+          lb[g] = P.mass * desired(P, ib, gx, gy, gz) - su;
+        });
+  }
+}
+
+// sdf_apply_S building block: out = S_II u (mode 0) or S u (mode 1).
+template <int DIM>
+__global__ void __launch_bounds__(NT) k_apply(OpParams P, const double *inst,
+                                              const uint8_t *mask, const double *u, double *out,
+                                              int mode, int GX) {
+  __shared__ TileSmem<DIM> sm;
+  double cb[3];
+  inst_cb(P, inst, cb);
+  const long long T = num_tiles<DIM>(P.nx, P.ny, P.nz);
+  for (long long t = blockIdx.x; t < T; t += GX) {
+    int ox, oy, oz;
+    tile_origin<DIM>(P, t, ox, oy, oz);
+    tile_S<DIM>(
+        P, cb, ox, oy, oz, sm,
+        [&](int, int, int, long long g) { return (mode == 0 && mask[g]) ? 0.0 : u[g]; },
+        [&](int, int, int, int, long long g, double su) {
+          out[g] = (mode == 0 && mask[g]) ? 0.0 : su;
+        });
+  }
+}
+
+// Kronecker sine modes (Sec. 2.2.7): Phi_c(j) = prod_l sqrt(2/(n_l+1)) sin(i_l pi j_l/(n_l+1)).
+struct ModeIdx {
+  int v[3 * SDF_MAX_K];
+};
+
+template <class PhiT>
+__global__ void k_sine_modes(int dim, int nx, int ny, int nz, ModeIdx idx, int k, PhiT *Phi,
+                             long long ld) {
+  long long N = (long long)nx * ny * nz;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N * k;
+       e += (long long)gridDim.x * blockDim.x) {
+    int c = (int)(e / N);
+    long long g = e % N;
+    int j0 = (int)(g % nx);
+    long long t = g / nx;
+    int j1 = (int)(t % ny), j2 = (int)(t / ny);
+    double v = sqrt(2.0 / (nx + 1)) * sinpi((double)idx.v[3 * c] * (j0 + 1) / (nx + 1));
+    v *= sqrt(2.0 / (ny + 1)) * sinpi((double)idx.v[3 * c + 1] * (j1 + 1) / (ny + 1));
+    if (dim == 3) v *= sqrt(2.0 / (nz + 1)) * sinpi((double)idx.v[3 * c + 2] * (j2 + 1) / (nz + 1));
+    Phi[(long long)c * ld + g] = (PhiT)v;
+  }
+}
+
+}  // namespace
+
+// ===========================================================================
+// host side
+
+struct sdf_problem {
+  sdf_problem_desc d;
+  std::vector<double> kappa;
+  OpParams P;
+  bool bound = false;
+  void *dev = nullptr;
+  size_t dev_bytes = 0;
+  double *dinv_shared = nullptr;
+  const void *phi = nullptr;
+  int k = 0;
+  long long ld = 0;
+  sdf_dtype phi_dtype = SDF_F64;
+  std::string err;
+  int nsm = 148;
+  int *pinned = nullptr;  // 2 ints of pinned host memory for polling
+};
+
+namespace {
+
+sdf_status fail(sdf_problem *p, sdf_status s, const std::string &msg) {
+  if (p) p->err = msg;
+  return s;
+}
+
+sdf_status cuda_check(sdf_problem *p, cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return SDF_OK;
+  return fail(p, SDF_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                               \
+  do {                                                         \
+    sdf_status _s = cuda_check(p, (call), #call);              \
+    if (_s != SDF_OK) return _s;                               \
+  } while (0)
+#define CKL(what)                                              \
+  do {                                                         \
+    sdf_status _s = cuda_check(p, cudaGetLastError(), what);   \
+    if (_s != SDF_OK) return _s;                               \
+  } while (0)
+
+int kmax_for(int k) { return k <= 16 ? 16 : k <= 32 ? 32 : k <= 64 ? 64 : 128; }
+
+Layout make_layout(const sdf_problem *p, int B) {
+  Layout L{};
+  const long long N = p->P.N;
+  const int k = std::max(p->k, 1), KM = kmax_for(k);
+  long long T = p->d.dim == 2 ? num_tiles<2>(p->P.nx, p->P.ny, p->P.nz)
+                              : num_tiles<3>(p->P.nx, p->P.ny, p->P.nz);
+  long long target = (long long)p->nsm * 2;
+  L.gx = (int)std::max<long long>(1, std::min<long long>(T, (target + B - 1) / B));
+  long long chunks = (N + NT - 1) / NT;
+  L.gxa = (int)std::max<long long>(1, std::min<long long>(chunks, (p->nsm * 8LL + B - 1) / B));
+  L.gxg = (int)std::max<long long>(1, std::min<long long>((N + 15) / 16, p->nsm * 2LL));
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = al(o + bytes);
+    return at;
+  };
+  size_t vec = sizeof(double) * (size_t)N * B;
+  L.x = take(vec);
+  L.r = take(vec);
+  L.p = take(vec);
+  L.q = take(vec);
+  L.dinv = take(p->d.convection ? vec : 8);
+  L.mask = take((size_t)N * B);
+  L.W = take(sizeof(double) * (size_t)N * k);
+  size_t kk = sizeof(double) * (size_t)k * k;
+  L.Einv = take(kk * B);
+  L.Eraw = take(kk * B);
+  L.G = take(kk * B);
+  L.coarse = take(kk * B * 5);
+  int gmax = std::max(L.gx, std::max(L.gxa, 1));
+  L.part = take(sizeof(double) * (size_t)B * gmax * (KM + 4));
+  L.gpart = take(sizeof(double) * (size_t)L.gxg * k * k);
+  L.state = take(sizeof(InstState) * (size_t)B);
+  L.cnt = take(sizeof(int) * (size_t)B * NCNT);
+  L.ctrl = take(sizeof(Ctrl));
+  L.total = o;
+  return L;
+}
+
+bool aligned(const void *ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
+
+template <class PhiT>
+const PhiT *phi_as(const sdf_problem *p) { return static_cast<const PhiT *>(p->phi); }
+
+// The solve, templated on dimension, mode-count bucket and Phi type.
+template <int DIM, int KMAX, class PhiT>
+sdf_status solve_impl(sdf_problem *p, const double *inst, int B, const double *psi,
+                      const sdf_opts &o, char *ws, cudaStream_t s, double *y, double *lam,
+                      uint8_t *active, sdf_stats *stats) {
+  const Layout L = make_layout(p, B);
+  const OpParams &P = p->P;
+  const long long N = P.N;
+  double *x = (double *)(ws + L.x), *r = (double *)(ws + L.r), *pp = (double *)(ws + L.p),
+         *q = (double *)(ws + L.q);
+  double *dinv = P.convection ? (double *)(ws + L.dinv) : p->dinv_shared;
+  uint8_t *mask = (uint8_t *)(ws + L.mask);
+  double *W = (double *)(ws + L.W), *Einv = (double *)(ws + L.Einv), *Eraw = (double *)(ws + L.Eraw),
+         *G = (double *)(ws + L.G), *coarse = (double *)(ws + L.coarse),
+         *part = (double *)(ws + L.part), *gpart = (double *)(ws + L.gpart);
+  InstState *st = (InstState *)(ws + L.state);
+  int *cnt = (int *)(ws + L.cnt);
+  Ctrl *ctrl = (Ctrl *)(ws + L.ctrl);
+  const bool defl = o.deflate && p->phi != nullptr && p->k > 0;
+  const int k = defl ? p->k : 0;
+  const PhiT *Phi = phi_as<PhiT>(p);
+  const long long ld = p->ld;
+
+  CK(cudaMemsetAsync(mask, 0, (size_t)N * B, s));
+  CK(cudaMemsetAsync(st, 0, sizeof(InstState) * B, s));
+  CK(cudaMemsetAsync(cnt, 0, sizeof(int) * B * NCNT, s));
+  CK(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s));
+
+  const dim3 gT(B, L.gx), gA(B, L.gxa);
+  long long launches = 0;
+  const long long max_launches = o.max_launches > 0 ? o.max_launches : 4LL * o.max_cg + 64;
+  const int chunk = std::max(1, o.check_every);
+  const double rtol2 = o.rtol * o.rtol;
+  int live = B;
+  for (int outer = 0; outer < o.max_outer && live > 0; ++outer) {
+    CK(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s));
+    k_outer_setup<DIM><<<gT, NT, 0, s>>>(P, inst, psi, mask, r, x, dinv, st, part, cnt, ctrl, L.gx);
+    CKL("k_outer_setup");
+    if (defl) {
+      for (int b = 0; b < B; ++b) {
+        k_modes_W<DIM, PhiT><<<dim3(k, L.gx), NT, 0, s>>>(P, inst, b, st, mask, Phi, ld, W, L.gx);
+        k_gram<KMAX, PhiT><<<L.gxg, NT, 0, s>>>(Phi, ld, W, mask, st, b, N, k, 0, gpart);
+        k_gram_reduce<<<(k * k + NT - 1) / NT, NT, 0, s>>>(gpart, L.gxg, k, st, b, Eraw + (size_t)b * k * k);
+        k_gram<KMAX, PhiT><<<L.gxg, NT, 0, s>>>(Phi, ld, W, mask, st, b, N, k, 1, gpart);
+        k_gram_reduce<<<(k * k + NT - 1) / NT, NT, 0, s>>>(gpart, L.gxg, k, st, b, G + (size_t)b * k * k);
+      }
+      CKL("coarse setup");
+      k_coarse<<<B, NT, 0, s>>>(k, st, G, Eraw, Einv, coarse, o.tau_cond);
+      CKL("k_coarse");
+      k_project<KMAX, PhiT><<<gA, NT, 0, s>>>(Phi, ld, k, N, mask, r, st, nullptr, part, cnt, L.gxa);
+      CKL("k_project");
+    }
+    // coarse-correction pass, then CG iterations in chunks
+    for (int it = 0;; ++it) {
+      int nrep = it == 0 ? 1 : chunk;
+      for (int rep = 0; rep < nrep; ++rep) {
+        k_expand<KMAX, PhiT><<<gA, NT, 0, s>>>(Phi, ld, k, N, st, Einv, mask, r, dinv,
+                                               P.convection, pp, L.gxa);
+        k_spmv<DIM><<<gT, NT, 0, s>>>(P, inst, st, mask, pp, q, part, cnt, ctrl, L.gx);
+        k_update<DIM, KMAX, PhiT><<<gT, NT, 0, s>>>(P, inst, Phi, ld, k, st, mask, r, q, pp, x,
+                                                    dinv, part, cnt, ctrl, L.gx, rtol2, o.max_cg);
+      }
+      CKL("cg iteration");
+      launches += nrep;
+      CK(cudaMemcpyAsync(p->pinned, &ctrl->running, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (p->pinned[0] <= 0) break;
+      if (launches > max_launches)
+        return fail(p, SDF_ERR_TIMEOUT, "solve exceeded its iteration launch budget");
+    }
+    k_active<<<gA, NT, 0, s>>>(N, psi, mask, x, y, st, part, cnt, ctrl, L.gxa, o.tau, o.max_outer);
+    CKL("k_active");
+    CK(cudaMemcpyAsync(p->pinned + 1, &ctrl->live, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    live = p->pinned[1];
+  }
+  if (active) CK(cudaMemcpyAsync(active, mask, (size_t)N * B, cudaMemcpyDeviceToDevice, s));
+  if (lam) {
+    k_lambda<DIM><<<gT, NT, 0, s>>>(P, inst, y, lam, L.gx);
+    CKL("k_lambda");
+  }
+  std::vector<InstState> hs(B);
+  CK(cudaMemcpyAsync(hs.data(), st, sizeof(InstState) * B, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  int worst = SDF_OK;
+  for (int b = 0; b < B; ++b) {
+    if (stats) stats[b] = hs[b].stats;
+    if (hs[b].stats.status != SDF_OK && worst == SDF_OK) worst = hs[b].stats.status;
+  }
+  if (worst != SDF_OK) p->err = "at least one instance did not converge (see stats)";
+  return (sdf_status)worst;
+}
+
+template <int DIM, int KMAX>
+sdf_status dispatch_phi(sdf_problem *p, const double *inst, int B, const double *psi,
+                        const sdf_opts &o, char *ws, cudaStream_t s, double *y, double *lam,
+                        uint8_t *active, sdf_stats *stats) {
+  switch (p->phi_dtype) {
+    case SDF_F64: return solve_impl<DIM, KMAX, double>(p, inst, B, psi, o, ws, s, y, lam, active, stats);
+    default: return fail(p, SDF_ERR_UNSUPPORTED, "the FP64 solve needs FP64 reference modes");
+  }
+}
+
+template <int DIM>
+sdf_status dispatch_k(sdf_problem *p, const double *inst, int B, const double *psi,
+                      const sdf_opts &o, char *ws, cudaStream_t s, double *y, double *lam,
+                      uint8_t *active, sdf_stats *stats) {
+  switch (kmax_for(std::max(p->k, 1))) {
+    case 16: return dispatch_phi<DIM, 16>(p, inst, B, psi, o, ws, s, y, lam, active, stats);
+    case 32: return dispatch_phi<DIM, 32>(p, inst, B, psi, o, ws, s, y, lam, active, stats);
+    case 64: return dispatch_phi<DIM, 64>(p, inst, B, psi, o, ws, s, y, lam, active, stats);
+    default: return dispatch_phi<DIM, 128>(p, inst, B, psi, o, ws, s, y, lam, active, stats);
+  }
+}
+
+size_t problem_bytes(const sdf_problem *p) {
+  const auto &d = p->d;
+  long long nx = d.n[0], ny = d.n[1], nz = d.dim == 3 ? d.n[2] : 1;
+  long long N = nx * ny * nz;
+  size_t o = 0;
+  o = al(o + sizeof(double) * N);  // shared Jacobi diagonal
+  if (d.has_kappa) {
+    o = al(o + sizeof(double) * N);                     // kappa
+    o = al(o + sizeof(double) * (nx + 1) * ny * nz);    // fx
+    o = al(o + sizeof(double) * nx * (ny + 1) * nz);    // fy
+    if (d.dim == 3) o = al(o + sizeof(double) * nx * ny * (nz + 1));
+  }
+  return o;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+
+extern "C" {
+
+void sdf_default_opts(sdf_opts *o) {
+  if (!o) return;
+  o->rtol = 1e-8;
+  o->tau = 1e-10;
+  o->tau_cond = 1e10;
+  o->max_outer = 30;
+  o->max_cg = 1000000;
+  o->deflate = 1;
+  o->check_every = 64;
+  o->max_launches = 0;
+}
+
+sdf_status sdf_problem_create(const sdf_problem_desc *desc, const double *kappa_host,
+                              sdf_problem **out) {
+  if (!desc || !out) return SDF_ERR_INVALID_ARG;
+  *out = nullptr;
+  const sdf_problem_desc &d = *desc;
+  if (d.dim != 2 && d.dim != 3) return SDF_ERR_INVALID_ARG;
+  for (int i = 0; i < d.dim; ++i)
+    if (d.n[i] < 1 || d.n[i] > (1 << 20)) return SDF_ERR_INVALID_ARG;
+  if (!(d.alpha > 0) || !(d.mass > 0) || !(d.kscale > 0) || !(d.diff_scale > 0) ||
+      !(d.yd_sigma > 0))
+    return SDF_ERR_INVALID_ARG;
+  if (d.has_kappa && !kappa_host) return SDF_ERR_INVALID_ARG;
+  long long nz = d.dim == 3 ? d.n[2] : 1;
+  long long N = (long long)d.n[0] * d.n[1] * nz;
+  if (N > (1LL << 31)) return SDF_ERR_INVALID_ARG;
+  sdf_problem *p = new sdf_problem();
+  p->d = d;
+  if (d.has_kappa) {
+    p->kappa.assign(kappa_host, kappa_host + N);
+    for (double v : p->kappa)
+      if (!(v > 0) || !std::isfinite(v)) {
+        delete p;
+        return SDF_ERR_INVALID_ARG;
+      }
+  }
+  OpParams &P = p->P;
+  memset(&P, 0, sizeof(P));
+  P.dim = d.dim;
+  P.nx = d.n[0];
+  P.ny = d.n[1];
+  P.nz = (int)nz;
+  P.N = N;
+  P.mass = d.mass;
+  P.wgt = d.alpha * d.kscale * d.kscale / d.mass;
+  int n3[3] = {P.nx, P.ny, P.nz};
+  for (int i = 0; i < 3; ++i) {
+    P.h[i] = i < d.dim ? 1.0 / (n3[i] + 1) : 1.0;
+    P.inv_h[i] = i < d.dim ? (double)(n3[i] + 1) : 0.0;
+    P.cdiff[i] = i < d.dim ? d.diff_scale * P.inv_h[i] * P.inv_h[i] : 0.0;
+  }
+  P.convection = d.convection;
+  P.yd_sigma = d.yd_sigma;
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      p->nsm = v;
+  }
+  if (cudaHostAlloc((void **)&p->pinned, 4 * sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    delete p;
+    return SDF_ERR_CUDA;
+  }
+  *out = p;
+  return SDF_OK;
+}
+
+sdf_status sdf_problem_device_bytes(const sdf_problem *p, size_t *bytes) {
+  if (!p || !bytes) return SDF_ERR_INVALID_ARG;
+  *bytes = problem_bytes(p);
+  return SDF_OK;
+}
+
+sdf_status sdf_problem_bind(sdf_problem *p, void *dev_buf, size_t bytes, void *stream) {
+  if (!p) return SDF_ERR_INVALID_ARG;
+  size_t need = problem_bytes(p);
+  if (!dev_buf || !aligned(dev_buf, 256))
+    return fail(p, SDF_ERR_INVALID_ARG, "problem buffer must be a 256-byte aligned device pointer");
+  if (bytes < need) return fail(p, SDF_ERR_WORKSPACE, "problem buffer too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  char *base = (char *)dev_buf;
+  OpParams &P = p->P;
+  size_t o = 0;
+  p->dinv_shared = (double *)(base + o);
+  o = al(o + sizeof(double) * P.N);
+  P.fx = P.fy = P.fz = nullptr;
+  if (p->d.has_kappa) {
+    double *kap = (double *)(base + o);
+    o = al(o + sizeof(double) * P.N);
+    double *fx = (double *)(base + o);
+    o = al(o + sizeof(double) * (P.nx + 1) * (long long)P.ny * P.nz);
+    double *fy = (double *)(base + o);
+    o = al(o + sizeof(double) * P.nx * (long long)(P.ny + 1) * P.nz);
+    double *fz = nullptr;
+    if (P.dim == 3) fz = (double *)(base + o);
+    CK(cudaMemcpyAsync(kap, p->kappa.data(), sizeof(double) * P.N, cudaMemcpyHostToDevice, s));
+    k_faces<<<p->nsm * 4, NT, 0, s>>>(P, kap, p->d.diff_scale, fx, fy, fz);
+    CKL("k_faces");
+    P.fx = fx;
+    P.fy = fy;
+    P.fz = fz;
+  }
+  if (P.dim == 2) k_diag_shared<2><<<p->nsm * 4, NT, 0, s>>>(P, p->dinv_shared);
+  else k_diag_shared<3><<<p->nsm * 4, NT, 0, s>>>(P, p->dinv_shared);
+  CKL("k_diag_shared");
+  CK(cudaStreamSynchronize(s));
+  p->dev = dev_buf;
+  p->dev_bytes = bytes;
+  p->bound = true;
+  return SDF_OK;
+}
+
+sdf_status sdf_set_reference_modes(sdf_problem *p, const void *phi_dev, int k, int64_t ld,
+                                   sdf_dtype dtype) {
+  if (!p) return SDF_ERR_INVALID_ARG;
+  if (k < 1 || k > SDF_MAX_K) return fail(p, SDF_ERR_UNSUPPORTED, "k must be in [1, SDF_MAX_K]");
+  if (!phi_dev || !aligned(phi_dev, 16))
+    return fail(p, SDF_ERR_INVALID_ARG, "Phi must be a 16-byte aligned device pointer");
+  if (ld < p->P.N) return fail(p, SDF_ERR_INVALID_ARG, "ld must be >= N");
+  if (dtype != SDF_F64 && dtype != SDF_F32 && dtype != SDF_BF16)
+    return fail(p, SDF_ERR_INVALID_ARG, "unknown dtype");
+  p->phi = phi_dev;
+  p->k = k;
+  p->ld = ld;
+  p->phi_dtype = dtype;
+  return SDF_OK;
+}
+
+sdf_status sdf_analytic_modes(sdf_problem *p, int k, void *phi_dev, int64_t ld, sdf_dtype dtype,
+                              double *eigvals_host, void *stream) {
+  if (!p) return SDF_ERR_INVALID_ARG;
+  if (!phi_dev || k < 1 || ld < p->P.N) return fail(p, SDF_ERR_INVALID_ARG, "bad arguments");
+  if (k > SDF_MAX_K) return fail(p, SDF_ERR_UNSUPPORTED, "k > SDF_MAX_K");
+  const int dim = p->d.dim;
+  int n[3] = {p->P.nx, p->P.ny, p->P.nz};
+  // enumerate multi-indices with small eigenvalue sums; mu_q per direction
+  int m[3] = {1, 1, 1};
+  int lim = (int)std::ceil(std::pow(4.0 * k, 1.0 / dim)) + 4;
+  for (int d = 0; d < dim; ++d) m[d] = std::min(n[d], lim);
+  struct Cand {
+    double lam;
+    int i[3];
+  };
+  std::vector<Cand> c;
+  for (int a = 1; a <= m[0]; ++a)
+    for (int b = 1; b <= m[1]; ++b)
+      for (int e = 1; e <= (dim == 3 ? m[2] : 1); ++e) {
+        int ii[3] = {a, b, dim == 3 ? e : 1};
+        double mu[3] = {0, 0, 0};
+        for (int d = 0; d < dim; ++d) {
+          double h = 1.0 / (n[d] + 1);
+          double sn = std::sin(ii[d] * M_PI / (2.0 * (n[d] + 1)));
+          mu[d] = 4.0 / (h * h) * sn * sn;
+        }
+        std::sort(mu, mu + dim);  // order-independent sum: exact ties stay ties
+        double sum = 0.0;
+        for (int d = 0; d < dim; ++d) sum += mu[d];
+        c.push_back({sum, {ii[0], ii[1], ii[2]}});
+      }
+  if ((int)c.size() < k) return fail(p, SDF_ERR_INVALID_ARG, "k larger than the grid supports");
+  std::stable_sort(c.begin(), c.end(), [&](const Cand &x, const Cand &y) {
+    if (x.lam != y.lam) return x.lam < y.lam;
+    for (int d = dim - 1; d >= 0; --d)
+      if (x.i[d] != y.i[d]) return x.i[d] < y.i[d];
+    return false;
+  });
+  std::vector<int> idx(3 * k);
+  for (int j = 0; j < k; ++j)
+    for (int d = 0; d < 3; ++d) idx[3 * j + d] = c[j].i[d];
+  if (eigvals_host) {
+    double ds = p->d.diff_scale;
+    for (int j = 0; j < k; ++j)
+      eigvals_host[j] = p->P.mass + p->P.wgt * (ds * c[j].lam) * (ds * c[j].lam);
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  ModeIdx tab;
+  memset(&tab, 0, sizeof(tab));
+  for (int j = 0; j < 3 * k; ++j) tab.v[j] = idx[j];
+  const int grid = p->nsm * 8;
+  switch (dtype) {
+    case SDF_F64:
+      k_sine_modes<double><<<grid, NT, 0, s>>>(dim, n[0], n[1], n[2], tab, k, (double *)phi_dev, ld);
+      break;
+    case SDF_F32:
+      k_sine_modes<float><<<grid, NT, 0, s>>>(dim, n[0], n[1], n[2], tab, k, (float *)phi_dev, ld);
+      break;
+    case SDF_BF16:
+      k_sine_modes<__nv_bfloat16><<<grid, NT, 0, s>>>(dim, n[0], n[1], n[2], tab, k,
+                                                      (__nv_bfloat16 *)phi_dev, ld);
+      break;
+    default:
+      return fail(p, SDF_ERR_INVALID_ARG, "unknown dtype");
+  }
+  CKL("k_sine_modes");
+  return SDF_OK;
+}
+
+sdf_status sdf_workspace_size(const sdf_problem *p, int batch, const sdf_opts *opts, size_t *bytes) {
+  if (!p || !bytes || batch < 1) return SDF_ERR_INVALID_ARG;
+  (void)opts;
+  *bytes = make_layout(p, batch).total;
+  return SDF_OK;
+}
+
+sdf_status sdf_host_io_bytes(const sdf_problem *p, int batch, size_t *bytes) {
+  if (!p || !bytes || batch < 1) return SDF_ERR_INVALID_ARG;
+  long long N = p->P.N;
+  *bytes = al(sizeof(double) * 7 * batch) + al(sizeof(double) * N) +
+           2 * al(sizeof(double) * N * batch) + al((size_t)N * batch);
+  return SDF_OK;
+}
+
+static sdf_status check_solve_args(sdf_problem *p, int batch, const sdf_opts *opts, void *ws,
+                                   size_t ws_bytes) {
+  if (!p) return SDF_ERR_INVALID_ARG;
+  if (!p->bound) return fail(p, SDF_ERR_INVALID_ARG, "problem not bound (sdf_problem_bind)");
+  if (batch < 1 || batch > 65535) return fail(p, SDF_ERR_INVALID_ARG, "batch out of range");
+  if (!opts) return fail(p, SDF_ERR_INVALID_ARG, "opts is NULL");
+  if (opts->max_outer < 1 || opts->max_outer > SDF_MAX_OUTER)
+    return fail(p, SDF_ERR_INVALID_ARG, "max_outer must be in [1, SDF_MAX_OUTER]");
+  if (opts->max_cg < 0 || !(opts->rtol >= 0)) return fail(p, SDF_ERR_INVALID_ARG, "bad opts");
+  if (!ws || !aligned(ws, 256))
+    return fail(p, SDF_ERR_INVALID_ARG, "workspace must be a 256-byte aligned device pointer");
+  size_t need = make_layout(p, batch).total;
+  if (ws_bytes < need) return fail(p, SDF_ERR_WORKSPACE, "workspace too small");
+  if (opts->deflate && p->phi && p->phi_dtype != SDF_F64)
+    return fail(p, SDF_ERR_UNSUPPORTED, "this solve path takes FP64 reference modes");
+  return SDF_OK;
+}
+
+sdf_status sdf_solve_batch(sdf_problem *p, const double *inst_dev, int batch, const double *psi_dev,
+                           const sdf_opts *opts, void *ws, size_t ws_bytes, void *stream,
+                           double *y_dev, double *lambda_dev, uint8_t *active_dev,
+                           sdf_stats *stats_host) {
+  sdf_status st = check_solve_args(p, batch, opts, ws, ws_bytes);
+  if (st != SDF_OK) return st;
+  if (!inst_dev || !psi_dev || !y_dev || !active_dev)
+    return fail(p, SDF_ERR_INVALID_ARG, "NULL input or output pointer");
+  p->err.clear();
+  cudaStream_t s = (cudaStream_t)stream;
+  if (p->d.dim == 2)
+    return dispatch_k<2>(p, inst_dev, batch, psi_dev, *opts, (char *)ws, s, y_dev, lambda_dev,
+                         active_dev, stats_host);
+  return dispatch_k<3>(p, inst_dev, batch, psi_dev, *opts, (char *)ws, s, y_dev, lambda_dev,
+                       active_dev, stats_host);
+}
+
+sdf_status sdf_solve_batch_host(sdf_problem *p, const double *inst_host, int batch,
+                                const double *psi_host, const sdf_opts *opts, void *ws,
+                                size_t ws_bytes, void *stream, double *y_host, double *lambda_host,
+                                uint8_t *active_host, sdf_stats *stats_host) {
+  if (!p) return SDF_ERR_INVALID_ARG;
+  if (!inst_host || !psi_host || !y_host || !active_host)
+    return fail(p, SDF_ERR_INVALID_ARG, "NULL host pointer");
+  size_t need = 0, io = 0;
+  if (batch < 1) return fail(p, SDF_ERR_INVALID_ARG, "batch out of range");
+  sdf_workspace_size(p, batch, opts, &need);
+  sdf_host_io_bytes(p, batch, &io);
+  if (ws_bytes < need + io) return fail(p, SDF_ERR_WORKSPACE, "workspace too small for host I/O");
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long N = p->P.N;
+  char *base = (char *)ws + al(need);
+  double *inst_d = (double *)base;
+  base += al(sizeof(double) * 7 * batch);
+  double *psi_d = (double *)base;
+  base += al(sizeof(double) * N);
+  double *y_d = (double *)base;
+  base += al(sizeof(double) * N * batch);
+  double *lam_d = (double *)base;
+  base += al(sizeof(double) * N * batch);
+  uint8_t *act_d = (uint8_t *)base;
+  if (ws_bytes < al(need) + io) return fail(p, SDF_ERR_WORKSPACE, "workspace too small for host I/O");
+  CK(cudaMemcpyAsync(inst_d, inst_host, sizeof(double) * 7 * batch, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(psi_d, psi_host, sizeof(double) * N, cudaMemcpyHostToDevice, s));
+  sdf_status st = sdf_solve_batch(p, inst_d, batch, psi_d, opts, ws, need, stream, y_d,
+                                  lambda_host ? lam_d : nullptr, act_d, stats_host);
+  if (st != SDF_OK && st != SDF_ERR_CG_MAXIT && st != SDF_ERR_OUTER_MAXIT &&
+      st != SDF_ERR_BREAKDOWN && st != SDF_ERR_NONFINITE)
+    return st;
+  CK(cudaMemcpyAsync(y_host, y_d, sizeof(double) * N * batch, cudaMemcpyDeviceToHost, s));
+  if (lambda_host)
+    CK(cudaMemcpyAsync(lambda_host, lam_d, sizeof(double) * N * batch, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(active_host, act_d, (size_t)N * batch, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return st;
+}
+
+sdf_status sdf_apply_S(sdf_problem *p, const double *inst_dev, const uint8_t *active_dev,
+                       const double *u_dev, double *out_dev, int mode, void *ws, size_t ws_bytes,
+                       void *stream) {
+  if (!p) return SDF_ERR_INVALID_ARG;
+  if (!p->bound) return fail(p, SDF_ERR_INVALID_ARG, "problem not bound");
+  if (!inst_dev || !u_dev || !out_dev || (mode == 0 && !active_dev) || (mode != 0 && mode != 1))
+    return fail(p, SDF_ERR_INVALID_ARG, "bad arguments");
+  (void)ws;
+  (void)ws_bytes;
+  cudaStream_t s = (cudaStream_t)stream;
+  const OpParams &P = p->P;
+  int GX = p->nsm * 4;
+  if (P.dim == 2) k_apply<2><<<GX, NT, 0, s>>>(P, inst_dev, active_dev, u_dev, out_dev, mode, GX);
+  else k_apply<3><<<GX, NT, 0, s>>>(P, inst_dev, active_dev, u_dev, out_dev, mode, GX);
+  CKL("k_apply");
+  return SDF_OK;
+}
+
+sdf_status sdf_project(sdf_problem *p, const uint8_t *active_dev, const double *v_dev,
+                       double *out_dev, void *ws, size_t ws_bytes, void *stream) {
+  if (!p) return SDF_ERR_INVALID_ARG;
+  if (!p->phi) return fail(p, SDF_ERR_INVALID_ARG, "no reference modes registered");
+  if (p->phi_dtype != SDF_F64) return fail(p, SDF_ERR_UNSUPPORTED, "FP64 modes expected");
+  if (!active_dev || !v_dev || !out_dev) return fail(p, SDF_ERR_INVALID_ARG, "NULL pointer");
+  int GX = p->nsm * 2;
+  int KM = kmax_for(p->k);
+  size_t need = al(sizeof(double) * (size_t)GX * KM) + al(sizeof(int) * NCNT);
+  if (!ws || !aligned(ws, 256) || ws_bytes < need)
+    return fail(p, SDF_ERR_WORKSPACE, "workspace too small for sdf_project");
+  double *part = (double *)ws;
+  int *cnt = (int *)((char *)ws + al(sizeof(double) * (size_t)GX * KM));
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemsetAsync(cnt, 0, sizeof(int) * NCNT, s));
+  const double *Phi = (const double *)p->phi;
+  dim3 g(1, GX);
+  switch (KM) {
+    case 16: k_project<16, double><<<g, NT, 0, s>>>(Phi, p->ld, p->k, p->P.N, active_dev, v_dev, nullptr, out_dev, part, cnt, GX); break;
+    case 32: k_project<32, double><<<g, NT, 0, s>>>(Phi, p->ld, p->k, p->P.N, active_dev, v_dev, nullptr, out_dev, part, cnt, GX); break;
+    case 64: k_project<64, double><<<g, NT, 0, s>>>(Phi, p->ld, p->k, p->P.N, active_dev, v_dev, nullptr, out_dev, part, cnt, GX); break;
+    default: k_project<128, double><<<g, NT, 0, s>>>(Phi, p->ld, p->k, p->P.N, active_dev, v_dev, nullptr, out_dev, part, cnt, GX); break;
+  }
+  CKL("k_project");
+  return SDF_OK;
+}
+
+const char *sdf_last_error(const sdf_problem *p) { return p ? p->err.c_str() : "null handle"; }
+
+void sdf_problem_destroy(sdf_problem *p) {
+  if (!p) return;
+  if (p->pinned) cudaFreeHost(p->pinned);
+  delete p;
+}
+
+}  // extern "C"

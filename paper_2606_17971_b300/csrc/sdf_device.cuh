@@ -1,0 +1,305 @@
+// sdf_device.cuh -- device-side building blocks of the sm_103a solver:
+// the matrix-free masked application of S = mass I + w A^T A (flux form,
+// halo-2 shared-memory tiles), projections onto the reference modes, and the
+// deterministic grid reductions.  Included only by sdf.cu.
+#pragma once
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/sdf.h"
+
+namespace sdf {
+
+constexpr int NT = 256;          // threads per block of every tile kernel
+constexpr int NWARP = NT / 32;
+
+// --------------------------------------------------------------------------
+// Operator description passed by value to kernels.
+struct OpParams {
+  int dim, nx, ny, nz;
+  long long N;
+  double mass, wgt;        // S = mass I + wgt A^T A, wgt = alpha kscale^2 / mass
+  double cdiff[3];         // diff_scale / h_d^2 for kappa = 1
+  double inv_h[3];
+  const double *fx, *fy, *fz;  // face coefficients (already scaled) or null
+  int convection;
+  double yd_sigma;
+  double h[3];
+};
+
+// Tile shapes: 2D 64 x 8 (halo 2 in x, y), 3D 32 x 4 x 4 (halo 2 everywhere).
+template <int DIM> struct TileCfg;
+template <> struct TileCfg<2> {
+  static constexpr int TX = 64, TY = 8, TZ = 1, HZ = 0, HZ1 = 0;
+};
+template <> struct TileCfg<3> {
+  static constexpr int TX = 32, TY = 4, TZ = 4, HZ = 2, HZ1 = 1;
+};
+
+template <int DIM> struct TileSmem {
+  using C = TileCfg<DIM>;
+  static constexpr int UX = C::TX + 4, UY = C::TY + 4, UZ = C::TZ + 2 * C::HZ;
+  static constexpr int WX = C::TX + 2, WY = C::TY + 2, WZ = C::TZ + 2 * C::HZ1;
+  static constexpr int TILE = C::TX * C::TY * C::TZ;
+  double u[UZ * UY * UX];
+  double w[WZ * WY * WX];
+  double v[TILE];
+};
+
+template <int DIM>
+__device__ __forceinline__ int uidx(int lx, int ly, int lz) {
+  using S = TileSmem<DIM>;
+  return (lx + 2) + S::UX * ((ly + 2) + S::UY * (lz + TileCfg<DIM>::HZ));
+}
+template <int DIM>
+__device__ __forceinline__ int widx(int lx, int ly, int lz) {
+  using S = TileSmem<DIM>;
+  return (lx + 1) + S::WX * ((ly + 1) + S::WY * (lz + TileCfg<DIM>::HZ1));
+}
+
+__device__ __forceinline__ double face_x(const OpParams &P, int i, int j, int l) {
+  return P.fx ? __ldg(P.fx + i + (long long)(P.nx + 1) * (j + (long long)P.ny * l)) : P.cdiff[0];
+}
+__device__ __forceinline__ double face_y(const OpParams &P, int i, int j, int l) {
+  return P.fy ? __ldg(P.fy + i + (long long)P.nx * (j + (long long)(P.ny + 1) * l)) : P.cdiff[1];
+}
+__device__ __forceinline__ double face_z(const OpParams &P, int i, int j, int l) {
+  return P.fz ? __ldg(P.fz + i + (long long)P.nx * (j + (long long)P.ny * l)) : P.cdiff[2];
+}
+
+// (A u)_p in flux form: sum over faces of k_f (u_p - u_nb) plus first-order
+// upwind convection; U(dx,dy,dz) returns u at the offset (0 outside the grid).
+template <int DIM, class U>
+__device__ __forceinline__ double apply_A(const OpParams &P, const double cb[3], int i, int j,
+                                          int l, U u) {
+  double c = u(0, 0, 0);
+  double s = face_x(P, i, j, l) * (c - u(-1, 0, 0)) + face_x(P, i + 1, j, l) * (c - u(1, 0, 0));
+  s += face_y(P, i, j, l) * (c - u(0, -1, 0)) + face_y(P, i, j + 1, l) * (c - u(0, 1, 0));
+  if (DIM == 3)
+    s += face_z(P, i, j, l) * (c - u(0, 0, -1)) + face_z(P, i, j, l + 1) * (c - u(0, 0, 1));
+  if (cb[0] > 0.0) s += cb[0] * (c - u(-1, 0, 0));
+  else if (cb[0] < 0.0) s -= cb[0] * (c - u(1, 0, 0));
+  if (cb[1] > 0.0) s += cb[1] * (c - u(0, -1, 0));
+  else if (cb[1] < 0.0) s -= cb[1] * (c - u(0, 1, 0));
+  if (DIM == 3) {
+    if (cb[2] > 0.0) s += cb[2] * (c - u(0, 0, -1));
+    else if (cb[2] < 0.0) s -= cb[2] * (c - u(0, 0, 1));
+  }
+  return s;
+}
+
+// (A^T w)_p: the diffusion part is symmetric; the upwind part is transposed
+// (a backward difference becomes a forward one and vice versa).
+template <int DIM, class U>
+__device__ __forceinline__ double apply_AT(const OpParams &P, const double cb[3], int i, int j,
+                                           int l, U w) {
+  double c = w(0, 0, 0);
+  double s = face_x(P, i, j, l) * (c - w(-1, 0, 0)) + face_x(P, i + 1, j, l) * (c - w(1, 0, 0));
+  s += face_y(P, i, j, l) * (c - w(0, -1, 0)) + face_y(P, i, j + 1, l) * (c - w(0, 1, 0));
+  if (DIM == 3)
+    s += face_z(P, i, j, l) * (c - w(0, 0, -1)) + face_z(P, i, j, l + 1) * (c - w(0, 0, 1));
+  if (cb[0] > 0.0) s += cb[0] * (c - w(1, 0, 0));
+  else if (cb[0] < 0.0) s -= cb[0] * (c - w(-1, 0, 0));
+  if (cb[1] > 0.0) s += cb[1] * (c - w(0, 1, 0));
+  else if (cb[1] < 0.0) s -= cb[1] * (c - w(0, -1, 0));
+  if (DIM == 3) {
+    if (cb[2] > 0.0) s += cb[2] * (c - w(0, 0, 1));
+    else if (cb[2] < 0.0) s -= cb[2] * (c - w(0, 0, -1));
+  }
+  return s;
+}
+
+// Diagonal of S at node p: mass + wgt (A_pp^2 + sum over grid neighbours q of A_qp^2).
+template <int DIM>
+__device__ double diag_S(const OpParams &P, const double cb[3], int i, int j, int l) {
+  int n[3] = {P.nx, P.ny, P.nz};
+  int c[3] = {i, j, l};
+  double app = 0.0, sq = 0.0;
+  for (int d = 0; d < DIM; ++d) {
+    double fw, fe;
+    if (d == 0) { fw = face_x(P, i, j, l); fe = face_x(P, i + 1, j, l); }
+    else if (d == 1) { fw = face_y(P, i, j, l); fe = face_y(P, i, j + 1, l); }
+    else { fw = face_z(P, i, j, l); fe = face_z(P, i, j, l + 1); }
+    double b = cb[d];
+    app += fw + fe + fabs(b);
+    if (c[d] - 1 >= 0) { double a = -fw - (b < 0.0 ? -b : 0.0); sq += a * a; }
+    if (c[d] + 1 < n[d]) { double a = -fe - (b > 0.0 ? b : 0.0); sq += a * a; }
+  }
+  return P.mass + P.wgt * (app * app + sq);
+}
+
+// Tile origin of tile t.
+template <int DIM>
+__device__ __forceinline__ void tile_origin(const OpParams &P, long long t, int &ox, int &oy, int &oz) {
+  using C = TileCfg<DIM>;
+  int ntx = (P.nx + C::TX - 1) / C::TX, nty = (P.ny + C::TY - 1) / C::TY;
+  ox = (int)(t % ntx) * C::TX;
+  long long r = t / ntx;
+  oy = (int)(r % nty) * C::TY;
+  oz = (int)(r / nty) * C::TZ;
+}
+
+template <int DIM>
+__host__ __device__ inline long long num_tiles(int nx, int ny, int nz) {
+  using C = TileCfg<DIM>;
+  return (long long)((nx + C::TX - 1) / C::TX) * ((ny + C::TY - 1) / C::TY) *
+         ((nz + C::TZ - 1) / C::TZ);
+}
+
+// Apply S to the tile with origin (ox,oy,oz): load(gx,gy,gz,g) gives u at a grid
+// node; store(e, gx, gy, gz, g, Su) receives S u at each grid node of the tile
+// (e = local tile index).  Two shared-memory passes: w = A u on the halo-1
+// ring, then mass u + wgt A^T w on the tile.
+template <int DIM, class Load, class Store>
+__device__ void tile_S(const OpParams &P, const double cb[3], int ox, int oy, int oz,
+                       TileSmem<DIM> &sm, Load load, Store store) {
+  using C = TileCfg<DIM>;
+  using SM = TileSmem<DIM>;
+  for (int e = threadIdx.x; e < SM::UZ * SM::UY * SM::UX; e += NT) {
+    int lx = e % SM::UX - 2;
+    int t = e / SM::UX;
+    int ly = t % SM::UY - 2;
+    int lz = t / SM::UY - C::HZ;
+    int gx = ox + lx, gy = oy + ly, gz = oz + lz;
+    bool in = gx >= 0 && gx < P.nx && gy >= 0 && gy < P.ny && gz >= 0 && gz < P.nz;
+    sm.u[e] = in ? load(gx, gy, gz, gx + (long long)P.nx * (gy + (long long)P.ny * gz)) : 0.0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < SM::WZ * SM::WY * SM::WX; e += NT) {
+    int lx = e % SM::WX - 1;
+    int t = e / SM::WX;
+    int ly = t % SM::WY - 1;
+    int lz = t / SM::WY - C::HZ1;
+    int gx = ox + lx, gy = oy + ly, gz = oz + lz;
+    bool in = gx >= 0 && gx < P.nx && gy >= 0 && gy < P.ny && gz >= 0 && gz < P.nz;
+    double val = 0.0;
+    if (in)
+      val = apply_A<DIM>(P, cb, gx, gy, gz, [&](int dx, int dy, int dz) {
+        return sm.u[uidx<DIM>(lx + dx, ly + dy, lz + dz)];
+      });
+    sm.w[e] = val;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < SM::TILE; e += NT) {
+    int lx = e % C::TX;
+    int t = e / C::TX;
+    int ly = t % C::TY;
+    int lz = t / C::TY;
+    int gx = ox + lx, gy = oy + ly, gz = oz + lz;
+    bool in = gx < P.nx && gy < P.ny && gz < P.nz;
+    if (!in) {
+      sm.v[e] = 0.0;
+      continue;
+    }
+    double uc = sm.u[uidx<DIM>(lx, ly, lz)];
+    double atw = apply_AT<DIM>(P, cb, gx, gy, gz, [&](int dx, int dy, int dz) {
+      return sm.w[widx<DIM>(lx + dx, ly + dy, lz + dz)];
+    });
+    store(e, gx, gy, gz, gx + (long long)P.nx * (gy + (long long)P.ny * gz), P.mass * uc + P.wgt * atw);
+  }
+  __syncthreads();
+}
+
+// Accumulate acc[jj] += sum over the tile of Phi_j(g) v(g) for modes
+// j = warp + NWARP*jj < k; lanes run over the contiguous x-rows of the tile
+// (coalesced reads of each mode).  v is the tile-local vector in shared memory
+// (zero outside I and outside the grid).
+template <int DIM, int KMAX, class PhiT>
+__device__ __forceinline__ void tile_project(const OpParams &P, const PhiT *__restrict__ Phi,
+                                             long long ld, int k, int ox, int oy, int oz,
+                                             const double *v_s, double (&acc)[KMAX / NWARP]) {
+  using C = TileCfg<DIM>;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+#pragma unroll
+  for (int jj = 0; jj < KMAX / NWARP; ++jj) {
+    int j = warp + NWARP * jj;
+    if (j < k) {
+      const PhiT *ph = Phi + (long long)j * ld;
+      double s = 0.0;
+      for (int e = lane; e < C::TX * C::TY * C::TZ; e += 32) {
+        int lx = e % C::TX;
+        int t = e / C::TX;
+        int gx = ox + lx, gy = oy + t % C::TY, gz = oz + t / C::TY;
+        if (gx < P.nx && gy < P.ny && gz < P.nz) {
+          long long g = gx + (long long)P.nx * (gy + (long long)P.ny * gz);
+          s = fma((double)ph[g], v_s[e], s);
+        }
+      }
+      acc[jj] += s;
+    }
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum of one double (all threads get the result).
+__device__ __forceinline__ double block_sum(double v, double *red /* NWARP doubles */) {
+  v = warp_sum(v);
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = v;
+  __syncthreads();
+  double s = 0.0;
+#pragma unroll
+  for (int w = 0; w < NWARP; ++w) s += red[w];
+  __syncthreads();
+  return s;
+}
+
+// Last-block detection: returns true in exactly one block per counter after
+// all `nblocks` blocks have published their partials.
+__device__ __forceinline__ bool last_block(int *counter, int nblocks, int *flag_smem) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int prev = atomicAdd(counter, 1);
+    *flag_smem = (prev == nblocks - 1);
+  }
+  __syncthreads();
+  bool last = *flag_smem != 0;
+  if (last) __threadfence();
+  return last;
+}
+
+// Deterministic reduction by the last block: out[f] = sum_g part[g*stride + f]
+// for f < nf, summed in block order g = 0..ng-1 (fixed order, identical on
+// every run).  Uses all threads: field f is split over `split` threads whose
+// partial sums are then combined in order.
+__device__ void reduce_fields(const double *part, int ng, int stride, int nf, double *out,
+                              double *scratch /* >= NT doubles */) {
+  int split = NT / nf;
+  if (split < 1) split = 1;
+  if (split > 32) split = 32;
+  int f = threadIdx.x / split, s = threadIdx.x % split;
+  double acc = 0.0;
+  if (f < nf) {
+    int per = (ng + split - 1) / split;
+    int g0 = s * per, g1 = min(ng, g0 + per);
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    int g = g0;
+    for (; g + 3 < g1; g += 4) {
+      a0 += __ldcg(part + (long long)g * stride + f);
+      a1 += __ldcg(part + (long long)(g + 1) * stride + f);
+      a2 += __ldcg(part + (long long)(g + 2) * stride + f);
+      a3 += __ldcg(part + (long long)(g + 3) * stride + f);
+    }
+    for (; g < g1; ++g) a0 += __ldcg(part + (long long)g * stride + f);
+    acc = (a0 + a1) + (a2 + a3);
+  }
+  scratch[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x < nf && threadIdx.x * 1 < NT) {
+    int ff = threadIdx.x;
+    if (ff < nf && ff * split < NT) {
+      double t = 0.0;
+      for (int q = 0; q < split; ++q) t += scratch[ff * split + q];
+      out[ff] = t;
+    }
+  }
+  __syncthreads();
+}
+
+}  // namespace sdf

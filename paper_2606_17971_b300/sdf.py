@@ -1,0 +1,239 @@
+"""Python binding of the C ABI in include/sdf.h (argument marshalling only).
+
+Every step of the solve runs in the CUDA library libsdf_b300.so; PyTorch only
+provides device memory (tensors whose data pointers are passed through) and
+the current CUDA stream.  Importing this module raises if the library is
+missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsdf_b300.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: run `python -m paper_2606_17971_b300.build` "
+                      "(the solver has no CPU fallback)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+SDF_MAX_K = 128
+SDF_MAX_OUTER = 32
+F64, F32, BF16 = 0, 1, 2
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "WORKSPACE", 3: "CUDA", 4: "NOT_SPD", 5: "CG_MAXIT",
+          6: "OUTER_MAXIT", 7: "BREAKDOWN", 8: "NONFINITE", 9: "TIMEOUT", 10: "UNSUPPORTED"}
+_TORCH_DTYPE = {F64: torch.float64, F32: torch.float32, BF16: torch.bfloat16}
+
+
+class ProblemDesc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("n", ctypes.c_int32 * 3), ("alpha", ctypes.c_double),
+                ("mass", ctypes.c_double), ("kscale", ctypes.c_double),
+                ("diff_scale", ctypes.c_double), ("has_kappa", ctypes.c_int32),
+                ("convection", ctypes.c_int32), ("yd_sigma", ctypes.c_double)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("tau", ctypes.c_double), ("tau_cond", ctypes.c_double),
+                ("max_outer", ctypes.c_int32), ("max_cg", ctypes.c_int32),
+                ("deflate", ctypes.c_int32), ("check_every", ctypes.c_int32),
+                ("max_launches", ctypes.c_int64)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("outer_iters", ctypes.c_int32),
+                ("cg_iters", ctypes.c_int32 * SDF_MAX_OUTER),
+                ("n_active", ctypes.c_int32 * SDF_MAX_OUTER),
+                ("fallback", ctypes.c_int32 * SDF_MAX_OUTER),
+                ("cond_E", ctypes.c_double * SDF_MAX_OUTER),
+                ("relres", ctypes.c_double * SDF_MAX_OUTER)]
+
+
+_vp, _sz = ctypes.c_void_p, ctypes.c_size_t
+_i32, _i64 = ctypes.c_int, ctypes.c_int64
+_sigs = {
+    "sdf_default_opts": (None, [ctypes.POINTER(Opts)]),
+    "sdf_problem_create": (_i32, [ctypes.POINTER(ProblemDesc), _vp, ctypes.POINTER(_vp)]),
+    "sdf_problem_device_bytes": (_i32, [_vp, ctypes.POINTER(_sz)]),
+    "sdf_problem_bind": (_i32, [_vp, _vp, _sz, _vp]),
+    "sdf_set_reference_modes": (_i32, [_vp, _vp, _i32, _i64, _i32]),
+    "sdf_analytic_modes": (_i32, [_vp, _i32, _vp, _i64, _i32, _vp, _vp]),
+    "sdf_workspace_size": (_i32, [_vp, _i32, ctypes.POINTER(Opts), ctypes.POINTER(_sz)]),
+    "sdf_host_io_bytes": (_i32, [_vp, _i32, ctypes.POINTER(_sz)]),
+    "sdf_solve_batch": (_i32, [_vp, _vp, _i32, _vp, ctypes.POINTER(Opts), _vp, _sz, _vp, _vp, _vp,
+                               _vp, _vp]),
+    "sdf_solve_batch_host": (_i32, [_vp, _vp, _i32, _vp, ctypes.POINTER(Opts), _vp, _sz, _vp, _vp,
+                                    _vp, _vp, _vp]),
+    "sdf_apply_S": (_i32, [_vp, _vp, _vp, _vp, _vp, _i32, _vp, _sz, _vp]),
+    "sdf_project": (_i32, [_vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "sdf_last_error": (ctypes.c_char_p, [_vp]),
+    "sdf_problem_destroy": (None, [_vp]),
+}
+for _name, (_res, _args) in _sigs.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_sigs)
+
+
+class SdfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    _lib.sdf_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def stats_dict(s: Stats) -> dict:
+    n = s.outer_iters
+    return dict(status=s.status, outer_iters=n, cg_iters=list(s.cg_iters[:n]),
+                n_active=list(s.n_active[:n]), fallback=list(s.fallback[:n]),
+                cond_E=list(s.cond_E[:n]), relres=list(s.relres[:n]))
+
+
+class Problem:
+    """Handle over sdf_problem: operator data bound to a device tensor."""
+
+    def __init__(self, dim, n, alpha=1e-4, kappa=None, mass=1.0, kscale=1.0, diff_scale=1.0,
+                 convection=False, yd_sigma=0.1, device="cuda"):
+        n = list(n) if hasattr(n, "__len__") else [n] * dim
+        while len(n) < 3:
+            n.append(1)
+        d = ProblemDesc(dim=dim, alpha=alpha, mass=mass, kscale=kscale, diff_scale=diff_scale,
+                        has_kappa=int(kappa is not None), convection=int(bool(convection)),
+                        yd_sigma=yd_sigma)
+        for i in range(3):
+            d.n[i] = n[i]
+        self.dim, self.n = dim, tuple(n[:dim])
+        self.N = int(np.prod(self.n))
+        self.device = torch.device(device)
+        kap = None if kappa is None else np.ascontiguousarray(kappa, dtype=np.float64)
+        h = ctypes.c_void_p()
+        st = _lib.sdf_problem_create(ctypes.byref(d), kap.ctypes.data if kap is not None else None,
+                                     ctypes.byref(h))
+        if st != 0:
+            raise SdfError(st, "sdf_problem_create")
+        self._h = h
+        nb = _sz()
+        self._check(_lib.sdf_problem_device_bytes(self._h, ctypes.byref(nb)))
+        self._buf = torch.empty(max(int(nb.value), 256), dtype=torch.uint8, device=self.device)
+        self._check(_lib.sdf_problem_bind(self._h, _ptr(self._buf), self._buf.numel(), _stream()))
+        self._phi = None
+        self._ws = None
+
+    def _check(self, st):
+        if st != 0:
+            raise SdfError(st, _lib.sdf_last_error(self._h).decode())
+        return st
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            _lib.sdf_problem_destroy(self._h)
+            self._h = None
+
+    # reference modes ------------------------------------------------------
+    def set_modes(self, phi: torch.Tensor):
+        """phi: (k, N) contiguous device tensor (mode j = row j), i.e. the
+        column-major N x k layout of the C ABI with ld = N."""
+        assert phi.is_cuda and phi.is_contiguous() and phi.shape[1] == self.N
+        dt = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}[phi.dtype]
+        self._check(_lib.sdf_set_reference_modes(self._h, _ptr(phi), phi.shape[0], self.N, dt))
+        self._phi = phi
+        return self
+
+    def analytic_modes(self, k, dtype=F64):
+        phi = torch.empty((k, self.N), dtype=_TORCH_DTYPE[dtype], device=self.device)
+        ev = np.zeros(k)
+        self._check(_lib.sdf_analytic_modes(self._h, k, _ptr(phi), self.N, dtype,
+                                            ev.ctypes.data, _stream()))
+        return phi, ev
+
+    # workspace --------------------------------------------------------------
+    def workspace(self, batch, opts=None, host_io=False):
+        opts = opts or default_opts()
+        nb = _sz()
+        self._check(_lib.sdf_workspace_size(self._h, batch, ctypes.byref(opts), ctypes.byref(nb)))
+        need = int(nb.value)
+        if host_io:
+            io = _sz()
+            self._check(_lib.sdf_host_io_bytes(self._h, batch, ctypes.byref(io)))
+            need = ((need + 255) // 256) * 256 + int(io.value)
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(need, dtype=torch.uint8, device=self.device)
+        return self._ws
+
+    # solves ---------------------------------------------------------------
+    def solve(self, inst: torch.Tensor, psi: torch.Tensor, opts=None, want_lambda=True,
+              out=None, raise_on_fail=False):
+        """inst: (B, 7) float64 device tensor; psi: (N,) float64 device tensor."""
+        opts = opts or default_opts()
+        B = inst.shape[0]
+        assert inst.dtype == torch.float64 and inst.is_contiguous() and inst.shape[1] == 7
+        ws = self.workspace(B, opts)
+        if out is None:
+            out = dict(y=torch.empty((B, self.N), dtype=torch.float64, device=self.device),
+                       lam=torch.empty((B, self.N), dtype=torch.float64, device=self.device)
+                       if want_lambda else None,
+                       active=torch.empty((B, self.N), dtype=torch.uint8, device=self.device))
+        stats = (Stats * B)()
+        st = _lib.sdf_solve_batch(self._h, _ptr(inst), B, _ptr(psi), ctypes.byref(opts),
+                                  _ptr(ws), ws.numel(), _stream(), _ptr(out["y"]),
+                                  _ptr(out["lam"]), _ptr(out["active"]), stats)
+        if st not in (0, 5, 6, 7, 8) or (raise_on_fail and st != 0):
+            self._check(st)
+        out["status"] = st
+        out["stats"] = [stats_dict(s) for s in stats]
+        return out
+
+    def solve_host(self, inst: np.ndarray, psi: np.ndarray, opts=None, y=None, lam=None,
+                   active=None):
+        """Host-memory variant (sdf_solve_batch_host): numpy in, numpy out."""
+        opts = opts or default_opts()
+        inst = np.ascontiguousarray(inst, dtype=np.float64)
+        psi = np.ascontiguousarray(psi, dtype=np.float64)
+        B = inst.shape[0]
+        ws = self.workspace(B, opts, host_io=True)
+        y = np.empty((B, self.N)) if y is None else y
+        active = np.empty((B, self.N), np.uint8) if active is None else active
+        stats = (Stats * B)()
+        st = _lib.sdf_solve_batch_host(self._h, inst.ctypes.data, B, psi.ctypes.data,
+                                       ctypes.byref(opts), _ptr(ws), ws.numel(), _stream(),
+                                       y.ctypes.data, None if lam is None else lam.ctypes.data,
+                                       active.ctypes.data, stats)
+        if st not in (0, 5, 6, 7, 8):
+            self._check(st)
+        return dict(y=y, lam=lam, active=active, status=st, stats=[stats_dict(s) for s in stats])
+
+    # building blocks --------------------------------------------------------
+    def apply_S(self, inst: torch.Tensor, u: torch.Tensor, active: torch.Tensor = None, mode=0):
+        out = torch.empty_like(u)
+        self._check(_lib.sdf_apply_S(self._h, _ptr(inst), _ptr(active), _ptr(u), _ptr(out), mode,
+                                     None, 0, _stream()))
+        return out
+
+    def project(self, active: torch.Tensor, v: torch.Tensor):
+        k = self._phi.shape[0]
+        out = torch.empty(k, dtype=torch.float64, device=self.device)
+        ws = torch.empty(1 << 20, dtype=torch.uint8, device=self.device)
+        self._check(_lib.sdf_project(self._h, _ptr(active), _ptr(v), _ptr(out), _ptr(ws),
+                                     ws.numel(), _stream()))
+        return out
