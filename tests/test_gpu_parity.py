@@ -3,8 +3,10 @@
 Tolerances (FP64 path): active sets bit-exact; states within relative L2
 error 1e-6 of the oracle (the paper's Eq. accuracy_rel_err metric); matrix-free
 operator applications within 1e-12 relative (flux form vs assembled CSR
-differ only in rounding order); CG iteration counts within +-2 per inner solve
-(reductions are summed in a different order).
+differ only in rounding order); CG iteration counts within max(2, 0.5%) per
+inner solve (the operator and the reductions round in a different order, which
+shifts the recurrence residual's crossing of rtol by a few iterations on solves
+of several hundred iterations).
 """
 import numpy as np
 import pytest
@@ -35,7 +37,7 @@ def inst_row(a, c, b=(0.0, 0.0, 0.0)):
     return [a, *c, *b]
 
 
-def compare_solves(gpu, orc_list, it_tol=2, y_tol=1e-6):
+def compare_solves(gpu, orc_list, it_tol=2, y_tol=1e-6, it_rel=0.005):
     for b, r in enumerate(orc_list):
         st = gpu["stats"][b]
         assert st["status"] == 0 == r["status"], (b, st, r["status"])
@@ -45,7 +47,7 @@ def compare_solves(gpu, orc_list, it_tol=2, y_tol=1e-6):
         assert st["n_active"] == r["n_active"]
         assert st["fallback"] == r["fallback"]
         for ig, io in zip(st["cg_iters"], r["cg_iters"]):
-            assert abs(ig - io) <= it_tol, (b, st["cg_iters"], r["cg_iters"])
+            assert abs(ig - io) <= max(it_tol, it_rel * io), (b, st["cg_iters"], r["cg_iters"])
         y = gpu["y"][b].cpu().numpy()
         assert np.linalg.norm(y - r["y"]) <= y_tol * np.linalg.norm(r["y"]), b
         if gpu.get("lam") is not None:
