@@ -95,6 +95,8 @@ typedef struct {
  *   deflate      1: A-DEF2 with the reference modes, 0: plain Jacobi-PCG [1]
  *   check_every  CG iterations enqueued between two host polls of the
  *                per-instance convergence flags                   [64]
+ *   profile      1: time the first CG iteration of every poll interval with
+ *                CUDA events on the solve's stream (see sdf_get_profile) [0]
  *   max_launches host watchdog: total iteration launches per solve call
  *                before SDF_ERR_TIMEOUT (0 = 4 * max_cg)          [0]        */
 typedef struct {
@@ -105,6 +107,7 @@ typedef struct {
   int32_t max_cg;
   int32_t deflate;
   int32_t check_every;
+  int32_t profile;
   int64_t max_launches;
 } sdf_opts;
 
@@ -203,6 +206,27 @@ sdf_status sdf_apply_S(sdf_problem *p, const double *inst_dev, const uint8_t *ac
  * `active_dev` N bytes (1 = active), v_dev N doubles (device). */
 sdf_status sdf_project(sdf_problem *p, const uint8_t *active_dev, const double *v_dev,
                        double *out_dev, void *ws, size_t ws_bytes, void *stream);
+
+/* Kernel timing and launch counts (tracing).  Kernel ids of sdf_profile:
+ *   0 expand   p = P z + beta p             (coarse GEMV + Phi expansion)
+ *   1 spmv     q = S_II p, (p, q)
+ *   2 update   x, r update, S_II z, Phi_I^T S_II z, (r, z), ||r||
+ *   3 setup    b = rhs_I - S_IA psi_A, Jacobi diagonal
+ *   4 coarse   W = S_II Phi_I, Gram matrices, k x k factorisation
+ *   5 active   active-set update
+ *   6 lambda   multiplier
+ *   7 other
+ * ms[i] / samples[i] is the mean duration of kernel i over the launches timed
+ * with opts.profile = 1; launches counts every kernel the library enqueued
+ * since the last reset (timed or not). */
+#define SDF_NPROF 8
+typedef struct {
+  double ms[SDF_NPROF];
+  int64_t samples[SDF_NPROF];
+  int64_t launches;
+} sdf_profile;
+sdf_status sdf_get_profile(const sdf_problem *p, sdf_profile *out);
+sdf_status sdf_reset_profile(sdf_problem *p);
 
 /* One-line description of the last error on this handle ("" if none). */
 const char *sdf_last_error(const sdf_problem *p);

@@ -1,0 +1,48 @@
+"""Write tests/golden/diff3d_128_oracle.json: full-size oracle solves of the
+first instances of the 128^3 diffusion workload (k = 60 closed-form reference
+modes, rtol 1e-8, psi = 1).  Calls only the oracle; takes tens of minutes per
+instance on a few CPU cores, so it is run once and its output committed.
+
+Usage: python -m oracle.full_size_reference [count]
+"""
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+from oracle import oracle as O  # noqa: E402
+from paper_2606_17971_b300 import workloads as W  # noqa: E402
+
+
+def main(count=2, name="diff3d_128"):
+    w = W.WORKLOADS[name]
+    P = O.Problem(w.dim, w.n, alpha=w.alpha)
+    Phi = O.analytic_modes(w.dim, w.n, w.k, w.alpha)[0]
+    psi = W.psi_vector(w)
+    rng = np.random.default_rng(12345)
+    sample = np.sort(rng.choice(w.N, size=64, replace=False))
+    out_path = os.path.join(ROOT, "tests", "golden", f"{name}_oracle.json")
+    res = {"workload": name, "rtol": 1e-8, "k": w.k, "modes": "closed-form sines (Sec. 2.2.7)",
+           "sample_index": sample.tolist(), "instances": []}
+    for i, ins in enumerate(W.draw_instances(w, count=count)):
+        _, rhs = P.desired_state(ins.a, ins.c[: w.dim], w.sigma)
+        t = time.time()
+        r = P.solve(rhs, psi, Phi, rtol=1e-8, max_cg=200000)
+        res["instances"].append({
+            "index": i, "a": ins.a, "c": list(ins.c), "status": r["status"],
+            "outer_iters": r["outer_iters"], "cg_iters": r["cg_iters"], "n_active": r["n_active"],
+            "y_norm": float(np.linalg.norm(r["y"])), "y_sample": r["y"][sample].tolist(),
+            "active_count": int(r["active"].sum()), "true_relres": r["true_relres"],
+            "seconds": time.time() - t, "threads": os.cpu_count()})
+        with open(out_path, "w") as f:
+            json.dump(res, f, indent=1)
+        print(i, r["cg_iters"], r["n_active"], "%.0fs" % (time.time() - t), flush=True)
+
+
+if __name__ == "__main__":
+    main(int(sys.argv[1]) if len(sys.argv) > 1 else 2)

@@ -867,6 +867,9 @@ struct sdf_problem {
   std::string err;
   int nsm = 148;
   int *pinned = nullptr;  // 2 ints of pinned host memory for polling
+  sdf_profile prof{};
+  cudaEvent_t ev[8] = {};
+  bool ev_ready = false;
 };
 
 namespace {
@@ -977,6 +980,7 @@ sdf_status solve_impl(sdf_problem *p, const double *inst, int B, const double *p
     CK(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s));
     k_outer_setup<DIM><<<gT, NT, 0, s>>>(P, inst, psi, mask, r, x, dinv, st, part, cnt, ctrl, L.gx);
     CKL("k_outer_setup");
+    p->prof.launches += 1;
     if (defl) {
       for (int b = 0; b < B; ++b) {
         k_modes_W<DIM, PhiT><<<dim3(k, L.gx), NT, 0, s>>>(P, inst, b, st, mask, Phi, ld, W, L.gx);
@@ -990,27 +994,51 @@ sdf_status solve_impl(sdf_problem *p, const double *inst, int B, const double *p
       CKL("k_coarse");
       k_project<KMAX, PhiT><<<gA, NT, 0, s>>>(Phi, ld, k, N, mask, r, st, nullptr, part, cnt, L.gxa);
       CKL("k_project");
+      p->prof.launches += 5LL * B + 2;
     }
     // coarse-correction pass, then CG iterations in chunks
     for (int it = 0;; ++it) {
       int nrep = it == 0 ? 1 : chunk;
+      const bool timed = o.profile && p->ev_ready && it > 0;
       for (int rep = 0; rep < nrep; ++rep) {
+        if (timed && rep == 0) CK(cudaEventRecord(p->ev[0], s));
         k_expand<KMAX, PhiT><<<gA, NT, 0, s>>>(Phi, ld, k, N, st, Einv, mask, r, dinv,
                                                P.convection, pp, L.gxa);
+        if (timed && rep == 0) CK(cudaEventRecord(p->ev[1], s));
         k_spmv<DIM><<<gT, NT, 0, s>>>(P, inst, st, mask, pp, q, part, cnt, ctrl, L.gx);
+        if (timed && rep == 0) CK(cudaEventRecord(p->ev[2], s));
         k_update<DIM, KMAX, PhiT><<<gT, NT, 0, s>>>(P, inst, Phi, ld, k, st, mask, r, q, pp, x,
                                                     dinv, part, cnt, ctrl, L.gx, rtol2, o.max_cg);
+        if (timed && rep == 0) CK(cudaEventRecord(p->ev[3], s));
       }
       CKL("cg iteration");
       launches += nrep;
+      p->prof.launches += 3LL * nrep;
       CK(cudaMemcpyAsync(p->pinned, &ctrl->running, sizeof(int), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
+      if (timed) {
+        // only launches that did work count: a poll interval whose first
+        // iteration already found every instance converged is skipped
+        float t0 = 0, t1 = 0, t2 = 0;
+        cudaEventElapsedTime(&t0, p->ev[0], p->ev[1]);
+        cudaEventElapsedTime(&t1, p->ev[1], p->ev[2]);
+        cudaEventElapsedTime(&t2, p->ev[2], p->ev[3]);
+        if (p->pinned[0] > 0 || nrep > 1) {
+          p->prof.ms[0] += t0;
+          p->prof.ms[1] += t1;
+          p->prof.ms[2] += t2;
+          p->prof.samples[0] += 1;
+          p->prof.samples[1] += 1;
+          p->prof.samples[2] += 1;
+        }
+      }
       if (p->pinned[0] <= 0) break;
       if (launches > max_launches)
         return fail(p, SDF_ERR_TIMEOUT, "solve exceeded its iteration launch budget");
     }
     k_active<<<gA, NT, 0, s>>>(N, psi, mask, x, y, st, part, cnt, ctrl, L.gxa, o.tau, o.max_outer);
     CKL("k_active");
+    p->prof.launches += 1;
     CK(cudaMemcpyAsync(p->pinned + 1, &ctrl->live, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     live = p->pinned[1];
@@ -1019,6 +1047,7 @@ sdf_status solve_impl(sdf_problem *p, const double *inst, int B, const double *p
   if (lam) {
     k_lambda<DIM><<<gT, NT, 0, s>>>(P, inst, y, lam, L.gx);
     CKL("k_lambda");
+    p->prof.launches += 1;
   }
   std::vector<InstState> hs(B);
   CK(cudaMemcpyAsync(hs.data(), st, sizeof(InstState) * B, cudaMemcpyDeviceToHost, s));
@@ -1085,6 +1114,7 @@ void sdf_default_opts(sdf_opts *o) {
   o->max_cg = 1000000;
   o->deflate = 1;
   o->check_every = 64;
+  o->profile = 0;
   o->max_launches = 0;
 }
 
@@ -1141,6 +1171,10 @@ sdf_status sdf_problem_create(const sdf_problem_desc *desc, const double *kappa_
     delete p;
     return SDF_ERR_CUDA;
   }
+  p->ev_ready = true;
+  for (int i = 0; i < 8; ++i)
+    if (cudaEventCreate(&p->ev[i]) != cudaSuccess) p->ev_ready = false;
+  cudaGetLastError();
   *out = p;
   return SDF_OK;
 }
@@ -1272,6 +1306,7 @@ sdf_status sdf_analytic_modes(sdf_problem *p, int k, void *phi_dev, int64_t ld, 
       return fail(p, SDF_ERR_INVALID_ARG, "unknown dtype");
   }
   CKL("k_sine_modes");
+  p->prof.launches += 1;
   return SDF_OK;
 }
 
@@ -1380,6 +1415,7 @@ sdf_status sdf_apply_S(sdf_problem *p, const double *inst_dev, const uint8_t *ac
   if (P.dim == 2) k_apply<2><<<GX, NT, 0, s>>>(P, inst_dev, active_dev, u_dev, out_dev, mode, GX);
   else k_apply<3><<<GX, NT, 0, s>>>(P, inst_dev, active_dev, u_dev, out_dev, mode, GX);
   CKL("k_apply");
+  p->prof.launches += 1;
   return SDF_OK;
 }
 
@@ -1407,6 +1443,19 @@ sdf_status sdf_project(sdf_problem *p, const uint8_t *active_dev, const double *
     default: k_project<128, double><<<g, NT, 0, s>>>(Phi, p->ld, p->k, p->P.N, active_dev, v_dev, nullptr, out_dev, part, cnt, GX); break;
   }
   CKL("k_project");
+  p->prof.launches += 1;
+  return SDF_OK;
+}
+
+sdf_status sdf_get_profile(const sdf_problem *p, sdf_profile *out) {
+  if (!p || !out) return SDF_ERR_INVALID_ARG;
+  *out = p->prof;
+  return SDF_OK;
+}
+
+sdf_status sdf_reset_profile(sdf_problem *p) {
+  if (!p) return SDF_ERR_INVALID_ARG;
+  memset(&p->prof, 0, sizeof(p->prof));
   return SDF_OK;
 }
 
@@ -1415,6 +1464,8 @@ const char *sdf_last_error(const sdf_problem *p) { return p ? p->err.c_str() : "
 void sdf_problem_destroy(sdf_problem *p) {
   if (!p) return;
   if (p->pinned) cudaFreeHost(p->pinned);
+  for (int i = 0; i < 8; ++i)
+    if (p->ev[i]) cudaEventDestroy(p->ev[i]);
   delete p;
 }
 

@@ -41,7 +41,16 @@ class Opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("tau", ctypes.c_double), ("tau_cond", ctypes.c_double),
                 ("max_outer", ctypes.c_int32), ("max_cg", ctypes.c_int32),
                 ("deflate", ctypes.c_int32), ("check_every", ctypes.c_int32),
-                ("max_launches", ctypes.c_int64)]
+                ("profile", ctypes.c_int32), ("max_launches", ctypes.c_int64)]
+
+
+SDF_NPROF = 8
+PROFILE_NAMES = ("expand", "spmv", "update", "setup", "coarse", "active", "lambda", "other")
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * SDF_NPROF), ("samples", ctypes.c_int64 * SDF_NPROF),
+                ("launches", ctypes.c_int64)]
 
 
 class Stats(ctypes.Structure):
@@ -70,6 +79,8 @@ _sigs = {
                                     _vp, _vp, _vp]),
     "sdf_apply_S": (_i32, [_vp, _vp, _vp, _vp, _vp, _i32, _vp, _sz, _vp]),
     "sdf_project": (_i32, [_vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "sdf_get_profile": (_i32, [_vp, ctypes.POINTER(Profile)]),
+    "sdf_reset_profile": (_i32, [_vp]),
     "sdf_last_error": (ctypes.c_char_p, [_vp]),
     "sdf_problem_destroy": (None, [_vp]),
 }
@@ -222,6 +233,18 @@ class Problem:
         if st not in (0, 5, 6, 7, 8):
             self._check(st)
         return dict(y=y, lam=lam, active=active, status=st, stats=[stats_dict(s) for s in stats])
+
+    # tracing ----------------------------------------------------------------
+    def profile(self):
+        pr = Profile()
+        self._check(_lib.sdf_get_profile(self._h, ctypes.byref(pr)))
+        mean = {n: (pr.ms[i] / pr.samples[i] if pr.samples[i] else None)
+                for i, n in enumerate(PROFILE_NAMES)}
+        return dict(mean_ms=mean, samples={n: pr.samples[i] for i, n in enumerate(PROFILE_NAMES)},
+                    launches=pr.launches)
+
+    def reset_profile(self):
+        self._check(_lib.sdf_reset_profile(self._h))
 
     # building blocks --------------------------------------------------------
     def apply_S(self, inst: torch.Tensor, u: torch.Tensor, active: torch.Tensor = None, mode=0):
