@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Benchmark: instances/sec to the converged active set at rtol 1e-8.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME] [--path PATH]
+
+One step solves one batch of synthetic instances of the workload (seeded
+inputs from paper_2606_17971_b300.workloads) through the C ABI: the primal
+active-set loop around A-DEF2-deflated Jacobi-PCG until every instance's active
+set is converged.  The timed region is bracketed by a barrier and
+cuda.synchronize on both sides, timed with CUDA events on the solve's stream,
+max over ranks; rank 0 prints one JSON line.  Multi-GPU runs are replicas:
+each rank solves its own instances (the path shards by instance with no
+collective), so scaling is weak.
+
+--impl reference times the CPU oracle (oracle/) on the host cores on a bounded
+sample of the same workload and prints the same line with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "instances/sec to converged active set at rtol 1e-8, batched+learned vs plain"
+UNIT = "instances/s"
+FP64_PEAK_TFLOPS = 1.25  # nominal B300 FP64 of the profiling recipe (probe measured 1.20)
+KSRC = [os.path.join(ROOT, "paper_2606_17971_b300", "csrc", f) for f in ("sdf.cu", "sdf_device.cuh")]
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for f in KSRC:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per dof and per launch (stated in the design doc)
+
+def stencil_flops(dim):
+    # A u in flux form: 2*dim differences + 2*dim FMAs (2 flops); same for A^T w;
+    # mass*u + wgt*A^T w: 3 flops
+    return 2 * (2 * dim + 4 * dim) + 3
+
+
+def kernel_work(name, dim, k, phi_bytes, vec_bytes=8):
+    """(flops, bytes) per dof per launch of the three CG kernels."""
+    if name == "update":   # r,q,p,x,dinv read; x,r written; Phi read; S z; Phi^T S z
+        return 2 * k + stencil_flops(dim) + 9, 7 * vec_bytes + 1 + k * phi_bytes
+    if name == "expand":   # r,dinv,p read; p written; Phi read; Phi c
+        return 2 * k + 4, 4 * vec_bytes + 1 + k * phi_bytes
+    if name == "spmv":     # p read, q written
+        return stencil_flops(dim) + 2, 2 * vec_bytes + 1
+    raise ValueError(name)
+
+
+def profile_traffic(kernel, workload):
+    """DRAM traffic per launch from the committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", f"k_{kernel}_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
+    t = re.search(r"traffic_bytes_per_launch_full_size:\s*([0-9.eE+]+)", txt)
+    if not m or not t or m.group(1) != source_hash():
+        return None
+    return float(t.group(1))
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        load = [v for v in sm if v > 0.5 * (smax or max(sm))] or sm
+        return {"sm_mhz": float(np.median(load)), "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+
+def make_problem(w, sdf, device):
+    from paper_2606_17971_b300 import workloads as W
+    kap = W.kappa_field(w)
+    G = sdf.Problem(w.dim, w.n, alpha=w.alpha, kappa=kap, diff_scale=w.diff_scale,
+                    convection=w.convection, yd_sigma=w.sigma, device=device)
+    phi, _ = G.analytic_modes(w.k)  # closed-form reference modes on the GPU (Sec. 2.2.7)
+    G.set_modes(phi)
+    return G, phi
+
+
+def cpu_sample(w, inst, m_iters=20):
+    """Bounded oracle sample: one restricted A-DEF2 solve at the full size,
+    truncated at m_iters CG iterations; returns (setup seconds, seconds per
+    CG iteration, threads)."""
+    from oracle import oracle as O
+    from paper_2606_17971_b300 import workloads as W
+    P = O.Problem(w.dim, w.n, kappa=W.kappa_field(w), diff_scale=w.diff_scale, alpha=w.alpha)
+    Phi = O.analytic_modes(w.dim, w.n, w.k, w.alpha, diff_scale=w.diff_scale)[0]
+    _, rhs = P.desired_state(inst.a, inst.c[: w.dim], w.sigma)
+    r = P.inner_solve(np.zeros(P.N, np.uint8), rhs, np.full(P.N, w.psi), Phi, maxit=m_iters)
+    return r["t_setup"], r["t_loop"] / max(1, r["iters"]), os.cpu_count()
+
+
+def oracle_counts(name):
+    path = os.path.join(ROOT, "tests", "golden", f"{name}_oracle.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    inst = d.get("instances", [])
+    if not inst:
+        return None
+    return (float(np.mean([i["outer_iters"] for i in inst])),
+            float(np.mean([sum(i["cg_iters"]) for i in inst])))
+
+
+def run_reference(args, w):
+    from paper_2606_17971_b300 import workloads as W
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    counts = oracle_counts(w.name)
+    if counts is None:
+        print(json.dumps({"impl": "reference", "unavailable":
+                          f"no full-size oracle iteration counts for {w.name} (tests/golden)"}))
+        return
+    n_outer, iters = counts
+    insts = W.draw_instances(w, count=args.warmup + args.steps)
+    for i in range(args.warmup):
+        cpu_sample(w, insts[i], 5)
+    per_inst = []
+    t0 = time.time()
+    for i in range(args.steps):
+        ts, ti, cores = cpu_sample(w, insts[args.warmup + i], 10)
+        per_inst.append(n_outer * ts + iters * ti)
+    wall = time.time() - t0
+    val = 1.0 / float(np.mean(per_inst))
+    sample = (f"oracle A-DEF2 at the full {w.n}^{w.dim} size, one restricted solve per step "
+              f"truncated at 10 CG iterations; instances/s = 1/(outer*t_setup + iters*t_iter) "
+              f"with outer={n_outer:.2f}, iters={iters:.0f} from the oracle's own full-size "
+              f"solves (tests/golden/{w.name}_oracle.json)")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": w.name, "path": "CPU oracle (plain C, FP64)"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="diff3d_128")
+    ap.add_argument("--n", type=int, default=0, help="grid override (profiling captures only)")
+    ap.add_argument("--max-cg", type=int, default=0, help="CG cap (profiling captures only)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    from paper_2606_17971_b300 import workloads as W
+    w = W.WORKLOADS[args.workload]
+    if args.n:
+        w = W.scaled(w, args.n)
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    import torch.distributed as dist
+    from paper_2606_17971_b300 import sdf
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    G, phi = make_problem(w, sdf, dev)
+    B = 1
+    steps, warm = args.steps, args.warmup
+    insts = W.draw_instances(w, count=(steps + warm) * B * world)
+    mine = insts[rank::world]
+    inst_t = [torch.as_tensor(W.instances_array(mine[i * B:(i + 1) * B]), device=dev)
+              for i in range(steps + warm)]
+    psi = torch.full((w.N,), w.psi, dtype=torch.float64, device=dev)
+    opts = sdf.default_opts(check_every=128)
+    if args.max_cg:
+        opts.max_cg = args.max_cg
+    out = {"y": torch.empty((B, w.N), dtype=torch.float64, device=dev), "lam": None,
+           "active": torch.empty((B, w.N), dtype=torch.uint8, device=dev)}
+    for i in range(warm):
+        G.solve(inst_t[i], psi, opts, out=out)
+    torch.cuda.synchronize()
+
+    # ---- timed region (device-resident inputs) ----
+    opts.profile = 1
+    G.reset_profile()
+    stats = []
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for i in range(steps):
+            res = G.solve(inst_t[warm + i], psi, opts, out=out)
+            stats.extend(res["stats"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    prof = G.profile()
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    value = steps * B * world / (ms * 1e-3)
+
+    # ---- e2e through the host-memory entry point ----
+    e2e = None
+    if not args.no_e2e:
+        opts.profile = 0
+        inst_h = [torch.from_numpy(W.instances_array(mine[i * B:(i + 1) * B])).pin_memory().numpy()
+                  for i in range(steps + warm)]
+        psi_h = torch.full((w.N,), w.psi, dtype=torch.float64).pin_memory().numpy()
+        y_h = torch.empty((B, w.N), dtype=torch.float64).pin_memory().numpy()
+        a_h = torch.empty((B, w.N), dtype=torch.uint8).pin_memory().numpy()
+        G.solve_host(inst_h[0], psi_h, opts, y=y_h, active=a_h)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(steps):
+            G.solve_host(inst_h[warm + i], psi_h, opts, y=y_h, active=a_h)
+        torch.cuda.synchronize()
+        te = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": steps * B * world / float(te.item()), "unit": UNIT,
+               "h2d_bytes_per_step": int(inst_h[0].nbytes + psi_h.nbytes),
+               "d2h_bytes_per_step": int(y_h.nbytes + a_h.nbytes)}
+
+    # ---- roofline of the dominant kernel ----
+    names = ("expand", "spmv", "update")
+    tot = {n: (prof["mean_ms"][n] or 0.0) * prof["samples"][n] for n in names}
+    dom = max(names, key=lambda n: tot[n])
+    flops_dof, bytes_dof = kernel_work(dom, w.dim, w.k, 8)
+    units = w.N * B
+    mean_s = prof["mean_ms"][dom] * 1e-3
+    achieved = flops_dof * units / mean_s / 1e12
+    hbm = peaks().get("hbm_gbs")
+    roof = {"kernel": f"k_{dom}", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+            "traffic": profile_traffic(dom, w.name),
+            "peak_source": "nominal FP64 of the profiling recipe (1.25 TFLOP/s; probe measured 1.20)",
+            "algorithmic_flops_per_launch": flops_dof * units,
+            "algorithmic_bytes_per_launch": bytes_dof * units,
+            "hbm_gbs_at_algorithmic_bytes": bytes_dof * units / mean_s / 1e9,
+            "hbm_peak_gbs": hbm, "mean_launch_ms": prof["mean_ms"][dom],
+            "timed_launches": prof["samples"][dom],
+            "kernel_mean_ms": {n: prof["mean_ms"][n] for n in names}}
+
+    cg = [sum(s["cg_iters"]) for s in stats]
+    outer = [s["outer_iters"] for s in stats]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+        "warmup": warm, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "grid": [w.n] * w.dim, "k": w.k, "alpha": w.alpha,
+                   "instances_per_step": B * world, "batch_per_gpu": B,
+                   "path": "plain FP64 A-DEF2 per instance (primal active-set loop)",
+                   "modes": "closed-form sines on the GPU (Sec. 2.2.7)",
+                   "l2": "inputs larger than L2: Phi is %.2f GB, read twice per CG iteration"
+                         % (w.N * w.k * 8 / 1e9),
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+        "cg_iters_per_instance": float(np.mean(cg)), "outer_iters_per_instance": float(np.mean(outer)),
+        "statuses": sorted(set(s["status"] for s in stats)),
+        "roofline": roof, "clocks": clk.summary(), "e2e": e2e,
+        "gpu_launches": int(prof["launches"]),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ts, ti, cores = cpu_sample(w, mine[0], 20)
+        per = np.mean(outer) * ts + np.mean(cg) * ti
+        line["cpu_baseline"] = {
+            "value": 1.0 / per, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"oracle A-DEF2 at the full {w.n}^{w.dim} size on instance 0, one restricted "
+                       f"solve truncated at 20 CG iterations (set-up {ts:.2f} s, {ti * 1e3:.1f} ms "
+                       f"per iteration); instances/s = 1/(outer*t_setup + iters*t_iter) with this "
+                       f"run's mean outer={np.mean(outer):.2f}, iters={np.mean(cg):.0f}")}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -105,6 +105,7 @@ def lib():
         _lib.orc_inner_solve.argtypes = [P, up, dp, dp, dp, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                          ctypes.c_double, dp, ip, dp, dp, ip]
+        _lib.orc_last_timing.argtypes = [dp, dp]
         _lib.orc_solve.restype = ctypes.c_int
         _lib.orc_solve.argtypes = [P, dp, dp, dp, ctypes.c_int, ctypes.c_int,
                                    ctypes.POINTER(Opts), dp, dp, dp, up,
@@ -217,8 +218,10 @@ class Problem:
                                    int(bool(deflate and k > 0)), rtol, maxit, tau_cond,
                                    _dp(x), ctypes.byref(it), ctypes.byref(rr),
                                    ctypes.byref(ce), ctypes.byref(fb))
+        ts, tl = ctypes.c_double(0), ctypes.c_double(0)
+        lib().orc_last_timing(ctypes.byref(ts), ctypes.byref(tl))
         return dict(x=x, status=st, iters=it.value, relres=rr.value, cond_E=ce.value,
-                    fallback=fb.value)
+                    fallback=fb.value, t_setup=ts.value, t_loop=tl.value)
 
     def solve(self, rhs, psi, Phi=None, deflate=True, rtol=1e-8, tau=1e-10,
               tau_cond=1e10, max_outer=30, max_cg=100000, rule=0, pdas_c=1.0,

@@ -35,8 +35,10 @@
  * the repository; the ones that change arithmetic are repeated at the
  * function that implements them.
  */
+#define _POSIX_C_SOURCE 199309L
 #include <math.h>
 #include <stdint.h>
+#include <time.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -91,6 +93,15 @@ typedef struct {
 
 /* ------------------------------------------------------------------------ */
 /* small helpers                                                            */
+
+/* wall-clock timing of the inner solve's phases (instrumentation only) */
+static double g_t_loop_start = 0.0, g_t_loop_end = 0.0;
+static double g_last_timing[2] = {0.0, 0.0};
+static double now_s(void) {
+  struct timespec ts;
+  clock_gettime(CLOCK_MONOTONIC, &ts);
+  return ts.tv_sec + 1e-9 * ts.tv_nsec;
+}
 
 static void csr_free(csr_t *m) {
   free(m->rp);
@@ -619,6 +630,7 @@ static int pcg_core(const csr_t *S, const double *b, double *x, double rtol,
   double bn = nrm2(n, b);
   int it = 0, st = ORC_OK;
   double rn = nrm2(n, r);
+  g_t_loop_start = now_s();
   while (rn > rtol * bn) {
     if (it >= maxit) {
       st = ORC_ERR_CG_MAXIT;
@@ -643,6 +655,7 @@ static int pcg_core(const csr_t *S, const double *b, double *x, double rtol,
     rn = nrm2(n, r);
     ++it;
   }
+  g_t_loop_end = now_s();
   *iters = it;
   *relres = bn > 0 ? rn / bn : 0.0;
   free(r);
@@ -758,6 +771,7 @@ static int adef2_core(const csr_t *S, const double *b, double *x,
   double bn = nrm2(n, b);
   double rn = nrm2(n, r);
   int it = 0, st = ORC_OK;
+  g_t_loop_start = now_s();
   while (rn > rtol * bn) {
     if (it >= maxit) {
       st = ORC_ERR_CG_MAXIT;
@@ -790,6 +804,7 @@ static int adef2_core(const csr_t *S, const double *b, double *x,
     rn = nrm2(n, r);
     ++it;
   }
+  g_t_loop_end = now_s();
   *iters = it;
   *relres = bn > 0 ? rn / bn : 0.0;
   free(SZ);
@@ -844,6 +859,8 @@ int orc_inner_solve(void *h, const unsigned char *active, const double *rhs,
                     double *x, int *iters, double *relres, double *condE,
                     int *fallback) {
   orc_problem *P = (orc_problem *)h;
+  double t_begin = now_s();
+  g_t_loop_start = g_t_loop_end = 0.0;
   int N = P->N;
   restr_t R;
   memset(&R, 0, sizeof(R));
@@ -880,7 +897,22 @@ int orc_inner_solve(void *h, const unsigned char *active, const double *rhs,
   free(b);
   free(xi);
   restrict_free(&R);
+  double t_end = now_s();
+  if (g_t_loop_end > g_t_loop_start && g_t_loop_start > 0.0) {
+    g_last_timing[1] = g_t_loop_end - g_t_loop_start;
+    g_last_timing[0] = (t_end - t_begin) - g_last_timing[1];
+  } else {
+    g_last_timing[1] = 0.0;
+    g_last_timing[0] = t_end - t_begin;
+  }
   return st;
+}
+
+/* Seconds spent by the last orc_inner_solve outside its CG loop (restriction,
+ * QR, E, guard, coarse start) and inside it. */
+void orc_last_timing(double *setup_s, double *loop_s) {
+  *setup_s = g_last_timing[0];
+  *loop_s = g_last_timing[1];
 }
 
 /* ------------------------------------------------------------------------ */
