@@ -97,6 +97,8 @@ typedef struct {
  *                per-instance convergence flags                   [64]
  *   profile      1: time the first CG iteration of every poll interval with
  *                CUDA events on the solve's stream (see sdf_get_profile) [0]
+ *   max_blocks   cap on the blocks per instance of the grid-stride kernels
+ *                (0 = automatic: about two blocks per SM in total)  [0]
  *   max_launches host watchdog: total iteration launches per solve call
  *                before SDF_ERR_TIMEOUT (0 = 4 * max_cg)          [0]        */
 typedef struct {
@@ -108,6 +110,7 @@ typedef struct {
   int32_t deflate;
   int32_t check_every;
   int32_t profile;
+  int32_t max_blocks;
   int64_t max_launches;
 } sdf_opts;
 

@@ -54,7 +54,7 @@ struct InstState {
   int32_t deflate;     // A-DEF2 in force for the current inner solve
   int32_t outer;       // index of the current inner solve
   int32_t changes;     // active-set changes of the last update
-  int32_t pad;
+  int32_t empty_I;     // every node active: nothing to solve
   double t[SDF_MAX_K]; // reduced projection Phi_I^T v
   sdf_stats stats;
 };
@@ -68,7 +68,7 @@ struct Ctrl {       // grid-wide control words (device)
 };
 
 struct Layout {
-  size_t x, r, p, q, dinv, mask, W, Einv, Eraw, G, coarse, part, gpart, state, cnt, ctrl, total;
+  size_t x, r, r2, p, q, dinv, mask, W, Einv, Eraw, G, coarse, part, gpart, state, cnt, ctrl, total;
   int gx, gxa, gxg;
 };
 
@@ -197,6 +197,7 @@ __global__ void __launch_bounds__(NT) k_outer_setup(OpParams P, const double *in
     cnt[b * NCNT + CNT_SETUP] = 0;
     S.bnorm2 = tot[0];
     S.stats.n_active[S.outer] = (int)tot[1];
+    S.empty_I = tot[1] >= (double)N ? 1 : 0;
     S.phase = 1;
     S.cg_done = 0;
     S.iters = 0;
@@ -418,6 +419,14 @@ __global__ void __launch_bounds__(NT) k_coarse(int k, InstState *st, const doubl
   double *Lg = wk + (size_t)b * 5 * kk, *Lgi = Lg + kk, *T = Lgi + kk, *E = T + kk, *Lei = E + kk;
   const double *Gb = G + (size_t)b * kk, *Eb = Eraw + (size_t)b * kk;
   double *Ei = Einv + (size_t)b * kk;
+  if (S.empty_I) {  // n_I = 0: nothing to solve, no guard decision (as the oracle)
+    if (threadIdx.x == 0) {
+      S.deflate = 0;
+      S.stats.cond_E[S.outer] = 0.0;
+      S.stats.fallback[S.outer] = 0;
+    }
+    return;
+  }
   for (size_t e = threadIdx.x; e < kk; e += NT) Lg[e] = Gb[e];
   __syncthreads();
   bool good = dev_cholesky(Lg, k, red, &ok, 1e-14);  // rank test: R_jj^2 <= 1e-14 max R^2
@@ -620,14 +629,17 @@ __global__ void __launch_bounds__(NT) k_spmv(OpParams P, const double *inst, Ins
 
 // Kernel C: x += alpha p, r -= alpha q, z = D^-1 r, v = S_II z,
 // t = Phi_I^T v, rho = (r, z), ||r||^2; the last block tests convergence
-// (App. B.2) and prepares beta for kernel A.
+// (App. B.2) and prepares beta for kernel A.  r is read (with its halo) from
+// r_in and written to r_out: blocks read neighbouring tiles' r while other
+// blocks update theirs, so the update cannot be in place.
 template <int DIM, int KMAX, class PhiT>
 __global__ void __launch_bounds__(NT) k_update(OpParams P, const double *inst, const PhiT *Phi,
                                                long long ld, int k, InstState *st,
-                                               const uint8_t *mask, double *r, const double *q,
-                                               const double *p, double *x, const double *dinv,
-                                               double *part, int *cnt, Ctrl *ctrl, int GX,
-                                               double rtol2, int max_cg) {
+                                               const uint8_t *mask, const double *r_in,
+                                               double *r_out, const double *q, const double *p,
+                                               double *x, const double *dinv, double *part,
+                                               int *cnt, Ctrl *ctrl, int GX, double rtol2,
+                                               int max_cg) {
   __shared__ TileSmem<DIM> sm;
   __shared__ double red[NWARP];
   __shared__ double scratch[NT];
@@ -643,7 +655,8 @@ __global__ void __launch_bounds__(NT) k_update(OpParams P, const double *inst, c
   double cb[3];
   inst_cb(P, inst + 7 * b, cb);
   const uint8_t *mk = mask + b * N;
-  double *rb = r + b * N, *xb = x + b * N;
+  const double *rb = r_in + b * N;
+  double *rw = r_out + b * N, *xb = x + b * N;
   const double *qb = q + b * N, *pb = p + b * N;
   const double *db = dinv + (P.convection ? b * N : 0);
   double rho = 0.0, rr = 0.0;
@@ -662,12 +675,13 @@ __global__ void __launch_bounds__(NT) k_update(OpParams P, const double *inst, c
         [&](int e, int, int, int, long long g, double su) {
           if (mk[g]) {
             sm.v[e] = 0.0;
+            rw[g] = 0.0;
             return;
           }
           double rn = rb[g] - alpha * qb[g];
           double z = db[g] * rn;
           xb[g] = xb[g] + alpha * pb[g];
-          rb[g] = rn;
+          rw[g] = rn;
           rho = fma(rn, z, rho);
           rr = fma(rn, rn, rr);
           sm.v[e] = su;
@@ -897,7 +911,7 @@ sdf_status cuda_check(sdf_problem *p, cudaError_t e, const char *what) {
 
 int kmax_for(int k) { return k <= 16 ? 16 : k <= 32 ? 32 : k <= 64 ? 64 : 128; }
 
-Layout make_layout(const sdf_problem *p, int B) {
+Layout make_layout(const sdf_problem *p, int B, int max_blocks = 0) {
   Layout L{};
   const long long N = p->P.N;
   const int k = std::max(p->k, 1), KM = kmax_for(k);
@@ -908,6 +922,10 @@ Layout make_layout(const sdf_problem *p, int B) {
   long long chunks = (N + NT - 1) / NT;
   L.gxa = (int)std::max<long long>(1, std::min<long long>(chunks, (p->nsm * 8LL + B - 1) / B));
   L.gxg = (int)std::max<long long>(1, std::min<long long>((N + 15) / 16, p->nsm * 2LL));
+  if (max_blocks > 0) {
+    L.gx = std::min(L.gx, max_blocks);
+    L.gxa = std::min(L.gxa, max_blocks);
+  }
   size_t o = 0;
   auto take = [&](size_t bytes) {
     size_t at = o;
@@ -917,6 +935,7 @@ Layout make_layout(const sdf_problem *p, int B) {
   size_t vec = sizeof(double) * (size_t)N * B;
   L.x = take(vec);
   L.r = take(vec);
+  L.r2 = take(vec);
   L.p = take(vec);
   L.q = take(vec);
   L.dinv = take(p->d.convection ? vec : 8);
@@ -947,11 +966,12 @@ template <int DIM, int KMAX, class PhiT>
 sdf_status solve_impl(sdf_problem *p, const double *inst, int B, const double *psi,
                       const sdf_opts &o, char *ws, cudaStream_t s, double *y, double *lam,
                       uint8_t *active, sdf_stats *stats) {
-  const Layout L = make_layout(p, B);
+  const Layout L = make_layout(p, B, o.max_blocks);
   const OpParams &P = p->P;
   const long long N = P.N;
-  double *x = (double *)(ws + L.x), *r = (double *)(ws + L.r), *pp = (double *)(ws + L.p),
-         *q = (double *)(ws + L.q);
+  double *x = (double *)(ws + L.x), *pp = (double *)(ws + L.p), *q = (double *)(ws + L.q);
+  double *rbuf[2] = {(double *)(ws + L.r), (double *)(ws + L.r2)};
+  double *r = rbuf[0];
   double *dinv = P.convection ? (double *)(ws + L.dinv) : p->dinv_shared;
   uint8_t *mask = (uint8_t *)(ws + L.mask);
   double *W = (double *)(ws + L.W), *Einv = (double *)(ws + L.Einv), *Eraw = (double *)(ws + L.Eraw),
@@ -996,19 +1016,24 @@ sdf_status solve_impl(sdf_problem *p, const double *inst, int B, const double *p
       CKL("k_project");
       p->prof.launches += 5LL * B + 2;
     }
-    // coarse-correction pass, then CG iterations in chunks
+    // coarse-correction pass, then CG iterations in chunks; r ping-pongs
+    // between the two buffers (uniform across the batch: finished instances
+    // skip every launch)
+    int par = 0;
     for (int it = 0;; ++it) {
       int nrep = it == 0 ? 1 : chunk;
       const bool timed = o.profile && p->ev_ready && it > 0;
       for (int rep = 0; rep < nrep; ++rep) {
         if (timed && rep == 0) CK(cudaEventRecord(p->ev[0], s));
-        k_expand<KMAX, PhiT><<<gA, NT, 0, s>>>(Phi, ld, k, N, st, Einv, mask, r, dinv,
+        k_expand<KMAX, PhiT><<<gA, NT, 0, s>>>(Phi, ld, k, N, st, Einv, mask, rbuf[par], dinv,
                                                P.convection, pp, L.gxa);
         if (timed && rep == 0) CK(cudaEventRecord(p->ev[1], s));
         k_spmv<DIM><<<gT, NT, 0, s>>>(P, inst, st, mask, pp, q, part, cnt, ctrl, L.gx);
         if (timed && rep == 0) CK(cudaEventRecord(p->ev[2], s));
-        k_update<DIM, KMAX, PhiT><<<gT, NT, 0, s>>>(P, inst, Phi, ld, k, st, mask, r, q, pp, x,
-                                                    dinv, part, cnt, ctrl, L.gx, rtol2, o.max_cg);
+        k_update<DIM, KMAX, PhiT><<<gT, NT, 0, s>>>(P, inst, Phi, ld, k, st, mask, rbuf[par],
+                                                    rbuf[par ^ 1], q, pp, x, dinv, part, cnt,
+                                                    ctrl, L.gx, rtol2, o.max_cg);
+        par ^= 1;
         if (timed && rep == 0) CK(cudaEventRecord(p->ev[3], s));
       }
       CKL("cg iteration");
@@ -1115,6 +1140,7 @@ void sdf_default_opts(sdf_opts *o) {
   o->deflate = 1;
   o->check_every = 64;
   o->profile = 0;
+  o->max_blocks = 0;
   o->max_launches = 0;
 }
 
@@ -1333,7 +1359,8 @@ static sdf_status check_solve_args(sdf_problem *p, int batch, const sdf_opts *op
   if (!opts) return fail(p, SDF_ERR_INVALID_ARG, "opts is NULL");
   if (opts->max_outer < 1 || opts->max_outer > SDF_MAX_OUTER)
     return fail(p, SDF_ERR_INVALID_ARG, "max_outer must be in [1, SDF_MAX_OUTER]");
-  if (opts->max_cg < 0 || !(opts->rtol >= 0)) return fail(p, SDF_ERR_INVALID_ARG, "bad opts");
+  if (opts->max_cg < 0 || !(opts->rtol >= 0) || opts->max_blocks < 0)
+    return fail(p, SDF_ERR_INVALID_ARG, "bad opts");
   if (!ws || !aligned(ws, 256))
     return fail(p, SDF_ERR_INVALID_ARG, "workspace must be a 256-byte aligned device pointer");
   size_t need = make_layout(p, batch).total;

@@ -41,7 +41,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("tau", ctypes.c_double), ("tau_cond", ctypes.c_double),
                 ("max_outer", ctypes.c_int32), ("max_cg", ctypes.c_int32),
                 ("deflate", ctypes.c_int32), ("check_every", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("max_launches", ctypes.c_int64)]
+                ("profile", ctypes.c_int32), ("max_blocks", ctypes.c_int32),
+                ("max_launches", ctypes.c_int64)]
 
 
 SDF_NPROF = 8

@@ -114,8 +114,8 @@ def _orc_solves(P, rhs_list, psi, Phi, deflate=True, **kw):
     return [P.solve(rhs, psi, Phi, deflate=deflate, **kw) for rhs in rhs_list]
 
 
-@pytest.mark.parametrize("deflate", [True, False])
-def test_32x32_workload_matches_oracle(deflate):
+@pytest.mark.parametrize("deflate,max_blocks", [(True, 0), (False, 0), (True, 2), (False, 3)])
+def test_32x32_workload_matches_oracle(deflate, max_blocks):
     w = W.WORKLOADS["diff2d_32"]
     P = O.Problem(2, w.n, alpha=w.alpha)
     Phi = O.dense_modes(P, w.k)[0]
@@ -125,13 +125,15 @@ def test_32x32_workload_matches_oracle(deflate):
     orc = _orc_solves(P, rhs, psi, Phi, deflate=deflate)
     G = sdf.Problem(2, w.n, alpha=w.alpha, yd_sigma=w.sigma)
     G.set_modes(modes_tensor(Phi))
-    out = G.solve(t64(W.instances_array(insts)), t64(psi), sdf.default_opts(deflate=int(deflate)))
+    out = G.solve(t64(W.instances_array(insts)), t64(psi),
+                  sdf.default_opts(deflate=int(deflate), max_blocks=max_blocks))
     assert out["status"] == 0
     compare_solves(out, orc)
     assert sum(a.any() for a in out["active"].cpu().numpy()) >= 3
 
 
-def test_ragged_multitile_block_kappa_batch():
+@pytest.mark.parametrize("max_blocks", [0, 1, 5])
+def test_ragged_multitile_block_kappa_batch(max_blocks):
     w = W.scaled(W.WORKLOADS["block2d_1024"], 70)
     n = (70, 45)  # 2 x 6 tiles of 64 x 8, ragged in both directions
     kap = np.ascontiguousarray(W.kappa_field(w).reshape(70, 70)[:45, :]).ravel()
@@ -144,7 +146,7 @@ def test_ragged_multitile_block_kappa_batch():
     orc = _orc_solves(P, rhs, psi, Phi)
     G = sdf.Problem(2, n, alpha=w.alpha, kappa=kap, yd_sigma=w.sigma)
     G.set_modes(modes_tensor(Phi))
-    out = G.solve(t64(W.instances_array(insts)), t64(psi))
+    out = G.solve(t64(W.instances_array(insts)), t64(psi), sdf.default_opts(max_blocks=max_blocks))
     compare_solves(out, orc)
     assert out["active"][0].any()
 
@@ -161,12 +163,13 @@ def test_convection_batch_of_different_velocities():
     G = sdf.Problem(2, 48, alpha=w.alpha, diff_scale=w.diff_scale, convection=True,
                     yd_sigma=w.sigma)
     G.set_modes(modes_tensor(Phi))
-    out = G.solve(t64(W.instances_array(insts)), t64(psi))
+    out = G.solve(t64(W.instances_array(insts)), t64(psi), sdf.default_opts(max_blocks=2))
     compare_solves(out, orc)
     assert any(a.any() for a in out["active"].cpu().numpy())
 
 
-def test_3d_batch_matches_oracle():
+@pytest.mark.parametrize("max_blocks", [0, 2])
+def test_3d_batch_matches_oracle(max_blocks):
     n = (14, 12, 10)
     P = O.Problem(3, n, alpha=1e-4)
     Phi = O.dense_modes(P, 10)[0]
@@ -177,7 +180,7 @@ def test_3d_batch_matches_oracle():
     orc = _orc_solves(P, [P.desired_state(i.a, i.c, w.sigma)[1] for i in insts], psi, Phi)
     G = sdf.Problem(3, n, alpha=1e-4, yd_sigma=w.sigma)
     G.set_modes(modes_tensor(Phi))
-    out = G.solve(t64(W.instances_array(insts)), t64(psi))
+    out = G.solve(t64(W.instances_array(insts)), t64(psi), sdf.default_opts(max_blocks=max_blocks))
     compare_solves(out, orc)
 
 
