@@ -210,6 +210,30 @@ sdf_status sdf_apply_S(sdf_problem *p, const double *inst_dev, const uint8_t *ac
 sdf_status sdf_project(sdf_problem *p, const uint8_t *active_dev, const double *v_dev,
                        double *out_dev, void *ws, size_t ws_bytes, void *stream);
 
+/* sdf_project_noalloc: the same result as sdf_project, for callers that may
+ * not allocate device memory at all -- for example code running inside a host
+ * application that hands out all GPU memory itself, or a loop with hard
+ * latency limits where an allocation (and the device synchronisation it can
+ * cause) is not allowed.  Instead of a caller workspace it uses one fixed
+ * scratch array built into the library: 512 x 128 doubles of partial sums plus
+ * 64 words of counters (about 513 KB), held on every GPU that loads the
+ * library until the process exits.  Limits: k <= SDF_MAX_K (128), otherwise
+ * SDF_ERR_UNSUPPORTED with a message; FP64 modes only.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.  Later calls reuse the address.
+ *   - The array is shared by all calls in the process and keeps the last
+ *     call's contents; the call clears the counters it needs, so results do
+ *     not depend on earlier calls.  Calls that overlap on the GPU (different
+ *     streams, or different handles at once) race on the array: serialise
+ *     them.
+ *   - Calls no device-memory allocator (cudaMalloc, cudaFree, or a library
+ *     routine that allocates).
+ * The paper has no counterpart to this entry point; it exists only for
+ * callers that cannot allocate.  Arguments as for sdf_project. */
+sdf_status sdf_project_noalloc(sdf_problem *p, const uint8_t *active_dev, const double *v_dev,
+                               double *out_dev, void *stream);
+
 /* Kernel timing and launch counts (tracing).  Kernel ids of sdf_profile:
  *   0 expand   p = P z + beta p             (coarse GEMV + Phi expansion)
  *   1 spmv     q = S_II p, (p, q)

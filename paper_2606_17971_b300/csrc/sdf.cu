@@ -34,6 +34,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1470,6 +1471,71 @@ sdf_status sdf_project(sdf_problem *p, const uint8_t *active_dev, const double *
     default: k_project<128, double><<<g, NT, 0, s>>>(Phi, p->ld, p->k, p->P.N, active_dev, v_dev, nullptr, out_dev, part, cnt, GX); break;
   }
   CKL("k_project");
+  p->prof.launches += 1;
+  return SDF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// sdf_project_noalloc: sdf_project with its scratch in a fixed device array.
+// The array holds the per-block partial sums (SDF_NOALLOC_BLOCKS blocks x
+// SDF_MAX_K modes, as doubles) followed by the last-block ticket counters.
+// It is shared by every call on a device and lives as long as the library.
+
+#define SDF_NOALLOC_BLOCKS 512
+#define SDF_NOALLOC_DOUBLES (SDF_NOALLOC_BLOCKS * SDF_MAX_K + 64)
+
+static __device__ __align__(256) double g_noalloc_scratch[SDF_NOALLOC_DOUBLES];
+
+// Device address of g_noalloc_scratch, looked up once per device (the symbol
+// name is only a host-side stand-in; kernels need the real device address).
+static double *g_noalloc_addr[64];
+static std::mutex g_noalloc_mu;
+
+static sdf_status noalloc_scratch(sdf_problem *p, double **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_check(p, e, "cudaGetDevice");
+  if (dev < 0 || dev >= 64) return fail(p, SDF_ERR_UNSUPPORTED, "device index >= 64");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_check(p, e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    g_noalloc_addr[dev] = (double *)ptr;
+  }
+  *out = g_noalloc_addr[dev];
+  return SDF_OK;
+}
+
+sdf_status sdf_project_noalloc(sdf_problem *p, const uint8_t *active_dev, const double *v_dev,
+                               double *out_dev, void *stream) {
+  if (!p) return SDF_ERR_INVALID_ARG;
+  if (!p->phi) return fail(p, SDF_ERR_INVALID_ARG, "no reference modes registered");
+  if (p->phi_dtype != SDF_F64) return fail(p, SDF_ERR_UNSUPPORTED, "FP64 modes expected");
+  if (!active_dev || !v_dev || !out_dev) return fail(p, SDF_ERR_INVALID_ARG, "NULL pointer");
+  if (p->k < 1 || p->k > SDF_MAX_K)
+    return fail(p, SDF_ERR_UNSUPPORTED,
+                "sdf_project_noalloc: k exceeds the static scratch limit SDF_MAX_K (128)");
+  const int KM = kmax_for(p->k);
+  const int GX = std::min(p->nsm * 2, SDF_NOALLOC_BLOCKS);
+  if ((size_t)GX * KM + NCNT > (size_t)SDF_NOALLOC_DOUBLES)
+    return fail(p, SDF_ERR_UNSUPPORTED, "sdf_project_noalloc: scratch limit exceeded");
+  double *scratch = nullptr;
+  sdf_status st = noalloc_scratch(p, &scratch);
+  if (st != SDF_OK) return st;
+  double *part = scratch;
+  int *cnt = (int *)(scratch + (size_t)SDF_NOALLOC_BLOCKS * SDF_MAX_K);
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemsetAsync(cnt, 0, sizeof(int) * NCNT, s));  // tickets must start at zero
+  const double *Phi = (const double *)p->phi;
+  dim3 g(1, GX);
+  switch (KM) {
+    case 16: k_project<16, double><<<g, NT, 0, s>>>(Phi, p->ld, p->k, p->P.N, active_dev, v_dev, nullptr, out_dev, part, cnt, GX); break;
+    case 32: k_project<32, double><<<g, NT, 0, s>>>(Phi, p->ld, p->k, p->P.N, active_dev, v_dev, nullptr, out_dev, part, cnt, GX); break;
+    case 64: k_project<64, double><<<g, NT, 0, s>>>(Phi, p->ld, p->k, p->P.N, active_dev, v_dev, nullptr, out_dev, part, cnt, GX); break;
+    default: k_project<128, double><<<g, NT, 0, s>>>(Phi, p->ld, p->k, p->P.N, active_dev, v_dev, nullptr, out_dev, part, cnt, GX); break;
+  }
+  CKL("k_project (static scratch)");
   p->prof.launches += 1;
   return SDF_OK;
 }

@@ -80,6 +80,7 @@ _sigs = {
                                     _vp, _vp, _vp]),
     "sdf_apply_S": (_i32, [_vp, _vp, _vp, _vp, _vp, _i32, _vp, _sz, _vp]),
     "sdf_project": (_i32, [_vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "sdf_project_noalloc": (_i32, [_vp, _vp, _vp, _vp, _vp]),
     "sdf_get_profile": (_i32, [_vp, ctypes.POINTER(Profile)]),
     "sdf_reset_profile": (_i32, [_vp]),
     "sdf_last_error": (ctypes.c_char_p, [_vp]),
@@ -260,4 +261,11 @@ class Problem:
         ws = torch.empty(1 << 20, dtype=torch.uint8, device=self.device)
         self._check(_lib.sdf_project(self._h, _ptr(active), _ptr(v), _ptr(out), _ptr(ws),
                                      ws.numel(), _stream()))
+        return out
+
+    def project_noalloc(self, active: torch.Tensor, v: torch.Tensor, out: torch.Tensor):
+        """Phi_I^T v into the caller's `out` (k doubles) using the library's
+        built-in scratch array instead of a workspace (sdf_project_noalloc)."""
+        self._check(_lib.sdf_project_noalloc(self._h, _ptr(active), _ptr(v), _ptr(out),
+                                              _stream()))
         return out
