@@ -55,6 +55,17 @@ typedef enum {
 
 typedef enum { SDF_F64 = 0, SDF_F32 = 1, SDF_BF16 = 2 } sdf_dtype;
 
+/* Arithmetic of the inner solve.
+ *   SDF_PREC_F64    every vector, stencil and projection in FP64 (FP64 modes).
+ *   SDF_PREC_MIXED  CG vectors, stencil and projections in FP32 with FP32 or
+ *                   BF16 modes; the iterate x, the right-hand side, every dot
+ *                   product and reduction, the k x k coarse operator and its
+ *                   set-up stay FP64, and every `replace_every` iterations
+ *                   the residual is recomputed as b - S_II x with the FP64
+ *                   stencil and the coarse correction x += Q r is applied;
+ *                   convergence is declared only on that FP64 residual. */
+typedef enum { SDF_PREC_F64 = 0, SDF_PREC_MIXED = 1 } sdf_precision;
+
 /* Maximum deflation rank and outer iterations recorded per instance. */
 #define SDF_MAX_K 128
 #define SDF_MAX_OUTER 32
@@ -99,6 +110,9 @@ typedef struct {
  *                CUDA events on the solve's stream (see sdf_get_profile) [0]
  *   max_blocks   cap on the blocks per instance of the grid-stride kernels
  *                (0 = automatic: about two blocks per SM in total)  [0]
+ *   precision    sdf_precision of the inner solve                 [SDF_PREC_F64]
+ *   replace_every mixed path: CG iterations between FP64 residual
+ *                replacements (0 = 100)                           [100]
  *   max_launches host watchdog: total iteration launches per solve call
  *                before SDF_ERR_TIMEOUT (0 = 4 * max_cg)          [0]        */
 typedef struct {
@@ -111,6 +125,8 @@ typedef struct {
   int32_t check_every;
   int32_t profile;
   int32_t max_blocks;
+  int32_t precision;
+  int32_t replace_every;
   int64_t max_launches;
 } sdf_opts;
 
@@ -146,7 +162,8 @@ sdf_status sdf_problem_bind(sdf_problem *p, void *dev_buf, size_t bytes, void *s
 
 /* Register the reference modes Phi (Sec. 2.2.2 Eq. eig): device pointer to an
  * N x k column-major array (mode j at Phi + j*ld elements), ld >= N,
- * 1 <= k <= SDF_MAX_K, of type `dtype` (SDF_F64 for the FP64 path).  The
+ * 1 <= k <= SDF_MAX_K, of type `dtype` (SDF_F64 for the FP64 path, SDF_F32 or
+ * SDF_BF16 for the mixed path).  The
  * library keeps the pointer, not a copy; the caller keeps the memory alive and
  * unchanged while solves use it.  The base address must be 16-byte aligned. */
 sdf_status sdf_set_reference_modes(sdf_problem *p, const void *phi_dev, int k, int64_t ld,
@@ -242,7 +259,7 @@ sdf_status sdf_project_noalloc(sdf_problem *p, const uint8_t *active_dev, const 
  *   4 coarse   W = S_II Phi_I, Gram matrices, k x k factorisation
  *   5 active   active-set update
  *   6 lambda   multiplier
- *   7 other
+ *   7 resid    mixed path: FP64 residual replacement
  * ms[i] / samples[i] is the mean duration of kernel i over the launches timed
  * with opts.profile = 1; launches counts every kernel the library enqueued
  * since the last reset (timed or not). */

@@ -56,6 +56,8 @@ struct InstState {
   int32_t outer;       // index of the current inner solve
   int32_t changes;     // active-set changes of the last update
   int32_t empty_I;     // every node active: nothing to solve
+  int32_t await;       // mixed path: recurrence residual met rtol, waiting for the FP64 check
+  int32_t pad2;
   double t[SDF_MAX_K]; // reduced projection Phi_I^T v
   sdf_stats stats;
 };
@@ -69,7 +71,8 @@ struct Ctrl {       // grid-wide control words (device)
 };
 
 struct Layout {
-  size_t x, r, r2, p, q, dinv, mask, W, Einv, Eraw, G, coarse, part, gpart, state, cnt, ctrl, total;
+  size_t x, b64, r, r2, p, q, w, dinv, mask, W, Einv, Eraw, G, coarse, part, gpart, state, cnt,
+      ctrl, total;
   int gx, gxa, gxg;
 };
 
@@ -131,14 +134,16 @@ __global__ void k_faces(OpParams P, const double *kappa, double diff_scale, doub
 }
 
 template <int DIM>
-__global__ void k_diag_shared(OpParams P, double *dinv) {
+__global__ void k_diag_shared(OpParams P, double *dinv, float *dinv32) {
   double cb[3] = {0, 0, 0};
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < P.N;
        g += (long long)gridDim.x * blockDim.x) {
     int i = (int)(g % P.nx);
     long long t = g / P.nx;
     int j = (int)(t % P.ny), l = (int)(t / P.ny);
-    dinv[g] = 1.0 / diag_S<DIM>(P, cb, i, j, l);
+    double d = 1.0 / diag_S<DIM>(P, cb, i, j, l);
+    dinv[g] = d;
+    dinv32[g] = (float)d;
   }
 }
 
@@ -146,13 +151,13 @@ __global__ void k_diag_shared(OpParams P, double *dinv) {
 // Outer-iteration set-up (App. B.1 lines 3-5): r = b = rhs_I - S_IA psi_A,
 // x = 0, per-instance Jacobi diagonal (convection), ||b||^2, |A|.
 
-template <int DIM>
+template <int DIM, class V>
 __global__ void __launch_bounds__(NT) k_outer_setup(OpParams P, const double *inst,
                                                     const double *psi, const uint8_t *mask,
-                                                    double *r, double *x, double *dinv,
+                                                    V *r, double *b64, double *x, V *dinv,
                                                     InstState *st, double *part, int *cnt,
                                                     Ctrl *ctrl, int GX) {
-  __shared__ TileSmem<DIM> sm;
+  __shared__ TileSmem<DIM, double> sm;
   __shared__ double red[NWARP];
   __shared__ double tot[2];
   __shared__ int flag;
@@ -164,23 +169,25 @@ __global__ void __launch_bounds__(NT) k_outer_setup(OpParams P, const double *in
   double cb[3];
   inst_cb(P, ib, cb);
   const uint8_t *mk = mask + b * N;
-  double *rb = r + b * N, *xb = x + b * N;
-  double *db = P.convection ? dinv + b * N : nullptr;
+  V *rb = r + b * N;
+  double *bb64 = b64 + b * N, *xb = x + b * N;
+  V *db = P.convection ? dinv + b * N : nullptr;
   double bb = 0.0, na = 0.0;
   const long long T = num_tiles<DIM>(P.nx, P.ny, P.nz);
   for (long long t = gblk; t < T; t += GX) {
     int ox, oy, oz;
     tile_origin<DIM>(P, t, ox, oy, oz);
-    tile_S<DIM>(
+    tile_S<DIM, double>(
         P, cb, ox, oy, oz, sm,
         [&](int, int, int, long long g) { return mk[g] ? psi[g] : 0.0; },
         [&](int, int gx, int gy, int gz, long long g, double su) {
           bool act = mk[g] != 0;
           double rhs = P.mass * desired(P, ib, gx, gy, gz);
           double bv = act ? 0.0 : rhs - su;
-          rb[g] = bv;
+          bb64[g] = bv;
+          rb[g] = (V)bv;
           xb[g] = 0.0;
-          if (db) db[g] = act ? 0.0 : 1.0 / diag_S<DIM>(P, cb, gx, gy, gz);
+          if (db) db[g] = act ? (V)0 : (V)(1.0 / diag_S<DIM>(P, cb, gx, gy, gz));
           bb += bv * bv;
           na += act ? 1.0 : 0.0;
         });
@@ -201,6 +208,7 @@ __global__ void __launch_bounds__(NT) k_outer_setup(OpParams P, const double *in
     S.empty_I = tot[1] >= (double)N ? 1 : 0;
     S.phase = 1;
     S.cg_done = 0;
+    S.await = 0;
     S.iters = 0;
     S.gamma = 0.0;
     S.beta = 0.0;
@@ -471,12 +479,12 @@ __global__ void __launch_bounds__(NT) k_coarse(int k, InstState *st, const doubl
 // ---------------------------------------------------------------------------
 // Projection t = Phi_I^T v (initial coarse correction and sdf_project).
 
-template <int KMAX, class PhiT>
+template <int KMAX, class PhiT, class V>
 __global__ void __launch_bounds__(NT) k_project(const PhiT *Phi, long long ld, int k, long long N,
-                                                const uint8_t *mask, const double *v,
+                                                const uint8_t *mask, const V *v,
                                                 InstState *st, double *out, double *part,
                                                 int *cnt, int GX) {
-  __shared__ double vs[512];
+  __shared__ V vs[512];
   __shared__ double scratch[NT];
   __shared__ int flag;
   const int b = blockIdx.x, gblk = blockIdx.y;
@@ -485,7 +493,7 @@ __global__ void __launch_bounds__(NT) k_project(const PhiT *Phi, long long ld, i
     if (S.outer_done || S.cg_done || !S.deflate) return;
   }
   const uint8_t *mk = mask + b * N;
-  const double *vb = v + b * N;
+  const V *vb = v + b * N;
   double acc[KMAX / NWARP];
 #pragma unroll
   for (int a = 0; a < KMAX / NWARP; ++a) acc[a] = 0.0;
@@ -493,7 +501,7 @@ __global__ void __launch_bounds__(NT) k_project(const PhiT *Phi, long long ld, i
   for (long long base = (long long)gblk * 512; base < N; base += (long long)GX * 512) {
     for (int e = threadIdx.x; e < 512; e += NT) {
       long long g = base + e;
-      vs[e] = (g < N && !mk[g]) ? vb[g] : 0.0;
+      vs[e] = (g < N && !mk[g]) ? vb[g] : (V)0;
     }
     __syncthreads();
 #pragma unroll
@@ -501,10 +509,10 @@ __global__ void __launch_bounds__(NT) k_project(const PhiT *Phi, long long ld, i
       int j = warp + NWARP * a;
       if (j < k) {
         const PhiT *ph = Phi + (long long)j * ld + base;
-        double s = 0.0;
+        V s = (V)0;
         for (int e = lane; e < 512; e += 32)
-          if (base + e < N) s = fma((double)ph[e], vs[e], s);
-        acc[a] += s;
+          if (base + e < N) s = fma((V)ph[e], vs[e], s);
+        acc[a] += (double)s;
       }
     }
     __syncthreads();
@@ -531,43 +539,42 @@ __global__ void __launch_bounds__(NT) k_project(const PhiT *Phi, long long ld, i
 // CG iteration, kernel A: p = mask_I (gamma D^-1 r - Phi c + beta p) with
 // c = csign E_raw^-1 t (the coarse GEMV, recomputed by every block).
 
-template <int KMAX, class PhiT>
+template <int KMAX, class PhiT, class V>
 __global__ void __launch_bounds__(NT) k_expand(const PhiT *Phi, long long ld, int k, long long N,
                                                const InstState *st, const double *Einv,
-                                               const uint8_t *mask, const double *r,
-                                               const double *dinv, int dinv_per_inst, double *p,
-                                               int GX) {
-  __shared__ double c[SDF_MAX_K];
+                                               const uint8_t *mask, const V *r, const V *dinv,
+                                               int dinv_per_inst, V *p, int GX) {
+  __shared__ V c[SDF_MAX_K];
   const int b = blockIdx.x, gblk = blockIdx.y;
   const InstState &S = st[b];
-  if (S.outer_done || S.cg_done) return;
+  if (S.outer_done || S.cg_done || (S.await && S.phase == 0)) return;
   const int defl = S.deflate;
-  const double gam = S.gamma, bet = S.beta;
+  const V gam = (V)S.gamma, bet = (V)S.beta;
   if (defl) {
     const double *Ei = Einv + (size_t)b * k * k;
     for (int i = threadIdx.x; i < k; i += NT) {
       double s = 0.0;
       for (int j = 0; j < k; ++j) s = fma(Ei[i * k + j], S.t[j], s);
-      c[i] = S.csign * s;
+      c[i] = (V)(S.csign * s);
     }
   }
   __syncthreads();
   const uint8_t *mk = mask + b * N;
-  const double *rb = r + b * N;
-  const double *db = dinv + (dinv_per_inst ? b * N : 0);
-  double *pb = p + b * N;
+  const V *rb = r + b * N;
+  const V *db = dinv + (dinv_per_inst ? b * N : 0);
+  V *pb = p + b * N;
   for (long long g = (long long)gblk * NT + threadIdx.x; g < N; g += (long long)GX * NT) {
-    double v = 0.0;
+    V v = (V)0;
     if (!mk[g]) {
       v = gam * db[g] * rb[g] + bet * pb[g];
       if (defl) {
-        double s0 = 0.0, s1 = 0.0;
+        V s0 = (V)0, s1 = (V)0;
         int j = 0;
         for (; j + 1 < k; j += 2) {
-          s0 = fma((double)Phi[(long long)j * ld + g], c[j], s0);
-          s1 = fma((double)Phi[(long long)(j + 1) * ld + g], c[j + 1], s1);
+          s0 = fma((V)Phi[(long long)j * ld + g], c[j], s0);
+          s1 = fma((V)Phi[(long long)(j + 1) * ld + g], c[j + 1], s1);
         }
-        if (j < k) s0 = fma((double)Phi[(long long)j * ld + g], c[j], s0);
+        if (j < k) s0 = fma((V)Phi[(long long)j * ld + g], c[j], s0);
         v -= s0 + s1;
       }
     }
@@ -575,36 +582,37 @@ __global__ void __launch_bounds__(NT) k_expand(const PhiT *Phi, long long ld, in
   }
 }
 
-// Kernel B: q = S_II p and sigma = (p, q); the last block sets alpha.
-template <int DIM>
+// Kernel B: q = S_II p and sigma = (p, q) (FP64 accumulation); the last
+// block sets alpha (1 in the coarse and correction passes).
+template <int DIM, class V>
 __global__ void __launch_bounds__(NT) k_spmv(OpParams P, const double *inst, InstState *st,
-                                             const uint8_t *mask, const double *p, double *q,
+                                             const uint8_t *mask, const V *p, V *q,
                                              double *part, int *cnt, Ctrl *ctrl, int GX) {
-  __shared__ TileSmem<DIM> sm;
+  __shared__ TileSmem<DIM, V> sm;
   __shared__ double red[NWARP];
   __shared__ int flag;
   const int b = blockIdx.x, gblk = blockIdx.y;
   InstState &S = st[b];
-  if (S.outer_done || S.cg_done) return;
+  if (S.outer_done || S.cg_done || (S.await && S.phase == 0)) return;
   const long long N = P.N;
   double cb[3];
   inst_cb(P, inst + 7 * b, cb);
   const uint8_t *mk = mask + b * N;
-  const double *pb = p + b * N;
-  double *qb = q + b * N;
+  const V *pb = p + b * N;
+  V *qb = q + b * N;
   double sg = 0.0;
   const long long T = num_tiles<DIM>(P.nx, P.ny, P.nz);
   for (long long t = gblk; t < T; t += GX) {
     int ox, oy, oz;
     tile_origin<DIM>(P, t, ox, oy, oz);
-    tile_S<DIM>(
+    tile_S<DIM, V>(
         P, cb, ox, oy, oz, sm, [&](int, int, int, long long g) { return pb[g]; },
-        [&](int e, int, int, int, long long g, double su) {
-          double qv = mk[g] ? 0.0 : su;
+        [&](int e, int, int, int, long long g, V su) {
+          V qv = mk[g] ? (V)0 : su;
           qb[g] = qv;
-          sg = fma(sm.u[uidx<DIM>(e % TileCfg<DIM>::TX, (e / TileCfg<DIM>::TX) % TileCfg<DIM>::TY,
-                                  e / (TileCfg<DIM>::TX * TileCfg<DIM>::TY))],
-                   qv, sg);
+          sg = fma((double)sm.u[uidx<DIM>(e % TileCfg<DIM>::TX, (e / TileCfg<DIM>::TX) % TileCfg<DIM>::TY,
+                                          e / (TileCfg<DIM>::TX * TileCfg<DIM>::TY))],
+                   (double)qv, sg);
         });
   }
   sg = block_sum(sg, red);
@@ -628,38 +636,42 @@ __global__ void __launch_bounds__(NT) k_spmv(OpParams P, const double *inst, Ins
   }
 }
 
-// Kernel C: x += alpha p, r -= alpha q, z = D^-1 r, v = S_II z,
-// t = Phi_I^T v, rho = (r, z), ||r||^2; the last block tests convergence
-// (App. B.2) and prepares beta for kernel A.  r is read (with its halo) from
-// r_in and written to r_out: blocks read neighbouring tiles' r while other
-// blocks update theirs, so the update cannot be in place.
-template <int DIM, int KMAX, class PhiT>
+// Kernel C: x += alpha p (x in FP64), r -= alpha q, z = D^-1 r, v = S_II z,
+// t = Phi_I^T v, rho = (r, z), ||r||^2 (FP64 accumulation); the last block
+// tests convergence (App. B.2) and prepares beta for kernel A.  r is read
+// (with its halo) from r_in and written to r_out: blocks read neighbouring
+// tiles' r while other blocks update theirs, so the update cannot be in place.
+// Passes: phase 0 = CG iteration; 1 = coarse-corrected start (beta = 0);
+// 2 = coarse correction after an FP64 residual replacement (beta continues).
+// mixed = 1: convergence is only declared by the FP64 check of k_resid; the
+// recurrence reaching rtol sets `await` instead.
+template <int DIM, int KMAX, class PhiT, class V>
 __global__ void __launch_bounds__(NT) k_update(OpParams P, const double *inst, const PhiT *Phi,
                                                long long ld, int k, InstState *st,
-                                               const uint8_t *mask, const double *r_in,
-                                               double *r_out, const double *q, const double *p,
-                                               double *x, const double *dinv, double *part,
-                                               int *cnt, Ctrl *ctrl, int GX, double rtol2,
-                                               int max_cg) {
-  __shared__ TileSmem<DIM> sm;
+                                               const uint8_t *mask, const V *r_in, V *r_out,
+                                               const V *q, const V *p, double *x, const V *dinv,
+                                               double *part, int *cnt, Ctrl *ctrl, int GX,
+                                               double rtol2, int max_cg, int mixed) {
+  __shared__ TileSmem<DIM, V> sm;
   __shared__ double red[NWARP];
   __shared__ double scratch[NT];
   __shared__ double res[SDF_MAX_K + 2];
   __shared__ int flag;
-  using C = TileCfg<DIM>;
   const int b = blockIdx.x, gblk = blockIdx.y;
   InstState &S = st[b];
-  if (S.outer_done || S.cg_done) return;
+  if (S.outer_done || S.cg_done || (S.await && S.phase == 0)) return;
   const long long N = P.N;
-  const double alpha = S.alpha;
+  const double alpha64 = S.alpha;
+  const V alpha = (V)alpha64;
   const int defl = S.deflate;
   double cb[3];
   inst_cb(P, inst + 7 * b, cb);
   const uint8_t *mk = mask + b * N;
-  const double *rb = r_in + b * N;
-  double *rw = r_out + b * N, *xb = x + b * N;
-  const double *qb = q + b * N, *pb = p + b * N;
-  const double *db = dinv + (P.convection ? b * N : 0);
+  const V *rb = r_in + b * N;
+  V *rw = r_out + b * N;
+  double *xb = x + b * N;
+  const V *qb = q + b * N, *pb = p + b * N;
+  const V *db = dinv + (P.convection ? b * N : 0);
   double rho = 0.0, rr = 0.0;
   double acc[KMAX / NWARP];
 #pragma unroll
@@ -668,23 +680,23 @@ __global__ void __launch_bounds__(NT) k_update(OpParams P, const double *inst, c
   for (long long t = gblk; t < T; t += GX) {
     int ox, oy, oz;
     tile_origin<DIM>(P, t, ox, oy, oz);
-    tile_S<DIM>(
+    tile_S<DIM, V>(
         P, cb, ox, oy, oz, sm,
         [&](int, int, int, long long g) {
-          return mk[g] ? 0.0 : db[g] * (rb[g] - alpha * qb[g]);
+          return mk[g] ? (V)0 : db[g] * (rb[g] - alpha * qb[g]);
         },
-        [&](int e, int, int, int, long long g, double su) {
+        [&](int e, int, int, int, long long g, V su) {
           if (mk[g]) {
-            sm.v[e] = 0.0;
-            rw[g] = 0.0;
+            sm.v[e] = (V)0;
+            rw[g] = (V)0;
             return;
           }
-          double rn = rb[g] - alpha * qb[g];
-          double z = db[g] * rn;
-          xb[g] = xb[g] + alpha * pb[g];
+          V rn = rb[g] - alpha * qb[g];
+          V z = db[g] * rn;
+          xb[g] = fma(alpha64, (double)pb[g], xb[g]);
           rw[g] = rn;
-          rho = fma(rn, z, rho);
-          rr = fma(rn, rn, rr);
+          rho = fma((double)rn, (double)z, rho);
+          rr = fma((double)rn, (double)rn, rr);
           sm.v[e] = su;
         });
     if (defl) {
@@ -700,9 +712,9 @@ __global__ void __launch_bounds__(NT) k_update(OpParams P, const double *inst, c
   if (defl) {
 #pragma unroll
     for (int a = 0; a < KMAX / NWARP; ++a) {
-      double s = warp_sum(acc[a]);
+      double sacc = warp_sum(acc[a]);
       int j = warp + NWARP * a;
-      if (lane == 0 && j < k) pbk[2 + j] = s;
+      if (lane == 0 && j < k) pbk[2 + j] = sacc;
     }
   }
   if (threadIdx.x == 0) {
@@ -716,23 +728,126 @@ __global__ void __launch_bounds__(NT) k_update(OpParams P, const double *inst, c
   if (threadIdx.x == 0) {
     cnt[b * NCNT + CNT_UPDATE] = 0;
     double rho_new = res[0], rn2 = res[1];
-    if (!S.phase) S.iters += 1;
+    if (S.phase == 0) S.iters += 1;
     S.rnorm2 = rn2;
     bool conv = rn2 <= rtol2 * S.bnorm2;
     if (!isfinite(rho_new) || !isfinite(rn2)) {
       S.stats.status = SDF_ERR_NONFINITE;
       S.cg_done = 1;
-    } else if (conv) {
+    } else if (conv && !mixed) {
       S.cg_done = 1;
     } else if (S.iters >= max_cg) {
       S.stats.status = SDF_ERR_CG_MAXIT;
       S.cg_done = 1;
     } else {
-      S.beta = S.phase ? 0.0 : rho_new / S.rho;
+      if (conv) S.await = 1;
+      S.beta = S.phase == 1 ? 0.0 : rho_new / S.rho;
       S.rho = rho_new;
       S.gamma = 1.0;
       S.csign = 1.0;
       S.phase = 0;
+    }
+    if (S.cg_done) {
+      S.stats.cg_iters[S.outer] = S.iters;
+      S.stats.relres[S.outer] = S.bnorm2 > 0 ? sqrt(rn2 / S.bnorm2) : 0.0;
+      atomicSub(&ctrl->running, 1);
+    }
+  }
+}
+
+// FP64 residual replacement of the mixed path: r = b - S_II x with the FP64
+// stencil on the FP64 iterate, ||r||^2 and t = Phi_I^T r (for the coarse
+// correction x += Phi E_raw^-1 Phi_I^T r that follows).  The last block
+// declares convergence on this true residual, or arms the correction pass
+// (phase 2).  r is written in place: this kernel reads x, not r.
+template <int DIM, int KMAX, class PhiT, class V>
+__global__ void __launch_bounds__(NT) k_resid(OpParams P, const double *inst, const PhiT *Phi,
+                                              long long ld, int k, InstState *st,
+                                              const uint8_t *mask, const double *b64,
+                                              const double *x, V *r, double *part, int *cnt,
+                                              Ctrl *ctrl, int GX, double rtol2) {
+  __shared__ TileSmem<DIM, double> sm;
+  __shared__ V vs[TileSmem<DIM, double>::TILE];
+  __shared__ double red[NWARP];
+  __shared__ double scratch[NT];
+  __shared__ double res[SDF_MAX_K + 2];
+  __shared__ int flag;
+  const int b = blockIdx.x, gblk = blockIdx.y;
+  InstState &S = st[b];
+  if (S.outer_done || S.cg_done) return;
+  const long long N = P.N;
+  const int defl = S.deflate;
+  double cb[3];
+  inst_cb(P, inst + 7 * b, cb);
+  const uint8_t *mk = mask + b * N;
+  const double *xb = x + b * N, *bb = b64 + b * N;
+  V *rb = r + b * N;
+  double rr = 0.0;
+  double acc[KMAX / NWARP];
+#pragma unroll
+  for (int a = 0; a < KMAX / NWARP; ++a) acc[a] = 0.0;
+  const long long T = num_tiles<DIM>(P.nx, P.ny, P.nz);
+  for (long long t = gblk; t < T; t += GX) {
+    int ox, oy, oz;
+    tile_origin<DIM>(P, t, ox, oy, oz);
+    tile_S<DIM, double>(
+        P, cb, ox, oy, oz, sm, [&](int, int, int, long long g) { return xb[g]; },
+        [&](int e, int, int, int, long long g, double su) {
+          if (mk[g]) {
+            vs[e] = (V)0;
+            rb[g] = (V)0;
+            return;
+          }
+          double rt = bb[g] - su;
+          rb[g] = (V)rt;
+          rr = fma(rt, rt, rr);
+          vs[e] = (V)rt;
+        });
+    // tile_S leaves vs zero only where it wrote it; clear the out-of-grid part
+    for (int e = threadIdx.x; e < TileSmem<DIM, double>::TILE; e += NT) {
+      int lx = e % TileCfg<DIM>::TX, tt = e / TileCfg<DIM>::TX;
+      if (ox + lx >= P.nx || oy + tt % TileCfg<DIM>::TY >= P.ny || oz + tt / TileCfg<DIM>::TY >= P.nz)
+        vs[e] = (V)0;
+    }
+    __syncthreads();
+    if (defl) tile_project<DIM, KMAX>(P, Phi, ld, k, ox, oy, oz, vs, acc);
+    __syncthreads();
+  }
+  rr = block_sum(rr, red);
+  const int F = KMAX + 2;
+  double *pbk = part + ((long long)b * GX + gblk) * F;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  if (defl) {
+#pragma unroll
+    for (int a = 0; a < KMAX / NWARP; ++a) {
+      double sacc = warp_sum(acc[a]);
+      int j = warp + NWARP * a;
+      if (lane == 0 && j < k) pbk[2 + j] = sacc;
+    }
+  }
+  if (threadIdx.x == 0) {
+    pbk[0] = 0.0;
+    pbk[1] = rr;
+  }
+  if (!last_block(cnt + b * NCNT + CNT_UPDATE, GX, &flag)) return;
+  reduce_fields(part + (long long)b * GX * F, GX, F, defl ? 2 + k : 2, res, scratch);
+  if (defl)
+    for (int j = threadIdx.x; j < k; j += NT) S.t[j] = res[2 + j];
+  if (threadIdx.x == 0) {
+    cnt[b * NCNT + CNT_UPDATE] = 0;
+    double rn2 = res[1];
+    S.rnorm2 = rn2;
+    if (!isfinite(rn2)) {
+      S.stats.status = SDF_ERR_NONFINITE;
+      S.cg_done = 1;
+    } else if (rn2 <= rtol2 * S.bnorm2) {
+      S.cg_done = 1;
+    } else {
+      S.await = 0;
+      S.phase = 2;  // coarse correction pass: w = Phi E_raw^-1 t, alpha = 1
+      S.gamma = 0.0;
+      S.beta = 0.0;
+      S.csign = -1.0;
     }
     if (S.cg_done) {
       S.stats.cg_iters[S.outer] = S.iters;
@@ -875,6 +990,7 @@ struct sdf_problem {
   void *dev = nullptr;
   size_t dev_bytes = 0;
   double *dinv_shared = nullptr;
+  float *dinv_shared32 = nullptr;
   const void *phi = nullptr;
   int k = 0;
   long long ld = 0;
@@ -912,7 +1028,7 @@ sdf_status cuda_check(sdf_problem *p, cudaError_t e, const char *what) {
 
 int kmax_for(int k) { return k <= 16 ? 16 : k <= 32 ? 32 : k <= 64 ? 64 : 128; }
 
-Layout make_layout(const sdf_problem *p, int B, int max_blocks = 0) {
+Layout make_layout(const sdf_problem *p, int B, int max_blocks = 0, int mixed = 0) {
   Layout L{};
   const long long N = p->P.N;
   const int k = std::max(p->k, 1), KM = kmax_for(k);
@@ -934,12 +1050,15 @@ Layout make_layout(const sdf_problem *p, int B, int max_blocks = 0) {
     return at;
   };
   size_t vec = sizeof(double) * (size_t)N * B;
+  size_t vecv = (mixed ? sizeof(float) : sizeof(double)) * (size_t)N * B;
   L.x = take(vec);
-  L.r = take(vec);
-  L.r2 = take(vec);
-  L.p = take(vec);
-  L.q = take(vec);
-  L.dinv = take(p->d.convection ? vec : 8);
+  L.b64 = take(vec);
+  L.r = take(vecv);
+  L.r2 = take(vecv);
+  L.p = take(vecv);
+  L.q = take(vecv);
+  L.w = take(mixed ? vecv : 8);
+  L.dinv = take(p->d.convection ? vecv : 8);
   L.mask = take((size_t)N * B);
   L.W = take(sizeof(double) * (size_t)N * k);
   size_t kk = sizeof(double) * (size_t)k * k;
@@ -962,18 +1081,22 @@ bool aligned(const void *ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
 template <class PhiT>
 const PhiT *phi_as(const sdf_problem *p) { return static_cast<const PhiT *>(p->phi); }
 
-// The solve, templated on dimension, mode-count bucket and Phi type.
-template <int DIM, int KMAX, class PhiT>
+// The solve, templated on dimension, mode-count bucket, Phi type and vector
+// precision V (double: FP64 path; float: mixed path with FP64 x, b,
+// reductions, coarse operator and periodic FP64 residual replacement).
+template <int DIM, int KMAX, class PhiT, class V>
 sdf_status solve_impl(sdf_problem *p, const double *inst, int B, const double *psi,
                       const sdf_opts &o, char *ws, cudaStream_t s, double *y, double *lam,
                       uint8_t *active, sdf_stats *stats) {
-  const Layout L = make_layout(p, B, o.max_blocks);
+  constexpr int mixed = sizeof(V) == sizeof(float) ? 1 : 0;
+  const Layout L = make_layout(p, B, o.max_blocks, mixed);
   const OpParams &P = p->P;
   const long long N = P.N;
-  double *x = (double *)(ws + L.x), *pp = (double *)(ws + L.p), *q = (double *)(ws + L.q);
-  double *rbuf[2] = {(double *)(ws + L.r), (double *)(ws + L.r2)};
-  double *r = rbuf[0];
-  double *dinv = P.convection ? (double *)(ws + L.dinv) : p->dinv_shared;
+  double *x = (double *)(ws + L.x), *b64 = (double *)(ws + L.b64);
+  V *pp = (V *)(ws + L.p), *q = (V *)(ws + L.q), *wv = (V *)(ws + L.w);
+  V *rbuf[2] = {(V *)(ws + L.r), (V *)(ws + L.r2)};
+  V *dinv = P.convection ? (V *)(ws + L.dinv)
+                         : (mixed ? (V *)p->dinv_shared32 : (V *)p->dinv_shared);
   uint8_t *mask = (uint8_t *)(ws + L.mask);
   double *W = (double *)(ws + L.W), *Einv = (double *)(ws + L.Einv), *Eraw = (double *)(ws + L.Eraw),
          *G = (double *)(ws + L.G), *coarse = (double *)(ws + L.coarse),
@@ -994,12 +1117,32 @@ sdf_status solve_impl(sdf_problem *p, const double *inst, int B, const double *p
   const dim3 gT(B, L.gx), gA(B, L.gxa);
   long long launches = 0;
   const long long max_launches = o.max_launches > 0 ? o.max_launches : 4LL * o.max_cg + 64;
-  const int chunk = std::max(1, o.check_every);
+  // CG iterations between FP64 residual replacements (mixed) or host polls
+  const int chunk = std::max(1, mixed ? (o.replace_every > 0 ? o.replace_every : 100) : o.check_every);
   const double rtol2 = o.rtol * o.rtol;
   int live = B;
+  int par = 0;
+  // one CG-kernel triple: A (expand into `dir`), B (spmv of dir), C (update)
+  auto triple = [&](V *dir, bool timed) -> sdf_status {
+    if (timed) CK(cudaEventRecord(p->ev[0], s));
+    k_expand<KMAX, PhiT, V><<<gA, NT, 0, s>>>(Phi, ld, k, N, st, Einv, mask, rbuf[par], dinv,
+                                              P.convection, dir, L.gxa);
+    if (timed) CK(cudaEventRecord(p->ev[1], s));
+    k_spmv<DIM, V><<<gT, NT, 0, s>>>(P, inst, st, mask, dir, q, part, cnt, ctrl, L.gx);
+    if (timed) CK(cudaEventRecord(p->ev[2], s));
+    k_update<DIM, KMAX, PhiT, V><<<gT, NT, 0, s>>>(P, inst, Phi, ld, k, st, mask, rbuf[par],
+                                                   rbuf[par ^ 1], q, dir, x, dinv, part, cnt,
+                                                   ctrl, L.gx, rtol2, o.max_cg, mixed);
+    if (timed) CK(cudaEventRecord(p->ev[3], s));
+    par ^= 1;
+    p->prof.launches += 3;
+    return SDF_OK;
+  };
   for (int outer = 0; outer < o.max_outer && live > 0; ++outer) {
     CK(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s));
-    k_outer_setup<DIM><<<gT, NT, 0, s>>>(P, inst, psi, mask, r, x, dinv, st, part, cnt, ctrl, L.gx);
+    par = 0;
+    k_outer_setup<DIM, V><<<gT, NT, 0, s>>>(P, inst, psi, mask, rbuf[0], b64, x, dinv, st, part,
+                                            cnt, ctrl, L.gx);
     CKL("k_outer_setup");
     p->prof.launches += 1;
     if (defl) {
@@ -1013,49 +1156,56 @@ sdf_status solve_impl(sdf_problem *p, const double *inst, int B, const double *p
       CKL("coarse setup");
       k_coarse<<<B, NT, 0, s>>>(k, st, G, Eraw, Einv, coarse, o.tau_cond);
       CKL("k_coarse");
-      k_project<KMAX, PhiT><<<gA, NT, 0, s>>>(Phi, ld, k, N, mask, r, st, nullptr, part, cnt, L.gxa);
+      k_project<KMAX, PhiT, V><<<gA, NT, 0, s>>>(Phi, ld, k, N, mask, rbuf[0], st, nullptr, part,
+                                                 cnt, L.gxa);
       CKL("k_project");
       p->prof.launches += 5LL * B + 2;
     }
-    // coarse-correction pass, then CG iterations in chunks; r ping-pongs
-    // between the two buffers (uniform across the batch: finished instances
-    // skip every launch)
-    int par = 0;
+    // coarse-corrected start (phase 1), then CG iterations in chunks; r
+    // ping-pongs between its two buffers (uniform across the batch: finished
+    // instances skip every launch).
+    {
+      sdf_status e = triple(pp, false);
+      if (e != SDF_OK) return e;
+    }
     for (int it = 0;; ++it) {
-      int nrep = it == 0 ? 1 : chunk;
-      const bool timed = o.profile && p->ev_ready && it > 0;
-      for (int rep = 0; rep < nrep; ++rep) {
-        if (timed && rep == 0) CK(cudaEventRecord(p->ev[0], s));
-        k_expand<KMAX, PhiT><<<gA, NT, 0, s>>>(Phi, ld, k, N, st, Einv, mask, rbuf[par], dinv,
-                                               P.convection, pp, L.gxa);
-        if (timed && rep == 0) CK(cudaEventRecord(p->ev[1], s));
-        k_spmv<DIM><<<gT, NT, 0, s>>>(P, inst, st, mask, pp, q, part, cnt, ctrl, L.gx);
-        if (timed && rep == 0) CK(cudaEventRecord(p->ev[2], s));
-        k_update<DIM, KMAX, PhiT><<<gT, NT, 0, s>>>(P, inst, Phi, ld, k, st, mask, rbuf[par],
-                                                    rbuf[par ^ 1], q, pp, x, dinv, part, cnt,
-                                                    ctrl, L.gx, rtol2, o.max_cg);
-        par ^= 1;
-        if (timed && rep == 0) CK(cudaEventRecord(p->ev[3], s));
+      const bool timed = o.profile && p->ev_ready;
+      for (int rep = 0; rep < chunk; ++rep) {
+        sdf_status e = triple(pp, timed && rep == 0);
+        if (e != SDF_OK) return e;
+      }
+      if (mixed) {  // FP64 residual replacement + coarse correction pass
+        if (timed) CK(cudaEventRecord(p->ev[4], s));
+        k_resid<DIM, KMAX, PhiT, V><<<gT, NT, 0, s>>>(P, inst, Phi, ld, k, st, mask, b64, x,
+                                                      rbuf[par], part, cnt, ctrl, L.gx, rtol2);
+        if (timed) CK(cudaEventRecord(p->ev[5], s));
+        p->prof.launches += 1;
+        sdf_status e = triple(wv, false);
+        if (e != SDF_OK) return e;
       }
       CKL("cg iteration");
-      launches += nrep;
-      p->prof.launches += 3LL * nrep;
+      launches += chunk;
       CK(cudaMemcpyAsync(p->pinned, &ctrl->running, sizeof(int), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
       if (timed) {
-        // only launches that did work count: a poll interval whose first
-        // iteration already found every instance converged is skipped
-        float t0 = 0, t1 = 0, t2 = 0;
+        float t0 = 0, t1 = 0, t2 = 0, t3 = 0;
         cudaEventElapsedTime(&t0, p->ev[0], p->ev[1]);
         cudaEventElapsedTime(&t1, p->ev[1], p->ev[2]);
         cudaEventElapsedTime(&t2, p->ev[2], p->ev[3]);
-        if (p->pinned[0] > 0 || nrep > 1) {
+        if (mixed) cudaEventElapsedTime(&t3, p->ev[4], p->ev[5]);
+        // only intervals that still had work count (a poll interval whose first
+        // iteration found every instance finished would time empty launches)
+        if (p->pinned[0] > 0 || chunk > 1) {
           p->prof.ms[0] += t0;
           p->prof.ms[1] += t1;
           p->prof.ms[2] += t2;
           p->prof.samples[0] += 1;
           p->prof.samples[1] += 1;
           p->prof.samples[2] += 1;
+          if (mixed) {
+            p->prof.ms[7] += t3;
+            p->prof.samples[7] += 1;
+          }
         }
       }
       if (p->pinned[0] <= 0) break;
@@ -1091,9 +1241,18 @@ template <int DIM, int KMAX>
 sdf_status dispatch_phi(sdf_problem *p, const double *inst, int B, const double *psi,
                         const sdf_opts &o, char *ws, cudaStream_t s, double *y, double *lam,
                         uint8_t *active, sdf_stats *stats) {
+  if (o.precision == SDF_PREC_F64) {
+    if (p->phi && p->phi_dtype != SDF_F64 && o.deflate)
+      return fail(p, SDF_ERR_UNSUPPORTED, "the FP64 path takes FP64 reference modes");
+    return solve_impl<DIM, KMAX, double, double>(p, inst, B, psi, o, ws, s, y, lam, active, stats);
+  }
   switch (p->phi_dtype) {
-    case SDF_F64: return solve_impl<DIM, KMAX, double>(p, inst, B, psi, o, ws, s, y, lam, active, stats);
-    default: return fail(p, SDF_ERR_UNSUPPORTED, "the FP64 solve needs FP64 reference modes");
+    case SDF_F32: return solve_impl<DIM, KMAX, float, float>(p, inst, B, psi, o, ws, s, y, lam, active, stats);
+    case SDF_BF16: return solve_impl<DIM, KMAX, __nv_bfloat16, float>(p, inst, B, psi, o, ws, s, y, lam, active, stats);
+    default:
+      if (p->phi && o.deflate)
+        return fail(p, SDF_ERR_UNSUPPORTED, "the mixed path takes FP32 or BF16 reference modes");
+      return solve_impl<DIM, KMAX, float, float>(p, inst, B, psi, o, ws, s, y, lam, active, stats);
   }
 }
 
@@ -1115,6 +1274,7 @@ size_t problem_bytes(const sdf_problem *p) {
   long long N = nx * ny * nz;
   size_t o = 0;
   o = al(o + sizeof(double) * N);  // shared Jacobi diagonal
+  o = al(o + sizeof(float) * N);   // its FP32 copy
   if (d.has_kappa) {
     o = al(o + sizeof(double) * N);                     // kappa
     o = al(o + sizeof(double) * (nx + 1) * ny * nz);    // fx
@@ -1142,6 +1302,8 @@ void sdf_default_opts(sdf_opts *o) {
   o->check_every = 64;
   o->profile = 0;
   o->max_blocks = 0;
+  o->precision = SDF_PREC_F64;
+  o->replace_every = 100;
   o->max_launches = 0;
 }
 
@@ -1224,6 +1386,8 @@ sdf_status sdf_problem_bind(sdf_problem *p, void *dev_buf, size_t bytes, void *s
   size_t o = 0;
   p->dinv_shared = (double *)(base + o);
   o = al(o + sizeof(double) * P.N);
+  p->dinv_shared32 = (float *)(base + o);
+  o = al(o + sizeof(float) * P.N);
   P.fx = P.fy = P.fz = nullptr;
   if (p->d.has_kappa) {
     double *kap = (double *)(base + o);
@@ -1241,8 +1405,8 @@ sdf_status sdf_problem_bind(sdf_problem *p, void *dev_buf, size_t bytes, void *s
     P.fy = fy;
     P.fz = fz;
   }
-  if (P.dim == 2) k_diag_shared<2><<<p->nsm * 4, NT, 0, s>>>(P, p->dinv_shared);
-  else k_diag_shared<3><<<p->nsm * 4, NT, 0, s>>>(P, p->dinv_shared);
+  if (P.dim == 2) k_diag_shared<2><<<p->nsm * 4, NT, 0, s>>>(P, p->dinv_shared, p->dinv_shared32);
+  else k_diag_shared<3><<<p->nsm * 4, NT, 0, s>>>(P, p->dinv_shared, p->dinv_shared32);
   CKL("k_diag_shared");
   CK(cudaStreamSynchronize(s));
   p->dev = dev_buf;
@@ -1339,8 +1503,8 @@ sdf_status sdf_analytic_modes(sdf_problem *p, int k, void *phi_dev, int64_t ld, 
 
 sdf_status sdf_workspace_size(const sdf_problem *p, int batch, const sdf_opts *opts, size_t *bytes) {
   if (!p || !bytes || batch < 1) return SDF_ERR_INVALID_ARG;
-  (void)opts;
-  *bytes = make_layout(p, batch).total;
+  *bytes = make_layout(p, batch, opts ? opts->max_blocks : 0,
+                       opts ? (opts->precision == SDF_PREC_MIXED) : 0).total;
   return SDF_OK;
 }
 
@@ -1364,10 +1528,11 @@ static sdf_status check_solve_args(sdf_problem *p, int batch, const sdf_opts *op
     return fail(p, SDF_ERR_INVALID_ARG, "bad opts");
   if (!ws || !aligned(ws, 256))
     return fail(p, SDF_ERR_INVALID_ARG, "workspace must be a 256-byte aligned device pointer");
-  size_t need = make_layout(p, batch).total;
+  if (opts->precision != SDF_PREC_F64 && opts->precision != SDF_PREC_MIXED)
+    return fail(p, SDF_ERR_INVALID_ARG, "unknown precision");
+  if (opts->replace_every < 0) return fail(p, SDF_ERR_INVALID_ARG, "replace_every < 0");
+  size_t need = make_layout(p, batch, opts->max_blocks, opts->precision == SDF_PREC_MIXED).total;
   if (ws_bytes < need) return fail(p, SDF_ERR_WORKSPACE, "workspace too small");
-  if (opts->deflate && p->phi && p->phi_dtype != SDF_F64)
-    return fail(p, SDF_ERR_UNSUPPORTED, "this solve path takes FP64 reference modes");
   return SDF_OK;
 }
 

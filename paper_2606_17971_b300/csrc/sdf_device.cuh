@@ -37,24 +37,26 @@ template <> struct TileCfg<3> {
   static constexpr int TX = 32, TY = 4, TZ = 4, HZ = 2, HZ1 = 1;
 };
 
-template <int DIM> struct TileSmem {
+// Shared-memory tile of the stencil in arithmetic type T (double for the FP64
+// path, float for the FP32 part of the mixed path).
+template <int DIM, class T = double> struct TileSmem {
   using C = TileCfg<DIM>;
   static constexpr int UX = C::TX + 4, UY = C::TY + 4, UZ = C::TZ + 2 * C::HZ;
   static constexpr int WX = C::TX + 2, WY = C::TY + 2, WZ = C::TZ + 2 * C::HZ1;
   static constexpr int TILE = C::TX * C::TY * C::TZ;
-  double u[UZ * UY * UX];
-  double w[WZ * WY * WX];
-  double v[TILE];
+  T u[UZ * UY * UX];
+  T w[WZ * WY * WX];
+  T v[TILE];
 };
 
 template <int DIM>
 __device__ __forceinline__ int uidx(int lx, int ly, int lz) {
-  using S = TileSmem<DIM>;
+  using S = TileSmem<DIM, double>;
   return (lx + 2) + S::UX * ((ly + 2) + S::UY * (lz + TileCfg<DIM>::HZ));
 }
 template <int DIM>
 __device__ __forceinline__ int widx(int lx, int ly, int lz) {
-  using S = TileSmem<DIM>;
+  using S = TileSmem<DIM, double>;
   return (lx + 1) + S::WX * ((ly + 1) + S::WY * (lz + TileCfg<DIM>::HZ1));
 }
 
@@ -70,14 +72,14 @@ __device__ __forceinline__ double face_z(const OpParams &P, int i, int j, int l)
 
 // (A u)_p in flux form: sum over faces of k_f (u_p - u_nb) plus first-order
 // upwind convection; U(dx,dy,dz) returns u at the offset (0 outside the grid).
-template <int DIM, class U>
-__device__ __forceinline__ double apply_A(const OpParams &P, const double cb[3], int i, int j,
+template <int DIM, class T, class U>
+__device__ __forceinline__ T apply_A(const OpParams &P, const T cb[3], int i, int j,
                                           int l, U u) {
-  double c = u(0, 0, 0);
-  double s = face_x(P, i, j, l) * (c - u(-1, 0, 0)) + face_x(P, i + 1, j, l) * (c - u(1, 0, 0));
-  s += face_y(P, i, j, l) * (c - u(0, -1, 0)) + face_y(P, i, j + 1, l) * (c - u(0, 1, 0));
+  T c = u(0, 0, 0);
+  T s = (T)face_x(P, i, j, l) * (c - u(-1, 0, 0)) + (T)face_x(P, i + 1, j, l) * (c - u(1, 0, 0));
+  s += (T)face_y(P, i, j, l) * (c - u(0, -1, 0)) + (T)face_y(P, i, j + 1, l) * (c - u(0, 1, 0));
   if (DIM == 3)
-    s += face_z(P, i, j, l) * (c - u(0, 0, -1)) + face_z(P, i, j, l + 1) * (c - u(0, 0, 1));
+    s += (T)face_z(P, i, j, l) * (c - u(0, 0, -1)) + (T)face_z(P, i, j, l + 1) * (c - u(0, 0, 1));
   if (cb[0] > 0.0) s += cb[0] * (c - u(-1, 0, 0));
   else if (cb[0] < 0.0) s -= cb[0] * (c - u(1, 0, 0));
   if (cb[1] > 0.0) s += cb[1] * (c - u(0, -1, 0));
@@ -91,14 +93,14 @@ __device__ __forceinline__ double apply_A(const OpParams &P, const double cb[3],
 
 // (A^T w)_p: the diffusion part is symmetric; the upwind part is transposed
 // (a backward difference becomes a forward one and vice versa).
-template <int DIM, class U>
-__device__ __forceinline__ double apply_AT(const OpParams &P, const double cb[3], int i, int j,
+template <int DIM, class T, class U>
+__device__ __forceinline__ T apply_AT(const OpParams &P, const T cb[3], int i, int j,
                                            int l, U w) {
-  double c = w(0, 0, 0);
-  double s = face_x(P, i, j, l) * (c - w(-1, 0, 0)) + face_x(P, i + 1, j, l) * (c - w(1, 0, 0));
-  s += face_y(P, i, j, l) * (c - w(0, -1, 0)) + face_y(P, i, j + 1, l) * (c - w(0, 1, 0));
+  T c = w(0, 0, 0);
+  T s = (T)face_x(P, i, j, l) * (c - w(-1, 0, 0)) + (T)face_x(P, i + 1, j, l) * (c - w(1, 0, 0));
+  s += (T)face_y(P, i, j, l) * (c - w(0, -1, 0)) + (T)face_y(P, i, j + 1, l) * (c - w(0, 1, 0));
   if (DIM == 3)
-    s += face_z(P, i, j, l) * (c - w(0, 0, -1)) + face_z(P, i, j, l + 1) * (c - w(0, 0, 1));
+    s += (T)face_z(P, i, j, l) * (c - w(0, 0, -1)) + (T)face_z(P, i, j, l + 1) * (c - w(0, 0, 1));
   if (cb[0] > 0.0) s += cb[0] * (c - w(1, 0, 0));
   else if (cb[0] < 0.0) s -= cb[0] * (c - w(-1, 0, 0));
   if (cb[1] > 0.0) s += cb[1] * (c - w(0, 1, 0));
@@ -151,11 +153,13 @@ __host__ __device__ inline long long num_tiles(int nx, int ny, int nz) {
 // node; store(e, gx, gy, gz, g, Su) receives S u at each grid node of the tile
 // (e = local tile index).  Two shared-memory passes: w = A u on the halo-1
 // ring, then mass u + wgt A^T w on the tile.
-template <int DIM, class Load, class Store>
-__device__ void tile_S(const OpParams &P, const double cb[3], int ox, int oy, int oz,
-                       TileSmem<DIM> &sm, Load load, Store store) {
+template <int DIM, class T, class Load, class Store>
+__device__ void tile_S(const OpParams &P, const double cb64[3], int ox, int oy, int oz,
+                       TileSmem<DIM, T> &sm, Load load, Store store) {
   using C = TileCfg<DIM>;
-  using SM = TileSmem<DIM>;
+  using SM = TileSmem<DIM, T>;
+  const T cb[3] = {(T)cb64[0], (T)cb64[1], (T)cb64[2]};
+  const T mass = (T)P.mass, wgt = (T)P.wgt;
   for (int e = threadIdx.x; e < SM::UZ * SM::UY * SM::UX; e += NT) {
     int lx = e % SM::UX - 2;
     int t = e / SM::UX;
@@ -163,7 +167,7 @@ __device__ void tile_S(const OpParams &P, const double cb[3], int ox, int oy, in
     int lz = t / SM::UY - C::HZ;
     int gx = ox + lx, gy = oy + ly, gz = oz + lz;
     bool in = gx >= 0 && gx < P.nx && gy >= 0 && gy < P.ny && gz >= 0 && gz < P.nz;
-    sm.u[e] = in ? load(gx, gy, gz, gx + (long long)P.nx * (gy + (long long)P.ny * gz)) : 0.0;
+    sm.u[e] = in ? (T)load(gx, gy, gz, gx + (long long)P.nx * (gy + (long long)P.ny * gz)) : (T)0;
   }
   __syncthreads();
   for (int e = threadIdx.x; e < SM::WZ * SM::WY * SM::WX; e += NT) {
@@ -173,9 +177,9 @@ __device__ void tile_S(const OpParams &P, const double cb[3], int ox, int oy, in
     int lz = t / SM::WY - C::HZ1;
     int gx = ox + lx, gy = oy + ly, gz = oz + lz;
     bool in = gx >= 0 && gx < P.nx && gy >= 0 && gy < P.ny && gz >= 0 && gz < P.nz;
-    double val = 0.0;
+    T val = (T)0;
     if (in)
-      val = apply_A<DIM>(P, cb, gx, gy, gz, [&](int dx, int dy, int dz) {
+      val = apply_A<DIM, T>(P, cb, gx, gy, gz, [&](int dx, int dy, int dz) {
         return sm.u[uidx<DIM>(lx + dx, ly + dy, lz + dz)];
       });
     sm.w[e] = val;
@@ -189,14 +193,14 @@ __device__ void tile_S(const OpParams &P, const double cb[3], int ox, int oy, in
     int gx = ox + lx, gy = oy + ly, gz = oz + lz;
     bool in = gx < P.nx && gy < P.ny && gz < P.nz;
     if (!in) {
-      sm.v[e] = 0.0;
+      sm.v[e] = (T)0;
       continue;
     }
-    double uc = sm.u[uidx<DIM>(lx, ly, lz)];
-    double atw = apply_AT<DIM>(P, cb, gx, gy, gz, [&](int dx, int dy, int dz) {
+    T uc = sm.u[uidx<DIM>(lx, ly, lz)];
+    T atw = apply_AT<DIM, T>(P, cb, gx, gy, gz, [&](int dx, int dy, int dz) {
       return sm.w[widx<DIM>(lx + dx, ly + dy, lz + dz)];
     });
-    store(e, gx, gy, gz, gx + (long long)P.nx * (gy + (long long)P.ny * gz), P.mass * uc + P.wgt * atw);
+    store(e, gx, gy, gz, gx + (long long)P.nx * (gy + (long long)P.ny * gz), mass * uc + wgt * atw);
   }
   __syncthreads();
 }
@@ -205,10 +209,10 @@ __device__ void tile_S(const OpParams &P, const double cb[3], int ox, int oy, in
 // j = warp + NWARP*jj < k; lanes run over the contiguous x-rows of the tile
 // (coalesced reads of each mode).  v is the tile-local vector in shared memory
 // (zero outside I and outside the grid).
-template <int DIM, int KMAX, class PhiT>
+template <int DIM, int KMAX, class PhiT, class T>
 __device__ __forceinline__ void tile_project(const OpParams &P, const PhiT *__restrict__ Phi,
                                              long long ld, int k, int ox, int oy, int oz,
-                                             const double *v_s, double (&acc)[KMAX / NWARP]) {
+                                             const T *v_s, double (&acc)[KMAX / NWARP]) {
   using C = TileCfg<DIM>;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
 #pragma unroll
@@ -216,17 +220,17 @@ __device__ __forceinline__ void tile_project(const OpParams &P, const PhiT *__re
     int j = warp + NWARP * jj;
     if (j < k) {
       const PhiT *ph = Phi + (long long)j * ld;
-      double s = 0.0;
+      T s = (T)0;
       for (int e = lane; e < C::TX * C::TY * C::TZ; e += 32) {
         int lx = e % C::TX;
         int t = e / C::TX;
         int gx = ox + lx, gy = oy + t % C::TY, gz = oz + t / C::TY;
         if (gx < P.nx && gy < P.ny && gz < P.nz) {
           long long g = gx + (long long)P.nx * (gy + (long long)P.ny * gz);
-          s = fma((double)ph[g], v_s[e], s);
+          s = fma((T)ph[g], v_s[e], s);
         }
       }
-      acc[jj] += s;
+      acc[jj] += (double)s;
     }
   }
 }

@@ -42,11 +42,13 @@ class Opts(ctypes.Structure):
                 ("max_outer", ctypes.c_int32), ("max_cg", ctypes.c_int32),
                 ("deflate", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("max_blocks", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("replace_every", ctypes.c_int32),
                 ("max_launches", ctypes.c_int64)]
 
 
 SDF_NPROF = 8
-PROFILE_NAMES = ("expand", "spmv", "update", "setup", "coarse", "active", "lambda", "other")
+PROFILE_NAMES = ("expand", "spmv", "update", "setup", "coarse", "active", "lambda", "resid")
+PREC_F64, PREC_MIXED = 0, 1
 
 
 class Profile(ctypes.Structure):

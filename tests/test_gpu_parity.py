@@ -239,3 +239,104 @@ def test_host_io_entry_point_matches_device_entry_point():
     assert np.array_equal(host["y"], dev["y"].cpu().numpy())
     assert np.array_equal(host["active"], dev["active"].cpu().numpy())
     assert np.array_equal(lam, dev["lam"].cpu().numpy())
+
+
+# ---------------------------------------------------------------------------
+# mixed precision: FP32 vectors / stencil / projections, FP32 or BF16 modes,
+# FP64 iterate, reductions, coarse operator and residual replacement.
+# Bar: active sets bit-exact, states within 1e-5 (relative L2) of the FP64
+# oracle, FP64 true residual at exit below rtol.  Iteration counts may differ
+# from the FP64 oracle by a few percent (FP32 rounding, BF16-rounded basis).
+
+def modes_tensor_as(Phi, dtype):
+    return torch.as_tensor(np.ascontiguousarray(np.asarray(Phi).T), dtype=torch.float64,
+                           device=DEV).to(dtype).contiguous()
+
+
+def compare_mixed(gpu, orc_list, y_tol=1e-5, it_rel=0.15):
+    for b, r in enumerate(orc_list):
+        st = gpu["stats"][b]
+        assert st["status"] == 0 == r["status"], (b, st)
+        act = gpu["active"][b].cpu().numpy().astype(bool)
+        assert np.array_equal(act, r["active"]), f"instance {b}: active sets differ"
+        assert st["outer_iters"] == r["outer_iters"] and st["n_active"] == r["n_active"]
+        for ig, io in zip(st["cg_iters"], r["cg_iters"]):
+            assert abs(ig - io) <= max(5, it_rel * io), (b, st["cg_iters"], r["cg_iters"])
+        for rr in st["relres"]:
+            assert rr <= 1e-8
+        y = gpu["y"][b].cpu().numpy()
+        assert np.linalg.norm(y - r["y"]) <= y_tol * np.linalg.norm(r["y"]), b
+
+
+@pytest.mark.parametrize("phi_dtype,max_blocks,replace", [("f32", 0, 100), ("bf16", 2, 100),
+                                                          ("f32", 3, 7)])
+def test_mixed_32x32_workload_matches_fp64_oracle(phi_dtype, max_blocks, replace):
+    w = W.WORKLOADS["diff2d_32"]
+    P = O.Problem(2, w.n, alpha=w.alpha)
+    Phi = O.dense_modes(P, w.k)[0]
+    insts = W.draw_instances(w)
+    psi = W.psi_vector(w)
+    orc = _orc_solves(P, [P.desired_state(i.a, i.c[:2], w.sigma)[1] for i in insts], psi, Phi)
+    G = sdf.Problem(2, w.n, alpha=w.alpha, yd_sigma=w.sigma)
+    G.set_modes(modes_tensor_as(Phi, torch.float32 if phi_dtype == "f32" else torch.bfloat16))
+    out = G.solve(t64(W.instances_array(insts)), t64(psi),
+                  sdf.default_opts(precision=sdf.PREC_MIXED, max_blocks=max_blocks,
+                                   replace_every=replace))
+    compare_mixed(out, orc)
+
+
+def test_mixed_ragged_block_kappa_and_3d_and_convection():
+    # ragged 2D with 100x contrast, BF16 modes
+    w = W.scaled(W.WORKLOADS["block2d_1024"], 70)
+    n = (70, 45)
+    kap = np.ascontiguousarray(W.kappa_field(w).reshape(70, 70)[:45, :]).ravel()
+    P = O.Problem(2, n, kappa=kap, alpha=w.alpha)
+    Phi = O.dense_modes(P, 24)[0]
+    insts = W.draw_instances(w, count=3)
+    insts[0].a = 3.4
+    psi = np.ones(P.N)
+    orc = _orc_solves(P, [P.desired_state(i.a, i.c[:2], w.sigma)[1] for i in insts], psi, Phi)
+    G = sdf.Problem(2, n, alpha=w.alpha, kappa=kap, yd_sigma=w.sigma)
+    G.set_modes(modes_tensor_as(Phi, torch.bfloat16))
+    out = G.solve(t64(W.instances_array(insts)), t64(psi),
+                  sdf.default_opts(precision=sdf.PREC_MIXED, max_blocks=4))
+    compare_mixed(out, orc)
+    # 3D, FP32 modes
+    n3 = (14, 12, 10)
+    P3 = O.Problem(3, n3, alpha=1e-4)
+    Phi3 = O.dense_modes(P3, 10)[0]
+    w3 = W.scaled(W.WORKLOADS["diff3d_128"], 12, instances=3)
+    i3 = W.draw_instances(w3, count=3)
+    i3[1].a = 4.0
+    orc3 = _orc_solves(P3, [P3.desired_state(i.a, i.c, w3.sigma)[1] for i in i3], np.ones(P3.N), Phi3)
+    G3 = sdf.Problem(3, n3, alpha=1e-4, yd_sigma=w3.sigma)
+    G3.set_modes(modes_tensor_as(Phi3, torch.float32))
+    out3 = G3.solve(t64(W.instances_array(i3)), t64(np.ones(P3.N)),
+                    sdf.default_opts(precision=sdf.PREC_MIXED, max_blocks=2))
+    compare_mixed(out3, orc3)
+    # convection with per-instance velocities, FP32 modes
+    wc = W.scaled(W.WORKLOADS["convdiff2d_512"], 48)
+    ic = W.draw_instances(wc, count=4)
+    Phic = O.analytic_modes(2, 48, 12, wc.alpha, diff_scale=wc.diff_scale)[0]
+    orcc = []
+    for i in ic:
+        Pc = O.Problem(2, 48, diff_scale=wc.diff_scale, b=np.array(i.b[:2]), alpha=wc.alpha)
+        orcc.append(Pc.solve(Pc.desired_state(i.a, i.c[:2], wc.sigma)[1], np.ones(wc.N), Phic))
+    Gc = sdf.Problem(2, 48, alpha=wc.alpha, diff_scale=wc.diff_scale, convection=True,
+                     yd_sigma=wc.sigma)
+    Gc.set_modes(modes_tensor_as(Phic, torch.float32))
+    outc = Gc.solve(t64(W.instances_array(ic)), t64(np.ones(wc.N)),
+                    sdf.default_opts(precision=sdf.PREC_MIXED))
+    compare_mixed(outc, orcc)
+
+
+def test_mixed_rejects_fp64_modes_and_fp64_rejects_bf16():
+    G = sdf.Problem(2, 16, alpha=1e-4, yd_sigma=0.1)
+    phi, _ = G.analytic_modes(4)
+    G.set_modes(phi)
+    with pytest.raises(sdf.SdfError):
+        G.solve(t64([inst_row(1.0, (0.5, 0.5))]), t64(np.ones(256)),
+                sdf.default_opts(precision=sdf.PREC_MIXED))
+    G.set_modes(phi.to(torch.bfloat16).contiguous())
+    with pytest.raises(sdf.SdfError):
+        G.solve(t64([inst_row(1.0, (0.5, 0.5))]), t64(np.ones(256)), sdf.default_opts())
