@@ -566,7 +566,8 @@ __global__ void __launch_bounds__(NT) k_expand(const PhiT *Phi, long long ld, in
   for (long long g = (long long)gblk * NT + threadIdx.x; g < N; g += (long long)GX * NT) {
     V v = (V)0;
     if (!mk[g]) {
-      v = gam * db[g] * rb[g] + bet * pb[g];
+      v = gam * db[g] * rb[g];
+      if (bet != (V)0) v += bet * pb[g];  // p is not read on the first pass (never written)
       if (defl) {
         V s0 = (V)0, s1 = (V)0;
         int j = 0;
