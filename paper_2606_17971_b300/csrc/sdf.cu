@@ -48,6 +48,7 @@ namespace {
 struct InstState {
   double rho, sigma, alpha, beta, gamma, csign;
   double rnorm2, bnorm2;
+  double rho_prev;     // rho before the last CG iteration (correction-pass beta)
   int32_t phase;       // 1: the coarse-correction pass is the next K_B/K_C
   int32_t cg_done;     // current inner solve finished (or failed)
   int32_t outer_done;  // instance finished
@@ -674,9 +675,17 @@ __global__ void __launch_bounds__(NT) k_update(OpParams P, const double *inst, c
   const V *qb = q + b * N, *pb = p + b * N;
   const V *db = dinv + (P.convection ? b * N : 0);
   double rho = 0.0, rr = 0.0;
-  double acc[KMAX / NWARP];
+  // FP64 path: warp-per-mode projection of the tile (tile_project).
+  // FP32 path: every thread accumulates Phi_j(g) v(g) for its own nodes and
+  // all modes in registers (coalesced, many independent loads in flight).
+  constexpr bool kThreadProj = sizeof(V) == sizeof(float);
+  constexpr int NACC = kThreadProj ? KMAX : KMAX / NWARP;
+  double acc[kThreadProj ? 1 : KMAX / NWARP];
+  float accf[kThreadProj ? KMAX : 1];
 #pragma unroll
-  for (int a = 0; a < KMAX / NWARP; ++a) acc[a] = 0.0;
+  for (int a = 0; a < (kThreadProj ? 1 : KMAX / NWARP); ++a) acc[a] = 0.0;
+#pragma unroll
+  for (int a = 0; a < (kThreadProj ? KMAX : 1); ++a) accf[a] = 0.0f;
   const long long T = num_tiles<DIM>(P.nx, P.ny, P.nz);
   for (long long t = gblk; t < T; t += GX) {
     int ox, oy, oz;
@@ -699,23 +708,37 @@ __global__ void __launch_bounds__(NT) k_update(OpParams P, const double *inst, c
           rho = fma((double)rn, (double)z, rho);
           rr = fma((double)rn, (double)rn, rr);
           sm.v[e] = su;
+          if constexpr (kThreadProj) {
+            if (defl) {
+#pragma unroll
+              for (int j = 0; j < KMAX; ++j)
+                if (j < k) accf[j] = fmaf((float)Phi[(long long)j * ld + g], (float)su, accf[j]);
+            }
+          }
         });
-    if (defl) {
-      tile_project<DIM, KMAX>(P, Phi, ld, k, ox, oy, oz, sm.v, acc);
-      __syncthreads();
+    if constexpr (!kThreadProj) {
+      if (defl) {
+        tile_project<DIM, KMAX>(P, Phi, ld, k, ox, oy, oz, sm.v, acc);
+        __syncthreads();
+      }
     }
   }
+  (void)NACC;
   rho = block_sum(rho, red);
   rr = block_sum(rr, red);
   const int F = KMAX + 2;
   double *pbk = part + ((long long)b * GX + gblk) * F;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   if (defl) {
+    if constexpr (kThreadProj) {
+      block_sum_modes<KMAX>(accf, k, pbk + 2, scratch);
+    } else {
 #pragma unroll
-    for (int a = 0; a < KMAX / NWARP; ++a) {
-      double sacc = warp_sum(acc[a]);
-      int j = warp + NWARP * a;
-      if (lane == 0 && j < k) pbk[2 + j] = sacc;
+      for (int a = 0; a < KMAX / NWARP; ++a) {
+        double sacc = warp_sum(acc[a]);
+        int j = warp + NWARP * a;
+        if (lane == 0 && j < k) pbk[2 + j] = sacc;
+      }
     }
   }
   if (threadIdx.x == 0) {
@@ -742,7 +765,10 @@ __global__ void __launch_bounds__(NT) k_update(OpParams P, const double *inst, c
       S.cg_done = 1;
     } else {
       if (conv) S.await = 1;
-      S.beta = S.phase == 1 ? 0.0 : rho_new / S.rho;
+      // A correction pass (phase 2) replaces the residual of the iteration
+      // that preceded it, so its beta divides by that iteration's old rho.
+      S.beta = S.phase == 1 ? 0.0 : rho_new / (S.phase == 2 ? S.rho_prev : S.rho);
+      if (S.phase != 2) S.rho_prev = S.rho;
       S.rho = rho_new;
       S.gamma = 1.0;
       S.csign = 1.0;
@@ -768,7 +794,6 @@ __global__ void __launch_bounds__(NT) k_resid(OpParams P, const double *inst, co
                                               const double *x, V *r, double *part, int *cnt,
                                               Ctrl *ctrl, int GX, double rtol2) {
   __shared__ TileSmem<DIM, double> sm;
-  __shared__ V vs[TileSmem<DIM, double>::TILE];
   __shared__ double red[NWARP];
   __shared__ double scratch[NT];
   __shared__ double res[SDF_MAX_K + 2];
@@ -784,48 +809,35 @@ __global__ void __launch_bounds__(NT) k_resid(OpParams P, const double *inst, co
   const double *xb = x + b * N, *bb = b64 + b * N;
   V *rb = r + b * N;
   double rr = 0.0;
-  double acc[KMAX / NWARP];
+  float accf[KMAX];
 #pragma unroll
-  for (int a = 0; a < KMAX / NWARP; ++a) acc[a] = 0.0;
+  for (int a = 0; a < KMAX; ++a) accf[a] = 0.0f;
   const long long T = num_tiles<DIM>(P.nx, P.ny, P.nz);
   for (long long t = gblk; t < T; t += GX) {
     int ox, oy, oz;
     tile_origin<DIM>(P, t, ox, oy, oz);
     tile_S<DIM, double>(
         P, cb, ox, oy, oz, sm, [&](int, int, int, long long g) { return xb[g]; },
-        [&](int e, int, int, int, long long g, double su) {
+        [&](int, int, int, int, long long g, double su) {
           if (mk[g]) {
-            vs[e] = (V)0;
             rb[g] = (V)0;
             return;
           }
           double rt = bb[g] - su;
           rb[g] = (V)rt;
           rr = fma(rt, rt, rr);
-          vs[e] = (V)rt;
+          if (defl) {
+            const float rf = (float)rt;
+#pragma unroll
+            for (int j = 0; j < KMAX; ++j)
+              if (j < k) accf[j] = fmaf((float)Phi[(long long)j * ld + g], rf, accf[j]);
+          }
         });
-    // tile_S leaves vs zero only where it wrote it; clear the out-of-grid part
-    for (int e = threadIdx.x; e < TileSmem<DIM, double>::TILE; e += NT) {
-      int lx = e % TileCfg<DIM>::TX, tt = e / TileCfg<DIM>::TX;
-      if (ox + lx >= P.nx || oy + tt % TileCfg<DIM>::TY >= P.ny || oz + tt / TileCfg<DIM>::TY >= P.nz)
-        vs[e] = (V)0;
-    }
-    __syncthreads();
-    if (defl) tile_project<DIM, KMAX>(P, Phi, ld, k, ox, oy, oz, vs, acc);
-    __syncthreads();
   }
   rr = block_sum(rr, red);
   const int F = KMAX + 2;
   double *pbk = part + ((long long)b * GX + gblk) * F;
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  if (defl) {
-#pragma unroll
-    for (int a = 0; a < KMAX / NWARP; ++a) {
-      double sacc = warp_sum(acc[a]);
-      int j = warp + NWARP * a;
-      if (lane == 0 && j < k) pbk[2 + j] = sacc;
-    }
-  }
+  if (defl) block_sum_modes<KMAX>(accf, k, pbk + 2, scratch);
   if (threadIdx.x == 0) {
     pbk[0] = 0.0;
     pbk[1] = rr;
@@ -1175,7 +1187,7 @@ sdf_status solve_impl(sdf_problem *p, const double *inst, int B, const double *p
         sdf_status e = triple(pp, timed && rep == 0);
         if (e != SDF_OK) return e;
       }
-      if (mixed) {  // FP64 residual replacement + coarse correction pass
+      if constexpr (mixed != 0) {  // FP64 residual replacement + coarse correction pass
         if (timed) CK(cudaEventRecord(p->ev[4], s));
         k_resid<DIM, KMAX, PhiT, V><<<gT, NT, 0, s>>>(P, inst, Phi, ld, k, st, mask, b64, x,
                                                       rbuf[par], part, cnt, ctrl, L.gx, rtol2);

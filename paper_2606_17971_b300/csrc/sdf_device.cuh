@@ -253,6 +253,35 @@ __device__ __forceinline__ double block_sum(double v, double *red /* NWARP doubl
   return s;
 }
 
+// Block reduction of per-thread mode accumulators: out[j] = sum over the
+// block's threads of acc[j], j < k (FP32 per thread, FP64 across threads).
+// scratch: NT doubles of shared memory.
+template <int KMAX>
+__device__ __forceinline__ void block_sum_modes(const float (&acc)[KMAX], int k, double *out,
+                                                double *scratch) {
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+#pragma unroll
+  for (int j0 = 0; j0 < KMAX; j0 += 32) {
+    // lane l of each warp ends with the warp's sum for mode j0 + l
+    double mine = 0.0;
+#pragma unroll
+    for (int l = 0; l < 32; ++l) {
+      double v = (j0 + l < KMAX) ? (double)acc[j0 + l < KMAX ? j0 + l : 0] : 0.0;
+      v = warp_sum(v);
+      if (lane == l) mine = v;
+    }
+    scratch[warp * 32 + lane] = mine;
+    __syncthreads();
+    if (threadIdx.x < 32 && j0 + threadIdx.x < k) {
+      double s = 0.0;
+#pragma unroll
+      for (int w = 0; w < NWARP; ++w) s += scratch[w * 32 + threadIdx.x];
+      out[j0 + threadIdx.x] = s;
+    }
+    __syncthreads();
+  }
+}
+
 // Last-block detection: returns true in exactly one block per counter after
 // all `nblocks` blocks have published their partials.
 __device__ __forceinline__ bool last_block(int *counter, int nblocks, int *flag_smem) {
