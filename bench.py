@@ -63,8 +63,8 @@ def stencil_flops(dim):
 
 def kernel_work(name, dim, k, phi_bytes, vec_bytes=8):
     """(flops, bytes) per dof per launch of the three CG kernels."""
-    if name == "update":   # r,q,p,x,dinv read; x,r written; Phi read; S z; Phi^T S z
-        return 2 * k + stencil_flops(dim) + 9, 7 * vec_bytes + 1 + k * phi_bytes
+    if name == "update":   # r,q,p,dinv read, r written; x (FP64) read+written; Phi; S z; Phi^T S z
+        return 2 * k + stencil_flops(dim) + 9, 5 * vec_bytes + 16 + 1 + k * phi_bytes
     if name == "expand":   # r,dinv,p read; p written; Phi read; Phi c
         return 2 * k + 4, 4 * vec_bytes + 1 + k * phi_bytes
     if name == "spmv":     # p read, q written
@@ -143,12 +143,12 @@ class ClockSampler:
 
 # ---------------------------------------------------------------------------
 
-def make_problem(w, sdf, device):
+def make_problem(w, sdf, device, phi_dtype=0):
     from paper_2606_17971_b300 import workloads as W
     kap = W.kappa_field(w)
     G = sdf.Problem(w.dim, w.n, alpha=w.alpha, kappa=kap, diff_scale=w.diff_scale,
                     convection=w.convection, yd_sigma=w.sigma, device=device)
-    phi, _ = G.analytic_modes(w.k)  # closed-form reference modes on the GPU (Sec. 2.2.7)
+    phi, _ = G.analytic_modes(w.k, phi_dtype)  # closed-form reference modes on the GPU (Sec. 2.2.7)
     G.set_modes(phi)
     return G, phi
 
@@ -222,6 +222,10 @@ def main():
     ap.add_argument("--workload", default="diff3d_128")
     ap.add_argument("--n", type=int, default=0, help="grid override (profiling captures only)")
     ap.add_argument("--max-cg", type=int, default=0, help="CG cap (profiling captures only)")
+    ap.add_argument("--path", default="plain", choices=["plain", "mixed"],
+                    help="plain: FP64 A-DEF2 per instance; mixed: FP32/BF16 with FP64 refinement")
+    ap.add_argument("--phi", default="bf16", choices=["f32", "bf16"], help="mode storage (mixed)")
+    ap.add_argument("--batch", type=int, default=1, help="instances per step and GPU")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -245,15 +249,17 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    G, phi = make_problem(w, sdf, dev)
-    B = 1
+    mixed = args.path == "mixed"
+    phi_dt = (sdf.BF16 if args.phi == "bf16" else sdf.F32) if mixed else sdf.F64
+    G, phi = make_problem(w, sdf, dev, phi_dt)
+    B = args.batch
     steps, warm = args.steps, args.warmup
     insts = W.draw_instances(w, count=(steps + warm) * B * world)
     mine = insts[rank::world]
     inst_t = [torch.as_tensor(W.instances_array(mine[i * B:(i + 1) * B]), device=dev)
               for i in range(steps + warm)]
     psi = torch.full((w.N,), w.psi, dtype=torch.float64, device=dev)
-    opts = sdf.default_opts(check_every=128)
+    opts = sdf.default_opts(check_every=128, precision=sdf.PREC_MIXED if mixed else sdf.PREC_F64)
     if args.max_cg:
         opts.max_cg = args.max_cg
     out = {"y": torch.empty((B, w.N), dtype=torch.float64, device=dev), "lam": None,
@@ -316,34 +322,45 @@ def main():
     names = ("expand", "spmv", "update")
     tot = {n: (prof["mean_ms"][n] or 0.0) * prof["samples"][n] for n in names}
     dom = max(names, key=lambda n: tot[n])
-    flops_dof, bytes_dof = kernel_work(dom, w.dim, w.k, 8)
+    phi_bytes = 8 if not mixed else (2 if args.phi == "bf16" else 4)
+    flops_dof, bytes_dof = kernel_work(dom, w.dim, w.k, phi_bytes, 4 if mixed else 8)
     units = w.N * B
     mean_s = prof["mean_ms"][dom] * 1e-3
-    achieved = flops_dof * units / mean_s / 1e12
     hbm = peaks().get("hbm_gbs")
-    roof = {"kernel": f"k_{dom}", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-            "traffic": profile_traffic(dom, w.name),
-            "peak_source": "nominal FP64 of the profiling recipe (1.25 TFLOP/s; probe measured 1.20)",
+    if mixed:  # FP32 arithmetic: the streaming kernels are HBM-bound by design
+        achieved = bytes_dof * units / mean_s / 1e9
+        roof = {"kernel": f"k_{dom}", "bound": "hbm", "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": profile_traffic(dom + "_mixed", w.name),
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+    else:
+        achieved = flops_dof * units / mean_s / 1e12
+        roof = {"kernel": f"k_{dom}", "bound": "alu", "achieved": achieved,
+                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": profile_traffic(dom, w.name),
+                "peak_source": "nominal FP64 of the profiling recipe (1.25 TFLOP/s; probe measured 1.20)"}
+    roof.update({
             "algorithmic_flops_per_launch": flops_dof * units,
             "algorithmic_bytes_per_launch": bytes_dof * units,
             "hbm_gbs_at_algorithmic_bytes": bytes_dof * units / mean_s / 1e9,
             "hbm_peak_gbs": hbm, "mean_launch_ms": prof["mean_ms"][dom],
             "timed_launches": prof["samples"][dom],
-            "kernel_mean_ms": {n: prof["mean_ms"][n] for n in names}}
+            "kernel_mean_ms": {n: prof["mean_ms"][n] for n in names + ("resid",)}})
 
     cg = [sum(s["cg_iters"]) for s in stats]
     outer = [s["outer_iters"] for s in stats]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
         "warmup": warm, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
         "config": {"workload": w.name, "grid": [w.n] * w.dim, "k": w.k, "alpha": w.alpha,
                    "instances_per_step": B * world, "batch_per_gpu": B,
-                   "path": "plain FP64 A-DEF2 per instance (primal active-set loop)",
+                   "path": ("mixed FP32/%s A-DEF2, FP64 x, reductions and residual replacement"
+                            % args.phi if mixed else "plain FP64 A-DEF2 per instance")
+                           + " (primal active-set loop)",
                    "modes": "closed-form sines on the GPU (Sec. 2.2.7)",
                    "l2": "inputs larger than L2: Phi is %.2f GB, read twice per CG iteration"
-                         % (w.N * w.k * 8 / 1e9),
+                         % (w.N * w.k * phi_bytes / 1e9),
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
         "cg_iters_per_instance": float(np.mean(cg)), "outer_iters_per_instance": float(np.mean(outer)),
         "statuses": sorted(set(s["status"] for s in stats)),

