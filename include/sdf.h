@@ -260,10 +260,11 @@ sdf_status sdf_project_noalloc(sdf_problem *p, const uint8_t *active_dev, const 
  *   5 active   active-set update
  *   6 lambda   multiplier
  *   7 resid    mixed path: FP64 residual replacement
+ *   8 project  mixed path: projection GEMM Phi^T [v_1..v_B] and coarse GEMV
  * ms[i] / samples[i] is the mean duration of kernel i over the launches timed
  * with opts.profile = 1; launches counts every kernel the library enqueued
  * since the last reset (timed or not). */
-#define SDF_NPROF 8
+#define SDF_NPROF 9
 typedef struct {
   double ms[SDF_NPROF];
   int64_t samples[SDF_NPROF];

@@ -73,8 +73,8 @@ struct Ctrl {       // grid-wide control words (device)
 
 struct Layout {
   size_t x, b64, r, r2, p, q, w, dinv, mask, W, Einv, Eraw, G, coarse, part, gpart, state, cnt,
-      ctrl, total;
-  int gx, gxa, gxg;
+      ctrl, v, cvec, ppart, total;
+  int gx, gxa, gxg, gxp, nb, bpad;
 };
 
 inline size_t al(size_t v) { return (v + 255) & ~size_t(255); }
@@ -783,35 +783,28 @@ __global__ void __launch_bounds__(NT) k_update(OpParams P, const double *inst, c
 }
 
 // FP64 residual replacement of the mixed path: r = b - S_II x with the FP64
-// stencil on the FP64 iterate, ||r||^2 and t = Phi_I^T r (for the coarse
-// correction x += Phi E_raw^-1 Phi_I^T r that follows).  The last block
-// declares convergence on this true residual, or arms the correction pass
-// (phase 2).  r is written in place: this kernel reads x, not r.
-template <int DIM, int KMAX, class PhiT, class V>
-__global__ void __launch_bounds__(NT) k_resid(OpParams P, const double *inst, const PhiT *Phi,
-                                              long long ld, int k, InstState *st,
+// stencil on the FP64 iterate and ||r||^2.  The last block declares
+// convergence on this true residual, or arms the coarse correction pass
+// (phase 2: w = Phi E_raw^-1 Phi_I^T r, alpha = 1) whose projection the GEMM
+// computes from the new r.  r is written in place: this kernel reads x, not r.
+template <int DIM>
+__global__ void __launch_bounds__(NT) k_resid(OpParams P, const double *inst, InstState *st,
                                               const uint8_t *mask, const double *b64,
-                                              const double *x, V *r, double *part, int *cnt,
+                                              const double *x, float *r, double *part, int *cnt,
                                               Ctrl *ctrl, int GX, double rtol2) {
   __shared__ TileSmem<DIM, double> sm;
   __shared__ double red[NWARP];
-  __shared__ double scratch[NT];
-  __shared__ double res[SDF_MAX_K + 2];
   __shared__ int flag;
   const int b = blockIdx.x, gblk = blockIdx.y;
   InstState &S = st[b];
   if (S.outer_done || S.cg_done) return;
   const long long N = P.N;
-  const int defl = S.deflate;
   double cb[3];
   inst_cb(P, inst + 7 * b, cb);
   const uint8_t *mk = mask + b * N;
   const double *xb = x + b * N, *bb = b64 + b * N;
-  V *rb = r + b * N;
+  float *rb = r + b * N;
   double rr = 0.0;
-  float accf[KMAX];
-#pragma unroll
-  for (int a = 0; a < KMAX; ++a) accf[a] = 0.0f;
   const long long T = num_tiles<DIM>(P.nx, P.ny, P.nz);
   for (long long t = gblk; t < T; t += GX) {
     int ox, oy, oz;
@@ -820,35 +813,21 @@ __global__ void __launch_bounds__(NT) k_resid(OpParams P, const double *inst, co
         P, cb, ox, oy, oz, sm, [&](int, int, int, long long g) { return xb[g]; },
         [&](int, int, int, int, long long g, double su) {
           if (mk[g]) {
-            rb[g] = (V)0;
+            rb[g] = 0.0f;
             return;
           }
-          double rt = bb[g] - su;
-          rb[g] = (V)rt;
+          const double rt = bb[g] - su;
+          rb[g] = (float)rt;
           rr = fma(rt, rt, rr);
-          if (defl) {
-            const float rf = (float)rt;
-#pragma unroll
-            for (int j = 0; j < KMAX; ++j)
-              if (j < k) accf[j] = fmaf((float)Phi[(long long)j * ld + g], rf, accf[j]);
-          }
         });
   }
   rr = block_sum(rr, red);
-  const int F = KMAX + 2;
-  double *pbk = part + ((long long)b * GX + gblk) * F;
-  if (defl) block_sum_modes<KMAX>(accf, k, pbk + 2, scratch);
-  if (threadIdx.x == 0) {
-    pbk[0] = 0.0;
-    pbk[1] = rr;
-  }
+  if (threadIdx.x == 0) part[(long long)b * GX + gblk] = rr;
   if (!last_block(cnt + b * NCNT + CNT_UPDATE, GX, &flag)) return;
-  reduce_fields(part + (long long)b * GX * F, GX, F, defl ? 2 + k : 2, res, scratch);
-  if (defl)
-    for (int j = threadIdx.x; j < k; j += NT) S.t[j] = res[2 + j];
   if (threadIdx.x == 0) {
+    double rn2 = 0.0;
+    for (int g = 0; g < GX; ++g) rn2 += __ldcg(part + (long long)b * GX + g);
     cnt[b * NCNT + CNT_UPDATE] = 0;
-    double rn2 = res[1];
     S.rnorm2 = rn2;
     if (!isfinite(rn2)) {
       S.stats.status = SDF_ERR_NONFINITE;
@@ -857,7 +836,7 @@ __global__ void __launch_bounds__(NT) k_resid(OpParams P, const double *inst, co
       S.cg_done = 1;
     } else {
       S.await = 0;
-      S.phase = 2;  // coarse correction pass: w = Phi E_raw^-1 t, alpha = 1
+      S.phase = 2;
       S.gamma = 0.0;
       S.beta = 0.0;
       S.csign = -1.0;
@@ -867,6 +846,282 @@ __global__ void __launch_bounds__(NT) k_resid(OpParams P, const double *inst, co
       S.stats.relres[S.outer] = S.bnorm2 > 0 ? sqrt(rn2 / S.bnorm2) : 0.0;
       atomicSub(&ctrl->running, 1);
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Mixed path, shared-Phi kernels.  The per-instance stencil work (k_spmv,
+// k_update_v) runs on tiles; everything that reads Phi reads it once per
+// launch for all instances of the batch: the expansion keeps one node's k mode
+// values in registers and applies them to every instance, and the projection
+// is a tall-skinny GEMM T = Phi^T [v_1 ... v_B] over shared-memory chunks.
+
+// Instance b takes part in the current pass.
+__device__ __forceinline__ bool inst_running(const InstState &S) {
+  return !(S.outer_done || S.cg_done || (S.await && S.phase == 0));
+}
+
+// p_b = mask_I (gamma_b D^-1 r_b - Phi c_b + beta_b p_b) for every running
+// instance.  Dynamic shared memory: c (B x KMAX floats), gamma, beta, flags.
+template <int KMAX, class PhiT>
+__global__ void __launch_bounds__(NT) k_expand_b(const PhiT *__restrict__ Phi, long long ld, int k,
+                                                 long long N, int B, const InstState *st,
+                                                 const float *cvec, const uint8_t *mask,
+                                                 const float *r, const float *dinv,
+                                                 int dinv_per_inst, float *p) {
+  extern __shared__ float dsm[];
+  float *cs = dsm;
+  float *gam = cs + (size_t)B * KMAX;
+  float *bet = gam + B;
+  int *act = (int *)(bet + B);
+  for (int b = threadIdx.x; b < B; b += NT) {
+    const InstState &S = st[b];
+    act[b] = inst_running(S) ? (1 | (S.deflate ? 2 : 0)) : 0;
+    gam[b] = (float)S.gamma;
+    bet[b] = (float)S.beta;
+  }
+  for (int e = threadIdx.x; e < B * KMAX; e += NT) cs[e] = cvec[e];
+  __syncthreads();
+  for (long long g = (long long)blockIdx.x * NT + threadIdx.x; g < N;
+       g += (long long)gridDim.x * NT) {
+    float ph[KMAX];
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) ph[j] = j < k ? (float)Phi[(long long)j * ld + g] : 0.0f;
+    for (int b = 0; b < B; ++b) {
+      const int a = act[b];
+      if (!a) continue;
+      const long long gb = (long long)b * N + g;
+      float v = 0.0f;
+      if (!mask[gb]) {
+        const float db = dinv[dinv_per_inst ? gb : g];
+        v = gam[b] * db * r[gb];
+        if (bet[b] != 0.0f) v = fmaf(bet[b], p[gb], v);
+        if (a & 2) {
+          const float *cb = cs + (size_t)b * KMAX;
+          float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+          for (int j = 0; j < KMAX; j += 2) {
+            s0 = fmaf(ph[j], cb[j], s0);
+            s1 = fmaf(ph[j + 1], cb[j + 1], s1);
+          }
+          v -= s0 + s1;
+        }
+      }
+      p[gb] = v;
+    }
+  }
+}
+
+// Stencil part of the CG update (mixed path): x += alpha p (FP64), r -= alpha q,
+// z = D^-1 r, v = S_II z (written for the projection GEMM), rho = (r, z),
+// ||r||^2 with FP32 products summed in FP64.  The last block applies the
+// convergence / beta logic of k_update (mixed = 1).
+template <int DIM>
+__global__ void __launch_bounds__(NT) k_update_v(OpParams P, const double *inst, InstState *st,
+                                                 const uint8_t *mask, const float *r_in,
+                                                 float *r_out, const float *q, const float *p,
+                                                 double *x, const float *dinv, float *v,
+                                                 double *part, int *cnt, Ctrl *ctrl, int GX,
+                                                 double rtol2, int max_cg) {
+  __shared__ TileSmem<DIM, float> sm;
+  __shared__ double red[NWARP];
+  __shared__ int flag;
+  const int b = blockIdx.x, gblk = blockIdx.y;
+  InstState &S = st[b];
+  if (!inst_running(S)) return;
+  const long long N = P.N;
+  const double alpha64 = S.alpha;
+  const float alpha = (float)alpha64;
+  double cb[3];
+  inst_cb(P, inst + 7 * b, cb);
+  const uint8_t *mk = mask + b * N;
+  const float *rb = r_in + b * N, *qb = q + b * N, *pb = p + b * N;
+  float *rw = r_out + b * N, *vb = v + b * N;
+  double *xb = x + b * N;
+  const float *db = dinv + (P.convection ? b * N : 0);
+  double rho = 0.0, rr = 0.0;
+  const long long T = num_tiles<DIM>(P.nx, P.ny, P.nz);
+  for (long long t = gblk; t < T; t += GX) {
+    int ox, oy, oz;
+    tile_origin<DIM>(P, t, ox, oy, oz);
+    tile_S<DIM, float>(
+        P, cb, ox, oy, oz, sm,
+        [&](int, int, int, long long g) { return mk[g] ? 0.0f : db[g] * (rb[g] - alpha * qb[g]); },
+        [&](int, int, int, int, long long g, float su) {
+          if (mk[g]) {
+            rw[g] = 0.0f;
+            vb[g] = 0.0f;
+            return;
+          }
+          const float rn = rb[g] - alpha * qb[g];
+          const float z = db[g] * rn;
+          xb[g] = fma(alpha64, (double)pb[g], xb[g]);
+          rw[g] = rn;
+          rho += (double)(rn * z);
+          rr += (double)(rn * rn);
+          vb[g] = su;
+        });
+  }
+  rho = block_sum(rho, red);
+  rr = block_sum(rr, red);
+  if (threadIdx.x == 0) {
+    part[((long long)b * GX + gblk) * 2 + 0] = rho;
+    part[((long long)b * GX + gblk) * 2 + 1] = rr;
+  }
+  if (!last_block(cnt + b * NCNT + CNT_UPDATE, GX, &flag)) return;
+  if (threadIdx.x == 0) {
+    double rho_new = 0.0, rn2 = 0.0;
+    for (int g = 0; g < GX; ++g) {
+      rho_new += __ldcg(part + ((long long)b * GX + g) * 2);
+      rn2 += __ldcg(part + ((long long)b * GX + g) * 2 + 1);
+    }
+    cnt[b * NCNT + CNT_UPDATE] = 0;
+    if (S.phase == 0) S.iters += 1;
+    S.rnorm2 = rn2;
+    const bool conv = rn2 <= rtol2 * S.bnorm2;
+    if (!isfinite(rho_new) || !isfinite(rn2)) {
+      S.stats.status = SDF_ERR_NONFINITE;
+      S.cg_done = 1;
+    } else if (S.iters >= max_cg) {
+      S.stats.status = SDF_ERR_CG_MAXIT;
+      S.cg_done = 1;
+    } else {
+      if (conv) S.await = 1;
+      S.beta = S.phase == 1 ? 0.0 : rho_new / (S.phase == 2 ? S.rho_prev : S.rho);
+      if (S.phase != 2) S.rho_prev = S.rho;
+      S.rho = rho_new;
+      S.gamma = 1.0;
+      S.csign = 1.0;
+      S.phase = 0;
+    }
+    if (S.cg_done) {
+      S.stats.cg_iters[S.outer] = S.iters;
+      S.stats.relres[S.outer] = S.bnorm2 > 0 ? sqrt(rn2 / S.bnorm2) : 0.0;
+      atomicSub(&ctrl->running, 1);
+    }
+  }
+}
+
+// Projection GEMM: part[gblk][b][j] = sum over block gblk's node range of
+// Phi_j(g) v_b(g), for NB instances per block (NB = 1: threads split modes x
+// node lanes; NB >= 16: threads split modes x instances).  FP32 products and
+// chunk sums, FP64 accumulation across chunks.  v is zero on each instance's
+// active set.
+template <int KMAX, int NB, class PhiT>
+__global__ void __launch_bounds__(NT) k_proj_gemm(const PhiT *__restrict__ Phi, long long ld, int k,
+                                                  long long N, int B, const InstState *st,
+                                                  const float *v, double *part, int Bpad) {
+  constexpr int CH = 32;
+  constexpr int MT = KMAX / 16;
+  constexpr int NT_N = NB >= 16 ? NB / 16 : 1;
+  __shared__ __align__(16) float Ps[CH][KMAX + 1];
+  __shared__ float Vs[CH][NB + 1];
+  __shared__ int run[NB];
+  const int ib = blockIdx.x * NB, gblk = blockIdx.y, GXp = gridDim.y;
+  for (int e = threadIdx.x; e < NB; e += NT) {
+    int bb = ib + e;
+    run[e] = (bb < B && !st[bb].outer_done && !st[bb].cg_done && st[bb].deflate) ? 1 : 0;
+  }
+  __syncthreads();
+  // contiguous node range of this block, in whole chunks
+  const long long nch = (N + CH - 1) / CH;
+  const long long c_lo = nch * gblk / GXp, c_hi = nch * (gblk + 1) / GXp;
+  const int ti = threadIdx.x / 16, tj = threadIdx.x % 16;
+  double acc64[MT][NT_N];
+#pragma unroll
+  for (int a = 0; a < MT; ++a)
+#pragma unroll
+    for (int c = 0; c < NT_N; ++c) acc64[a][c] = 0.0;
+  for (long long ch = c_lo; ch < c_hi; ++ch) {
+    const long long g0 = ch * CH;
+    for (int e = threadIdx.x; e < CH * KMAX; e += NT) {
+      int c = e % CH, j = e / CH;
+      long long g = g0 + c;
+      Ps[c][j] = (j < k && g < N) ? (float)Phi[(long long)j * ld + g] : 0.0f;
+    }
+    for (int e = threadIdx.x; e < CH * NB; e += NT) {
+      int c = e % CH, bq = e / CH;
+      long long g = g0 + c;
+      Vs[c][bq] = (run[bq] && g < N) ? v[(long long)(ib + bq) * N + g] : 0.0f;
+    }
+    __syncthreads();
+    float acc[MT][NT_N];
+#pragma unroll
+    for (int a = 0; a < MT; ++a)
+#pragma unroll
+      for (int c = 0; c < NT_N; ++c) acc[a][c] = 0.0f;
+    if constexpr (NB >= 16) {
+#pragma unroll 8
+      for (int c = 0; c < CH; ++c) {
+        float pa[MT], vb[NT_N];
+#pragma unroll
+        for (int a = 0; a < MT; ++a) pa[a] = Ps[c][ti + 16 * a];
+#pragma unroll
+        for (int q = 0; q < NT_N; ++q) vb[q] = Vs[c][tj + 16 * q];
+#pragma unroll
+        for (int a = 0; a < MT; ++a)
+#pragma unroll
+          for (int q = 0; q < NT_N; ++q) acc[a][q] = fmaf(pa[a], vb[q], acc[a][q]);
+      }
+    } else {  // NB == 1: lane tj takes nodes tj, tj + 16 of the chunk
+#pragma unroll
+      for (int c = tj; c < CH; c += 16) {
+        const float vv = Vs[c][0];
+#pragma unroll
+        for (int a = 0; a < MT; ++a) acc[a][0] = fmaf(Ps[c][ti + 16 * a], vv, acc[a][0]);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < MT; ++a)
+#pragma unroll
+      for (int q = 0; q < NT_N; ++q) acc64[a][q] += (double)acc[a][q];
+    __syncthreads();
+  }
+  if constexpr (NB >= 16) {
+#pragma unroll
+    for (int a = 0; a < MT; ++a)
+#pragma unroll
+      for (int q = 0; q < NT_N; ++q) {
+        int j = ti + 16 * a, bb = ib + tj + 16 * q;
+        if (bb < Bpad) part[((long long)gblk * Bpad + bb) * KMAX + j] = acc64[a][q];
+      }
+  } else {  // reduce the 16 node lanes through shared memory (reuse Ps)
+    double *red = reinterpret_cast<double *>(&Ps[0][0]);  // KMAX*16 doubles fit in Ps
+#pragma unroll
+    for (int a = 0; a < MT; ++a) red[(ti + 16 * a) * 16 + tj] = acc64[a][0];
+    __syncthreads();
+    for (int j = threadIdx.x; j < KMAX; j += NT) {
+      double sum = 0.0;
+      for (int l = 0; l < 16; ++l) sum += red[j * 16 + l];
+      part[((long long)gblk * Bpad + ib) * KMAX + j] = sum;
+    }
+  }
+}
+
+// Sum the projection partials of each instance in block order and form the
+// coarse coefficients c_b = csign_b E_raw,b^-1 t_b (FP64), stored as FP32.
+template <int KMAX>
+__global__ void k_proj_reduce(const double *part, int GXp, int Bpad, int k, const InstState *st,
+                              const double *Einv, float *cvec) {
+  __shared__ double t[KMAX];
+  const int b = blockIdx.x;
+  const InstState &S = st[b];
+  if (S.outer_done || S.cg_done) return;
+  for (int j = threadIdx.x; j < KMAX; j += blockDim.x) {
+    double s = 0.0;
+    if (j < k && S.deflate)
+      for (int g = 0; g < GXp; ++g) s += part[((long long)g * Bpad + b) * KMAX + j];
+    t[j] = s;
+  }
+  __syncthreads();
+  const double *Ei = Einv + (size_t)b * k * k;
+  for (int i = threadIdx.x; i < KMAX; i += blockDim.x) {
+    double c = 0.0;
+    if (i < k && S.deflate) {
+      for (int j = 0; j < k; ++j) c = fma(Ei[i * k + j], t[j], c);
+      c *= S.csign;
+    }
+    cvec[(size_t)b * KMAX + i] = (float)c;
   }
 }
 
@@ -1085,6 +1340,14 @@ Layout make_layout(const sdf_problem *p, int B, int max_blocks = 0, int mixed = 
   L.state = take(sizeof(InstState) * (size_t)B);
   L.cnt = take(sizeof(int) * (size_t)B * NCNT);
   L.ctrl = take(sizeof(Ctrl));
+  // mixed path: v = S_II z, coarse coefficients, projection-GEMM partials
+  L.nb = B == 1 ? 1 : (B <= 16 ? 16 : 64);
+  L.bpad = (int)(((B + L.nb - 1) / L.nb) * L.nb);
+  L.gxp = std::max(1, (p->nsm * 2) / ((B + L.nb - 1) / L.nb));
+  if (max_blocks > 0) L.gxp = std::min(L.gxp, max_blocks);
+  L.v = take(mixed ? sizeof(float) * (size_t)N * B : 8);
+  L.cvec = take(sizeof(float) * (size_t)B * KM);
+  L.ppart = take(mixed ? sizeof(double) * (size_t)L.gxp * L.bpad * KM : 8);
   L.total = o;
   return L;
 }
@@ -1187,15 +1450,6 @@ sdf_status solve_impl(sdf_problem *p, const double *inst, int B, const double *p
         sdf_status e = triple(pp, timed && rep == 0);
         if (e != SDF_OK) return e;
       }
-      if constexpr (mixed != 0) {  // FP64 residual replacement + coarse correction pass
-        if (timed) CK(cudaEventRecord(p->ev[4], s));
-        k_resid<DIM, KMAX, PhiT, V><<<gT, NT, 0, s>>>(P, inst, Phi, ld, k, st, mask, b64, x,
-                                                      rbuf[par], part, cnt, ctrl, L.gx, rtol2);
-        if (timed) CK(cudaEventRecord(p->ev[5], s));
-        p->prof.launches += 1;
-        sdf_status e = triple(wv, false);
-        if (e != SDF_OK) return e;
-      }
       CKL("cg iteration");
       launches += chunk;
       CK(cudaMemcpyAsync(p->pinned, &ctrl->running, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1250,6 +1504,169 @@ sdf_status solve_impl(sdf_problem *p, const double *inst, int B, const double *p
   return (sdf_status)worst;
 }
 
+// Mixed-precision solve (SDF_PREC_MIXED): FP32 vectors, stencil and
+// shared-Phi kernels; FP64 iterate, right-hand side, reductions, coarse
+// operator and periodic residual replacement (k_resid) with coarse correction.
+template <int DIM, int KMAX, class PhiT>
+sdf_status solve_mixed(sdf_problem *p, const double *inst, int B, const double *psi,
+                       const sdf_opts &o, char *ws, cudaStream_t s, double *y, double *lam,
+                       uint8_t *active, sdf_stats *stats) {
+  const Layout L = make_layout(p, B, o.max_blocks, 1);
+  const OpParams &P = p->P;
+  const long long N = P.N;
+  double *x = (double *)(ws + L.x), *b64 = (double *)(ws + L.b64);
+  float *pp = (float *)(ws + L.p), *q = (float *)(ws + L.q), *wv = (float *)(ws + L.w);
+  float *vv = (float *)(ws + L.v), *cvec = (float *)(ws + L.cvec);
+  double *ppart = (double *)(ws + L.ppart);
+  float *rbuf[2] = {(float *)(ws + L.r), (float *)(ws + L.r2)};
+  float *dinv = P.convection ? (float *)(ws + L.dinv) : p->dinv_shared32;
+  uint8_t *mask = (uint8_t *)(ws + L.mask);
+  double *W = (double *)(ws + L.W), *Einv = (double *)(ws + L.Einv), *Eraw = (double *)(ws + L.Eraw),
+         *G = (double *)(ws + L.G), *coarse = (double *)(ws + L.coarse),
+         *part = (double *)(ws + L.part), *gpart = (double *)(ws + L.gpart);
+  InstState *st = (InstState *)(ws + L.state);
+  int *cnt = (int *)(ws + L.cnt);
+  Ctrl *ctrl = (Ctrl *)(ws + L.ctrl);
+  const bool defl = o.deflate && p->phi != nullptr && p->k > 0;
+  const int k = defl ? p->k : 0;
+  const PhiT *Phi = phi_as<PhiT>(p);
+  const long long ld = p->ld;
+
+  CK(cudaMemsetAsync(mask, 0, (size_t)N * B, s));
+  CK(cudaMemsetAsync(st, 0, sizeof(InstState) * B, s));
+  CK(cudaMemsetAsync(cnt, 0, sizeof(int) * B * NCNT, s));
+  CK(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s));
+  CK(cudaMemsetAsync(cvec, 0, sizeof(float) * B * KMAX, s));
+
+  const size_t esm = sizeof(float) * (size_t)B * KMAX + 3 * sizeof(float) * B;
+  if (esm > 48 * 1024)
+    CK(cudaFuncSetAttribute(k_expand_b<KMAX, PhiT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                            (int)esm));
+  const dim3 gT(B, L.gx);
+  const int gxe = (int)std::max<long long>(1, std::min<long long>((N + NT - 1) / NT, p->nsm * 4LL));
+  const dim3 gP((B + L.nb - 1) / L.nb, L.gxp);
+  long long launches = 0;
+  const long long max_launches = o.max_launches > 0 ? o.max_launches : 4LL * o.max_cg + 64;
+  const int chunk = std::max(1, o.replace_every > 0 ? o.replace_every : 100);
+  const double rtol2 = o.rtol * o.rtol;
+  int live = B;
+  int par = 0;
+  auto project = [&](const float *src) -> sdf_status {  // cvec <- csign E^-1 Phi_I^T src
+    if (!defl) return SDF_OK;
+    if (L.nb == 1)
+      k_proj_gemm<KMAX, 1, PhiT><<<gP, NT, 0, s>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad);
+    else if (L.nb == 16)
+      k_proj_gemm<KMAX, 16, PhiT><<<gP, NT, 0, s>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad);
+    else
+      k_proj_gemm<KMAX, 64, PhiT><<<gP, NT, 0, s>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad);
+    k_proj_reduce<KMAX><<<B, KMAX, 0, s>>>(ppart, L.gxp, L.bpad, k, st, Einv, cvec);
+    p->prof.launches += 2;
+    return SDF_OK;
+  };
+  auto triple = [&](float *dir, bool timed) -> sdf_status {
+    if (timed) CK(cudaEventRecord(p->ev[0], s));
+    k_expand_b<KMAX, PhiT><<<gxe, NT, esm, s>>>(Phi, ld, k, N, B, st, cvec, mask, rbuf[par], dinv,
+                                                P.convection, dir);
+    if (timed) CK(cudaEventRecord(p->ev[1], s));
+    k_spmv<DIM, float><<<gT, NT, 0, s>>>(P, inst, st, mask, dir, q, part, cnt, ctrl, L.gx);
+    if (timed) CK(cudaEventRecord(p->ev[2], s));
+    k_update_v<DIM><<<gT, NT, 0, s>>>(P, inst, st, mask, rbuf[par], rbuf[par ^ 1], q, dir, x, dinv,
+                                      vv, part, cnt, ctrl, L.gx, rtol2, o.max_cg);
+    if (timed) CK(cudaEventRecord(p->ev[3], s));
+    sdf_status e = project(vv);
+    if (e != SDF_OK) return e;
+    if (timed) CK(cudaEventRecord(p->ev[4], s));
+    par ^= 1;
+    p->prof.launches += 3;
+    return SDF_OK;
+  };
+  for (int outer = 0; outer < o.max_outer && live > 0; ++outer) {
+    CK(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s));
+    par = 0;
+    k_outer_setup<DIM, float><<<gT, NT, 0, s>>>(P, inst, psi, mask, rbuf[0], b64, x, dinv, st,
+                                                part, cnt, ctrl, L.gx);
+    CKL("k_outer_setup");
+    p->prof.launches += 1;
+    if (defl) {
+      for (int b = 0; b < B; ++b) {
+        k_modes_W<DIM, PhiT><<<dim3(k, L.gx), NT, 0, s>>>(P, inst, b, st, mask, Phi, ld, W, L.gx);
+        k_gram<KMAX, PhiT><<<L.gxg, NT, 0, s>>>(Phi, ld, W, mask, st, b, N, k, 0, gpart);
+        k_gram_reduce<<<(k * k + NT - 1) / NT, NT, 0, s>>>(gpart, L.gxg, k, st, b, Eraw + (size_t)b * k * k);
+        k_gram<KMAX, PhiT><<<L.gxg, NT, 0, s>>>(Phi, ld, W, mask, st, b, N, k, 1, gpart);
+        k_gram_reduce<<<(k * k + NT - 1) / NT, NT, 0, s>>>(gpart, L.gxg, k, st, b, G + (size_t)b * k * k);
+      }
+      CKL("coarse setup");
+      k_coarse<<<B, NT, 0, s>>>(k, st, G, Eraw, Einv, coarse, o.tau_cond);
+      CKL("k_coarse");
+      p->prof.launches += 5LL * B + 1;
+      sdf_status e = project(rbuf[0]);  // coarse-corrected start: c = -E^-1 Phi_I^T b
+      if (e != SDF_OK) return e;
+    }
+    {
+      sdf_status e = triple(pp, false);  // phase 1
+      if (e != SDF_OK) return e;
+    }
+    for (;;) {
+      const bool timed = o.profile && p->ev_ready;
+      for (int rep = 0; rep < chunk; ++rep) {
+        sdf_status e = triple(pp, timed && rep == 0);
+        if (e != SDF_OK) return e;
+      }
+      if (timed) CK(cudaEventRecord(p->ev[5], s));
+      k_resid<DIM><<<gT, NT, 0, s>>>(P, inst, st, mask, b64, x, rbuf[par], part, cnt, ctrl, L.gx,
+                                     rtol2);
+      if (timed) CK(cudaEventRecord(p->ev[6], s));
+      p->prof.launches += 1;
+      {
+        sdf_status e = project(rbuf[par]);  // correction pass: c = -E^-1 Phi_I^T r
+        if (e != SDF_OK) return e;
+        e = triple(wv, false);
+        if (e != SDF_OK) return e;
+      }
+      CKL("cg iteration");
+      launches += chunk;
+      CK(cudaMemcpyAsync(p->pinned, &ctrl->running, sizeof(int), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (timed) {
+        float t[6] = {0, 0, 0, 0, 0, 0};
+        for (int i = 0; i < 4; ++i) cudaEventElapsedTime(&t[i], p->ev[i], p->ev[i + 1]);
+        cudaEventElapsedTime(&t[4], p->ev[5], p->ev[6]);
+        const int ids[5] = {0, 1, 2, 8, 7};
+        for (int i = 0; i < 5; ++i) {
+          p->prof.ms[ids[i]] += t[i];
+          p->prof.samples[ids[i]] += 1;
+        }
+      }
+      if (p->pinned[0] <= 0) break;
+      if (launches > max_launches)
+        return fail(p, SDF_ERR_TIMEOUT, "solve exceeded its iteration launch budget");
+    }
+    k_active<<<dim3(B, L.gxa), NT, 0, s>>>(N, psi, mask, x, y, st, part, cnt, ctrl, L.gxa, o.tau,
+                                           o.max_outer);
+    CKL("k_active");
+    p->prof.launches += 1;
+    CK(cudaMemcpyAsync(p->pinned + 1, &ctrl->live, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    live = p->pinned[1];
+  }
+  if (active) CK(cudaMemcpyAsync(active, mask, (size_t)N * B, cudaMemcpyDeviceToDevice, s));
+  if (lam) {
+    k_lambda<DIM><<<gT, NT, 0, s>>>(P, inst, y, lam, L.gx);
+    CKL("k_lambda");
+    p->prof.launches += 1;
+  }
+  std::vector<InstState> hs(B);
+  CK(cudaMemcpyAsync(hs.data(), st, sizeof(InstState) * B, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  int worst = SDF_OK;
+  for (int b = 0; b < B; ++b) {
+    if (stats) stats[b] = hs[b].stats;
+    if (hs[b].stats.status != SDF_OK && worst == SDF_OK) worst = hs[b].stats.status;
+  }
+  if (worst != SDF_OK) p->err = "at least one instance did not converge (see stats)";
+  return (sdf_status)worst;
+}
+
 template <int DIM, int KMAX>
 sdf_status dispatch_phi(sdf_problem *p, const double *inst, int B, const double *psi,
                         const sdf_opts &o, char *ws, cudaStream_t s, double *y, double *lam,
@@ -1260,12 +1677,12 @@ sdf_status dispatch_phi(sdf_problem *p, const double *inst, int B, const double 
     return solve_impl<DIM, KMAX, double, double>(p, inst, B, psi, o, ws, s, y, lam, active, stats);
   }
   switch (p->phi_dtype) {
-    case SDF_F32: return solve_impl<DIM, KMAX, float, float>(p, inst, B, psi, o, ws, s, y, lam, active, stats);
-    case SDF_BF16: return solve_impl<DIM, KMAX, __nv_bfloat16, float>(p, inst, B, psi, o, ws, s, y, lam, active, stats);
+    case SDF_F32: return solve_mixed<DIM, KMAX, float>(p, inst, B, psi, o, ws, s, y, lam, active, stats);
+    case SDF_BF16: return solve_mixed<DIM, KMAX, __nv_bfloat16>(p, inst, B, psi, o, ws, s, y, lam, active, stats);
     default:
       if (p->phi && o.deflate)
         return fail(p, SDF_ERR_UNSUPPORTED, "the mixed path takes FP32 or BF16 reference modes");
-      return solve_impl<DIM, KMAX, float, float>(p, inst, B, psi, o, ws, s, y, lam, active, stats);
+      return solve_mixed<DIM, KMAX, float>(p, inst, B, psi, o, ws, s, y, lam, active, stats);
   }
 }
 

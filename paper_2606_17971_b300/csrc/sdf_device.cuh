@@ -60,6 +60,21 @@ __device__ __forceinline__ int widx(int lx, int ly, int lz) {
   return (lx + 1) + S::WX * ((ly + 1) + S::WY * (lz + TileCfg<DIM>::HZ1));
 }
 
+// Face coefficients in arithmetic type T: constant-kappa problems use the
+// per-kernel constant cd[d] (no FP64 -> FP32 conversion per use).
+template <class T>
+__device__ __forceinline__ T fx_T(const OpParams &P, const T cd[3], int i, int j, int l) {
+  return P.fx ? (T)__ldg(P.fx + i + (long long)(P.nx + 1) * (j + (long long)P.ny * l)) : cd[0];
+}
+template <class T>
+__device__ __forceinline__ T fy_T(const OpParams &P, const T cd[3], int i, int j, int l) {
+  return P.fy ? (T)__ldg(P.fy + i + (long long)P.nx * (j + (long long)(P.ny + 1) * l)) : cd[1];
+}
+template <class T>
+__device__ __forceinline__ T fz_T(const OpParams &P, const T cd[3], int i, int j, int l) {
+  return P.fz ? (T)__ldg(P.fz + i + (long long)P.nx * (j + (long long)P.ny * l)) : cd[2];
+}
+
 __device__ __forceinline__ double face_x(const OpParams &P, int i, int j, int l) {
   return P.fx ? __ldg(P.fx + i + (long long)(P.nx + 1) * (j + (long long)P.ny * l)) : P.cdiff[0];
 }
@@ -73,13 +88,13 @@ __device__ __forceinline__ double face_z(const OpParams &P, int i, int j, int l)
 // (A u)_p in flux form: sum over faces of k_f (u_p - u_nb) plus first-order
 // upwind convection; U(dx,dy,dz) returns u at the offset (0 outside the grid).
 template <int DIM, class T, class U>
-__device__ __forceinline__ T apply_A(const OpParams &P, const T cb[3], int i, int j,
-                                          int l, U u) {
+__device__ __forceinline__ T apply_A(const OpParams &P, const T cb[3], const T cd[3], int i,
+                                     int j, int l, U u) {
   T c = u(0, 0, 0);
-  T s = (T)face_x(P, i, j, l) * (c - u(-1, 0, 0)) + (T)face_x(P, i + 1, j, l) * (c - u(1, 0, 0));
-  s += (T)face_y(P, i, j, l) * (c - u(0, -1, 0)) + (T)face_y(P, i, j + 1, l) * (c - u(0, 1, 0));
+  T s = fx_T(P, cd, i, j, l) * (c - u(-1, 0, 0)) + fx_T(P, cd, i + 1, j, l) * (c - u(1, 0, 0));
+  s += fy_T(P, cd, i, j, l) * (c - u(0, -1, 0)) + fy_T(P, cd, i, j + 1, l) * (c - u(0, 1, 0));
   if (DIM == 3)
-    s += (T)face_z(P, i, j, l) * (c - u(0, 0, -1)) + (T)face_z(P, i, j, l + 1) * (c - u(0, 0, 1));
+    s += fz_T(P, cd, i, j, l) * (c - u(0, 0, -1)) + fz_T(P, cd, i, j, l + 1) * (c - u(0, 0, 1));
   if (cb[0] > 0.0) s += cb[0] * (c - u(-1, 0, 0));
   else if (cb[0] < 0.0) s -= cb[0] * (c - u(1, 0, 0));
   if (cb[1] > 0.0) s += cb[1] * (c - u(0, -1, 0));
@@ -94,13 +109,13 @@ __device__ __forceinline__ T apply_A(const OpParams &P, const T cb[3], int i, in
 // (A^T w)_p: the diffusion part is symmetric; the upwind part is transposed
 // (a backward difference becomes a forward one and vice versa).
 template <int DIM, class T, class U>
-__device__ __forceinline__ T apply_AT(const OpParams &P, const T cb[3], int i, int j,
-                                           int l, U w) {
+__device__ __forceinline__ T apply_AT(const OpParams &P, const T cb[3], const T cd[3], int i,
+                                      int j, int l, U w) {
   T c = w(0, 0, 0);
-  T s = (T)face_x(P, i, j, l) * (c - w(-1, 0, 0)) + (T)face_x(P, i + 1, j, l) * (c - w(1, 0, 0));
-  s += (T)face_y(P, i, j, l) * (c - w(0, -1, 0)) + (T)face_y(P, i, j + 1, l) * (c - w(0, 1, 0));
+  T s = fx_T(P, cd, i, j, l) * (c - w(-1, 0, 0)) + fx_T(P, cd, i + 1, j, l) * (c - w(1, 0, 0));
+  s += fy_T(P, cd, i, j, l) * (c - w(0, -1, 0)) + fy_T(P, cd, i, j + 1, l) * (c - w(0, 1, 0));
   if (DIM == 3)
-    s += (T)face_z(P, i, j, l) * (c - w(0, 0, -1)) + (T)face_z(P, i, j, l + 1) * (c - w(0, 0, 1));
+    s += fz_T(P, cd, i, j, l) * (c - w(0, 0, -1)) + fz_T(P, cd, i, j, l + 1) * (c - w(0, 0, 1));
   if (cb[0] > 0.0) s += cb[0] * (c - w(1, 0, 0));
   else if (cb[0] < 0.0) s -= cb[0] * (c - w(-1, 0, 0));
   if (cb[1] > 0.0) s += cb[1] * (c - w(0, 1, 0));
@@ -159,6 +174,7 @@ __device__ void tile_S(const OpParams &P, const double cb64[3], int ox, int oy, 
   using C = TileCfg<DIM>;
   using SM = TileSmem<DIM, T>;
   const T cb[3] = {(T)cb64[0], (T)cb64[1], (T)cb64[2]};
+  const T cd[3] = {(T)P.cdiff[0], (T)P.cdiff[1], (T)P.cdiff[2]};
   const T mass = (T)P.mass, wgt = (T)P.wgt;
   for (int e = threadIdx.x; e < SM::UZ * SM::UY * SM::UX; e += NT) {
     int lx = e % SM::UX - 2;
@@ -179,7 +195,7 @@ __device__ void tile_S(const OpParams &P, const double cb64[3], int ox, int oy, 
     bool in = gx >= 0 && gx < P.nx && gy >= 0 && gy < P.ny && gz >= 0 && gz < P.nz;
     T val = (T)0;
     if (in)
-      val = apply_A<DIM, T>(P, cb, gx, gy, gz, [&](int dx, int dy, int dz) {
+      val = apply_A<DIM, T>(P, cb, cd, gx, gy, gz, [&](int dx, int dy, int dz) {
         return sm.u[uidx<DIM>(lx + dx, ly + dy, lz + dz)];
       });
     sm.w[e] = val;
@@ -197,7 +213,7 @@ __device__ void tile_S(const OpParams &P, const double cb64[3], int ox, int oy, 
       continue;
     }
     T uc = sm.u[uidx<DIM>(lx, ly, lz)];
-    T atw = apply_AT<DIM, T>(P, cb, gx, gy, gz, [&](int dx, int dy, int dz) {
+    T atw = apply_AT<DIM, T>(P, cb, cd, gx, gy, gz, [&](int dx, int dy, int dz) {
       return sm.w[widx<DIM>(lx + dx, ly + dy, lz + dz)];
     });
     store(e, gx, gy, gz, gx + (long long)P.nx * (gy + (long long)P.ny * gz), mass * uc + wgt * atw);

@@ -46,8 +46,9 @@ class Opts(ctypes.Structure):
                 ("max_launches", ctypes.c_int64)]
 
 
-SDF_NPROF = 8
-PROFILE_NAMES = ("expand", "spmv", "update", "setup", "coarse", "active", "lambda", "resid")
+SDF_NPROF = 9
+PROFILE_NAMES = ("expand", "spmv", "update", "setup", "coarse", "active", "lambda", "resid",
+                 "project")
 PREC_F64, PREC_MIXED = 0, 1
 
 
