@@ -63,7 +63,9 @@ typedef enum { SDF_F64 = 0, SDF_F32 = 1, SDF_BF16 = 2 } sdf_dtype;
  *                   set-up stay FP64, and every `replace_every` iterations
  *                   the residual is recomputed as b - S_II x with the FP64
  *                   stencil and the coarse correction x += Q r is applied;
- *                   convergence is declared only on that FP64 residual. */
+ *                   convergence is declared only on that FP64 residual.
+ *                   Not available with per-instance convection
+ *                   (SDF_ERR_UNSUPPORTED). */
 typedef enum { SDF_PREC_F64 = 0, SDF_PREC_MIXED = 1 } sdf_precision;
 
 /* Maximum deflation rank and outer iterations recorded per instance. */

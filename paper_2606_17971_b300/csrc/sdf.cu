@@ -620,9 +620,11 @@ __global__ void __launch_bounds__(NT) k_spmv(OpParams P, const double *inst, Ins
   sg = block_sum(sg, red);
   if (threadIdx.x == 0) part[b * GX + gblk] = sg;
   if (!last_block(cnt + b * NCNT + CNT_SIGMA, GX, &flag)) return;
+  __shared__ double scratch[NT];
+  __shared__ double tot1[1];
+  reduce_fields(part + (long long)b * GX, GX, 1, 1, tot1, scratch);
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int g = 0; g < GX; ++g) s += __ldcg(part + b * GX + g);
+    double s = tot1[0];
     cnt[b * NCNT + CNT_SIGMA] = 0;
     S.sigma = s;
     if (S.phase) {
@@ -824,9 +826,11 @@ __global__ void __launch_bounds__(NT) k_resid(OpParams P, const double *inst, In
   rr = block_sum(rr, red);
   if (threadIdx.x == 0) part[(long long)b * GX + gblk] = rr;
   if (!last_block(cnt + b * NCNT + CNT_UPDATE, GX, &flag)) return;
+  __shared__ double scratch[NT];
+  __shared__ double tot1[1];
+  reduce_fields(part + (long long)b * GX, GX, 1, 1, tot1, scratch);
   if (threadIdx.x == 0) {
-    double rn2 = 0.0;
-    for (int g = 0; g < GX; ++g) rn2 += __ldcg(part + (long long)b * GX + g);
+    const double rn2 = tot1[0];
     cnt[b * NCNT + CNT_UPDATE] = 0;
     S.rnorm2 = rn2;
     if (!isfinite(rn2)) {
@@ -969,12 +973,11 @@ __global__ void __launch_bounds__(NT) k_update_v(OpParams P, const double *inst,
     part[((long long)b * GX + gblk) * 2 + 1] = rr;
   }
   if (!last_block(cnt + b * NCNT + CNT_UPDATE, GX, &flag)) return;
+  __shared__ double scratch[NT];
+  __shared__ double tot2[2];
+  reduce_fields(part + (long long)b * GX * 2, GX, 2, 2, tot2, scratch);
   if (threadIdx.x == 0) {
-    double rho_new = 0.0, rn2 = 0.0;
-    for (int g = 0; g < GX; ++g) {
-      rho_new += __ldcg(part + ((long long)b * GX + g) * 2);
-      rn2 += __ldcg(part + ((long long)b * GX + g) * 2 + 1);
-    }
+    const double rho_new = tot2[0], rn2 = tot2[1];
     cnt[b * NCNT + CNT_UPDATE] = 0;
     if (S.phase == 0) S.iters += 1;
     S.rnorm2 = rn2;
@@ -1011,7 +1014,7 @@ template <int KMAX, int NB, class PhiT>
 __global__ void __launch_bounds__(NT) k_proj_gemm(const PhiT *__restrict__ Phi, long long ld, int k,
                                                   long long N, int B, const InstState *st,
                                                   const float *v, double *part, int Bpad) {
-  constexpr int CH = 32;
+  constexpr int CH = (KMAX <= 64 && NB <= 64) ? 64 : 32;
   constexpr int MT = KMAX / 16;
   constexpr int NT_N = NB >= 16 ? NB / 16 : 1;
   __shared__ __align__(16) float Ps[CH][KMAX + 1];
@@ -1063,7 +1066,7 @@ __global__ void __launch_bounds__(NT) k_proj_gemm(const PhiT *__restrict__ Phi, 
 #pragma unroll
           for (int q = 0; q < NT_N; ++q) acc[a][q] = fmaf(pa[a], vb[q], acc[a][q]);
       }
-    } else {  // NB == 1: lane tj takes nodes tj, tj + 16 of the chunk
+    } else {  // NB == 1: lane tj takes nodes tj, tj + 16, ... of the chunk
 #pragma unroll
       for (int c = tj; c < CH; c += 16) {
         const float vv = Vs[c][0];
@@ -1157,9 +1160,11 @@ __global__ void __launch_bounds__(NT) k_active(long long N, const double *psi, u
   ch = block_sum(ch, red);
   if (threadIdx.x == 0) part[b * GX + gblk] = ch;
   if (!last_block(cnt + b * NCNT + CNT_ACTIVE, GX, &flag)) return;
+  __shared__ double scratch[NT];
+  __shared__ double tot1[1];
+  reduce_fields(part + (long long)b * GX, GX, 1, 1, tot1, scratch);
   if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int g = 0; g < GX; ++g) s += __ldcg(part + b * GX + g);
+    double s = tot1[0];
     cnt[b * NCNT + CNT_ACTIVE] = 0;
     S.changes = (int)s;
     S.stats.outer_iters = S.outer + 1;
@@ -1302,7 +1307,9 @@ Layout make_layout(const sdf_problem *p, int B, int max_blocks = 0, int mixed = 
   const int k = std::max(p->k, 1), KM = kmax_for(k);
   long long T = p->d.dim == 2 ? num_tiles<2>(p->P.nx, p->P.ny, p->P.nz)
                               : num_tiles<3>(p->P.nx, p->P.ny, p->P.nz);
-  long long target = (long long)p->nsm * 2;
+  // FP64 path: two blocks per SM in total (FP64-pipe bound, large partials);
+  // mixed path: eight (latency-bound stencil tiles need more resident blocks)
+  long long target = (long long)p->nsm * (mixed ? 8 : 2);
   L.gx = (int)std::max<long long>(1, std::min<long long>(T, (target + B - 1) / B));
   long long chunks = (N + NT - 1) / NT;
   L.gxa = (int)std::max<long long>(1, std::min<long long>(chunks, (p->nsm * 8LL + B - 1) / B));
@@ -1343,7 +1350,7 @@ Layout make_layout(const sdf_problem *p, int B, int max_blocks = 0, int mixed = 
   // mixed path: v = S_II z, coarse coefficients, projection-GEMM partials
   L.nb = B == 1 ? 1 : (B <= 16 ? 16 : 64);
   L.bpad = (int)(((B + L.nb - 1) / L.nb) * L.nb);
-  L.gxp = std::max(1, (p->nsm * 2) / ((B + L.nb - 1) / L.nb));
+  L.gxp = std::max(1, (p->nsm * 6) / ((B + L.nb - 1) / L.nb));
   if (max_blocks > 0) L.gxp = std::min(L.gxp, max_blocks);
   L.v = take(mixed ? sizeof(float) * (size_t)N * B : 8);
   L.cvec = take(sizeof(float) * (size_t)B * KM);
@@ -1960,6 +1967,10 @@ static sdf_status check_solve_args(sdf_problem *p, int batch, const sdf_opts *op
     return fail(p, SDF_ERR_INVALID_ARG, "workspace must be a 256-byte aligned device pointer");
   if (opts->precision != SDF_PREC_F64 && opts->precision != SDF_PREC_MIXED)
     return fail(p, SDF_ERR_INVALID_ARG, "unknown precision");
+  if (opts->precision == SDF_PREC_MIXED && p->d.convection)
+    return fail(p, SDF_ERR_UNSUPPORTED,
+                "the mixed path is not validated for convection (FP32 attainable accuracy above "
+                "rtol stalls its refinement loop); use SDF_PREC_F64");
   if (opts->replace_every < 0) return fail(p, SDF_ERR_INVALID_ARG, "replace_every < 0");
   size_t need = make_layout(p, batch, opts->max_blocks, opts->precision == SDF_PREC_MIXED).total;
   if (ws_bytes < need) return fail(p, SDF_ERR_WORKSPACE, "workspace too small");

@@ -307,7 +307,7 @@ def test_mixed_32x32_workload_matches_fp64_oracle(phi_dtype, max_blocks, replace
     compare_mixed(out, orc)
 
 
-def test_mixed_ragged_block_kappa_and_3d_and_convection():
+def test_mixed_ragged_block_kappa_and_3d_and_no_convection():
     # ragged 2D with 100x contrast, BF16 modes
     w = W.scaled(W.WORKLOADS["block2d_1024"], 70)
     n = (70, 45)
@@ -336,20 +336,15 @@ def test_mixed_ragged_block_kappa_and_3d_and_convection():
     out3 = G3.solve(t64(W.instances_array(i3)), t64(np.ones(P3.N)),
                     sdf.default_opts(precision=sdf.PREC_MIXED, max_blocks=2))
     compare_mixed(out3, orc3)
-    # convection with per-instance velocities, FP32 modes
+    # convection: the mixed path refuses (FP32 attainable accuracy above rtol)
     wc = W.scaled(W.WORKLOADS["convdiff2d_512"], 48)
-    ic = W.draw_instances(wc, count=4)
-    Phic = O.analytic_modes(2, 48, 12, wc.alpha, diff_scale=wc.diff_scale)[0]
-    orcc = []
-    for i in ic:
-        Pc = O.Problem(2, 48, diff_scale=wc.diff_scale, b=np.array(i.b[:2]), alpha=wc.alpha)
-        orcc.append(Pc.solve(Pc.desired_state(i.a, i.c[:2], wc.sigma)[1], np.ones(wc.N), Phic))
     Gc = sdf.Problem(2, 48, alpha=wc.alpha, diff_scale=wc.diff_scale, convection=True,
                      yd_sigma=wc.sigma)
-    Gc.set_modes(modes_tensor_as(Phic, torch.float32))
-    outc = Gc.solve(t64(W.instances_array(ic)), t64(np.ones(wc.N)),
-                    sdf.default_opts(precision=sdf.PREC_MIXED))
-    compare_mixed(outc, orcc)
+    Gc.set_modes(modes_tensor_as(O.analytic_modes(2, 48, 12, wc.alpha, diff_scale=wc.diff_scale)[0],
+                                 torch.float32))
+    with pytest.raises(sdf.SdfError):
+        Gc.solve(t64(W.instances_array(W.draw_instances(wc, count=2))), t64(np.ones(wc.N)),
+                 sdf.default_opts(precision=sdf.PREC_MIXED))
 
 
 def test_mixed_rejects_fp64_modes_and_fp64_rejects_bf16():
