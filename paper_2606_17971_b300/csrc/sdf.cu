@@ -990,7 +990,17 @@ __global__ void __launch_bounds__(NT) k_update_v(OpParams P, const double *inst,
       S.cg_done = 1;
     } else {
       if (conv) S.await = 1;
-      S.beta = S.phase == 1 ? 0.0 : rho_new / (S.phase == 2 ? S.rho_prev : S.rho);
+      if (S.phase == 1) {
+        S.beta = 0.0;
+      } else if (S.phase == 2) {
+        // Correction pass after an FP64 residual replacement: continue CG
+        // (beta from the replaced iteration's rho) while the true residual is
+        // close to the recurrence residual; restart (beta = 0) when the
+        // recurrence had run ahead of FP32's attainable accuracy.
+        S.beta = rho_new > 4.0 * S.rho ? 0.0 : rho_new / S.rho_prev;
+      } else {
+        S.beta = rho_new / S.rho;
+      }
       if (S.phase != 2) S.rho_prev = S.rho;
       S.rho = rho_new;
       S.gamma = 1.0;
