@@ -917,9 +917,14 @@ __global__ void __launch_bounds__(NT) k_expand_b(const PhiT *__restrict__ Phi, l
 }
 
 // Stencil part of the CG update (mixed path): x += alpha p (FP64), r -= alpha q,
-// z = D^-1 r, v = S_II z (written for the projection GEMM), rho = (r, z),
+// z = D^-1 r, v = S_II z - r (written for the projection GEMM), rho = (r, z),
 // ||r||^2 with FP32 products summed in FP64.  The last block applies the
 // convergence / beta logic of k_update (mixed = 1).
+// The next direction is p = P z + Q r + beta p = z - Phi E^-1 Phi_I^T (S z - r)
+// + beta p: the full A-DEF2 preconditioner P^T M^-1 + Q of the cited
+// framework.  Q r vanishes in exact arithmetic (Z^T r = 0), which is why the
+// FP64 path drops it; in FP32 it removes the coarse-space component that
+// rounding puts into r every iteration, without which the iteration stalls.
 template <int DIM>
 __global__ void __launch_bounds__(NT) k_update_v(OpParams P, const double *inst, InstState *st,
                                                  const uint8_t *mask, const float *r_in,
@@ -963,7 +968,7 @@ __global__ void __launch_bounds__(NT) k_update_v(OpParams P, const double *inst,
           rw[g] = rn;
           rho += (double)(rn * z);
           rr += (double)(rn * rn);
-          vb[g] = su;
+          vb[g] = su - rn;  // S z - r: the projection feeds P z + Q r (see below)
         });
   }
   rho = block_sum(rho, red);
