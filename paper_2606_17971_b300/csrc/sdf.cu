@@ -73,7 +73,7 @@ struct Ctrl {       // grid-wide control words (device)
 
 struct Layout {
   size_t x, b64, r, r2, p, q, w, dinv, mask, W, Einv, Eraw, G, coarse, part, gpart, state, cnt,
-      ctrl, v, cvec, ppart, total;
+      ctrl, v, cvec, ppart, xlo, total;
   int gx, gxa, gxg, gxp, nb, bpad;
 };
 
@@ -603,6 +603,7 @@ __global__ void __launch_bounds__(NT) k_spmv(OpParams P, const double *inst, Ins
   const V *pb = p + b * N;
   V *qb = q + b * N;
   double sg = 0.0;
+  KahanF sgf;  // FP32 path: compensated FP32 sum, FP64 across threads
   const long long T = num_tiles<DIM>(P.nx, P.ny, P.nz);
   for (long long t = gblk; t < T; t += GX) {
     int ox, oy, oz;
@@ -612,11 +613,13 @@ __global__ void __launch_bounds__(NT) k_spmv(OpParams P, const double *inst, Ins
         [&](int e, int, int, int, long long g, V su) {
           V qv = mk[g] ? (V)0 : su;
           qb[g] = qv;
-          sg = fma((double)sm.u[uidx<DIM>(e % TileCfg<DIM>::TX, (e / TileCfg<DIM>::TX) % TileCfg<DIM>::TY,
-                                          e / (TileCfg<DIM>::TX * TileCfg<DIM>::TY))],
-                   (double)qv, sg);
+          const V pv = sm.u[uidx<DIM>(e % TileCfg<DIM>::TX, (e / TileCfg<DIM>::TX) % TileCfg<DIM>::TY,
+                                      e / (TileCfg<DIM>::TX * TileCfg<DIM>::TY))];
+          if constexpr (sizeof(V) == sizeof(float)) sgf.add(pv * qv);
+          else sg = fma((double)pv, (double)qv, sg);
         });
   }
+  if constexpr (sizeof(V) == sizeof(float)) sg = sgf.value();
   sg = block_sum(sg, red);
   if (threadIdx.x == 0) part[b * GX + gblk] = sg;
   if (!last_block(cnt + b * NCNT + CNT_SIGMA, GX, &flag)) return;
@@ -792,8 +795,9 @@ __global__ void __launch_bounds__(NT) k_update(OpParams P, const double *inst, c
 template <int DIM>
 __global__ void __launch_bounds__(NT) k_resid(OpParams P, const double *inst, InstState *st,
                                               const uint8_t *mask, const double *b64,
-                                              const double *x, float *r, double *part, int *cnt,
-                                              Ctrl *ctrl, int GX, double rtol2) {
+                                              const double *x, const float *xlo, float *r,
+                                              double *part, int *cnt, Ctrl *ctrl, int GX,
+                                              double rtol2) {
   __shared__ TileSmem<DIM, double> sm;
   __shared__ double red[NWARP];
   __shared__ int flag;
@@ -805,6 +809,7 @@ __global__ void __launch_bounds__(NT) k_resid(OpParams P, const double *inst, In
   inst_cb(P, inst + 7 * b, cb);
   const uint8_t *mk = mask + b * N;
   const double *xb = x + b * N, *bb = b64 + b * N;
+  const float *xl = xlo + b * N;
   float *rb = r + b * N;
   double rr = 0.0;
   const long long T = num_tiles<DIM>(P.nx, P.ny, P.nz);
@@ -812,7 +817,8 @@ __global__ void __launch_bounds__(NT) k_resid(OpParams P, const double *inst, In
     int ox, oy, oz;
     tile_origin<DIM>(P, t, ox, oy, oz);
     tile_S<DIM, double>(
-        P, cb, ox, oy, oz, sm, [&](int, int, int, long long g) { return xb[g]; },
+        P, cb, ox, oy, oz, sm,
+        [&](int, int, int, long long g) { return xb[g] + (double)xl[g]; },
         [&](int, int, int, int, long long g, double su) {
           if (mk[g]) {
             rb[g] = 0.0f;
@@ -929,7 +935,7 @@ template <int DIM>
 __global__ void __launch_bounds__(NT) k_update_v(OpParams P, const double *inst, InstState *st,
                                                  const uint8_t *mask, const float *r_in,
                                                  float *r_out, const float *q, const float *p,
-                                                 double *x, const float *dinv, float *v,
+                                                 double *x, float *xlo, const float *dinv, float *v,
                                                  double *part, int *cnt, Ctrl *ctrl, int GX,
                                                  double rtol2, int max_cg) {
   __shared__ TileSmem<DIM, float> sm;
@@ -945,9 +951,11 @@ __global__ void __launch_bounds__(NT) k_update_v(OpParams P, const double *inst,
   inst_cb(P, inst + 7 * b, cb);
   const uint8_t *mk = mask + b * N;
   const float *rb = r_in + b * N, *qb = q + b * N, *pb = p + b * N;
-  float *rw = r_out + b * N, *vb = v + b * N;
+  float *rw = r_out + b * N, *vb = v + b * N, *xl = xlo + b * N;
   double *xb = x + b * N;
   const float *db = dinv + (P.convection ? b * N : 0);
+  const bool fold = S.phase == 2;  // correction pass: fold x_lo into the FP64 iterate
+  KahanF rhof, rrf;
   double rho = 0.0, rr = 0.0;
   const long long T = num_tiles<DIM>(P.nx, P.ny, P.nz);
   for (long long t = gblk; t < T; t += GX) {
@@ -964,15 +972,20 @@ __global__ void __launch_bounds__(NT) k_update_v(OpParams P, const double *inst,
           }
           const float rn = rb[g] - alpha * qb[g];
           const float z = db[g] * rn;
-          xb[g] = fma(alpha64, (double)pb[g], xb[g]);
+          if (fold) {
+            xb[g] = xb[g] + (double)xl[g] + alpha64 * (double)pb[g];
+            xl[g] = 0.0f;
+          } else {
+            xl[g] = fmaf(alpha, pb[g], xl[g]);
+          }
           rw[g] = rn;
-          rho += (double)(rn * z);
-          rr += (double)(rn * rn);
+          rhof.add(rn * z);
+          rrf.add(rn * rn);
           vb[g] = su - rn;  // S z - r: the projection feeds P z + Q r (see below)
         });
   }
-  rho = block_sum(rho, red);
-  rr = block_sum(rr, red);
+  rho = block_sum(rhof.value(), red);
+  rr = block_sum(rrf.value(), red);
   if (threadIdx.x == 0) {
     part[((long long)b * GX + gblk) * 2 + 0] = rho;
     part[((long long)b * GX + gblk) * 2 + 1] = rr;
@@ -1045,11 +1058,7 @@ __global__ void __launch_bounds__(NT) k_proj_gemm(const PhiT *__restrict__ Phi, 
   const long long nch = (N + CH - 1) / CH;
   const long long c_lo = nch * gblk / GXp, c_hi = nch * (gblk + 1) / GXp;
   const int ti = threadIdx.x / 16, tj = threadIdx.x % 16;
-  double acc64[MT][NT_N];
-#pragma unroll
-  for (int a = 0; a < MT; ++a)
-#pragma unroll
-    for (int c = 0; c < NT_N; ++c) acc64[a][c] = 0.0;
+  KahanF acck[MT][NT_N];  // FP32 chunk sums, compensated across chunks
   for (long long ch = c_lo; ch < c_hi; ++ch) {
     const long long g0 = ch * CH;
     for (int e = threadIdx.x; e < CH * KMAX; e += NT) {
@@ -1092,7 +1101,7 @@ __global__ void __launch_bounds__(NT) k_proj_gemm(const PhiT *__restrict__ Phi, 
 #pragma unroll
     for (int a = 0; a < MT; ++a)
 #pragma unroll
-      for (int q = 0; q < NT_N; ++q) acc64[a][q] += (double)acc[a][q];
+      for (int q = 0; q < NT_N; ++q) acck[a][q].add(acc[a][q]);
     __syncthreads();
   }
   if constexpr (NB >= 16) {
@@ -1101,12 +1110,12 @@ __global__ void __launch_bounds__(NT) k_proj_gemm(const PhiT *__restrict__ Phi, 
 #pragma unroll
       for (int q = 0; q < NT_N; ++q) {
         int j = ti + 16 * a, bb = ib + tj + 16 * q;
-        if (bb < Bpad) part[((long long)gblk * Bpad + bb) * KMAX + j] = acc64[a][q];
+        if (bb < Bpad) part[((long long)gblk * Bpad + bb) * KMAX + j] = acck[a][q].value();
       }
   } else {  // reduce the 16 node lanes through shared memory (reuse Ps)
     double *red = reinterpret_cast<double *>(&Ps[0][0]);  // KMAX*16 doubles fit in Ps
 #pragma unroll
-    for (int a = 0; a < MT; ++a) red[(ti + 16 * a) * 16 + tj] = acc64[a][0];
+    for (int a = 0; a < MT; ++a) red[(ti + 16 * a) * 16 + tj] = acck[a][0].value();
     __syncthreads();
     for (int j = threadIdx.x; j < KMAX; j += NT) {
       double sum = 0.0;
@@ -1147,9 +1156,9 @@ __global__ void k_proj_reduce(const double *part, int GXp, int Bpad, int k, cons
 // Active-set update (App. B.1 lines 7-11): y = psi on A, x on I;
 // A_new = {y > psi - tau}; count changes; stop when A_new = A.
 __global__ void __launch_bounds__(NT) k_active(long long N, const double *psi, uint8_t *mask,
-                                               const double *x, double *y, InstState *st,
-                                               double *part, int *cnt, Ctrl *ctrl, int GX,
-                                               double tau, int max_outer) {
+                                               const double *x, const float *xlo, double *y,
+                                               InstState *st, double *part, int *cnt, Ctrl *ctrl,
+                                               int GX, double tau, int max_outer) {
   __shared__ double red[NWARP];
   __shared__ int flag;
   const int b = blockIdx.x, gblk = blockIdx.y;
@@ -1162,7 +1171,7 @@ __global__ void __launch_bounds__(NT) k_active(long long N, const double *psi, u
   double ch = 0.0;
   for (long long g = (long long)gblk * NT + threadIdx.x; g < N; g += (long long)GX * NT) {
     uint8_t a = mk[g];
-    double yv = a ? psi[g] : xb[g];
+    double yv = a ? psi[g] : (xlo ? xb[g] + (double)xlo[b * N + g] : xb[g]);
     yb[g] = yv;
     if (!failed) {
       uint8_t an = yv > psi[g] - tau ? 1 : 0;
@@ -1368,6 +1377,7 @@ Layout make_layout(const sdf_problem *p, int B, int max_blocks = 0, int mixed = 
   L.gxp = std::max(1, (p->nsm * 6) / ((B + L.nb - 1) / L.nb));
   if (max_blocks > 0) L.gxp = std::min(L.gxp, max_blocks);
   L.v = take(mixed ? sizeof(float) * (size_t)N * B : 8);
+  L.xlo = take(mixed ? sizeof(float) * (size_t)N * B : 8);
   L.cvec = take(sizeof(float) * (size_t)B * KM);
   L.ppart = take(mixed ? sizeof(double) * (size_t)L.gxp * L.bpad * KM : 8);
   L.total = o;
@@ -1501,7 +1511,8 @@ sdf_status solve_impl(sdf_problem *p, const double *inst, int B, const double *p
       if (launches > max_launches)
         return fail(p, SDF_ERR_TIMEOUT, "solve exceeded its iteration launch budget");
     }
-    k_active<<<gA, NT, 0, s>>>(N, psi, mask, x, y, st, part, cnt, ctrl, L.gxa, o.tau, o.max_outer);
+    k_active<<<gA, NT, 0, s>>>(N, psi, mask, x, nullptr, y, st, part, cnt, ctrl, L.gxa, o.tau,
+                               o.max_outer);
     CKL("k_active");
     p->prof.launches += 1;
     CK(cudaMemcpyAsync(p->pinned + 1, &ctrl->live, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1538,7 +1549,7 @@ sdf_status solve_mixed(sdf_problem *p, const double *inst, int B, const double *
   const long long N = P.N;
   double *x = (double *)(ws + L.x), *b64 = (double *)(ws + L.b64);
   float *pp = (float *)(ws + L.p), *q = (float *)(ws + L.q), *wv = (float *)(ws + L.w);
-  float *vv = (float *)(ws + L.v), *cvec = (float *)(ws + L.cvec);
+  float *vv = (float *)(ws + L.v), *cvec = (float *)(ws + L.cvec), *xlo = (float *)(ws + L.xlo);
   double *ppart = (double *)(ws + L.ppart);
   float *rbuf[2] = {(float *)(ws + L.r), (float *)(ws + L.r2)};
   float *dinv = P.convection ? (float *)(ws + L.dinv) : p->dinv_shared32;
@@ -1592,8 +1603,8 @@ sdf_status solve_mixed(sdf_problem *p, const double *inst, int B, const double *
     if (timed) CK(cudaEventRecord(p->ev[1], s));
     k_spmv<DIM, float><<<gT, NT, 0, s>>>(P, inst, st, mask, dir, q, part, cnt, ctrl, L.gx);
     if (timed) CK(cudaEventRecord(p->ev[2], s));
-    k_update_v<DIM><<<gT, NT, 0, s>>>(P, inst, st, mask, rbuf[par], rbuf[par ^ 1], q, dir, x, dinv,
-                                      vv, part, cnt, ctrl, L.gx, rtol2, o.max_cg);
+    k_update_v<DIM><<<gT, NT, 0, s>>>(P, inst, st, mask, rbuf[par], rbuf[par ^ 1], q, dir, x, xlo,
+                                      dinv, vv, part, cnt, ctrl, L.gx, rtol2, o.max_cg);
     if (timed) CK(cudaEventRecord(p->ev[3], s));
     sdf_status e = project(vv);
     if (e != SDF_OK) return e;
@@ -1604,6 +1615,7 @@ sdf_status solve_mixed(sdf_problem *p, const double *inst, int B, const double *
   };
   for (int outer = 0; outer < o.max_outer && live > 0; ++outer) {
     CK(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s));
+    CK(cudaMemsetAsync(xlo, 0, sizeof(float) * (size_t)N * B, s));
     par = 0;
     k_outer_setup<DIM, float><<<gT, NT, 0, s>>>(P, inst, psi, mask, rbuf[0], b64, x, dinv, st,
                                                 part, cnt, ctrl, L.gx);
@@ -1635,8 +1647,8 @@ sdf_status solve_mixed(sdf_problem *p, const double *inst, int B, const double *
         if (e != SDF_OK) return e;
       }
       if (timed) CK(cudaEventRecord(p->ev[5], s));
-      k_resid<DIM><<<gT, NT, 0, s>>>(P, inst, st, mask, b64, x, rbuf[par], part, cnt, ctrl, L.gx,
-                                     rtol2);
+      k_resid<DIM><<<gT, NT, 0, s>>>(P, inst, st, mask, b64, x, xlo, rbuf[par], part, cnt, ctrl,
+                                     L.gx, rtol2);
       if (timed) CK(cudaEventRecord(p->ev[6], s));
       p->prof.launches += 1;
       {
@@ -1663,8 +1675,8 @@ sdf_status solve_mixed(sdf_problem *p, const double *inst, int B, const double *
       if (launches > max_launches)
         return fail(p, SDF_ERR_TIMEOUT, "solve exceeded its iteration launch budget");
     }
-    k_active<<<dim3(B, L.gxa), NT, 0, s>>>(N, psi, mask, x, y, st, part, cnt, ctrl, L.gxa, o.tau,
-                                           o.max_outer);
+    k_active<<<dim3(B, L.gxa), NT, 0, s>>>(N, psi, mask, x, xlo, y, st, part, cnt, ctrl, L.gxa,
+                                           o.tau, o.max_outer);
     CKL("k_active");
     p->prof.launches += 1;
     CK(cudaMemcpyAsync(p->pinned + 1, &ctrl->live, sizeof(int), cudaMemcpyDeviceToHost, s));

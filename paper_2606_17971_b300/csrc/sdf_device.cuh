@@ -95,13 +95,13 @@ __device__ __forceinline__ T apply_A(const OpParams &P, const T cb[3], const T c
   s += fy_T(P, cd, i, j, l) * (c - u(0, -1, 0)) + fy_T(P, cd, i, j + 1, l) * (c - u(0, 1, 0));
   if (DIM == 3)
     s += fz_T(P, cd, i, j, l) * (c - u(0, 0, -1)) + fz_T(P, cd, i, j, l + 1) * (c - u(0, 0, 1));
-  if (cb[0] > 0.0) s += cb[0] * (c - u(-1, 0, 0));
-  else if (cb[0] < 0.0) s -= cb[0] * (c - u(1, 0, 0));
-  if (cb[1] > 0.0) s += cb[1] * (c - u(0, -1, 0));
-  else if (cb[1] < 0.0) s -= cb[1] * (c - u(0, 1, 0));
+  if (cb[0] > (T)0) s += cb[0] * (c - u(-1, 0, 0));
+  else if (cb[0] < (T)0) s -= cb[0] * (c - u(1, 0, 0));
+  if (cb[1] > (T)0) s += cb[1] * (c - u(0, -1, 0));
+  else if (cb[1] < (T)0) s -= cb[1] * (c - u(0, 1, 0));
   if (DIM == 3) {
-    if (cb[2] > 0.0) s += cb[2] * (c - u(0, 0, -1));
-    else if (cb[2] < 0.0) s -= cb[2] * (c - u(0, 0, 1));
+    if (cb[2] > (T)0) s += cb[2] * (c - u(0, 0, -1));
+    else if (cb[2] < (T)0) s -= cb[2] * (c - u(0, 0, 1));
   }
   return s;
 }
@@ -116,13 +116,13 @@ __device__ __forceinline__ T apply_AT(const OpParams &P, const T cb[3], const T 
   s += fy_T(P, cd, i, j, l) * (c - w(0, -1, 0)) + fy_T(P, cd, i, j + 1, l) * (c - w(0, 1, 0));
   if (DIM == 3)
     s += fz_T(P, cd, i, j, l) * (c - w(0, 0, -1)) + fz_T(P, cd, i, j, l + 1) * (c - w(0, 0, 1));
-  if (cb[0] > 0.0) s += cb[0] * (c - w(1, 0, 0));
-  else if (cb[0] < 0.0) s -= cb[0] * (c - w(-1, 0, 0));
-  if (cb[1] > 0.0) s += cb[1] * (c - w(0, 1, 0));
-  else if (cb[1] < 0.0) s -= cb[1] * (c - w(0, -1, 0));
+  if (cb[0] > (T)0) s += cb[0] * (c - w(1, 0, 0));
+  else if (cb[0] < (T)0) s -= cb[0] * (c - w(-1, 0, 0));
+  if (cb[1] > (T)0) s += cb[1] * (c - w(0, 1, 0));
+  else if (cb[1] < (T)0) s -= cb[1] * (c - w(0, -1, 0));
   if (DIM == 3) {
-    if (cb[2] > 0.0) s += cb[2] * (c - w(0, 0, 1));
-    else if (cb[2] < 0.0) s -= cb[2] * (c - w(0, 0, -1));
+    if (cb[2] > (T)0) s += cb[2] * (c - w(0, 0, 1));
+    else if (cb[2] < (T)0) s -= cb[2] * (c - w(0, 0, -1));
   }
   return s;
 }
@@ -250,6 +250,19 @@ __device__ __forceinline__ void tile_project(const OpParams &P, const PhiT *__re
     }
   }
 }
+
+// Compensated (Kahan) FP32 accumulator: FP32 adds with the rounding error
+// carried along, converted to FP64 once per thread.
+struct KahanF {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float v) {
+    float y = v - c;
+    float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
