@@ -167,58 +167,136 @@ __host__ __device__ inline long long num_tiles(int nx, int ny, int nz) {
 // Apply S to the tile with origin (ox,oy,oz): load(gx,gy,gz,g) gives u at a grid
 // node; store(e, gx, gy, gz, g, Su) receives S u at each grid node of the tile
 // (e = local tile index).  Two shared-memory passes: w = A u on the halo-1
-// ring, then mass u + wgt A^T w on the tile.
+// ring, then mass u + wgt A^T w on the tile.  Work is mapped by x-rows: each
+// warp takes whole rows and its lanes the x index, so the row's coordinates,
+// global base index and bounds are computed once per row, and shared-memory
+// neighbours are fixed offsets from the row base.
+template <int DIM, class T, bool VARK, class Load, class Store>
+__device__ __forceinline__ void tile_S_rows(const OpParams &P, const T cb[3], const T cd[3], T mass,
+                                            T wgt, int ox, int oy, int oz, TileSmem<DIM, T> &sm,
+                                            Load &load, Store &store) {
+  using C = TileCfg<DIM>;
+  using SM = TileSmem<DIM, T>;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const long long nxy = (long long)P.nx * P.ny;
+  // phase 1: u on the halo-2 box, rows (ly, lz) of UX elements
+  for (int row = warp; row < SM::UY * SM::UZ; row += NWARP) {
+    const int ly = row % SM::UY - 2, lz = row / SM::UY - C::HZ;
+    const int gy = oy + ly, gz = oz + lz;
+    const bool rin = gy >= 0 && gy < P.ny && gz >= 0 && gz < P.nz;
+    const long long g0 = (long long)gy * P.nx + gz * nxy + ox - 2;
+    T *urow = sm.u + row * SM::UX;
+    for (int lx = lane; lx < SM::UX; lx += 32) {
+      const int gx = ox - 2 + lx;
+      urow[lx] = (rin && gx >= 0 && gx < P.nx) ? (T)load(gx, gy, gz, g0 + lx) : (T)0;
+    }
+  }
+  __syncthreads();
+  // phase 2: w = A u on the halo-1 ring (zero outside the grid)
+  constexpr int DU_X = 1, DU_Y = SM::UX, DU_Z = SM::UX * SM::UY;
+  for (int row = warp; row < SM::WY * SM::WZ; row += NWARP) {
+    const int ly = row % SM::WY - 1, lz = row / SM::WY - C::HZ1;
+    const int gy = oy + ly, gz = oz + lz;
+    const bool rin = gy >= 0 && gy < P.ny && gz >= 0 && gz < P.nz;
+    const T *ubase = sm.u + (ly + 2) * SM::UX + (lz + C::HZ) * DU_Z + 2;  // u at (lx = 0)
+    T *wrow = sm.w + row * SM::WX;
+    for (int wx = lane; wx < SM::WX; wx += 32) {
+      const int lx = wx - 1, gx = ox + lx;
+      T val = (T)0;
+      if (rin && gx >= 0 && gx < P.nx) {
+        const T *uc = ubase + lx;
+        const T c = uc[0];
+        T fw, fe, fs, fn, fb = 0, ft = 0;
+        if (VARK) {
+          fw = fx_T(P, cd, gx, gy, gz); fe = fx_T(P, cd, gx + 1, gy, gz);
+          fs = fy_T(P, cd, gx, gy, gz); fn = fy_T(P, cd, gx, gy + 1, gz);
+          if (DIM == 3) { fb = fz_T(P, cd, gx, gy, gz); ft = fz_T(P, cd, gx, gy, gz + 1); }
+        } else {
+          fw = fe = cd[0]; fs = fn = cd[1];
+          if (DIM == 3) fb = ft = cd[2];
+        }
+        const T um = uc[-DU_X], up = uc[DU_X], vm = uc[-DU_Y], vp = uc[DU_Y];
+        T sacc = fw * (c - um) + fe * (c - up) + fs * (c - vm) + fn * (c - vp);
+        T zm = 0, zp = 0;
+        if (DIM == 3) {
+          zm = uc[-DU_Z];
+          zp = uc[DU_Z];
+          sacc += fb * (c - zm) + ft * (c - zp);
+        }
+        if (cb[0] > (T)0) sacc += cb[0] * (c - um);
+        else if (cb[0] < (T)0) sacc -= cb[0] * (c - up);
+        if (cb[1] > (T)0) sacc += cb[1] * (c - vm);
+        else if (cb[1] < (T)0) sacc -= cb[1] * (c - vp);
+        if (DIM == 3) {
+          if (cb[2] > (T)0) sacc += cb[2] * (c - zm);
+          else if (cb[2] < (T)0) sacc -= cb[2] * (c - zp);
+        }
+        val = sacc;
+      }
+      wrow[wx] = val;
+    }
+  }
+  __syncthreads();
+  // phase 3: mass u + wgt A^T w on the tile
+  constexpr int DW_X = 1, DW_Y = SM::WX, DW_Z = SM::WX * SM::WY;
+  for (int row = warp; row < C::TY * C::TZ; row += NWARP) {
+    const int ly = row % C::TY, lz = row / C::TY;
+    const int gy = oy + ly, gz = oz + lz;
+    const bool rin = gy < P.ny && gz < P.nz;
+    const long long g0 = (long long)gy * P.nx + gz * nxy + ox;
+    const T *wbase = sm.w + (ly + 1) * SM::WX + (lz + C::HZ1) * DW_Z + 1;
+    const T *ubase = sm.u + (ly + 2) * SM::UX + (lz + C::HZ) * DU_Z + 2;
+    for (int lx = lane; lx < C::TX; lx += 32) {
+      const int e = lx + C::TX * row;
+      const int gx = ox + lx;
+      if (!rin || gx >= P.nx) {
+        sm.v[e] = (T)0;
+        continue;
+      }
+      const T *wc = wbase + lx;
+      const T c = wc[0];
+      T fw, fe, fs, fn, fb = 0, ft = 0;
+      if (VARK) {
+        fw = fx_T(P, cd, gx, gy, gz); fe = fx_T(P, cd, gx + 1, gy, gz);
+        fs = fy_T(P, cd, gx, gy, gz); fn = fy_T(P, cd, gx, gy + 1, gz);
+        if (DIM == 3) { fb = fz_T(P, cd, gx, gy, gz); ft = fz_T(P, cd, gx, gy, gz + 1); }
+      } else {
+        fw = fe = cd[0]; fs = fn = cd[1];
+        if (DIM == 3) fb = ft = cd[2];
+      }
+      const T wm = wc[-DW_X], wp = wc[DW_X], vm = wc[-DW_Y], vp = wc[DW_Y];
+      T sacc = fw * (c - wm) + fe * (c - wp) + fs * (c - vm) + fn * (c - vp);
+      T zm = 0, zp = 0;
+      if (DIM == 3) {
+        zm = wc[-DW_Z];
+        zp = wc[DW_Z];
+        sacc += fb * (c - zm) + ft * (c - zp);
+      }
+      // transposed upwind part
+      if (cb[0] > (T)0) sacc += cb[0] * (c - wp);
+      else if (cb[0] < (T)0) sacc -= cb[0] * (c - wm);
+      if (cb[1] > (T)0) sacc += cb[1] * (c - vp);
+      else if (cb[1] < (T)0) sacc -= cb[1] * (c - vm);
+      if (DIM == 3) {
+        if (cb[2] > (T)0) sacc += cb[2] * (c - zp);
+        else if (cb[2] < (T)0) sacc -= cb[2] * (c - zm);
+      }
+      store(e, gx, gy, gz, g0 + lx, mass * ubase[lx] + wgt * sacc);
+    }
+  }
+  __syncthreads();
+}
+
 template <int DIM, class T, class Load, class Store>
 __device__ void tile_S(const OpParams &P, const double cb64[3], int ox, int oy, int oz,
                        TileSmem<DIM, T> &sm, Load load, Store store) {
-  using C = TileCfg<DIM>;
-  using SM = TileSmem<DIM, T>;
   const T cb[3] = {(T)cb64[0], (T)cb64[1], (T)cb64[2]};
   const T cd[3] = {(T)P.cdiff[0], (T)P.cdiff[1], (T)P.cdiff[2]};
   const T mass = (T)P.mass, wgt = (T)P.wgt;
-  for (int e = threadIdx.x; e < SM::UZ * SM::UY * SM::UX; e += NT) {
-    int lx = e % SM::UX - 2;
-    int t = e / SM::UX;
-    int ly = t % SM::UY - 2;
-    int lz = t / SM::UY - C::HZ;
-    int gx = ox + lx, gy = oy + ly, gz = oz + lz;
-    bool in = gx >= 0 && gx < P.nx && gy >= 0 && gy < P.ny && gz >= 0 && gz < P.nz;
-    sm.u[e] = in ? (T)load(gx, gy, gz, gx + (long long)P.nx * (gy + (long long)P.ny * gz)) : (T)0;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < SM::WZ * SM::WY * SM::WX; e += NT) {
-    int lx = e % SM::WX - 1;
-    int t = e / SM::WX;
-    int ly = t % SM::WY - 1;
-    int lz = t / SM::WY - C::HZ1;
-    int gx = ox + lx, gy = oy + ly, gz = oz + lz;
-    bool in = gx >= 0 && gx < P.nx && gy >= 0 && gy < P.ny && gz >= 0 && gz < P.nz;
-    T val = (T)0;
-    if (in)
-      val = apply_A<DIM, T>(P, cb, cd, gx, gy, gz, [&](int dx, int dy, int dz) {
-        return sm.u[uidx<DIM>(lx + dx, ly + dy, lz + dz)];
-      });
-    sm.w[e] = val;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < SM::TILE; e += NT) {
-    int lx = e % C::TX;
-    int t = e / C::TX;
-    int ly = t % C::TY;
-    int lz = t / C::TY;
-    int gx = ox + lx, gy = oy + ly, gz = oz + lz;
-    bool in = gx < P.nx && gy < P.ny && gz < P.nz;
-    if (!in) {
-      sm.v[e] = (T)0;
-      continue;
-    }
-    T uc = sm.u[uidx<DIM>(lx, ly, lz)];
-    T atw = apply_AT<DIM, T>(P, cb, cd, gx, gy, gz, [&](int dx, int dy, int dz) {
-      return sm.w[widx<DIM>(lx + dx, ly + dy, lz + dz)];
-    });
-    store(e, gx, gy, gz, gx + (long long)P.nx * (gy + (long long)P.ny * gz), mass * uc + wgt * atw);
-  }
-  __syncthreads();
+  if (P.fx)
+    tile_S_rows<DIM, T, true>(P, cb, cd, mass, wgt, ox, oy, oz, sm, load, store);
+  else
+    tile_S_rows<DIM, T, false>(P, cb, cd, mass, wgt, ox, oy, oz, sm, load, store);
 }
 
 // Accumulate acc[jj] += sum over the tile of Phi_j(g) v(g) for modes
