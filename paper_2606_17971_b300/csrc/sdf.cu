@@ -897,15 +897,20 @@ __global__ void __launch_bounds__(NT) k_expand_b(const PhiT *__restrict__ Phi, l
     float ph[KMAX];
 #pragma unroll
     for (int j = 0; j < KMAX; ++j) ph[j] = j < k ? (float)Phi[(long long)j * ld + g] : 0.0f;
+    const float d_shared = dinv_per_inst ? 0.0f : dinv[g];
     for (int b = 0; b < B; ++b) {
       const int a = act[b];
       if (!a) continue;
       const long long gb = (long long)b * N + g;
+      // issue every load before the mask test (r and p are zero on A)
+      const uint8_t mk = mask[gb];
+      const float db = dinv_per_inst ? dinv[gb] : d_shared;
+      const float rv = r[gb];
+      const float pv = bet[b] != 0.0f ? p[gb] : 0.0f;
       float v = 0.0f;
-      if (!mask[gb]) {
-        const float db = dinv[dinv_per_inst ? gb : g];
-        v = gam[b] * db * r[gb];
-        if (bet[b] != 0.0f) v = fmaf(bet[b], p[gb], v);
+      if (!mk) {
+        v = gam[b] * db * rv;
+        v = fmaf(bet[b], pv, v);
         if (a & 2) {
           const float *cb = cs + (size_t)b * KMAX;
           float s0 = 0.0f, s1 = 0.0f;
@@ -963,7 +968,8 @@ __global__ void __launch_bounds__(NT) k_update_v(OpParams P, const double *inst,
     tile_origin<DIM>(P, t, ox, oy, oz);
     tile_S<DIM, float>(
         P, cb, ox, oy, oz, sm,
-        [&](int, int, int, long long g) { return mk[g] ? 0.0f : db[g] * (rb[g] - alpha * qb[g]); },
+        // r and q are zero on the active set, so z needs no mask test here
+        [&](int, int, int, long long g) { return db[g] * (rb[g] - alpha * qb[g]); },
         [&](int, int, int, int, long long g, float su) {
           if (mk[g]) {
             rw[g] = 0.0f;
