@@ -61,8 +61,25 @@ def stencil_flops(dim):
     return 2 * (2 * dim + 4 * dim) + 3
 
 
-def kernel_work(name, dim, k, phi_bytes, vec_bytes=8):
-    """(flops, bytes) per dof per launch of the three CG kernels."""
+def kernel_work(name, dim, k, phi_bytes, vec_bytes=8, mixed=False, batch=1):
+    """(flops, bytes) per dof and instance of one launch of a CG kernel.
+
+    Mixed path (FP32 vectors; Phi shared by the batch, so its bytes are
+    divided by the batch size):
+      update  k_update_v: r, q, p, mask, x_lo read; r_out, v, x_lo written
+      expand  k_expand_b: mask, r, p read, p written, Phi (shared)
+      spmv    k_spmv:     p read, q written
+      project k_proj_gemm: v read, Phi (shared)
+    FP64 path: see the per-kernel comments below."""
+    if mixed:
+        if name == "update":
+            return stencil_flops(dim) + 9, 4 * 4 + 1 + 8 + 4 + 4
+        if name == "expand":
+            return 2 * k + 4, 1 + 4 + 8 + k * phi_bytes / batch
+        if name == "spmv":
+            return stencil_flops(dim) + 2, 4 + 4 + 1
+        if name == "project":
+            return 2 * k, 4 + k * phi_bytes / batch
     if name == "update":   # r,q,p,dinv read, r written; x (FP64) read+written; Phi; S z; Phi^T S z
         return 2 * k + stencil_flops(dim) + 9, 5 * vec_bytes + 16 + 1 + k * phi_bytes
     if name == "expand":   # r,dinv,p read; p written; Phi read; Phi c
@@ -222,12 +239,14 @@ def main():
     ap.add_argument("--workload", default="diff3d_128")
     ap.add_argument("--n", type=int, default=0, help="grid override (profiling captures only)")
     ap.add_argument("--max-cg", type=int, default=0, help="CG cap (profiling captures only)")
-    ap.add_argument("--path", default="plain", choices=["plain", "mixed"],
+    ap.add_argument("--path", default="mixed", choices=["plain", "mixed"],
                     help="plain: FP64 A-DEF2 per instance; mixed: FP32/BF16 with FP64 refinement")
     ap.add_argument("--phi", default="bf16", choices=["f32", "bf16"], help="mode storage (mixed)")
-    ap.add_argument("--batch", type=int, default=1, help="instances per step and GPU")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="instances per step and GPU (default: 16 mixed, 1 plain)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-path comparison")
     args = ap.parse_args()
 
     from paper_2606_17971_b300 import workloads as W
@@ -252,7 +271,7 @@ def main():
     mixed = args.path == "mixed"
     phi_dt = (sdf.BF16 if args.phi == "bf16" else sdf.F32) if mixed else sdf.F64
     G, phi = make_problem(w, sdf, dev, phi_dt)
-    B = args.batch
+    B = args.batch or (16 if mixed else 1)
     steps, warm = args.steps, args.warmup
     insts = W.draw_instances(w, count=(steps + warm) * B * world)
     mine = insts[rank::world]
@@ -260,12 +279,13 @@ def main():
               for i in range(steps + warm)]
     psi = torch.full((w.N,), w.psi, dtype=torch.float64, device=dev)
     opts = sdf.default_opts(check_every=128, precision=sdf.PREC_MIXED if mixed else sdf.PREC_F64)
+    opts_lambda = False
     if args.max_cg:
         opts.max_cg = args.max_cg
     out = {"y": torch.empty((B, w.N), dtype=torch.float64, device=dev), "lam": None,
            "active": torch.empty((B, w.N), dtype=torch.uint8, device=dev)}
     for i in range(warm):
-        G.solve(inst_t[i], psi, opts, out=out)
+        G.solve(inst_t[i], psi, opts, out=out, want_lambda=opts_lambda)
     torch.cuda.synchronize()
 
     # ---- timed region (device-resident inputs) ----
@@ -280,7 +300,7 @@ def main():
     with ClockSampler(local) as clk:
         e0.record(stream)
         for i in range(steps):
-            res = G.solve(inst_t[warm + i], psi, opts, out=out)
+            res = G.solve(inst_t[warm + i], psi, opts, out=out, want_lambda=opts_lambda)
             stats.extend(res["stats"])
         e1.record(stream)
         torch.cuda.synchronize()
@@ -319,11 +339,11 @@ def main():
                "d2h_bytes_per_step": int(y_h.nbytes + a_h.nbytes)}
 
     # ---- roofline of the dominant kernel ----
-    names = ("expand", "spmv", "update")
+    names = ("expand", "spmv", "update") + (("project",) if mixed else ())
     tot = {n: (prof["mean_ms"][n] or 0.0) * prof["samples"][n] for n in names}
     dom = max(names, key=lambda n: tot[n])
     phi_bytes = 8 if not mixed else (2 if args.phi == "bf16" else 4)
-    flops_dof, bytes_dof = kernel_work(dom, w.dim, w.k, phi_bytes, 4 if mixed else 8)
+    flops_dof, bytes_dof = kernel_work(dom, w.dim, w.k, phi_bytes, 4 if mixed else 8, mixed, B)
     units = w.N * B
     mean_s = prof["mean_ms"][dom] * 1e-3
     hbm = peaks().get("hbm_gbs")
@@ -345,7 +365,8 @@ def main():
             "hbm_gbs_at_algorithmic_bytes": bytes_dof * units / mean_s / 1e9,
             "hbm_peak_gbs": hbm, "mean_launch_ms": prof["mean_ms"][dom],
             "timed_launches": prof["samples"][dom],
-            "kernel_mean_ms": {n: prof["mean_ms"][n] for n in names + ("resid",)}})
+            "kernel_mean_ms": {n: prof["mean_ms"][n] for n in names + ("resid",)},
+            "units_per_launch": units})
 
     cg = [sum(s["cg_iters"]) for s in stats]
     outer = [s["outer_iters"] for s in stats]
@@ -367,6 +388,25 @@ def main():
         "roofline": roof, "clocks": clk.summary(), "e2e": e2e,
         "gpu_launches": int(prof["launches"]),
     }
+    if mixed and not args.no_plain:
+        # the metric compares against the plain per-instance FP64 path: one
+        # instance of the same workload after one warm-up solve
+        Gp, _ = make_problem(w, sdf, dev, sdf.F64)
+        op = sdf.default_opts(check_every=128)
+        one = inst_t[0][:1].contiguous()
+        Gp.solve(one, psi, op, want_lambda=False)
+        torch.cuda.synchronize()
+        ep0, ep1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ep0.record(stream)
+        rp = Gp.solve(inst_t[1][:1].contiguous(), psi, op, want_lambda=False)
+        ep1.record(stream)
+        torch.cuda.synchronize()
+        pv = 1e3 / ep0.elapsed_time(ep1)
+        line["plain_fp64_per_instance"] = {
+            "value": pv, "unit": UNIT, "instances_timed": 1,
+            "cg_iters": sum(rp["stats"][0]["cg_iters"]), "note": "same workload, same run"}
+        line["speedup_vs_plain"] = value / pv
+        del Gp
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ts, ti, cores = cpu_sample(w, mine[0], 20)
         per = np.mean(outer) * ts + np.mean(cg) * ti
