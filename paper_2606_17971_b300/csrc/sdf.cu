@@ -74,7 +74,7 @@ struct Ctrl {       // grid-wide control words (device)
 struct Layout {
   size_t x, b64, r, r2, p, q, w, dinv, mask, W, Einv, Eraw, G, coarse, part, gpart, state, cnt,
       ctrl, v, cvec, ppart, xlo, total;
-  int gx, gxa, gxg, gxp, nb, bpad;
+  int gx, gxa, gxg, gxp, nb, bpad, gxc, zc;
 };
 
 inline size_t al(size_t v) { return (v + 255) & ~size_t(255); }
@@ -927,6 +927,46 @@ __global__ void __launch_bounds__(NT) k_expand_b(const PhiT *__restrict__ Phi, l
   }
 }
 
+__device__ __forceinline__ void update_epilogue(InstState &S, double rho_new, double rn2, int *cnt_slot,
+                                                Ctrl *ctrl, double rtol2, int max_cg) {
+  {
+    *cnt_slot = 0;
+    if (S.phase == 0) S.iters += 1;
+    S.rnorm2 = rn2;
+    const bool conv = rn2 <= rtol2 * S.bnorm2;
+    if (!isfinite(rho_new) || !isfinite(rn2)) {
+      S.stats.status = SDF_ERR_NONFINITE;
+      S.cg_done = 1;
+    } else if (S.iters >= max_cg) {
+      S.stats.status = SDF_ERR_CG_MAXIT;
+      S.cg_done = 1;
+    } else {
+      if (conv) S.await = 1;
+      if (S.phase == 1) {
+        S.beta = 0.0;
+      } else if (S.phase == 2) {
+        // Correction pass after an FP64 residual replacement: continue CG
+        // (beta from the replaced iteration's rho) while the true residual is
+        // close to the recurrence residual; restart (beta = 0) when the
+        // recurrence had run ahead of FP32's attainable accuracy.
+        S.beta = rho_new > 4.0 * S.rho ? 0.0 : rho_new / S.rho_prev;
+      } else {
+        S.beta = rho_new / S.rho;
+      }
+      if (S.phase != 2) S.rho_prev = S.rho;
+      S.rho = rho_new;
+      S.gamma = 1.0;
+      S.csign = 1.0;
+      S.phase = 0;
+    }
+    if (S.cg_done) {
+      S.stats.cg_iters[S.outer] = S.iters;
+      S.stats.relres[S.outer] = S.bnorm2 > 0 ? sqrt(rn2 / S.bnorm2) : 0.0;
+      atomicSub(&ctrl->running, 1);
+    }
+  }
+}
+
 // Stencil part of the CG update (mixed path): x += alpha p (FP64), r -= alpha q,
 // z = D^-1 r, v = S_II z - r (written for the projection GEMM), rho = (r, z),
 // ||r||^2 with FP32 products summed in FP64.  The last block applies the
@@ -1000,43 +1040,128 @@ __global__ void __launch_bounds__(NT) k_update_v(OpParams P, const double *inst,
   __shared__ double scratch[NT];
   __shared__ double tot2[2];
   reduce_fields(part + (long long)b * GX * 2, GX, 2, 2, tot2, scratch);
+  if (threadIdx.x == 0) update_epilogue(S, tot2[0], tot2[1], cnt + b * NCNT + CNT_UPDATE, ctrl,
+                                        rtol2, max_cg);
+}
+
+// 3D column variants (2.5D z-marching) of k_spmv and k_update_v for the mixed
+// path; same arithmetic and reductions, different traversal.
+__device__ __forceinline__ void sigma_epilogue(InstState &S, int b, double sg, double *part, int *cnt,
+                                               Ctrl *ctrl, int GX, double *red, double *scratch,
+                                               double *tot1, int *flag) {
+  const int gblk = blockIdx.y;
+  sg = block_sum(sg, red);
+  if (threadIdx.x == 0) part[(long long)b * GX + gblk] = sg;
+  if (!last_block(cnt + b * NCNT + CNT_SIGMA, GX, flag)) return;
+  reduce_fields(part + (long long)b * GX, GX, 1, 1, tot1, scratch);
   if (threadIdx.x == 0) {
-    const double rho_new = tot2[0], rn2 = tot2[1];
-    cnt[b * NCNT + CNT_UPDATE] = 0;
-    if (S.phase == 0) S.iters += 1;
-    S.rnorm2 = rn2;
-    const bool conv = rn2 <= rtol2 * S.bnorm2;
-    if (!isfinite(rho_new) || !isfinite(rn2)) {
-      S.stats.status = SDF_ERR_NONFINITE;
-      S.cg_done = 1;
-    } else if (S.iters >= max_cg) {
-      S.stats.status = SDF_ERR_CG_MAXIT;
-      S.cg_done = 1;
+    double s = tot1[0];
+    cnt[b * NCNT + CNT_SIGMA] = 0;
+    S.sigma = s;
+    if (S.phase) {
+      S.alpha = 1.0;
+    } else if (s > 0.0 && isfinite(s)) {
+      S.alpha = S.rho / s;
     } else {
-      if (conv) S.await = 1;
-      if (S.phase == 1) {
-        S.beta = 0.0;
-      } else if (S.phase == 2) {
-        // Correction pass after an FP64 residual replacement: continue CG
-        // (beta from the replaced iteration's rho) while the true residual is
-        // close to the recurrence residual; restart (beta = 0) when the
-        // recurrence had run ahead of FP32's attainable accuracy.
-        S.beta = rho_new > 4.0 * S.rho ? 0.0 : rho_new / S.rho_prev;
-      } else {
-        S.beta = rho_new / S.rho;
-      }
-      if (S.phase != 2) S.rho_prev = S.rho;
-      S.rho = rho_new;
-      S.gamma = 1.0;
-      S.csign = 1.0;
-      S.phase = 0;
-    }
-    if (S.cg_done) {
+      S.stats.status = isfinite(s) ? SDF_ERR_BREAKDOWN : SDF_ERR_NONFINITE;
+      S.cg_done = 1;
       S.stats.cg_iters[S.outer] = S.iters;
-      S.stats.relres[S.outer] = S.bnorm2 > 0 ? sqrt(rn2 / S.bnorm2) : 0.0;
       atomicSub(&ctrl->running, 1);
     }
   }
+}
+
+__global__ void __launch_bounds__(NT) k_spmv3c(OpParams P, const double *inst, InstState *st,
+                                               const uint8_t *mask, const float *p, float *q,
+                                               double *part, int *cnt, Ctrl *ctrl, int GX, int zc) {
+  __shared__ ColSmem<float> sm;
+  __shared__ double red[NWARP], scratch[NT], tot1[1];
+  __shared__ int flag;
+  const int b = blockIdx.x, gblk = blockIdx.y;
+  InstState &S = st[b];
+  if (S.outer_done || S.cg_done || (S.await && S.phase == 0)) return;
+  const long long N = P.N;
+  double cb[3];
+  inst_cb(P, inst + 7 * b, cb);
+  const uint8_t *mk = mask + b * N;
+  const float *pb = p + b * N;
+  float *qb = q + b * N;
+  KahanF sgf;
+  const long long items = col_items(P.nx, P.ny, P.nz, zc);
+  for (long long t = gblk; t < items; t += GX) {
+    int x0, y0, z0, z1;
+    col_origin(P, t, zc, x0, y0, z0, z1);
+    col_S3<float>(
+        P, cb, x0, y0, z0, z1, sm, [&](long long g) { return pb[g]; },
+        [&](int, int, int, long long g, float su, float uc) {
+          const float qv = mk[g] ? 0.0f : su;
+          qb[g] = qv;
+          sgf.add(uc * qv);
+        });
+  }
+  sigma_epilogue(S, b, sgf.value(), part, cnt, ctrl, GX, red, scratch, tot1, &flag);
+}
+
+__global__ void __launch_bounds__(NT) k_update_v3c(OpParams P, const double *inst, InstState *st,
+                                                   const uint8_t *mask, const float *r_in,
+                                                   float *r_out, const float *q, const float *p,
+                                                   double *x, float *xlo, const float *dinv,
+                                                   float *v, double *part, int *cnt, Ctrl *ctrl,
+                                                   int GX, int zc, double rtol2, int max_cg) {
+  __shared__ ColSmem<float> sm;
+  __shared__ double red[NWARP], scratch[NT], tot2[2];
+  __shared__ int flag;
+  const int b = blockIdx.x, gblk = blockIdx.y;
+  InstState &S = st[b];
+  if (!inst_running(S)) return;
+  const long long N = P.N;
+  const double alpha64 = S.alpha;
+  const float alpha = (float)alpha64;
+  double cb[3];
+  inst_cb(P, inst + 7 * b, cb);
+  const uint8_t *mk = mask + b * N;
+  const float *rb = r_in + b * N, *qb = q + b * N, *pb = p + b * N;
+  float *rw = r_out + b * N, *vb = v + b * N, *xl = xlo + b * N;
+  double *xb = x + b * N;
+  const float *db = dinv + (P.convection ? b * N : 0);
+  const bool fold = S.phase == 2;
+  KahanF rhof, rrf;
+  const long long items = col_items(P.nx, P.ny, P.nz, zc);
+  for (long long t = gblk; t < items; t += GX) {
+    int x0, y0, z0, z1;
+    col_origin(P, t, zc, x0, y0, z0, z1);
+    col_S3<float>(
+        P, cb, x0, y0, z0, z1, sm,
+        [&](long long g) { return db[g] * (rb[g] - alpha * qb[g]); },
+        [&](int, int, int, long long g, float su, float z) {
+          if (mk[g]) {
+            rw[g] = 0.0f;
+            vb[g] = 0.0f;
+            return;
+          }
+          const float rn = rb[g] - alpha * qb[g];
+          if (fold) {
+            xb[g] = xb[g] + (double)xl[g] + alpha64 * (double)pb[g];
+            xl[g] = 0.0f;
+          } else {
+            xl[g] = fmaf(alpha, pb[g], xl[g]);
+          }
+          rw[g] = rn;
+          rhof.add(rn * z);
+          rrf.add(rn * rn);
+          vb[g] = su - rn;
+        });
+  }
+  const double rho = block_sum(rhof.value(), red);
+  const double rr = block_sum(rrf.value(), red);
+  if (threadIdx.x == 0) {
+    part[((long long)b * GX + gblk) * 2 + 0] = rho;
+    part[((long long)b * GX + gblk) * 2 + 1] = rr;
+  }
+  if (!last_block(cnt + b * NCNT + CNT_UPDATE, GX, &flag)) return;
+  reduce_fields(part + (long long)b * GX * 2, GX, 2, 2, tot2, scratch);
+  if (threadIdx.x == 0) update_epilogue(S, tot2[0], tot2[1], cnt + b * NCNT + CNT_UPDATE, ctrl,
+                                        rtol2, max_cg);
 }
 
 // Projection GEMM: part[gblk][b][j] = sum over block gblk's node range of
@@ -1371,7 +1496,15 @@ Layout make_layout(const sdf_problem *p, int B, int max_blocks = 0, int mixed = 
   L.Eraw = take(kk * B);
   L.G = take(kk * B);
   L.coarse = take(kk * B * 5);
-  int gmax = std::max(L.gx, std::max(L.gxa, 1));
+  // 3D column traversal of the mixed path: z-chunks of zc planes
+  L.zc = B >= 8 ? 32 : (B >= 2 ? 16 : 8);
+  L.gxc = 1;
+  if (p->d.dim == 3) {
+    long long items = col_items(p->P.nx, p->P.ny, p->P.nz, L.zc);
+    L.gxc = (int)std::max<long long>(1, std::min<long long>(items, (target + B - 1) / B));
+    if (max_blocks > 0) L.gxc = std::min(L.gxc, max_blocks);
+  }
+  int gmax = std::max(std::max(L.gx, L.gxc), std::max(L.gxa, 1));
   L.part = take(sizeof(double) * (size_t)B * gmax * (KM + 4));
   L.gpart = take(sizeof(double) * (size_t)L.gxg * k * k);
   L.state = take(sizeof(InstState) * (size_t)B);
@@ -1607,10 +1740,18 @@ sdf_status solve_mixed(sdf_problem *p, const double *inst, int B, const double *
     k_expand_b<KMAX, PhiT><<<gxe, NT, esm, s>>>(Phi, ld, k, N, B, st, cvec, mask, rbuf[par], dinv,
                                                 P.convection, dir);
     if (timed) CK(cudaEventRecord(p->ev[1], s));
-    k_spmv<DIM, float><<<gT, NT, 0, s>>>(P, inst, st, mask, dir, q, part, cnt, ctrl, L.gx);
-    if (timed) CK(cudaEventRecord(p->ev[2], s));
-    k_update_v<DIM><<<gT, NT, 0, s>>>(P, inst, st, mask, rbuf[par], rbuf[par ^ 1], q, dir, x, xlo,
-                                      dinv, vv, part, cnt, ctrl, L.gx, rtol2, o.max_cg);
+    if constexpr (DIM == 3) {
+      const dim3 gC(B, L.gxc);
+      k_spmv3c<<<gC, NT, 0, s>>>(P, inst, st, mask, dir, q, part, cnt, ctrl, L.gxc, L.zc);
+      if (timed) CK(cudaEventRecord(p->ev[2], s));
+      k_update_v3c<<<gC, NT, 0, s>>>(P, inst, st, mask, rbuf[par], rbuf[par ^ 1], q, dir, x, xlo,
+                                     dinv, vv, part, cnt, ctrl, L.gxc, L.zc, rtol2, o.max_cg);
+    } else {
+      k_spmv<DIM, float><<<gT, NT, 0, s>>>(P, inst, st, mask, dir, q, part, cnt, ctrl, L.gx);
+      if (timed) CK(cudaEventRecord(p->ev[2], s));
+      k_update_v<DIM><<<gT, NT, 0, s>>>(P, inst, st, mask, rbuf[par], rbuf[par ^ 1], q, dir, x,
+                                        xlo, dinv, vv, part, cnt, ctrl, L.gx, rtol2, o.max_cg);
+    }
     if (timed) CK(cudaEventRecord(p->ev[3], s));
     sdf_status e = project(vv);
     if (e != SDF_OK) return e;

@@ -299,6 +299,169 @@ __device__ void tile_S(const OpParams &P, const double cb64[3], int ox, int oy, 
     tile_S_rows<DIM, T, false>(P, cb, cd, mass, wgt, ox, oy, oz, sm, load, store);
 }
 
+// ---------------------------------------------------------------------------
+// 3D column stencil (2.5D blocking): an xy tile of CX x CY = 32 x 8 nodes
+// marches in z through [z0, z1).  Shared memory holds a ring of five u planes
+// (z-2 .. z+2, halo 2 in x and y) and a ring of three w = A u planes (z-1 ..
+// z+1, halo 1), so each node's u is loaded 36*12/256 = 1.7 times and its w
+// computed 34*10/256 = 1.3 times; per-thread plane offsets are fixed.
+constexpr int CX = 32, CY = 8;
+constexpr int CUX = CX + 4, CUY = CY + 4, CWX = CX + 2, CWY = CY + 2;
+
+template <class T> struct ColSmem {
+  T u[5][CUY * CUX];
+  T w[3][CWY * CWX];
+};
+
+__device__ __forceinline__ int ring5(int z) { return ((z % 5) + 5) % 5; }
+__device__ __forceinline__ int ring3(int z) { return ((z % 3) + 3) % 3; }
+
+// load(g) gives u at grid node g; store(gx, gy, gz, g, Su, u_center) receives
+// S u at every grid node of the column.  NT threads.
+template <class T, bool VARK, class Load, class Store>
+__device__ __forceinline__ void col_S3_impl(const OpParams &P, const T cb[3], const T cd[3], T mass,
+                                            T wgt, int x0, int y0, int z0, int z1,
+                                            ColSmem<T> &sm, Load &load, Store &store) {
+  const long long nxy = (long long)P.nx * P.ny;
+  // per-thread u-load slots (<= 2): local index, xy-in-grid flag, xy offset
+  int ue[2];
+  bool uin[2];
+  long long uoff[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    int e = threadIdx.x + q * NT;
+    ue[q] = e < CUY * CUX ? e : -1;
+    int lx = e % CUX - 2, ly = e / CUX - 2;
+    int gx = x0 + lx, gy = y0 + ly;
+    uin[q] = ue[q] >= 0 && gx >= 0 && gx < P.nx && gy >= 0 && gy < P.ny;
+    uoff[q] = (long long)gy * P.nx + gx;
+  }
+  // per-thread w slots (<= 2)
+  int we[2], wgx[2], wgy[2], wuc[2];
+  bool win[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    int e = threadIdx.x + q * NT;
+    we[q] = e < CWY * CWX ? e : -1;
+    int lx = e % CWX - 1, ly = e / CWX - 1;
+    wgx[q] = x0 + lx;
+    wgy[q] = y0 + ly;
+    win[q] = we[q] >= 0 && wgx[q] >= 0 && wgx[q] < P.nx && wgy[q] >= 0 && wgy[q] < P.ny;
+    wuc[q] = (ly + 2) * CUX + (lx + 2);  // center in the u plane
+  }
+  // output slot (exactly one per thread)
+  const int olx = threadIdx.x % CX, oly = threadIdx.x / CX;
+  const int ogx = x0 + olx, ogy = y0 + oly;
+  const bool oin = ogx < P.nx && ogy < P.ny;
+  const int owc = (oly + 1) * CWX + (olx + 1), ouc = (oly + 2) * CUX + (olx + 2);
+  const long long ooff = (long long)ogy * P.nx + ogx;
+
+  auto load_u = [&](int z) {
+    T *up = sm.u[ring5(z)];
+    const bool zin = z >= 0 && z < P.nz;
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+      if (ue[q] >= 0) up[ue[q]] = (zin && uin[q]) ? (T)load((long long)z * nxy + uoff[q]) : (T)0;
+  };
+  auto comp_w = [&](int z) {  // w plane z from u planes z-1, z, z+1
+    T *wp = sm.w[ring3(z)];
+    const T *um = sm.u[ring5(z - 1)], *uc = sm.u[ring5(z)], *upl = sm.u[ring5(z + 1)];
+    const bool zin = z >= 0 && z < P.nz;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      if (we[q] < 0) continue;
+      T val = (T)0;
+      if (zin && win[q]) {
+        const int c0 = wuc[q];
+        const T c = uc[c0];
+        const T xm = uc[c0 - 1], xp = uc[c0 + 1], ym = uc[c0 - CUX], yp = uc[c0 + CUX];
+        const T zm = um[c0], zp = upl[c0];
+        T fw, fe, fs, fn, fb, ft;
+        if (VARK) {
+          const int gx = wgx[q], gy = wgy[q];
+          fw = fx_T(P, cd, gx, gy, z); fe = fx_T(P, cd, gx + 1, gy, z);
+          fs = fy_T(P, cd, gx, gy, z); fn = fy_T(P, cd, gx, gy + 1, z);
+          fb = fz_T(P, cd, gx, gy, z); ft = fz_T(P, cd, gx, gy, z + 1);
+        } else {
+          fw = fe = cd[0]; fs = fn = cd[1]; fb = ft = cd[2];
+        }
+        T acc = fw * (c - xm) + fe * (c - xp) + fs * (c - ym) + fn * (c - yp) + fb * (c - zm) +
+                ft * (c - zp);
+        if (cb[0] > (T)0) acc += cb[0] * (c - xm);
+        else if (cb[0] < (T)0) acc -= cb[0] * (c - xp);
+        if (cb[1] > (T)0) acc += cb[1] * (c - ym);
+        else if (cb[1] < (T)0) acc -= cb[1] * (c - yp);
+        if (cb[2] > (T)0) acc += cb[2] * (c - zm);
+        else if (cb[2] < (T)0) acc -= cb[2] * (c - zp);
+        val = acc;
+      }
+      wp[we[q]] = val;
+    }
+  };
+  // prologue: u planes z0-2 .. z0+1, w planes z0-1, z0
+  for (int z = z0 - 2; z <= z0 + 1; ++z) load_u(z);
+  __syncthreads();
+  comp_w(z0 - 1);
+  comp_w(z0);
+  for (int z = z0; z < z1; ++z) {
+    load_u(z + 2);
+    __syncthreads();
+    comp_w(z + 1);
+    __syncthreads();
+    if (oin && z < P.nz) {
+      const T *wm = sm.w[ring3(z - 1)], *wc = sm.w[ring3(z)], *wpl = sm.w[ring3(z + 1)];
+      const T c = wc[owc];
+      const T xm = wc[owc - 1], xp = wc[owc + 1], ym = wc[owc - CWX], yp = wc[owc + CWX];
+      const T zm = wm[owc], zp = wpl[owc];
+      T fw, fe, fs, fn, fb, ft;
+      if (VARK) {
+        fw = fx_T(P, cd, ogx, ogy, z); fe = fx_T(P, cd, ogx + 1, ogy, z);
+        fs = fy_T(P, cd, ogx, ogy, z); fn = fy_T(P, cd, ogx, ogy + 1, z);
+        fb = fz_T(P, cd, ogx, ogy, z); ft = fz_T(P, cd, ogx, ogy, z + 1);
+      } else {
+        fw = fe = cd[0]; fs = fn = cd[1]; fb = ft = cd[2];
+      }
+      T acc = fw * (c - xm) + fe * (c - xp) + fs * (c - ym) + fn * (c - yp) + fb * (c - zm) +
+              ft * (c - zp);
+      if (cb[0] > (T)0) acc += cb[0] * (c - xp);
+      else if (cb[0] < (T)0) acc -= cb[0] * (c - xm);
+      if (cb[1] > (T)0) acc += cb[1] * (c - yp);
+      else if (cb[1] < (T)0) acc -= cb[1] * (c - ym);
+      if (cb[2] > (T)0) acc += cb[2] * (c - zp);
+      else if (cb[2] < (T)0) acc -= cb[2] * (c - zm);
+      const T uc = sm.u[ring5(z)][ouc];
+      store(ogx, ogy, z, (long long)z * nxy + ooff, mass * uc + wgt * acc, uc);
+    }
+  }
+  __syncthreads();
+}
+
+template <class T, class Load, class Store>
+__device__ void col_S3(const OpParams &P, const double cb64[3], int x0, int y0, int z0, int z1,
+                       ColSmem<T> &sm, Load load, Store store) {
+  const T cb[3] = {(T)cb64[0], (T)cb64[1], (T)cb64[2]};
+  const T cd[3] = {(T)P.cdiff[0], (T)P.cdiff[1], (T)P.cdiff[2]};
+  const T mass = (T)P.mass, wgt = (T)P.wgt;
+  if (P.fx)
+    col_S3_impl<T, true>(P, cb, cd, mass, wgt, x0, y0, z0, z1, sm, load, store);
+  else
+    col_S3_impl<T, false>(P, cb, cd, mass, wgt, x0, y0, z0, z1, sm, load, store);
+}
+
+// Column work items of a 3D grid: xy tiles x z-chunks of zc planes.
+__host__ __device__ inline long long col_items(int nx, int ny, int nz, int zc) {
+  return (long long)((nx + CX - 1) / CX) * ((ny + CY - 1) / CY) * ((nz + zc - 1) / zc);
+}
+__device__ __forceinline__ void col_origin(const OpParams &P, long long t, int zc, int &x0, int &y0,
+                                           int &z0, int &z1) {
+  int ntx = (P.nx + CX - 1) / CX, nty = (P.ny + CY - 1) / CY;
+  x0 = (int)(t % ntx) * CX;
+  long long r = t / ntx;
+  y0 = (int)(r % nty) * CY;
+  z0 = (int)(r / nty) * zc;
+  z1 = min(z0 + zc, P.nz);
+}
+
 // Accumulate acc[jj] += sum over the tile of Phi_j(g) v(g) for modes
 // j = warp + NWARP*jj < k; lanes run over the contiguous x-rows of the tile
 // (coalesced reads of each mode).  v is the tile-local vector in shared memory
