@@ -1071,7 +1071,7 @@ __device__ __forceinline__ void sigma_epilogue(InstState &S, int b, double sg, d
   }
 }
 
-__global__ void __launch_bounds__(NT) k_spmv3c(OpParams P, const double *inst, InstState *st,
+__global__ void __launch_bounds__(NT, 3) k_spmv3c(OpParams P, const double *inst, InstState *st,
                                                const uint8_t *mask, const float *p, float *q,
                                                double *part, int *cnt, Ctrl *ctrl, int GX, int zc) {
   __shared__ ColSmem<float> sm;
@@ -1102,7 +1102,7 @@ __global__ void __launch_bounds__(NT) k_spmv3c(OpParams P, const double *inst, I
   sigma_epilogue(S, b, sgf.value(), part, cnt, ctrl, GX, red, scratch, tot1, &flag);
 }
 
-__global__ void __launch_bounds__(NT) k_update_v3c(OpParams P, const double *inst, InstState *st,
+__global__ void __launch_bounds__(NT, 3) k_update_v3c(OpParams P, const double *inst, InstState *st,
                                                    const uint8_t *mask, const float *r_in,
                                                    float *r_out, const float *q, const float *p,
                                                    double *x, float *xlo, const float *dinv,

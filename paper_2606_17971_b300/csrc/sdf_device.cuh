@@ -356,12 +356,22 @@ __device__ __forceinline__ void col_S3_impl(const OpParams &P, const T cb[3], co
   const int owc = (oly + 1) * CWX + (olx + 1), ouc = (oly + 2) * CUX + (olx + 2);
   const long long ooff = (long long)ogy * P.nx + ogx;
 
-  auto load_u = [&](int z) {
-    T *up = sm.u[ring5(z)];
+  auto fetch_u = [&](int z, T (&val)[2]) {  // global -> registers
     const bool zin = z >= 0 && z < P.nz;
 #pragma unroll
     for (int q = 0; q < 2; ++q)
-      if (ue[q] >= 0) up[ue[q]] = (zin && uin[q]) ? (T)load((long long)z * nxy + uoff[q]) : (T)0;
+      val[q] = (ue[q] >= 0 && zin && uin[q]) ? (T)load((long long)z * nxy + uoff[q]) : (T)0;
+  };
+  auto put_u = [&](int z, const T (&val)[2]) {  // registers -> shared ring slot
+    T *up = sm.u[ring5(z)];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+      if (ue[q] >= 0) up[ue[q]] = val[q];
+  };
+  auto load_u = [&](int z) {
+    T val[2];
+    fetch_u(z, val);
+    put_u(z, val);
   };
   auto comp_w = [&](int z) {  // w plane z from u planes z-1, z, z+1
     T *wp = sm.w[ring3(z)];
@@ -398,13 +408,18 @@ __device__ __forceinline__ void col_S3_impl(const OpParams &P, const T cb[3], co
       wp[we[q]] = val;
     }
   };
-  // prologue: u planes z0-2 .. z0+1, w planes z0-1, z0
+  // prologue: u planes z0-2 .. z0+1, w planes z0-1, z0; plane z0+2 in flight
   for (int z = z0 - 2; z <= z0 + 1; ++z) load_u(z);
+  T nxt[2];
+  fetch_u(z0 + 2, nxt);
   __syncthreads();
   comp_w(z0 - 1);
   comp_w(z0);
   for (int z = z0; z < z1; ++z) {
-    load_u(z + 2);
+    // software pipeline: plane z+2 arrived in registers during the previous
+    // step; plane z+3 is requested now and lands while this plane computes
+    put_u(z + 2, nxt);
+    if (z + 1 < z1) fetch_u(z + 3, nxt);
     __syncthreads();
     comp_w(z + 1);
     __syncthreads();
