@@ -102,7 +102,7 @@ __device__ __forceinline__ double desired(const OpParams &P, const double *inst,
 // problem set-up: face coefficients and the shared Jacobi diagonal
 
 __global__ void k_faces(OpParams P, const double *kappa, double diff_scale, double *fx,
-                        double *fy, double *fz) {
+                        double *fy, double *fz, float *fxf, float *fyf, float *fzf) {
   long long nfx = (long long)(P.nx + 1) * P.ny * P.nz;
   long long nfy = (long long)P.nx * (P.ny + 1) * P.nz;
   long long nfz = P.dim == 3 ? (long long)P.nx * P.ny * (P.nz + 1) : 0;
@@ -116,6 +116,7 @@ __global__ void k_faces(OpParams P, const double *kappa, double diff_scale, doub
       int j = (int)(t % P.ny), l = (int)(t / P.ny);
       double kf = i == 0 ? kap(0, j, l) : i == P.nx ? kap(P.nx - 1, j, l) : hm(kap(i - 1, j, l), kap(i, j, l));
       fx[e] = diff_scale * kf * P.inv_h[0] * P.inv_h[0];
+      fxf[e] = (float)fx[e];
     } else if (e < nfx + nfy) {
       long long f = e - nfx;
       int i = (int)(f % P.nx);
@@ -123,6 +124,7 @@ __global__ void k_faces(OpParams P, const double *kappa, double diff_scale, doub
       int j = (int)(t % (P.ny + 1)), l = (int)(t / (P.ny + 1));
       double kf = j == 0 ? kap(i, 0, l) : j == P.ny ? kap(i, P.ny - 1, l) : hm(kap(i, j - 1, l), kap(i, j, l));
       fy[f] = diff_scale * kf * P.inv_h[1] * P.inv_h[1];
+      fyf[f] = (float)fy[f];
     } else {
       long long f = e - nfx - nfy;
       int i = (int)(f % P.nx);
@@ -130,6 +132,7 @@ __global__ void k_faces(OpParams P, const double *kappa, double diff_scale, doub
       int j = (int)(t % P.ny), l = (int)(t / P.ny);
       double kf = l == 0 ? kap(i, j, 0) : l == P.nz ? kap(i, j, P.nz - 1) : hm(kap(i, j, l - 1), kap(i, j, l));
       fz[f] = diff_scale * kf * P.inv_h[2] * P.inv_h[2];
+      fzf[f] = (float)fz[f];
     }
   }
 }
@@ -898,31 +901,41 @@ __global__ void __launch_bounds__(NT) k_expand_b(const PhiT *__restrict__ Phi, l
 #pragma unroll
     for (int j = 0; j < KMAX; ++j) ph[j] = j < k ? (float)Phi[(long long)j * ld + g] : 0.0f;
     const float d_shared = dinv_per_inst ? 0.0f : dinv[g];
-    for (int b = 0; b < B; ++b) {
-      const int a = act[b];
-      if (!a) continue;
-      const long long gb = (long long)b * N + g;
-      // issue every load before the mask test (r and p are zero on A)
-      const uint8_t mk = mask[gb];
-      const float db = dinv_per_inst ? dinv[gb] : d_shared;
-      const float rv = r[gb];
-      const float pv = bet[b] != 0.0f ? p[gb] : 0.0f;
-      float v = 0.0f;
-      if (!mk) {
-        v = gam[b] * db * rv;
-        v = fmaf(bet[b], pv, v);
-        if (a & 2) {
-          const float *cb = cs + (size_t)b * KMAX;
-          float s0 = 0.0f, s1 = 0.0f;
+    // instances in groups of four: every load of the group is issued before
+    // the mode sums, so the memory latency of one instance overlaps the others
+    for (int b0 = 0; b0 < B; b0 += 4) {
+      uint8_t mk[4];
+      float dv[4], rv[4], pv[4];
 #pragma unroll
-          for (int j = 0; j < KMAX; j += 2) {
-            s0 = fmaf(ph[j], cb[j], s0);
-            s1 = fmaf(ph[j + 1], cb[j + 1], s1);
-          }
-          v -= s0 + s1;
-        }
+      for (int u = 0; u < 4; ++u) {
+        const int b = b0 + u;
+        const bool on = b < B && act[b];
+        const long long gb = (long long)b * N + g;
+        mk[u] = on ? mask[gb] : (uint8_t)1;
+        dv[u] = on ? (dinv_per_inst ? dinv[gb] : d_shared) : 0.0f;
+        rv[u] = on ? r[gb] : 0.0f;
+        pv[u] = (on && bet[b] != 0.0f) ? p[gb] : 0.0f;
       }
-      p[gb] = v;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int b = b0 + u;
+        if (b >= B || !act[b]) continue;
+        float v = 0.0f;
+        if (!mk[u]) {
+          v = fmaf(bet[b], pv[u], gam[b] * dv[u] * rv[u]);
+          if (act[b] & 2) {
+            const float *cb = cs + (size_t)b * KMAX;
+            float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+            for (int j = 0; j < KMAX; j += 2) {
+              s0 = fmaf(ph[j], cb[j], s0);
+              s1 = fmaf(ph[j + 1], cb[j + 1], s1);
+            }
+            v -= s0 + s1;
+          }
+        }
+        p[(long long)b * N + g] = v;
+      }
     }
   }
 }
@@ -1071,6 +1084,66 @@ __device__ __forceinline__ void sigma_epilogue(InstState &S, int b, double sg, d
   }
 }
 
+// Column-stencil sources and outputs of the two mixed-path kernels.
+struct ColSrcP {  // u = p
+  const float *p;
+  using Raw = float;
+  __device__ __forceinline__ Raw fetch(long long g) const { return p[g]; }
+  __device__ __forceinline__ float value(Raw r) const { return r; }
+};
+struct ColOutQ {  // q = S_II p (zero on the active set), sigma = (p, q)
+  const uint8_t *mk;
+  float *q;
+  KahanF sg;
+  struct Pre { uint8_t m; };
+  __device__ __forceinline__ Pre fetch(long long g) const { return Pre{mk[g]}; }
+  __device__ __forceinline__ void store(long long g, float su, float uc, const Pre &pr) {
+    const float qv = pr.m ? 0.0f : su;
+    q[g] = qv;
+    sg.add(uc * qv);
+  }
+};
+struct ColSrcZ {  // u = z = D^-1 (r - alpha q); r and q vanish on the active set
+  const float *r, *q, *dinv;
+  float alpha;
+  struct Raw { float r, q, d; };
+  __device__ __forceinline__ Raw fetch(long long g) const { return Raw{r[g], q[g], dinv[g]}; }
+  __device__ __forceinline__ float value(const Raw &a) const { return a.d * (a.r - alpha * a.q); }
+};
+// FOLD: correction pass, which folds x_lo into the FP64 iterate.  A separate
+// instantiation keeps the FP64 arithmetic (1/64 of the FP32 rate on this part)
+// out of the other 99 of every 100 passes.
+template <bool FOLD> struct ColOutUpd {  // r, x, v = S z - r and the CG dot products
+  const uint8_t *mk;
+  const float *r, *q, *p;
+  float *rw, *v, *xl;
+  double *x;
+  float alpha;
+  double alpha64;
+  KahanF rho, rr;
+  struct Pre { float r, q, p, xl; uint8_t m; };
+  __device__ __forceinline__ Pre fetch(long long g) const { return Pre{r[g], q[g], p[g], xl[g], mk[g]}; }
+  __device__ __forceinline__ void store(long long g, float su, float z, const Pre &a) {
+    if (a.m) {
+      rw[g] = 0.0f;
+      v[g] = 0.0f;
+      return;
+    }
+    const float rn = a.r - alpha * a.q;
+    if (FOLD) {
+      x[g] = x[g] + (double)a.xl + alpha64 * (double)a.p;
+      xl[g] = 0.0f;
+    } else {
+      xl[g] = fmaf(alpha, a.p, a.xl);
+    }
+    rw[g] = rn;
+    rho.add(rn * z);
+    rr.add(rn * rn);
+    v[g] = su - rn;
+  }
+};
+
+template <bool VARK>
 __global__ void __launch_bounds__(NT, 3) k_spmv3c(OpParams P, const double *inst, InstState *st,
                                                const uint8_t *mask, const float *p, float *q,
                                                double *part, int *cnt, Ctrl *ctrl, int GX, int zc) {
@@ -1083,25 +1156,18 @@ __global__ void __launch_bounds__(NT, 3) k_spmv3c(OpParams P, const double *inst
   const long long N = P.N;
   double cb[3];
   inst_cb(P, inst + 7 * b, cb);
-  const uint8_t *mk = mask + b * N;
-  const float *pb = p + b * N;
-  float *qb = q + b * N;
-  KahanF sgf;
+  const ColSrcP src{p + b * N};
+  ColOutQ out{mask + b * N, q + b * N};
   const long long items = col_items(P.nx, P.ny, P.nz, zc);
   for (long long t = gblk; t < items; t += GX) {
     int x0, y0, z0, z1;
     col_origin(P, t, zc, x0, y0, z0, z1);
-    col_S3<float>(
-        P, cb, x0, y0, z0, z1, sm, [&](long long g) { return pb[g]; },
-        [&](int, int, int, long long g, float su, float uc) {
-          const float qv = mk[g] ? 0.0f : su;
-          qb[g] = qv;
-          sgf.add(uc * qv);
-        });
+    col_S3<float, VARK, false>(P, cb, x0, y0, z0, z1, sm, src, out);
   }
-  sigma_epilogue(S, b, sgf.value(), part, cnt, ctrl, GX, red, scratch, tot1, &flag);
+  sigma_epilogue(S, b, out.sg.value(), part, cnt, ctrl, GX, red, scratch, tot1, &flag);
 }
 
+template <bool VARK>
 __global__ void __launch_bounds__(NT, 3) k_update_v3c(OpParams P, const double *inst, InstState *st,
                                                    const uint8_t *mask, const float *r_in,
                                                    float *r_out, const float *q, const float *p,
@@ -1119,41 +1185,26 @@ __global__ void __launch_bounds__(NT, 3) k_update_v3c(OpParams P, const double *
   const float alpha = (float)alpha64;
   double cb[3];
   inst_cb(P, inst + 7 * b, cb);
-  const uint8_t *mk = mask + b * N;
-  const float *rb = r_in + b * N, *qb = q + b * N, *pb = p + b * N;
-  float *rw = r_out + b * N, *vb = v + b * N, *xl = xlo + b * N;
-  double *xb = x + b * N;
-  const float *db = dinv + (P.convection ? b * N : 0);
-  const bool fold = S.phase == 2;
-  KahanF rhof, rrf;
+  const ColSrcZ src{r_in + b * N, q + b * N, dinv + (P.convection ? b * N : 0), alpha};
   const long long items = col_items(P.nx, P.ny, P.nz, zc);
-  for (long long t = gblk; t < items; t += GX) {
-    int x0, y0, z0, z1;
-    col_origin(P, t, zc, x0, y0, z0, z1);
-    col_S3<float>(
-        P, cb, x0, y0, z0, z1, sm,
-        [&](long long g) { return db[g] * (rb[g] - alpha * qb[g]); },
-        [&](int, int, int, long long g, float su, float z) {
-          if (mk[g]) {
-            rw[g] = 0.0f;
-            vb[g] = 0.0f;
-            return;
-          }
-          const float rn = rb[g] - alpha * qb[g];
-          if (fold) {
-            xb[g] = xb[g] + (double)xl[g] + alpha64 * (double)pb[g];
-            xl[g] = 0.0f;
-          } else {
-            xl[g] = fmaf(alpha, pb[g], xl[g]);
-          }
-          rw[g] = rn;
-          rhof.add(rn * z);
-          rrf.add(rn * rn);
-          vb[g] = su - rn;
-        });
-  }
-  const double rho = block_sum(rhof.value(), red);
-  const double rr = block_sum(rrf.value(), red);
+  double rho_b, rr_b;
+  auto run = [&](auto out) {
+    for (long long t = gblk; t < items; t += GX) {
+      int x0, y0, z0, z1;
+      col_origin(P, t, zc, x0, y0, z0, z1);
+      col_S3<float, VARK, false>(P, cb, x0, y0, z0, z1, sm, src, out);
+    }
+    rho_b = out.rho.value();
+    rr_b = out.rr.value();
+  };
+  if (S.phase == 2)
+    run(ColOutUpd<true>{mask + b * N, r_in + b * N, q + b * N, p + b * N, r_out + b * N,
+                        v + b * N, xlo + b * N, x + b * N, alpha, alpha64});
+  else
+    run(ColOutUpd<false>{mask + b * N, r_in + b * N, q + b * N, p + b * N, r_out + b * N,
+                         v + b * N, xlo + b * N, x + b * N, alpha, alpha64});
+  const double rho = block_sum(rho_b, red);
+  const double rr = block_sum(rr_b, red);
   if (threadIdx.x == 0) {
     part[((long long)b * GX + gblk) * 2 + 0] = rho;
     part[((long long)b * GX + gblk) * 2 + 1] = rr;
@@ -1501,7 +1552,9 @@ Layout make_layout(const sdf_problem *p, int B, int max_blocks = 0, int mixed = 
   L.gxc = 1;
   if (p->d.dim == 3) {
     long long items = col_items(p->P.nx, p->P.ny, p->P.nz, L.zc);
-    L.gxc = (int)std::max<long long>(1, std::min<long long>(items, (target + B - 1) / B));
+    // one column item per block: the hardware block scheduler balances the
+    // items of all instances across the SMs
+    L.gxc = (int)std::max<long long>(1, std::min<long long>(items, 65535));
     if (max_blocks > 0) L.gxc = std::min(L.gxc, max_blocks);
   }
   int gmax = std::max(std::max(L.gx, L.gxc), std::max(L.gxa, 1));
@@ -1742,10 +1795,13 @@ sdf_status solve_mixed(sdf_problem *p, const double *inst, int B, const double *
     if (timed) CK(cudaEventRecord(p->ev[1], s));
     if constexpr (DIM == 3) {
       const dim3 gC(B, L.gxc);
-      k_spmv3c<<<gC, NT, 0, s>>>(P, inst, st, mask, dir, q, part, cnt, ctrl, L.gxc, L.zc);
+      // the mixed path has no convection (rejected at entry): VARK only
+      auto spmv = P.fx ? k_spmv3c<true> : k_spmv3c<false>;
+      auto upd = P.fx ? k_update_v3c<true> : k_update_v3c<false>;
+      spmv<<<gC, NT, 0, s>>>(P, inst, st, mask, dir, q, part, cnt, ctrl, L.gxc, L.zc);
       if (timed) CK(cudaEventRecord(p->ev[2], s));
-      k_update_v3c<<<gC, NT, 0, s>>>(P, inst, st, mask, rbuf[par], rbuf[par ^ 1], q, dir, x, xlo,
-                                     dinv, vv, part, cnt, ctrl, L.gxc, L.zc, rtol2, o.max_cg);
+      upd<<<gC, NT, 0, s>>>(P, inst, st, mask, rbuf[par], rbuf[par ^ 1], q, dir, x, xlo, dinv, vv,
+                            part, cnt, ctrl, L.gxc, L.zc, rtol2, o.max_cg);
     } else {
       k_spmv<DIM, float><<<gT, NT, 0, s>>>(P, inst, st, mask, dir, q, part, cnt, ctrl, L.gx);
       if (timed) CK(cudaEventRecord(p->ev[2], s));
@@ -1891,6 +1947,9 @@ size_t problem_bytes(const sdf_problem *p) {
     o = al(o + sizeof(double) * (nx + 1) * ny * nz);    // fx
     o = al(o + sizeof(double) * nx * (ny + 1) * nz);    // fy
     if (d.dim == 3) o = al(o + sizeof(double) * nx * ny * (nz + 1));
+    o = al(o + sizeof(float) * (nx + 1) * ny * nz);     // FP32 copies of fx, fy, fz
+    o = al(o + sizeof(float) * nx * (ny + 1) * nz);
+    if (d.dim == 3) o = al(o + sizeof(float) * nx * ny * (nz + 1));
   }
   return o;
 }
@@ -1957,7 +2016,10 @@ sdf_status sdf_problem_create(const sdf_problem_desc *desc, const double *kappa_
     P.h[i] = i < d.dim ? 1.0 / (n3[i] + 1) : 1.0;
     P.inv_h[i] = i < d.dim ? (double)(n3[i] + 1) : 0.0;
     P.cdiff[i] = i < d.dim ? d.diff_scale * P.inv_h[i] * P.inv_h[i] : 0.0;
+    P.cdf[i] = (float)P.cdiff[i];
   }
+  P.massf = (float)P.mass;
+  P.wgtf = (float)P.wgt;
   P.convection = d.convection;
   P.yd_sigma = d.yd_sigma;
   int dev = 0;
@@ -2000,6 +2062,7 @@ sdf_status sdf_problem_bind(sdf_problem *p, void *dev_buf, size_t bytes, void *s
   p->dinv_shared32 = (float *)(base + o);
   o = al(o + sizeof(float) * P.N);
   P.fx = P.fy = P.fz = nullptr;
+  P.fxf = P.fyf = P.fzf = nullptr;
   if (p->d.has_kappa) {
     double *kap = (double *)(base + o);
     o = al(o + sizeof(double) * P.N);
@@ -2008,13 +2071,24 @@ sdf_status sdf_problem_bind(sdf_problem *p, void *dev_buf, size_t bytes, void *s
     double *fy = (double *)(base + o);
     o = al(o + sizeof(double) * P.nx * (long long)(P.ny + 1) * P.nz);
     double *fz = nullptr;
-    if (P.dim == 3) fz = (double *)(base + o);
+    if (P.dim == 3) {
+      fz = (double *)(base + o);
+      o = al(o + sizeof(double) * P.nx * (long long)P.ny * (P.nz + 1));
+    }
+    float *fxf = (float *)(base + o);
+    o = al(o + sizeof(float) * (P.nx + 1) * (long long)P.ny * P.nz);
+    float *fyf = (float *)(base + o);
+    o = al(o + sizeof(float) * P.nx * (long long)(P.ny + 1) * P.nz);
+    float *fzf = P.dim == 3 ? (float *)(base + o) : nullptr;
     CK(cudaMemcpyAsync(kap, p->kappa.data(), sizeof(double) * P.N, cudaMemcpyHostToDevice, s));
-    k_faces<<<p->nsm * 4, NT, 0, s>>>(P, kap, p->d.diff_scale, fx, fy, fz);
+    k_faces<<<p->nsm * 4, NT, 0, s>>>(P, kap, p->d.diff_scale, fx, fy, fz, fxf, fyf, fzf);
     CKL("k_faces");
     P.fx = fx;
     P.fy = fy;
     P.fz = fz;
+    P.fxf = fxf;
+    P.fyf = fyf;
+    P.fzf = fzf;
   }
   if (P.dim == 2) k_diag_shared<2><<<p->nsm * 4, NT, 0, s>>>(P, p->dinv_shared, p->dinv_shared32);
   else k_diag_shared<3><<<p->nsm * 4, NT, 0, s>>>(P, p->dinv_shared, p->dinv_shared32);

@@ -26,6 +26,30 @@ struct OpParams {
   int convection;
   double yd_sigma;
   double h[3];
+  // FP32 copies for the FP32 stencils of the mixed path: read straight from
+  // the parameter bank, never converted per use (a conversion issues on the
+  // FP64 pipe, 1/64 of the FP32 rate on this part)
+  float cdf[3], massf, wgtf;
+  const float *fxf, *fyf, *fzf;  // face coefficients in FP32 or null
+};
+
+// Operator constants and face arrays in arithmetic type T.
+template <class T> struct OpT;
+template <> struct OpT<double> {
+  static __device__ __forceinline__ double cd(const OpParams &P, int d) { return P.cdiff[d]; }
+  static __device__ __forceinline__ double mass(const OpParams &P) { return P.mass; }
+  static __device__ __forceinline__ double wgt(const OpParams &P) { return P.wgt; }
+  static __device__ __forceinline__ const double *fx(const OpParams &P) { return P.fx; }
+  static __device__ __forceinline__ const double *fy(const OpParams &P) { return P.fy; }
+  static __device__ __forceinline__ const double *fz(const OpParams &P) { return P.fz; }
+};
+template <> struct OpT<float> {
+  static __device__ __forceinline__ float cd(const OpParams &P, int d) { return P.cdf[d]; }
+  static __device__ __forceinline__ float mass(const OpParams &P) { return P.massf; }
+  static __device__ __forceinline__ float wgt(const OpParams &P) { return P.wgtf; }
+  static __device__ __forceinline__ const float *fx(const OpParams &P) { return P.fxf; }
+  static __device__ __forceinline__ const float *fy(const OpParams &P) { return P.fyf; }
+  static __device__ __forceinline__ const float *fz(const OpParams &P) { return P.fzf; }
 };
 
 // Tile shapes: 2D 64 x 8 (halo 2 in x, y), 3D 32 x 4 x 4 (halo 2 everywhere).
@@ -61,18 +85,21 @@ __device__ __forceinline__ int widx(int lx, int ly, int lz) {
 }
 
 // Face coefficients in arithmetic type T: constant-kappa problems use the
-// per-kernel constant cd[d] (no FP64 -> FP32 conversion per use).
+// per-kernel constant cd[d]; variable kappa reads the array of type T.
 template <class T>
 __device__ __forceinline__ T fx_T(const OpParams &P, const T cd[3], int i, int j, int l) {
-  return P.fx ? (T)__ldg(P.fx + i + (long long)(P.nx + 1) * (j + (long long)P.ny * l)) : cd[0];
+  const T *f = OpT<T>::fx(P);
+  return f ? __ldg(f + i + (long long)(P.nx + 1) * (j + (long long)P.ny * l)) : cd[0];
 }
 template <class T>
 __device__ __forceinline__ T fy_T(const OpParams &P, const T cd[3], int i, int j, int l) {
-  return P.fy ? (T)__ldg(P.fy + i + (long long)P.nx * (j + (long long)(P.ny + 1) * l)) : cd[1];
+  const T *f = OpT<T>::fy(P);
+  return f ? __ldg(f + i + (long long)P.nx * (j + (long long)(P.ny + 1) * l)) : cd[1];
 }
 template <class T>
 __device__ __forceinline__ T fz_T(const OpParams &P, const T cd[3], int i, int j, int l) {
-  return P.fz ? (T)__ldg(P.fz + i + (long long)P.nx * (j + (long long)P.ny * l)) : cd[2];
+  const T *f = OpT<T>::fz(P);
+  return f ? __ldg(f + i + (long long)P.nx * (j + (long long)P.ny * l)) : cd[2];
 }
 
 __device__ __forceinline__ double face_x(const OpParams &P, int i, int j, int l) {
@@ -291,8 +318,8 @@ template <int DIM, class T, class Load, class Store>
 __device__ void tile_S(const OpParams &P, const double cb64[3], int ox, int oy, int oz,
                        TileSmem<DIM, T> &sm, Load load, Store store) {
   const T cb[3] = {(T)cb64[0], (T)cb64[1], (T)cb64[2]};
-  const T cd[3] = {(T)P.cdiff[0], (T)P.cdiff[1], (T)P.cdiff[2]};
-  const T mass = (T)P.mass, wgt = (T)P.wgt;
+  const T cd[3] = {OpT<T>::cd(P, 0), OpT<T>::cd(P, 1), OpT<T>::cd(P, 2)};
+  const T mass = OpT<T>::mass(P), wgt = OpT<T>::wgt(P);
   if (P.fx)
     tile_S_rows<DIM, T, true>(P, cb, cd, mass, wgt, ox, oy, oz, sm, load, store);
   else
@@ -300,95 +327,107 @@ __device__ void tile_S(const OpParams &P, const double cb64[3], int ox, int oy, 
 }
 
 // ---------------------------------------------------------------------------
-// 3D column stencil (2.5D blocking): an xy tile of CX x CY = 32 x 8 nodes
-// marches in z through [z0, z1).  Shared memory holds a ring of five u planes
-// (z-2 .. z+2, halo 2 in x and y) and a ring of three w = A u planes (z-1 ..
-// z+1, halo 1), so each node's u is loaded 36*12/256 = 1.7 times and its w
-// computed 34*10/256 = 1.3 times; per-thread plane offsets are fixed.
-constexpr int CX = 32, CY = 8;
+// 3D column stencil (2.5D blocking): an xy tile of CX x CY = 32 x 16 nodes
+// marches in z through [z0, z1); each thread owns two output nodes.  Shared
+// memory holds a ring of five u planes (z-2 .. z+2, halo 2 in x and y) and a
+// ring of three w = A u planes (z-1 .. z+1, halo 1), so each node's u is
+// loaded 36*20/512 = 1.4 times and its w computed 34*18/512 = 1.2 times.
+// Ring slots rotate in registers.  Global loads run ahead of their use: the
+// raw source values of plane z+3 and the output operands of plane z+1 are
+// requested while plane z computes, and consumed one step later.
+constexpr int CX = 32, CY = 16;
 constexpr int CUX = CX + 4, CUY = CY + 4, CWX = CX + 2, CWY = CY + 2;
+constexpr int CNU = CUX * CUY, CNW = CWX * CWY, CNO = CX * CY;
+constexpr int CSU = (CNU + NT - 1) / NT, CSW = (CNW + NT - 1) / NT, CSO = CNO / NT;
+static_assert(CNO % NT == 0, "whole output slots per thread");
 
 template <class T> struct ColSmem {
-  T u[5][CUY * CUX];
-  T w[3][CWY * CWX];
+  T u[5][CNU];
+  T w[3][CNW];
 };
 
-__device__ __forceinline__ int ring5(int z) { return ((z % 5) + 5) % 5; }
-__device__ __forceinline__ int ring3(int z) { return ((z % 3) + 3) % 3; }
-
-// load(g) gives u at grid node g; store(gx, gy, gz, g, Su, u_center) receives
-// S u at every grid node of the column.  NT threads.
-template <class T, bool VARK, class Load, class Store>
+// Src: `Raw fetch(g)` issues the global loads of u at grid node g and
+// `T value(const Raw &)` turns them into u.  Out: `Pre fetch(g)` loads the
+// per-node operands of the output at g, `store(g, Su, u_g, pre)` receives S u.
+// CONV = false drops the upwind terms (all convection coefficients zero).
+template <class T, bool VARK, bool CONV, class Src, class Out>
 __device__ __forceinline__ void col_S3_impl(const OpParams &P, const T cb[3], const T cd[3], T mass,
                                             T wgt, int x0, int y0, int z0, int z1,
-                                            ColSmem<T> &sm, Load &load, Store &store) {
-  const long long nxy = (long long)P.nx * P.ny;
-  // per-thread u-load slots (<= 2): local index, xy-in-grid flag, xy offset
-  int ue[2];
-  bool uin[2];
-  long long uoff[2];
+                                            ColSmem<T> &sm, const Src &src, Out &out) {
+  using Raw = typename Src::Raw;
+  using Pre = typename Out::Pre;
+  const int nx = P.nx, ny = P.ny, nz = P.nz;
+  const long long nxy = (long long)nx * ny, base = (long long)y0 * nx + x0;
+  // u slots: shared index (-1: idle), in-grid flag, xy offset from the tile origin
+  int ue[CSU], uoff[CSU];
+  bool uok[CSU];
 #pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    int e = threadIdx.x + q * NT;
-    ue[q] = e < CUY * CUX ? e : -1;
-    int lx = e % CUX - 2, ly = e / CUX - 2;
-    int gx = x0 + lx, gy = y0 + ly;
-    uin[q] = ue[q] >= 0 && gx >= 0 && gx < P.nx && gy >= 0 && gy < P.ny;
-    uoff[q] = (long long)gy * P.nx + gx;
+  for (int q = 0; q < CSU; ++q) {
+    const int e = threadIdx.x + q * NT;
+    const int lx = e % CUX - 2, ly = e / CUX - 2;
+    ue[q] = e < CNU ? e : -1;
+    uok[q] = e < CNU && x0 + lx >= 0 && x0 + lx < nx && y0 + ly >= 0 && y0 + ly < ny;
+    uoff[q] = ly * nx + lx;
   }
-  // per-thread w slots (<= 2)
-  int we[2], wgx[2], wgy[2], wuc[2];
-  bool win[2];
+  // w slots: shared index, centre in the u plane, in-grid flag
+  int we[CSW], wuc[CSW];
+  bool wok[CSW];
 #pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    int e = threadIdx.x + q * NT;
-    we[q] = e < CWY * CWX ? e : -1;
-    int lx = e % CWX - 1, ly = e / CWX - 1;
-    wgx[q] = x0 + lx;
-    wgy[q] = y0 + ly;
-    win[q] = we[q] >= 0 && wgx[q] >= 0 && wgx[q] < P.nx && wgy[q] >= 0 && wgy[q] < P.ny;
-    wuc[q] = (ly + 2) * CUX + (lx + 2);  // center in the u plane
+  for (int q = 0; q < CSW; ++q) {
+    const int e = threadIdx.x + q * NT;
+    const int lx = e % CWX - 1, ly = e / CWX - 1;
+    we[q] = e < CNW ? e : -1;
+    wok[q] = e < CNW && x0 + lx >= 0 && x0 + lx < nx && y0 + ly >= 0 && y0 + ly < ny;
+    wuc[q] = (ly + 2) * CUX + (lx + 2);
   }
-  // output slot (exactly one per thread)
-  const int olx = threadIdx.x % CX, oly = threadIdx.x / CX;
-  const int ogx = x0 + olx, ogy = y0 + oly;
-  const bool oin = ogx < P.nx && ogy < P.ny;
-  const int owc = (oly + 1) * CWX + (olx + 1), ouc = (oly + 2) * CUX + (olx + 2);
-  const long long ooff = (long long)ogy * P.nx + ogx;
+  // output slots
+  int owc[CSO], ouc[CSO], ooff[CSO];
+  bool ook[CSO];
+#pragma unroll
+  for (int q = 0; q < CSO; ++q) {
+    const int e = threadIdx.x + q * NT;
+    const int lx = e % CX, ly = e / CX;
+    ook[q] = x0 + lx < nx && y0 + ly < ny;
+    owc[q] = (ly + 1) * CWX + (lx + 1);
+    ouc[q] = (ly + 2) * CUX + (lx + 2);
+    ooff[q] = ly * nx + lx;
+  }
 
-  auto fetch_u = [&](int z, T (&val)[2]) {  // global -> registers
-    const bool zin = z >= 0 && z < P.nz;
+  auto fetch = [&](int z, Raw (&raw)[CSU]) {
+    const bool zin = z >= 0 && z < nz;
+    const long long zb = (long long)z * nxy + base;
 #pragma unroll
-    for (int q = 0; q < 2; ++q)
-      val[q] = (ue[q] >= 0 && zin && uin[q]) ? (T)load((long long)z * nxy + uoff[q]) : (T)0;
+    for (int q = 0; q < CSU; ++q) raw[q] = (zin && uok[q]) ? src.fetch(zb + uoff[q]) : Raw{};
   };
-  auto put_u = [&](int z, const T (&val)[2]) {  // registers -> shared ring slot
-    T *up = sm.u[ring5(z)];
+  auto put = [&](int z, int slot, const Raw (&raw)[CSU]) {
+    const bool zin = z >= 0 && z < nz;
+    T *up = sm.u[slot];
 #pragma unroll
-    for (int q = 0; q < 2; ++q)
-      if (ue[q] >= 0) up[ue[q]] = val[q];
+    for (int q = 0; q < CSU; ++q)
+      if (ue[q] >= 0) up[ue[q]] = (zin && uok[q]) ? src.value(raw[q]) : (T)0;
   };
-  auto load_u = [&](int z) {
-    T val[2];
-    fetch_u(z, val);
-    put_u(z, val);
-  };
-  auto comp_w = [&](int z) {  // w plane z from u planes z-1, z, z+1
-    T *wp = sm.w[ring3(z)];
-    const T *um = sm.u[ring5(z - 1)], *uc = sm.u[ring5(z)], *upl = sm.u[ring5(z + 1)];
-    const bool zin = z >= 0 && z < P.nz;
+  auto prefetch = [&](int z, Pre (&pr)[CSO]) {
+    const long long zb = (long long)z * nxy + base;
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < CSO; ++q) pr[q] = ook[q] ? out.fetch(zb + ooff[q]) : Pre{};
+  };
+  // w = A u at plane z into slot ws, from u slots sm1, s0, sp1 (planes z-1, z, z+1)
+  auto comp_w = [&](int z, int ws, int sm1, int s0, int sp1) {
+    T *wp = sm.w[ws];
+    const T *um = sm.u[sm1], *uc = sm.u[s0], *upl = sm.u[sp1];
+    const bool zin = z >= 0 && z < nz;
+#pragma unroll
+    for (int q = 0; q < CSW; ++q) {
       if (we[q] < 0) continue;
       T val = (T)0;
-      if (zin && win[q]) {
+      if (zin && wok[q]) {
         const int c0 = wuc[q];
         const T c = uc[c0];
         const T xm = uc[c0 - 1], xp = uc[c0 + 1], ym = uc[c0 - CUX], yp = uc[c0 + CUX];
         const T zm = um[c0], zp = upl[c0];
         T fw, fe, fs, fn, fb, ft;
         if (VARK) {
-          const int gx = wgx[q], gy = wgy[q];
+          const int gx = x0 + we[q] % CWX - 1, gy = y0 + we[q] / CWX - 1;
           fw = fx_T(P, cd, gx, gy, z); fe = fx_T(P, cd, gx + 1, gy, z);
           fs = fy_T(P, cd, gx, gy, z); fn = fy_T(P, cd, gx, gy + 1, z);
           fb = fz_T(P, cd, gx, gy, z); ft = fz_T(P, cd, gx, gy, z + 1);
@@ -397,70 +436,104 @@ __device__ __forceinline__ void col_S3_impl(const OpParams &P, const T cb[3], co
         }
         T acc = fw * (c - xm) + fe * (c - xp) + fs * (c - ym) + fn * (c - yp) + fb * (c - zm) +
                 ft * (c - zp);
-        if (cb[0] > (T)0) acc += cb[0] * (c - xm);
-        else if (cb[0] < (T)0) acc -= cb[0] * (c - xp);
-        if (cb[1] > (T)0) acc += cb[1] * (c - ym);
-        else if (cb[1] < (T)0) acc -= cb[1] * (c - yp);
-        if (cb[2] > (T)0) acc += cb[2] * (c - zm);
-        else if (cb[2] < (T)0) acc -= cb[2] * (c - zp);
+        if (CONV) {
+          if (cb[0] > (T)0) acc += cb[0] * (c - xm);
+          else if (cb[0] < (T)0) acc -= cb[0] * (c - xp);
+          if (cb[1] > (T)0) acc += cb[1] * (c - ym);
+          else if (cb[1] < (T)0) acc -= cb[1] * (c - yp);
+          if (cb[2] > (T)0) acc += cb[2] * (c - zm);
+          else if (cb[2] < (T)0) acc -= cb[2] * (c - zp);
+        }
         val = acc;
       }
       wp[we[q]] = val;
     }
   };
-  // prologue: u planes z0-2 .. z0+1, w planes z0-1, z0; plane z0+2 in flight
-  for (int z = z0 - 2; z <= z0 + 1; ++z) load_u(z);
-  T nxt[2];
-  fetch_u(z0 + 2, nxt);
-  __syncthreads();
-  comp_w(z0 - 1);
-  comp_w(z0);
-  for (int z = z0; z < z1; ++z) {
-    // software pipeline: plane z+2 arrived in registers during the previous
-    // step; plane z+3 is requested now and lands while this plane computes
-    put_u(z + 2, nxt);
-    if (z + 1 < z1) fetch_u(z + 3, nxt);
-    __syncthreads();
-    comp_w(z + 1);
-    __syncthreads();
-    if (oin && z < P.nz) {
-      const T *wm = sm.w[ring3(z - 1)], *wc = sm.w[ring3(z)], *wpl = sm.w[ring3(z + 1)];
-      const T c = wc[owc];
-      const T xm = wc[owc - 1], xp = wc[owc + 1], ym = wc[owc - CWX], yp = wc[owc + CWX];
-      const T zm = wm[owc], zp = wpl[owc];
+  // S u = mass u + wgt A^T w at plane z
+  auto outputs = [&](int z, int wsm, int ws0, int wsp, int us0, const Pre (&pr)[CSO]) {
+    const T *wm = sm.w[wsm], *wc = sm.w[ws0], *wpl = sm.w[wsp], *uc = sm.u[us0];
+    const long long zb = (long long)z * nxy + base;
+#pragma unroll
+    for (int q = 0; q < CSO; ++q) {
+      if (!ook[q]) continue;
+      const int o = owc[q];
+      const T c = wc[o];
+      const T xm = wc[o - 1], xp = wc[o + 1], ym = wc[o - CWX], yp = wc[o + CWX];
+      const T zm = wm[o], zp = wpl[o];
       T fw, fe, fs, fn, fb, ft;
       if (VARK) {
-        fw = fx_T(P, cd, ogx, ogy, z); fe = fx_T(P, cd, ogx + 1, ogy, z);
-        fs = fy_T(P, cd, ogx, ogy, z); fn = fy_T(P, cd, ogx, ogy + 1, z);
-        fb = fz_T(P, cd, ogx, ogy, z); ft = fz_T(P, cd, ogx, ogy, z + 1);
+        const int e = threadIdx.x + q * NT;
+        const int gx = x0 + e % CX, gy = y0 + e / CX;
+        fw = fx_T(P, cd, gx, gy, z); fe = fx_T(P, cd, gx + 1, gy, z);
+        fs = fy_T(P, cd, gx, gy, z); fn = fy_T(P, cd, gx, gy + 1, z);
+        fb = fz_T(P, cd, gx, gy, z); ft = fz_T(P, cd, gx, gy, z + 1);
       } else {
         fw = fe = cd[0]; fs = fn = cd[1]; fb = ft = cd[2];
       }
       T acc = fw * (c - xm) + fe * (c - xp) + fs * (c - ym) + fn * (c - yp) + fb * (c - zm) +
               ft * (c - zp);
-      if (cb[0] > (T)0) acc += cb[0] * (c - xp);
-      else if (cb[0] < (T)0) acc -= cb[0] * (c - xm);
-      if (cb[1] > (T)0) acc += cb[1] * (c - yp);
-      else if (cb[1] < (T)0) acc -= cb[1] * (c - ym);
-      if (cb[2] > (T)0) acc += cb[2] * (c - zp);
-      else if (cb[2] < (T)0) acc -= cb[2] * (c - zm);
-      const T uc = sm.u[ring5(z)][ouc];
-      store(ogx, ogy, z, (long long)z * nxy + ooff, mass * uc + wgt * acc, uc);
+      if (CONV) {
+        if (cb[0] > (T)0) acc += cb[0] * (c - xp);
+        else if (cb[0] < (T)0) acc -= cb[0] * (c - xm);
+        if (cb[1] > (T)0) acc += cb[1] * (c - yp);
+        else if (cb[1] < (T)0) acc -= cb[1] * (c - ym);
+        if (cb[2] > (T)0) acc += cb[2] * (c - zp);
+        else if (cb[2] < (T)0) acc -= cb[2] * (c - zm);
+      }
+      const T u0 = uc[ouc[q]];
+      out.store(zb + ooff[q], mass * u0 + wgt * acc, u0, pr[q]);
     }
+  };
+
+  // ring slots of u planes z-2 .. z+2 and of w planes z-1 .. z+1
+  int s0 = 0, s1 = 1, s2 = 2, s3 = 3, s4 = 4, t0 = 0, t1 = 1, t2 = 2;
+  {  // prologue: u planes z0-2 .. z0+1 requested together
+    Raw a[CSU], b[CSU], c[CSU], d[CSU];
+    fetch(z0 - 2, a);
+    fetch(z0 - 1, b);
+    fetch(z0, c);
+    fetch(z0 + 1, d);
+    put(z0 - 2, 0, a);
+    put(z0 - 1, 1, b);
+    put(z0, 2, c);
+    put(z0 + 1, 3, d);
+  }
+  Raw nxt[CSU];
+  Pre pc[CSO], pn[CSO];
+  fetch(z0 + 2, nxt);
+  prefetch(z0, pc);
+  __syncthreads();
+  comp_w(z0 - 1, 0, 0, 1, 2);
+  comp_w(z0, 1, 1, 2, 3);
+  for (int z = z0; z < z1; ++z) {
+    put(z + 2, s4, nxt);
+    if (z + 1 < z1) {
+      fetch(z + 3, nxt);
+      prefetch(z + 1, pn);
+    }
+    __syncthreads();
+    comp_w(z + 1, t2, s2, s3, s4);
+    __syncthreads();
+    outputs(z, t0, t1, t2, s2, pc);
+    const int s = s0;
+    s0 = s1; s1 = s2; s2 = s3; s3 = s4; s4 = s;
+    const int t = t0;
+    t0 = t1; t1 = t2; t2 = t;
+#pragma unroll
+    for (int q = 0; q < CSO; ++q) pc[q] = pn[q];
   }
   __syncthreads();
 }
 
-template <class T, class Load, class Store>
-__device__ void col_S3(const OpParams &P, const double cb64[3], int x0, int y0, int z0, int z1,
-                       ColSmem<T> &sm, Load load, Store store) {
+// Entry of the column stencil for kernels compiled per coefficient kind
+// (VARK: face coefficients from kappa; CONV: upwind convection present).
+template <class T, bool VARK, bool CONV, class Src, class Out>
+__device__ __forceinline__ void col_S3(const OpParams &P, const double cb64[3], int x0, int y0,
+                                       int z0, int z1, ColSmem<T> &sm, const Src &src, Out &out) {
   const T cb[3] = {(T)cb64[0], (T)cb64[1], (T)cb64[2]};
-  const T cd[3] = {(T)P.cdiff[0], (T)P.cdiff[1], (T)P.cdiff[2]};
-  const T mass = (T)P.mass, wgt = (T)P.wgt;
-  if (P.fx)
-    col_S3_impl<T, true>(P, cb, cd, mass, wgt, x0, y0, z0, z1, sm, load, store);
-  else
-    col_S3_impl<T, false>(P, cb, cd, mass, wgt, x0, y0, z0, z1, sm, load, store);
+  const T cd[3] = {OpT<T>::cd(P, 0), OpT<T>::cd(P, 1), OpT<T>::cd(P, 2)};
+  col_S3_impl<T, VARK, CONV>(P, cb, cd, OpT<T>::mass(P), OpT<T>::wgt(P), x0, y0, z0, z1, sm, src,
+                             out);
 }
 
 // Column work items of a 3D grid: xy tiles x z-chunks of zc planes.
