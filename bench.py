@@ -53,7 +53,7 @@ def peaks():
 
 
 # ---------------------------------------------------------------------------
-# algorithmic work per dof and per launch (stated in the design doc)
+# algorithmic work per dof and per launch
 
 def stencil_flops(dim):
     # A u in flux form: 2*dim differences + 2*dim FMAs (2 flops); same for A^T w;

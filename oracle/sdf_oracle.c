@@ -31,9 +31,8 @@
  *                           unprojected residual recurrence, stop on
  *                           ||r|| < eps ||b|| (App. B.2).
  *
- * Readings where the paper is silent or garbled are listed in the design doc of
- * the repository; the ones that change arithmetic are repeated at the
- * function that implements them.
+ * Where the paper is silent or garbled, the reading that changes arithmetic
+ * is stated at the function that implements it.
  */
 #define _POSIX_C_SOURCE 199309L
 #include <math.h>
