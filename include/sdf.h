@@ -202,6 +202,18 @@ sdf_status sdf_solve_batch(sdf_problem *p, const double *inst_dev, int batch,
                            void *stream, double *y_dev, double *lambda_dev, uint8_t *active_dev,
                            sdf_stats *stats_host);
 
+/* The same solve with a given start instead of zero: the first inner solve
+ * (A = {}) starts from x0_dev (batch x N doubles, device) and every later one
+ * from the previous outer iterate, each restricted to its inactive set.  The
+ * active-set path is the cold one (A grows from {} by the same rule); only the
+ * CG iterations change.  x0 is meant to approximate the solution of the
+ * first (unconstrained) solve, e.g. the learned warm start below.  No
+ * counterpart in the paper, whose inner solves start from zero. */
+sdf_status sdf_solve_batch_x0(sdf_problem *p, const double *inst_dev, int batch,
+                              const double *psi_dev, const double *x0_dev, const sdf_opts *opts,
+                              void *ws, size_t ws_bytes, void *stream, double *y_dev,
+                              double *lambda_dev, uint8_t *active_dev, sdf_stats *stats_host);
+
 /* The same solve with every input and output in HOST memory: the instance
  * array and psi are copied to the device inside the call and y, lambda (if not
  * NULL) and active are copied back; the workspace (device) must be at least
@@ -280,6 +292,135 @@ const char *sdf_last_error(const sdf_problem *p);
 
 /* Release the host handle (device buffers stay the caller's). */
 void sdf_problem_destroy(sdf_problem *p);
+
+/* ==========================================================================
+ * Learned warm start (no counterpart in the paper, which lists learned
+ * initialisations only as related work).  A multilayer perceptron maps the
+ * instance parameters to the coefficients of a POD basis of solved states
+ * (the paper's POD, Sec. 2.2.5, mean-centred); the expansion
+ * x0 = ybar + Psi c is the start of every inner solve (sdf_solve_batch_x0).
+ * The MLP's products run on the tensor cores (tcgen05.mma, BF16 operands,
+ * FP32 accumulation in tensor memory); everything else is FP32 (MLP) or FP64
+ * (POD).  These entry points take no problem handle; their error text is
+ * returned by sdf_aux_last_error() (per host thread).
+ * ========================================================================== */
+
+#define SDF_MLP_MAX_LAYERS 8
+#define SDF_POD_MAX_R 64
+#define SDF_POD_MAX_SNAPSHOTS 512
+
+/* width[0] inputs, width[1..n_layers-1] hidden (GELU), width[n_layers]
+ * outputs (identity); every width in 1..256. */
+typedef struct {
+  int32_t n_layers;
+  int32_t width[SDF_MLP_MAX_LAYERS + 1];
+} sdf_mlp_desc;
+
+/* Parameters (FP32, device): for each layer l = 1..n_layers, W_l
+ * (width[l] x width[l-1], row-major) then b_l (width[l]).  Returns the count,
+ * or -1 for a bad description. */
+int64_t sdf_mlp_param_count(const sdf_mlp_desc *d);
+
+/* Workspace (device, 256-byte aligned) of sdf_mlp_forward and
+ * sdf_mlp_loss_grad for `batch` rows. */
+sdf_status sdf_mlp_workspace_size(const sdf_mlp_desc *d, int batch, size_t *bytes);
+
+/* y = f(x): x_dev batch x width[0] FP32 row-major, y_dev batch x
+ * width[n_layers] FP32 (device).  Weights and layer inputs are rounded to
+ * BF16 for the products; biases and GELU are FP32.  SDF_ERR_TIMEOUT if a
+ * tensor-core completion wait gave up (the result is then undefined). */
+sdf_status sdf_mlp_forward(const sdf_mlp_desc *d, const float *theta_dev, const float *x_dev,
+                           int batch, float *y_dev, void *ws, size_t ws_bytes, void *stream);
+
+/* Mean squared error L = mean((f(x) - t)^2) over the batch and the outputs,
+ * written to *loss_dev (one double, device), and its gradient with respect to
+ * theta (grad_dev, same layout as theta, FP32, device).  t_dev: batch x
+ * width[n_layers] FP32.  The back-propagated errors are rounded to BF16 for
+ * the products, as the layer inputs are. */
+sdf_status sdf_mlp_loss_grad(const sdf_mlp_desc *d, const float *theta_dev, const float *x_dev,
+                             const float *t_dev, int batch, float *grad_dev, double *loss_dev,
+                             void *ws, size_t ws_bytes, void *stream);
+
+/* One Adam step with bias correction (Kingma & Ba) on n FP32 parameters:
+ * m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ * theta -= lr (m / (1-b1^step)) / (sqrt(v / (1-b2^step)) + eps); step >= 1. */
+sdf_status sdf_adam_step(float *theta_dev, const float *grad_dev, float *m_dev, float *v_dev,
+                         int64_t n, int step, float lr, float beta1, float beta2, float eps,
+                         void *stream);
+
+/* POD of m solved states Y_dev (m x n FP64, one state per row, device):
+ * ybar_dev (n FP64) the mean; the r leading left singular vectors of the
+ * centred snapshots (method of snapshots: eigen-decomposition of the m x m
+ * Gram matrix, FP64), each column's sign chosen so that its largest-magnitude
+ * entry is positive, written node-major in BF16 (psi_rm_bf16_dev, n x r,
+ * r contiguous) and column-major in FP64 (psi_cm_dev, n x r); the singular
+ * values (sing_host, r) and the snapshots' coefficients (coef_host, m x r,
+ * may be NULL).  2 <= m <= SDF_POD_MAX_SNAPSHOTS, 1 <= r <= min(m - 1,
+ * SDF_POD_MAX_R), m * r <= 25600.  SDF_ERR_NOT_SPD if fewer than r singular
+ * values are positive. */
+sdf_status sdf_pod_workspace_size(int64_t n, int m, size_t *bytes);
+sdf_status sdf_pod(const double *Y_dev, int m, int64_t n, int r, double *ybar_dev,
+                   void *psi_rm_bf16_dev, double *psi_cm_dev, double *sing_host,
+                   double *coef_host, void *ws, size_t ws_bytes, void *stream);
+
+/* x0[b] = ybar + Psi (cstd[b] * cscale + cmean) for b < batch (<= 256):
+ * psi_rm_bf16_dev n x r BF16 node-major (16-byte aligned, r a multiple of 16),
+ * cstd_dev batch x r FP32 (standardised coefficients, e.g. the MLP output),
+ * cmean_dev / cscale_dev r FP32, x0_dev batch x n FP64 (all device).  The
+ * coefficients are rounded to BF16 for the tensor-core product. */
+sdf_status sdf_warm_expand_workspace_size(int batch, int r, size_t *bytes);
+sdf_status sdf_warm_expand(const void *psi_rm_bf16_dev, const double *ybar_dev, int64_t n, int r,
+                           const float *cstd_dev, const float *cmean_dev, const float *cscale_dev,
+                           int batch, double *x0_dev, void *ws, size_t ws_bytes, void *stream);
+
+/* A warm-start model: every pointer is a caller-owned device buffer.
+ *   mlp        width[0] = number of instance parameters used as inputs (the
+ *              first width[0] of the SDF_INSTANCE_DOUBLES, e.g. a, c_x, c_y,
+ *              c_z in 3D), width[n_layers] = r
+ *   r          POD rank, a multiple of 16, <= SDF_POD_MAX_R
+ *   n          state length N
+ *   in_lo/hi   parameter box: inputs are scaled to [-1, 1] by min-max
+ *   theta      sdf_mlp_param_count FP32 (initialised by the caller before
+ *              sdf_warm_fit: the initial weights are an input)
+ *   ybar       n FP64; psi n x r FP64 column-major (mode j at psi + j n)
+ *   cmean, cscale  r FP32: the targets are (c_j - cmean_j) / cscale_j with
+ *              cmean_j the mean of coefficient j over the training snapshots
+ *              and one common scale cscale_j = max_j std(c_j), so that the
+ *              loss weighs each coefficient by its share of the state */
+typedef struct {
+  sdf_mlp_desc mlp;
+  int32_t r;
+  int64_t n;
+  double in_lo[8], in_hi[8];
+  float *theta;
+  double *ybar;
+  double *psi;
+  float *cmean, *cscale;
+} sdf_warm_model;
+
+/* Fit the model to m solved states Y_dev (m x n FP64, device) of the
+ * instances inst_dev (m x SDF_INSTANCE_DOUBLES, device): POD (writes ybar,
+ * psi), target scaling (cmean, cscale), then `epochs` full-batch Adam steps
+ * (beta 0.9 / 0.999, eps 1e-8) with the learning rate decaying from lr0 to 0
+ * on a cosine, starting from the caller's theta.  loss_host (epochs doubles,
+ * may be NULL) receives the loss before each step.  m <= 512, epochs <= 4096. */
+sdf_status sdf_warm_fit_workspace_size(const sdf_warm_model *M, int m, size_t *bytes);
+sdf_status sdf_warm_fit(sdf_warm_model *M, const double *Y_dev, const double *inst_dev, int m,
+                        int epochs, float lr0, double *loss_host, void *ws, size_t ws_bytes,
+                        void *stream);
+
+/* x0 (batch x n FP64, device) = ybar + psi (f(scaled inst) * cscale + cmean)
+ * for the instances inst_dev (batch x SDF_INSTANCE_DOUBLES, device),
+ * batch <= 256: the start for sdf_solve_batch_x0.  The MLP runs on the
+ * tensor cores; the expansion is FP64, because BF16 rounding of psi (2^-9
+ * relative, uncorrelated from node to node) would put high-frequency error
+ * into x0 that the stiff S amplifies in the starting residual. */
+sdf_status sdf_warm_predict_workspace_size(const sdf_warm_model *M, int batch, size_t *bytes);
+sdf_status sdf_warm_predict(const sdf_warm_model *M, const double *inst_dev, int batch,
+                            double *x0_dev, void *ws, size_t ws_bytes, void *stream);
+
+/* Error text of the last failing call above on this host thread. */
+const char *sdf_aux_last_error(void);
 
 #ifdef __cplusplus
 }

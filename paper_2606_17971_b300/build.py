@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsdf_b300.so")
-SOURCES = ["sdf.cu"]
+SOURCES = ["sdf.cu", "warm.cu"]
 HEADERS = ["sdf_device.cuh"]
 
 NVCC_FLAGS = [

@@ -153,14 +153,18 @@ __global__ void k_diag_shared(OpParams P, double *dinv, float *dinv32) {
 
 // ---------------------------------------------------------------------------
 // Outer-iteration set-up (App. B.1 lines 3-5): r = b = rhs_I - S_IA psi_A,
-// x = 0, per-instance Jacobi diagonal (convection), ||b||^2, |A|.
+// x = 0, per-instance Jacobi diagonal (convection), ||b||^2, |A|.  With a
+// given start (x0 != null) the first outer iteration starts from x0 and each
+// later one from the previous iterate y_prev, both restricted to I;
+// k_start_resid then replaces r by b - S_II x.
 
 template <int DIM, class V>
 __global__ void __launch_bounds__(NT) k_outer_setup(OpParams P, const double *inst,
                                                     const double *psi, const uint8_t *mask,
                                                     V *r, double *b64, double *x, V *dinv,
                                                     InstState *st, double *part, int *cnt,
-                                                    Ctrl *ctrl, int GX) {
+                                                    Ctrl *ctrl, int GX, const double *x0,
+                                                    const double *y_prev) {
   __shared__ TileSmem<DIM, double> sm;
   __shared__ double red[NWARP];
   __shared__ double tot[2];
@@ -175,6 +179,7 @@ __global__ void __launch_bounds__(NT) k_outer_setup(OpParams P, const double *in
   const uint8_t *mk = mask + b * N;
   V *rb = r + b * N;
   double *bb64 = b64 + b * N, *xb = x + b * N;
+  const double *x0b = x0 ? (S.outer == 0 ? x0 : y_prev) + b * N : nullptr;
   V *db = P.convection ? dinv + b * N : nullptr;
   double bb = 0.0, na = 0.0;
   const long long T = num_tiles<DIM>(P.nx, P.ny, P.nz);
@@ -190,7 +195,7 @@ __global__ void __launch_bounds__(NT) k_outer_setup(OpParams P, const double *in
           double bv = act ? 0.0 : rhs - su;
           bb64[g] = bv;
           rb[g] = (V)bv;
-          xb[g] = 0.0;
+          xb[g] = (act || !x0b) ? 0.0 : x0b[g];
           if (db) db[g] = act ? (V)0 : (V)(1.0 / diag_S<DIM>(P, cb, gx, gy, gz));
           bb += bv * bv;
           na += act ? 1.0 : 0.0;
@@ -222,6 +227,34 @@ __global__ void __launch_bounds__(NT) k_outer_setup(OpParams P, const double *in
     S.alpha = 1.0;
     for (int j = 0; j < SDF_MAX_K; ++j) S.t[j] = 0.0;
     atomicAdd(&ctrl->running, 1);
+  }
+}
+
+// Residual of a given start: r = b - S_II x on I, 0 on A (x is zero on A),
+// with the FP64 stencil.  Used only when the caller supplies x0.
+template <int DIM, class V>
+__global__ void __launch_bounds__(NT) k_start_resid(OpParams P, const double *inst,
+                                                    const InstState *st, const uint8_t *mask,
+                                                    const double *b64, const double *x, V *r,
+                                                    int GX) {
+  __shared__ TileSmem<DIM, double> sm;
+  const int b = blockIdx.x, gblk = blockIdx.y;
+  if (st[b].outer_done) return;
+  const long long N = P.N;
+  double cb[3];
+  inst_cb(P, inst + 7 * b, cb);
+  const uint8_t *mk = mask + b * N;
+  const double *xb = x + b * N, *bb = b64 + b * N;
+  V *rb = r + b * N;
+  const long long T = num_tiles<DIM>(P.nx, P.ny, P.nz);
+  for (long long t = gblk; t < T; t += GX) {
+    int ox, oy, oz;
+    tile_origin<DIM>(P, t, ox, oy, oz);
+    tile_S<DIM, double>(
+        P, cb, ox, oy, oz, sm, [&](int, int, int, long long g) { return xb[g]; },
+        [&](int, int, int, int, long long g, double su) {
+          rb[g] = mk[g] ? (V)0 : (V)(bb[g] - su);
+        });
   }
 }
 
@@ -315,6 +348,15 @@ __global__ void k_gram_reduce(const double *gpart, int nblk, int k, const InstSt
   double s = 0.0;
   for (int g = 0; g < nblk; ++g) s += gpart[(long long)g * k * k + e];
   out[e] = s;
+}
+
+// Copy instance 0's E_raw and G to instances 1.. (one block per instance).
+__global__ void k_coarse_copy(int k, double *Eraw, double *G) {
+  const size_t kk = (size_t)k * k, b = blockIdx.x + 1;
+  for (size_t e = threadIdx.x; e < kk; e += blockDim.x) {
+    Eraw[b * kk + e] = Eraw[e];
+    G[b * kk + e] = G[e];
+  }
 }
 
 // k x k coarse factorisation for each instance (one block per instance):
@@ -1480,6 +1522,7 @@ struct sdf_problem {
   sdf_profile prof{};
   cudaEvent_t ev[8] = {};
   bool ev_ready = false;
+  const double *x0 = nullptr;  // start of every inner solve (set for one call)
 };
 
 namespace {
@@ -1564,7 +1607,7 @@ Layout make_layout(const sdf_problem *p, int B, int max_blocks = 0, int mixed = 
   L.cnt = take(sizeof(int) * (size_t)B * NCNT);
   L.ctrl = take(sizeof(Ctrl));
   // mixed path: v = S_II z, coarse coefficients, projection-GEMM partials
-  L.nb = B == 1 ? 1 : (B <= 16 ? 16 : 64);
+  L.nb = B == 1 ? 1 : (B <= 16 ? 16 : (B <= 32 ? 32 : 64));
   L.bpad = (int)(((B + L.nb - 1) / L.nb) * L.nb);
   L.gxp = std::max(1, (p->nsm * 6) / ((B + L.nb - 1) / L.nb));
   if (max_blocks > 0) L.gxp = std::min(L.gxp, max_blocks);
@@ -1593,7 +1636,7 @@ sdf_status solve_impl(sdf_problem *p, const double *inst, int B, const double *p
   const OpParams &P = p->P;
   const long long N = P.N;
   double *x = (double *)(ws + L.x), *b64 = (double *)(ws + L.b64);
-  V *pp = (V *)(ws + L.p), *q = (V *)(ws + L.q), *wv = (V *)(ws + L.w);
+  V *pp = (V *)(ws + L.p), *q = (V *)(ws + L.q);
   V *rbuf[2] = {(V *)(ws + L.r), (V *)(ws + L.r2)};
   V *dinv = P.convection ? (V *)(ws + L.dinv)
                          : (mixed ? (V *)p->dinv_shared32 : (V *)p->dinv_shared);
@@ -1642,24 +1685,35 @@ sdf_status solve_impl(sdf_problem *p, const double *inst, int B, const double *p
     CK(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s));
     par = 0;
     k_outer_setup<DIM, V><<<gT, NT, 0, s>>>(P, inst, psi, mask, rbuf[0], b64, x, dinv, st, part,
-                                            cnt, ctrl, L.gx);
+                                            cnt, ctrl, L.gx, p->x0, y);
     CKL("k_outer_setup");
     p->prof.launches += 1;
+    if (p->x0) {
+      k_start_resid<DIM, V><<<gT, NT, 0, s>>>(P, inst, st, mask, b64, x, rbuf[0], L.gx);
+      CKL("k_start_resid");
+      p->prof.launches += 1;
+    }
     if (defl) {
-      for (int b = 0; b < B; ++b) {
+      // The first outer iteration of every instance has A = {} (cold start);
+      // without per-instance convection S_II and Phi_I are then the same for
+      // the whole batch, and so are E_raw and G: set up once, copied.
+      const int nset = (outer == 0 && !P.convection) ? 1 : B;
+      for (int b = 0; b < nset; ++b) {
         k_modes_W<DIM, PhiT><<<dim3(k, L.gx), NT, 0, s>>>(P, inst, b, st, mask, Phi, ld, W, L.gx);
         k_gram<KMAX, PhiT><<<L.gxg, NT, 0, s>>>(Phi, ld, W, mask, st, b, N, k, 0, gpart);
         k_gram_reduce<<<(k * k + NT - 1) / NT, NT, 0, s>>>(gpart, L.gxg, k, st, b, Eraw + (size_t)b * k * k);
         k_gram<KMAX, PhiT><<<L.gxg, NT, 0, s>>>(Phi, ld, W, mask, st, b, N, k, 1, gpart);
         k_gram_reduce<<<(k * k + NT - 1) / NT, NT, 0, s>>>(gpart, L.gxg, k, st, b, G + (size_t)b * k * k);
       }
+      if (nset < B)
+        k_coarse_copy<<<B - 1, NT, 0, s>>>(k, Eraw, G);
       CKL("coarse setup");
       k_coarse<<<B, NT, 0, s>>>(k, st, G, Eraw, Einv, coarse, o.tau_cond);
       CKL("k_coarse");
       k_project<KMAX, PhiT, V><<<gA, NT, 0, s>>>(Phi, ld, k, N, mask, rbuf[0], st, nullptr, part,
                                                  cnt, L.gxa);
       CKL("k_project");
-      p->prof.launches += 5LL * B + 2;
+      p->prof.launches += 5LL * nset + (nset < B ? 1 : 0) + 2;
     }
     // coarse-corrected start (phase 1), then CG iterations in chunks; r
     // ping-pongs between its two buffers (uniform across the batch: finished
@@ -1782,6 +1836,8 @@ sdf_status solve_mixed(sdf_problem *p, const double *inst, int B, const double *
       k_proj_gemm<KMAX, 1, PhiT><<<gP, NT, 0, s>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad);
     else if (L.nb == 16)
       k_proj_gemm<KMAX, 16, PhiT><<<gP, NT, 0, s>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad);
+    else if (L.nb == 32)
+      k_proj_gemm<KMAX, 32, PhiT><<<gP, NT, 0, s>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad);
     else
       k_proj_gemm<KMAX, 64, PhiT><<<gP, NT, 0, s>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad);
     k_proj_reduce<KMAX><<<B, KMAX, 0, s>>>(ppart, L.gxp, L.bpad, k, st, Einv, cvec);
@@ -1821,21 +1877,32 @@ sdf_status solve_mixed(sdf_problem *p, const double *inst, int B, const double *
     CK(cudaMemsetAsync(xlo, 0, sizeof(float) * (size_t)N * B, s));
     par = 0;
     k_outer_setup<DIM, float><<<gT, NT, 0, s>>>(P, inst, psi, mask, rbuf[0], b64, x, dinv, st,
-                                                part, cnt, ctrl, L.gx);
+                                                part, cnt, ctrl, L.gx, p->x0, y);
     CKL("k_outer_setup");
     p->prof.launches += 1;
+    if (p->x0) {
+      k_start_resid<DIM, float><<<gT, NT, 0, s>>>(P, inst, st, mask, b64, x, rbuf[0], L.gx);
+      CKL("k_start_resid");
+      p->prof.launches += 1;
+    }
     if (defl) {
-      for (int b = 0; b < B; ++b) {
+      // The first outer iteration of every instance has A = {} (cold start);
+      // without per-instance convection S_II and Phi_I are then the same for
+      // the whole batch, and so are E_raw and G: set up once, copied.
+      const int nset = (outer == 0 && !P.convection) ? 1 : B;
+      for (int b = 0; b < nset; ++b) {
         k_modes_W<DIM, PhiT><<<dim3(k, L.gx), NT, 0, s>>>(P, inst, b, st, mask, Phi, ld, W, L.gx);
         k_gram<KMAX, PhiT><<<L.gxg, NT, 0, s>>>(Phi, ld, W, mask, st, b, N, k, 0, gpart);
         k_gram_reduce<<<(k * k + NT - 1) / NT, NT, 0, s>>>(gpart, L.gxg, k, st, b, Eraw + (size_t)b * k * k);
         k_gram<KMAX, PhiT><<<L.gxg, NT, 0, s>>>(Phi, ld, W, mask, st, b, N, k, 1, gpart);
         k_gram_reduce<<<(k * k + NT - 1) / NT, NT, 0, s>>>(gpart, L.gxg, k, st, b, G + (size_t)b * k * k);
       }
+      if (nset < B)
+        k_coarse_copy<<<B - 1, NT, 0, s>>>(k, Eraw, G);
       CKL("coarse setup");
       k_coarse<<<B, NT, 0, s>>>(k, st, G, Eraw, Einv, coarse, o.tau_cond);
       CKL("k_coarse");
-      p->prof.launches += 5LL * B + 1;
+      p->prof.launches += 5LL * nset + (nset < B ? 1 : 0) + 1;
       sdf_status e = project(rbuf[0]);  // coarse-corrected start: c = -E^-1 Phi_I^T b
       if (e != SDF_OK) return e;
     }
@@ -2240,6 +2307,19 @@ sdf_status sdf_solve_batch(sdf_problem *p, const double *inst_dev, int batch, co
                          active_dev, stats_host);
   return dispatch_k<3>(p, inst_dev, batch, psi_dev, *opts, (char *)ws, s, y_dev, lambda_dev,
                        active_dev, stats_host);
+}
+
+sdf_status sdf_solve_batch_x0(sdf_problem *p, const double *inst_dev, int batch,
+                              const double *psi_dev, const double *x0_dev, const sdf_opts *opts,
+                              void *ws, size_t ws_bytes, void *stream, double *y_dev,
+                              double *lambda_dev, uint8_t *active_dev, sdf_stats *stats_host) {
+  if (!p) return SDF_ERR_INVALID_ARG;
+  if (!x0_dev) return fail(p, SDF_ERR_INVALID_ARG, "NULL x0");
+  p->x0 = x0_dev;
+  sdf_status st = sdf_solve_batch(p, inst_dev, batch, psi_dev, opts, ws, ws_bytes, stream, y_dev,
+                                  lambda_dev, active_dev, stats_host);
+  p->x0 = nullptr;
+  return st;
 }
 
 sdf_status sdf_solve_batch_host(sdf_problem *p, const double *inst_host, int batch,

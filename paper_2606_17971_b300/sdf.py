@@ -88,6 +88,23 @@ _sigs = {
     "sdf_reset_profile": (_i32, [_vp]),
     "sdf_last_error": (ctypes.c_char_p, [_vp]),
     "sdf_problem_destroy": (None, [_vp]),
+    "sdf_solve_batch_x0": (_i32, [_vp, _vp, _i32, _vp, _vp, ctypes.POINTER(Opts), _vp, _sz, _vp,
+                                  _vp, _vp, _vp, _vp]),
+    "sdf_mlp_param_count": (_i64, [_vp]),
+    "sdf_mlp_workspace_size": (_i32, [_vp, _i32, ctypes.POINTER(_sz)]),
+    "sdf_mlp_forward": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _sz, _vp]),
+    "sdf_mlp_loss_grad": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _sz, _vp]),
+    "sdf_adam_step": (_i32, [_vp, _vp, _vp, _vp, _i64, _i32, ctypes.c_float, ctypes.c_float,
+                             ctypes.c_float, ctypes.c_float, _vp]),
+    "sdf_pod_workspace_size": (_i32, [_i64, _i32, ctypes.POINTER(_sz)]),
+    "sdf_pod": (_i32, [_vp, _i32, _i64, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "sdf_warm_expand_workspace_size": (_i32, [_i32, _i32, ctypes.POINTER(_sz)]),
+    "sdf_warm_expand": (_i32, [_vp, _vp, _i64, _i32, _vp, _vp, _vp, _i32, _vp, _vp, _sz, _vp]),
+    "sdf_aux_last_error": (ctypes.c_char_p, []),
+    "sdf_warm_fit_workspace_size": (_i32, [_vp, _i32, ctypes.POINTER(_sz)]),
+    "sdf_warm_fit": (_i32, [_vp, _vp, _vp, _i32, _i32, ctypes.c_float, _vp, _vp, _sz, _vp]),
+    "sdf_warm_predict_workspace_size": (_i32, [_vp, _i32, ctypes.POINTER(_sz)]),
+    "sdf_warm_predict": (_i32, [_vp, _vp, _i32, _vp, _vp, _sz, _vp]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(_lib, _name)
@@ -220,6 +237,29 @@ class Problem:
         out["stats"] = [stats_dict(s) for s in stats]
         return out
 
+    def solve_x0(self, inst: torch.Tensor, psi: torch.Tensor, x0: torch.Tensor, opts=None,
+                 want_lambda=False, out=None):
+        """sdf_solve_batch_x0: every inner solve starts from x0 (B, N) float64
+        restricted to its inactive set."""
+        opts = opts or default_opts()
+        B = inst.shape[0]
+        assert x0.dtype == torch.float64 and x0.is_contiguous() and x0.shape == (B, self.N)
+        ws = self.workspace(B, opts)
+        if out is None:
+            out = dict(y=torch.empty((B, self.N), dtype=torch.float64, device=self.device),
+                       lam=torch.empty((B, self.N), dtype=torch.float64, device=self.device)
+                       if want_lambda else None,
+                       active=torch.empty((B, self.N), dtype=torch.uint8, device=self.device))
+        stats = (Stats * B)()
+        st = _lib.sdf_solve_batch_x0(self._h, _ptr(inst), B, _ptr(psi), _ptr(x0),
+                                     ctypes.byref(opts), _ptr(ws), ws.numel(), _stream(),
+                                     _ptr(out["y"]), _ptr(out["lam"]), _ptr(out["active"]), stats)
+        if st not in (0, 5, 6, 7, 8):
+            self._check(st)
+        out["status"] = st
+        out["stats"] = [stats_dict(s) for s in stats]
+        return out
+
     def solve_host(self, inst: np.ndarray, psi: np.ndarray, opts=None, y=None, lam=None,
                    active=None):
         """Host-memory variant (sdf_solve_batch_host): numpy in, numpy out."""
@@ -272,3 +312,154 @@ class Problem:
         self._check(_lib.sdf_project_noalloc(self._h, _ptr(active), _ptr(v), _ptr(out),
                                               _stream()))
         return out
+
+
+# ---------------------------------------------------------------------------
+# learned warm start: MLP (tensor-core products), Adam, POD, expansion
+
+SDF_MLP_MAX_LAYERS = 8
+SDF_POD_MAX_R = 64
+
+
+class MlpDesc(ctypes.Structure):
+    _fields_ = [("n_layers", ctypes.c_int32), ("width", ctypes.c_int32 * (SDF_MLP_MAX_LAYERS + 1))]
+
+
+def _aux_check(st):
+    if st != 0:
+        raise SdfError(st, _lib.sdf_aux_last_error().decode())
+
+
+class Mlp:
+    """Widths (w0, ..., wL); parameters are one flat FP32 device tensor laid
+    out as W_1, b_1, ..., W_L, b_L (W row-major out x in)."""
+
+    def __init__(self, widths, device="cuda"):
+        self.widths = tuple(int(w) for w in widths)
+        self.desc = MlpDesc(n_layers=len(self.widths) - 1)
+        for i, w in enumerate(self.widths):
+            self.desc.width[i] = w
+        self.n_params = int(_lib.sdf_mlp_param_count(ctypes.byref(self.desc)))
+        if self.n_params < 0:
+            raise SdfError(1, "bad MLP widths")
+        self.device = torch.device(device)
+        self._ws = None
+
+    def _workspace(self, batch):
+        nb = _sz()
+        _aux_check(_lib.sdf_mlp_workspace_size(ctypes.byref(self.desc), batch, ctypes.byref(nb)))
+        if self._ws is None or self._ws.numel() < nb.value:
+            self._ws = torch.empty(int(nb.value), dtype=torch.uint8, device=self.device)
+        return self._ws
+
+    def forward(self, theta: torch.Tensor, x: torch.Tensor) -> torch.Tensor:
+        x = x.contiguous()
+        B = x.shape[0]
+        y = torch.empty((B, self.widths[-1]), dtype=torch.float32, device=self.device)
+        ws = self._workspace(B)
+        _aux_check(_lib.sdf_mlp_forward(ctypes.byref(self.desc), _ptr(theta), _ptr(x), B, _ptr(y),
+                                        _ptr(ws), ws.numel(), _stream()))
+        return y
+
+    def loss_grad(self, theta: torch.Tensor, x: torch.Tensor, t: torch.Tensor, grad=None,
+                  loss=None):
+        x, t = x.contiguous(), t.contiguous()
+        B = x.shape[0]
+        grad = torch.empty_like(theta) if grad is None else grad
+        loss = torch.empty(1, dtype=torch.float64, device=self.device) if loss is None else loss
+        ws = self._workspace(B)
+        _aux_check(_lib.sdf_mlp_loss_grad(ctypes.byref(self.desc), _ptr(theta), _ptr(x), _ptr(t),
+                                          B, _ptr(grad), _ptr(loss), _ptr(ws), ws.numel(),
+                                          _stream()))
+        return loss, grad
+
+
+def adam_step(theta, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    _aux_check(_lib.sdf_adam_step(_ptr(theta), _ptr(grad), _ptr(m), _ptr(v), theta.numel(), step,
+                                  lr, beta1, beta2, eps, _stream()))
+
+
+def pod(Y: torch.Tensor, r: int):
+    """POD of the rows of Y (m, N) float64 device tensor; returns ybar (N,),
+    psi_rm (N, r) bf16 node-major, psi_cm (r, N) float64 (column j = row j),
+    singular values (r,) and coefficients (m, r) as numpy arrays."""
+    Y = Y.contiguous()
+    m, N = Y.shape
+    nb = _sz()
+    _aux_check(_lib.sdf_pod_workspace_size(N, m, ctypes.byref(nb)))
+    ws = torch.empty(int(nb.value), dtype=torch.uint8, device=Y.device)
+    ybar = torch.empty(N, dtype=torch.float64, device=Y.device)
+    psi_rm = torch.empty((N, r), dtype=torch.bfloat16, device=Y.device)
+    psi_cm = torch.empty((r, N), dtype=torch.float64, device=Y.device)
+    sing = np.zeros(r)
+    coef = np.zeros((m, r))
+    _aux_check(_lib.sdf_pod(_ptr(Y), m, N, r, _ptr(ybar), _ptr(psi_rm), _ptr(psi_cm),
+                            sing.ctypes.data, coef.ctypes.data, _ptr(ws), ws.numel(), _stream()))
+    return ybar, psi_rm, psi_cm, sing, coef
+
+
+def warm_expand(psi_rm: torch.Tensor, ybar: torch.Tensor, cstd: torch.Tensor,
+                cmean: torch.Tensor, cscale: torch.Tensor) -> torch.Tensor:
+    """x0[b] = ybar + psi (cstd[b] * cscale + cmean), (B, N) float64."""
+    N, r = psi_rm.shape
+    B = cstd.shape[0]
+    nb = _sz()
+    _aux_check(_lib.sdf_warm_expand_workspace_size(B, r, ctypes.byref(nb)))
+    ws = torch.empty(int(nb.value), dtype=torch.uint8, device=psi_rm.device)
+    x0 = torch.empty((B, N), dtype=torch.float64, device=psi_rm.device)
+    _aux_check(_lib.sdf_warm_expand(_ptr(psi_rm), _ptr(ybar), N, r, _ptr(cstd.contiguous()),
+                                    _ptr(cmean), _ptr(cscale), B, _ptr(x0), _ptr(ws), ws.numel(),
+                                    _stream()))
+    return x0
+
+
+class WarmModelDesc(ctypes.Structure):
+    _fields_ = [("mlp", MlpDesc), ("r", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("in_lo", ctypes.c_double * 8), ("in_hi", ctypes.c_double * 8),
+                ("theta", _vp), ("ybar", _vp), ("psi", _vp), ("cmean", _vp), ("cscale", _vp)]
+
+
+class WarmModel:
+    """Learned warm start (sdf_warm_fit / sdf_warm_predict): device tensors for
+    the MLP parameters and the POD basis; theta0 (FP32 tensor) is the
+    caller's initial parameter vector."""
+
+    def __init__(self, widths, n, in_lo, in_hi, theta0: torch.Tensor):
+        self.mlp = Mlp(widths, theta0.device)
+        r = int(widths[-1])
+        dev = theta0.device
+        assert theta0.numel() == self.mlp.n_params and theta0.dtype == torch.float32
+        self.theta = theta0.clone().contiguous()
+        self.ybar = torch.empty(n, dtype=torch.float64, device=dev)
+        self.psi = torch.empty((r, n), dtype=torch.float64, device=dev)  # column-major n x r
+        self.cmean = torch.empty(r, dtype=torch.float32, device=dev)
+        self.cscale = torch.empty(r, dtype=torch.float32, device=dev)
+        d = WarmModelDesc(mlp=self.mlp.desc, r=r, n=n)
+        for i, (a, b) in enumerate(zip(in_lo, in_hi)):
+            d.in_lo[i], d.in_hi[i] = float(a), float(b)
+        d.theta, d.ybar, d.psi = _ptr(self.theta), _ptr(self.ybar), _ptr(self.psi)
+        d.cmean, d.cscale = _ptr(self.cmean), _ptr(self.cscale)
+        self.desc = d
+        self.device = dev
+
+    def fit(self, Y: torch.Tensor, inst: torch.Tensor, epochs=500, lr0=1e-3):
+        m = Y.shape[0]
+        nb = _sz()
+        _aux_check(_lib.sdf_warm_fit_workspace_size(ctypes.byref(self.desc), m, ctypes.byref(nb)))
+        ws = torch.empty(int(nb.value), dtype=torch.uint8, device=self.device)
+        loss = np.zeros(epochs)
+        _aux_check(_lib.sdf_warm_fit(ctypes.byref(self.desc), _ptr(Y.contiguous()),
+                                     _ptr(inst.contiguous()), m, epochs, lr0, loss.ctypes.data,
+                                     _ptr(ws), ws.numel(), _stream()))
+        return loss
+
+    def predict(self, inst: torch.Tensor) -> torch.Tensor:
+        B = inst.shape[0]
+        nb = _sz()
+        _aux_check(_lib.sdf_warm_predict_workspace_size(ctypes.byref(self.desc), B,
+                                                        ctypes.byref(nb)))
+        ws = torch.empty(int(nb.value), dtype=torch.uint8, device=self.device)
+        x0 = torch.empty((B, self.desc.n), dtype=torch.float64, device=self.device)
+        _aux_check(_lib.sdf_warm_predict(ctypes.byref(self.desc), _ptr(inst.contiguous()), B,
+                                         _ptr(x0), _ptr(ws), ws.numel(), _stream()))
+        return x0

@@ -147,3 +147,28 @@ def gaussian_field_2d(n: int, ell: float, sigma: float, rng) -> np.ndarray:
 
 def psi_vector(w: Workload) -> np.ndarray:
     return np.full(w.N, w.psi, dtype=np.float64)
+
+
+# ---------------------------------------------------------------------------
+# learned warm start: the input box and the seeded initial MLP parameters
+
+WARM_WIDTHS = (4, 256, 256, 256, 64)
+
+
+def input_box(w: Workload):
+    """Lower and upper bounds of the MLP inputs (a, c_1 .. c_dim)."""
+    lo = [w.a_range[0]] + [w.c_range[0]] * w.dim
+    hi = [w.a_range[1]] + [w.c_range[1]] * w.dim
+    return lo, hi
+
+
+def mlp_init(widths=WARM_WIDTHS, seed: int = 7) -> np.ndarray:
+    """Initial MLP parameters (FP32 flat vector, layout W_1, b_1, ..., W_L,
+    b_L with W row-major out x in): W ~ N(0, 1/fan_in), b = 0."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for i in range(len(widths) - 1):
+        fi, fo = widths[i], widths[i + 1]
+        parts.append((rng.standard_normal((fo, fi)) / np.sqrt(fi)).ravel())
+        parts.append(np.zeros(fo))
+    return np.concatenate(parts).astype(np.float32)
