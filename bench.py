@@ -35,7 +35,8 @@ sys.path.insert(0, ROOT)
 METRIC = "instances/sec to converged active set at rtol 1e-8, batched+learned vs plain"
 UNIT = "instances/s"
 FP64_PEAK_TFLOPS = 1.25  # nominal B300 FP64 of the profiling recipe (probe measured 1.20)
-KSRC = [os.path.join(ROOT, "paper_2606_17971_b300", "csrc", f) for f in ("sdf.cu", "sdf_device.cuh")]
+KSRC = [os.path.join(ROOT, "paper_2606_17971_b300", "csrc", f)
+        for f in ("sdf.cu", "sdf_device.cuh", "tc_device.cuh")]
 
 
 def source_hash() -> str:
@@ -247,6 +248,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-path comparison")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="mixed path without the learned warm start")
+    ap.add_argument("--train", type=int, default=128,
+                    help="training instances of the learned warm start (first solves)")
+    ap.add_argument("--epochs", type=int, default=2000, help="Adam epochs of the warm-start MLP")
     args = ap.parse_args()
 
     from paper_2606_17971_b300 import workloads as W
@@ -284,8 +290,43 @@ def main():
         opts.max_cg = args.max_cg
     out = {"y": torch.empty((B, w.N), dtype=torch.float64, device=dev), "lam": None,
            "active": torch.empty((B, w.N), dtype=torch.uint8, device=dev)}
+
+    # ---- learned warm start: trained before the timed region ----
+    learned = mixed and not args.no_learned
+    model, train_info = None, None
+    if learned:
+        t0 = time.perf_counter()
+        ntr = args.train
+        tr = W.draw_instances(w, count=ntr, seed=w.seed + 1000 + rank)
+        it_tr = torch.as_tensor(W.instances_array(tr), device=dev)
+        o1 = sdf.default_opts(check_every=128, precision=sdf.PREC_MIXED, max_outer=1)
+        Ytr = torch.empty((ntr, w.N), dtype=torch.float64, device=dev)
+        tb = min(128, ntr)
+        for j in range(0, ntr, tb):
+            Ytr[j:j + tb] = G.solve(it_tr[j:j + tb].contiguous(), psi, o1, want_lambda=False)["y"]
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        widths = (1 + w.dim, 256, 256, 256, 64)
+        lo, hi = W.input_box(w)
+        model = sdf.WarmModel(widths, w.N, lo, hi, torch.from_numpy(W.mlp_init(widths)).to(dev))
+        loss = model.fit(Ytr, it_tr, epochs=args.epochs, lr0=1e-3)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        del Ytr
+        train_info = {"instances": ntr, "solve_s": t1 - t0, "fit_s": t2 - t1,
+                      "epochs": args.epochs, "loss_first": float(loss[0]),
+                      "loss_last": float(loss[-1]), "widths": list(widths), "pod_rank": 64,
+                      "note": "first (unconstrained) solves of separate training instances; "
+                              "not part of the timed region"}
+
+    def one_step(inst):
+        if model is not None:
+            x0 = model.predict(inst)
+            return G.solve_x0(inst, psi, x0, opts, out=out, want_lambda=opts_lambda)
+        return G.solve(inst, psi, opts, out=out, want_lambda=opts_lambda)
+
     for i in range(warm):
-        G.solve(inst_t[i], psi, opts, out=out, want_lambda=opts_lambda)
+        one_step(inst_t[i])
     torch.cuda.synchronize()
 
     # ---- timed region (device-resident inputs) ----
@@ -300,7 +341,7 @@ def main():
     with ClockSampler(local) as clk:
         e0.record(stream)
         for i in range(steps):
-            res = G.solve(inst_t[warm + i], psi, opts, out=out, want_lambda=opts_lambda)
+            res = one_step(inst_t[warm + i])
             stats.extend(res["stats"])
         e1.record(stream)
         torch.cuda.synchronize()
@@ -314,29 +355,61 @@ def main():
     ms = float(t.item())
     value = steps * B * world / (ms * 1e-3)
 
-    # ---- e2e through the host-memory entry point ----
+    # ---- e2e: host buffers in, host buffers out, copies inside the timed region ----
     e2e = None
     if not args.no_e2e:
         opts.profile = 0
-        inst_h = [torch.from_numpy(W.instances_array(mine[i * B:(i + 1) * B])).pin_memory().numpy()
+        inst_h = [torch.from_numpy(W.instances_array(mine[i * B:(i + 1) * B])).pin_memory()
                   for i in range(steps + warm)]
-        psi_h = torch.full((w.N,), w.psi, dtype=torch.float64).pin_memory().numpy()
-        y_h = torch.empty((B, w.N), dtype=torch.float64).pin_memory().numpy()
-        a_h = torch.empty((B, w.N), dtype=torch.uint8).pin_memory().numpy()
-        G.solve_host(inst_h[0], psi_h, opts, y=y_h, active=a_h)
+        psi_h = torch.full((w.N,), w.psi, dtype=torch.float64).pin_memory()
+        y_h = torch.empty((B, w.N), dtype=torch.float64).pin_memory()
+        a_h = torch.empty((B, w.N), dtype=torch.uint8).pin_memory()
+        if model is None:
+            def e2e_step(i):
+                G.solve_host(inst_h[i].numpy(), psi_h.numpy(), opts, y=y_h.numpy(),
+                             active=a_h.numpy())
+        else:
+            # the learned pipeline through the binding: copy mu and psi in, predict
+            # x0 (tensor-core MLP + FP64 expansion), solve, copy y and A out
+            def e2e_step(i):
+                inst_d = inst_h[i].to(dev, non_blocking=True)
+                psi_d = psi_h.to(dev, non_blocking=True)
+                x0 = model.predict(inst_d)
+                r = G.solve_x0(inst_d, psi_d, x0, opts, out=out, want_lambda=False)
+                y_h.copy_(r["y"], non_blocking=True)
+                a_h.copy_(r["active"], non_blocking=True)
+                torch.cuda.current_stream().synchronize()
+        e2e_step(0)
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for i in range(steps):
-            G.solve_host(inst_h[warm + i], psi_h, opts, y=y_h, active=a_h)
+            e2e_step(warm + i)
         torch.cuda.synchronize()
         te = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
         if world > 1:
             dist.all_reduce(te, op=dist.ReduceOp.MAX)
         e2e = {"value": steps * B * world / float(te.item()), "unit": UNIT,
-               "h2d_bytes_per_step": int(inst_h[0].nbytes + psi_h.nbytes),
-               "d2h_bytes_per_step": int(y_h.nbytes + a_h.nbytes)}
+               "h2d_bytes_per_step": int(inst_h[0].numel() * 8 + psi_h.numel() * 8),
+               "d2h_bytes_per_step": int(y_h.numel() * 8 + a_h.numel()),
+               "path": "learned pipeline through the Python binding" if model is not None
+               else "sdf_solve_batch_host"}
+
+    # ---- the same batch without the learned start (untimed comparison) ----
+    cold_cmp = None
+    if model is not None:
+        opts.profile = 0
+        ec0, ec1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ec0.record(stream)
+        rc = G.solve(inst_t[warm], psi, opts, out=out, want_lambda=False)
+        ec1.record(stream)
+        torch.cuda.synchronize()
+        cold_cmp = {"ms": ec0.elapsed_time(ec1),
+                    "cg_iters_per_instance": float(np.mean([sum(s["cg_iters"]) for s in rc["stats"]])),
+                    "learned_cg_iters_per_instance":
+                        float(np.mean([sum(s["cg_iters"]) for s in stats[:B]])),
+                    "note": "first timed batch solved again from x0 = 0"}
 
     # ---- roofline of the dominant kernel ----
     names = ("expand", "spmv", "update") + (("project",) if mixed else ())
@@ -378,6 +451,7 @@ def main():
                    "instances_per_step": B * world, "batch_per_gpu": B,
                    "path": ("mixed FP32/%s A-DEF2, FP64 x, reductions and residual replacement"
                             % args.phi if mixed else "plain FP64 A-DEF2 per instance")
+                           + (", learned warm start" if learned else "")
                            + " (primal active-set loop)",
                    "modes": "closed-form sines on the GPU (Sec. 2.2.7)",
                    "l2": "inputs larger than L2: Phi is %.2f GB, read twice per CG iteration"
@@ -386,8 +460,13 @@ def main():
         "cg_iters_per_instance": float(np.mean(cg)), "outer_iters_per_instance": float(np.mean(outer)),
         "statuses": sorted(set(s["status"] for s in stats)),
         "roofline": roof, "clocks": clk.summary(), "e2e": e2e,
-        "gpu_launches": int(prof["launches"]),
+        # the solver's launches plus the warm-start prediction's per step: per
+        # layer one weight conversion and one product, then input conversion,
+        # input scaling and the expansion
+        "gpu_launches": int(prof["launches"]) + (steps * (2 * 4 + 3) if model is not None else 0),
     }
+    if model is not None:
+        line["learned"] = {"training": train_info, "same_batch_cold": cold_cmp}
     if mixed and not args.no_plain:
         # the metric compares against the plain per-instance FP64 path: one
         # instance of the same workload after one warm-up solve
