@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsdf_b300.so")
 SOURCES = ["sdf.cu", "warm.cu"]
-HEADERS = ["sdf_device.cuh"]
+HEADERS = ["sdf_device.cuh", "tc_device.cuh"]
 
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",

@@ -31,6 +31,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -39,6 +40,7 @@
 #include <vector>
 
 #include "sdf_device.cuh"
+#include "tc_device.cuh"
 
 using namespace sdf;
 
@@ -75,9 +77,19 @@ struct Layout {
   size_t x, b64, r, r2, p, q, w, dinv, mask, W, Einv, Eraw, G, coarse, part, gpart, state, cnt,
       ctrl, v, cvec, ppart, xlo, total;
   int gx, gxa, gxg, gxp, nb, bpad, gxc, zc;
+  int tcp, nbp;  // tensor-core projection (BF16 modes, batch <= 256) and its padded batch
+  int tce, kp;   // tensor-core expansion and the padded mode count of its node-major copy
+  size_t phin;   // node-major BF16 copy of the modes (tensor-core expansion)
 };
 
 inline size_t al(size_t v) { return (v + 255) & ~size_t(255); }
+
+// dynamic shared memory of k_expand_tc: the mode tile (128 nodes x KP) and
+// three BF16 terms of the coefficients (NBP x KP), in 64-wide K blocks
+inline size_t expand_tc_smem(int nbp, int kp) {
+  const size_t nkb = (kp + 63) / 64;
+  return nkb * 128 * 64 * 2 + 3 * nkb * (size_t)nbp * 64 * 2;
+}
 
 // ---------------------------------------------------------------------------
 // helpers
@@ -982,6 +994,162 @@ __global__ void __launch_bounds__(NT) k_expand_b(const PhiT *__restrict__ Phi, l
   }
 }
 
+// Node-major BF16 copy of the modes for the tensor-core expansion:
+// phin[g][j] (KP = k rounded up to 16 per row, zero beyond k).
+__global__ void k_phi_node_major(const __nv_bfloat16 *Phi, long long ld, int k, long long N, int KP,
+                                 __nv_bfloat16 *phin) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N * KP;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long g = e / KP;
+    const int j = (int)(e % KP);
+    phin[e] = j < k ? Phi[(long long)j * ld + g] : __float2bfloat16_rn(0.0f);
+  }
+}
+
+// Tensor-core expansion (BF16 modes): for 128-node tiles, D = Phi_tile C with
+// C = [c_1 .. c_B] (K = modes) accumulated in tensor memory, then
+// p_b = mask_I (gamma_b D^-1 r_b - D[:, b] + beta_b p_b) as in k_expand_b.
+// The coefficients enter as three BF16 terms (24 significant bits) staged
+// once per block; the modes come from the node-major copy.  A timed-out
+// completion wait writes NaN directions (reported as SDF_ERR_NONFINITE).
+template <int NBP>
+__global__ void __launch_bounds__(tc::GTH) k_expand_tc(const __nv_bfloat16 *__restrict__ phin,
+                                                       int KP, long long N, int B,
+                                                       const InstState *st, const float *cvec,
+                                                       int KMAX, const uint8_t *mask,
+                                                       const float *r, const float *dinv,
+                                                       int dinv_per_inst, float *p) {
+  using namespace tc;
+  constexpr uint32_t TCOLS = NBP <= 32 ? 32 : NBP;
+  extern __shared__ __align__(1024) uint8_t xsm[];
+  // A: 128 nodes x KP modes; C: 3 terms x NBP instances x KP modes (64-wide K blocks)
+  const int nkb = (KP + GK - 1) / GK;
+  uint8_t *sa = xsm;
+  uint8_t *sc = xsm + (size_t)nkb * GM * GK * 2;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tbase;
+  __shared__ float gam[NBP], bet[NBP];
+  __shared__ int act[NBP];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t mb = smem_u32(&mbar);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tbase)), "r"(TCOLS) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(mb, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int b = tid; b < NBP; b += GTH) {
+    const bool on = b < B && inst_running(st[b]);
+    act[b] = on ? (1 | (st[b].deflate ? 2 : 0)) : 0;
+    gam[b] = on ? (float)st[b].gamma : 0.0f;
+    bet[b] = on ? (float)st[b].beta : 0.0f;
+  }
+  __syncthreads();
+  // coefficients (instances without deflation contribute zero rows)
+  const size_t cterm = (size_t)nkb * NBP * GK * 2;  // bytes of one term
+  for (int e = tid; e < NBP * nkb * (GK / 8); e += GTH) {
+    const int b = e / (nkb * (GK / 8)), rest = e % (nkb * (GK / 8));
+    const int kb = rest / (GK / 8), kg = (rest % (GK / 8)) * 8;
+    __nv_bfloat16 h1[8], h2[8], h3[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int j = kb * GK + kg + i;
+      const float f = ((act[b] & 2) && j < KP) ? cvec[(size_t)b * KMAX + j] : 0.0f;
+      h1[i] = __float2bfloat16_rn(f);
+      const float r1 = f - __bfloat162float(h1[i]);
+      h2[i] = __float2bfloat16_rn(r1);
+      h3[i] = __float2bfloat16_rn(r1 - __bfloat162float(h2[i]));
+    }
+    const size_t o = (size_t)kb * NBP * GK * 2 + cm_off(b, kg);
+    *reinterpret_cast<uint4 *>(sc + o) = *reinterpret_cast<const uint4 *>(h1);
+    *reinterpret_cast<uint4 *>(sc + cterm + o) = *reinterpret_cast<const uint4 *>(h2);
+    *reinterpret_cast<uint4 *>(sc + 2 * cterm + o) = *reinterpret_cast<const uint4 *>(h3);
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tbase;
+  const long long ntile = (N + GM - 1) / GM;
+  bool all_ok = true;
+  uint32_t phase = 0;
+  for (long long t = blockIdx.x; t < ntile; t += gridDim.x) {
+    const long long g0 = t * GM;
+    for (int e = tid; e < GM * nkb * (GK / 8); e += GTH) {  // node rows of the modes
+      const int row = e / (nkb * (GK / 8)), rest = e % (nkb * (GK / 8));
+      const int kb = rest / (GK / 8), kg = (rest % (GK / 8)) * 8;
+      uint4 val = make_uint4(0, 0, 0, 0);
+      if (g0 + row < N && kb * GK + kg < KP)
+        val = *reinterpret_cast<const uint4 *>(phin + (g0 + row) * KP + kb * GK + kg);
+      *reinterpret_cast<uint4 *>(sa + (size_t)kb * GM * GK * 2 + cm_off(row, kg)) = val;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(sa), c0 = smem_u32(sc);
+      const uint32_t idesc = idesc_bf16(GM, NBP);
+      bool first = true;
+      for (int kb = 0; kb < nkb; ++kb)
+        for (int s = 0; s < GK / 16; ++s) {
+          if (kb * GK + 16 * s >= KP) break;
+          for (int q = 0; q < 3; ++q) {
+            tc_mma(tmem, smem_desc(a0 + kb * GM * GK * 2 + s * 2 * LBO),
+                   smem_desc(c0 + q * (uint32_t)cterm + kb * NBP * GK * 2 + s * 2 * LBO), idesc,
+                   first ? 0u : 1u);
+            first = false;
+          }
+        }
+      tc_commit(mb);
+    }
+    const bool ok = mbar_wait(mb, phase, MBAR_LIMIT);
+    phase ^= 1;
+    tc_fence_after();
+    all_ok = __syncthreads_and(ok) != 0;
+    // epilogue: thread = node g (TMEM lane), columns = instances
+    const long long g = g0 + warp * 32 + (tid & 31);
+    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+    const float dsh = (!dinv_per_inst && g < N) ? dinv[g] : 0.0f;
+#pragma unroll 1
+    for (int cb = 0; cb < NBP; cb += 16) {
+      float d[16];
+      __syncwarp();
+      if (all_ok) tc_ld16(lane_addr + (uint32_t)cb, d);
+      if (g < N) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int b = cb + q;
+          if (b >= B || !act[b]) continue;
+          const long long gb = (long long)b * N + g;
+          float v = 0.0f;
+          if (!mask[gb]) {
+            const float dv = dinv_per_inst ? dinv[gb] : dsh;
+            v = gam[b] * dv * r[gb];
+            if (bet[b] != 0.0f) v = fmaf(bet[b], p[gb], v);
+            v = all_ok ? v - d[q] : __int_as_float(0x7fc00000);
+          }
+          p[gb] = v;
+        }
+      }
+    }
+    // the next tile's MMAs overwrite the accumulator: every lane has read it
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (!all_ok) break;
+  }
+  if (!all_ok && tid == 0) mbar_wait(mb, phase, MBAR_LIMIT);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS)
+                 : "memory");
+  }
+}
+
 __device__ __forceinline__ void update_epilogue(InstState &S, double rho_new, double rn2, int *cnt_slot,
                                                 Ctrl *ctrl, double rtol2, int max_cg) {
   {
@@ -1349,6 +1517,150 @@ __global__ void __launch_bounds__(NT) k_proj_gemm(const PhiT *__restrict__ Phi, 
   }
 }
 
+// Tensor-core projection (BF16 modes): part[blk][b][j] = sum over block blk's
+// node range of Phi_j(g) v_b(g), for every instance of the batch at once.
+// D (modes x instances) accumulates in tensor memory over the block's 64-node
+// chunks; A = the modes' rows (K = nodes, contiguous in the column-major Phi),
+// B = the instances' rows of v (K = nodes, contiguous).  v is FP32: it enters
+// as three BF16 terms v1 = bf16(v), v2 = bf16(v - v1), v3 = bf16(v - v1 - v2)
+// (24 significant bits), each multiplied by the exactly stored modes.  A
+// timed-out completion wait leaves NaN partials, which the CG reports as
+// SDF_ERR_NONFINITE.
+template <int NBP>
+__global__ void __launch_bounds__(tc::GTH) k_proj_tc(const __nv_bfloat16 *__restrict__ Phi,
+                                                     long long ld, int k, long long N, int B,
+                                                     const InstState *st, const float *v,
+                                                     double *part, int Bpad, int KM) {
+  using namespace tc;
+  static_assert(NBP % 16 == 0 && NBP >= 16 && NBP <= 256, "batch tile");
+  constexpr uint32_t TCOLS = NBP <= 32 ? 32 : NBP;
+  extern __shared__ __align__(1024) uint8_t tsm[];
+  uint8_t *sa = tsm;              // 128 modes x 64 nodes (rows >= k zero)
+  uint8_t *sb = tsm + GM * GK * 2;  // 3 terms x NBP instances x 64 nodes
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tbase;
+  __shared__ int run[NBP];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const uint32_t mb = smem_u32(&mbar);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tbase)), "r"(TCOLS) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(mb, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int b = tid; b < NBP; b += GTH)
+    run[b] = (b < B && !st[b].outer_done && !st[b].cg_done && st[b].deflate) ? 1 : 0;
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tbase;
+  const long long nch = (N + GK - 1) / GK;
+  const long long c_lo = nch * blockIdx.x / gridDim.x, c_hi = nch * (blockIdx.x + 1) / gridDim.x;
+  const bool vphi = (ld % 8) == 0, vv = (N % 4) == 0;
+  bool all_ok = true;
+  uint32_t phase = 0;
+  for (long long ch = c_lo; ch < c_hi; ++ch) {
+    const long long g0 = ch * GK;
+    for (int e = tid; e < GM * (GK / 8); e += GTH) {  // modes
+      const int j = e >> 3, kg = (e & 7) * 8;
+      const long long g = g0 + kg;
+      uint4 val = make_uint4(0, 0, 0, 0);
+      if (j < k && g < N) {
+        const __nv_bfloat16 *src = Phi + (long long)j * ld + g;
+        if (vphi && g + 8 <= N) {
+          val = *reinterpret_cast<const uint4 *>(src);
+        } else {
+          __nv_bfloat16 h[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) h[i] = g + i < N ? src[i] : __float2bfloat16_rn(0.0f);
+          val = *reinterpret_cast<const uint4 *>(h);
+        }
+      }
+      *reinterpret_cast<uint4 *>(sa + cm_off(j, kg)) = val;
+    }
+    for (int e = tid; e < NBP * (GK / 8); e += GTH) {  // instances, three BF16 terms
+      const int b = e >> 3, kg = (e & 7) * 8;
+      const long long g = g0 + kg;
+      float f[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) f[i] = 0.0f;
+      if (run[b] && g < N) {
+        const float *src = v + (long long)b * N + g;
+        if (vv && g + 8 <= N) {
+          const float4 a = *reinterpret_cast<const float4 *>(src);
+          const float4 c = *reinterpret_cast<const float4 *>(src + 4);
+          f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w;
+          f[4] = c.x; f[5] = c.y; f[6] = c.z; f[7] = c.w;
+        } else {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) f[i] = g + i < N ? src[i] : 0.0f;
+        }
+      }
+      __nv_bfloat16 h1[8], h2[8], h3[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        h1[i] = __float2bfloat16_rn(f[i]);
+        const float r1 = f[i] - __bfloat162float(h1[i]);
+        h2[i] = __float2bfloat16_rn(r1);
+        h3[i] = __float2bfloat16_rn(r1 - __bfloat162float(h2[i]));
+      }
+      const uint32_t o = cm_off(b, kg);
+      *reinterpret_cast<uint4 *>(sb + o) = *reinterpret_cast<const uint4 *>(h1);
+      *reinterpret_cast<uint4 *>(sb + NBP * 128 + o) = *reinterpret_cast<const uint4 *>(h2);
+      *reinterpret_cast<uint4 *>(sb + 2 * NBP * 128 + o) = *reinterpret_cast<const uint4 *>(h3);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(sa), b0 = smem_u32(sb);
+      const uint32_t idesc = idesc_bf16(GM, NBP);
+#pragma unroll
+      for (int s = 0; s < GK / 16; ++s)
+#pragma unroll
+        for (int t = 0; t < 3; ++t)
+          tc_mma(tmem, smem_desc(a0 + s * 2 * LBO), smem_desc(b0 + t * NBP * 128 + s * 2 * LBO),
+                 idesc, (ch > c_lo || s > 0 || t > 0) ? 1u : 0u);
+      tc_commit(mb);
+    }
+    const bool ok = mbar_wait(mb, phase, MBAR_LIMIT);
+    phase ^= 1;
+    tc_fence_after();
+    all_ok = __syncthreads_and(ok) != 0;
+    if (!all_ok) break;
+  }
+  // epilogue: lane j of warp w (row 32 w + j) holds mode 32 w + j
+  const int j = warp * 32 + (tid & 31);
+  const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+  const bool any = c_hi > c_lo;
+#pragma unroll 1
+  for (int c0 = 0; c0 < NBP; c0 += 16) {
+    float d[16];
+    __syncwarp();
+    if (any && all_ok) tc_ld16(lane_addr + (uint32_t)c0, d);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int b = c0 + q;
+      if (j < KM && b < Bpad) {
+        const double val = !all_ok ? __longlong_as_double(0x7ff8000000000000LL)
+                                   : (any ? (double)d[q] : 0.0);
+        part[((long long)blockIdx.x * Bpad + b) * KM + j] = val;
+      }
+    }
+  }
+  if (!all_ok && tid == 0) mbar_wait(mb, phase, MBAR_LIMIT);
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS)
+                 : "memory");
+  }
+}
+
 // Sum the projection partials of each instance in block order and form the
 // coarse coefficients c_b = csign_b E_raw,b^-1 t_b (FP64), stored as FP32.
 template <int KMAX>
@@ -1610,11 +1922,22 @@ Layout make_layout(const sdf_problem *p, int B, int max_blocks = 0, int mixed = 
   L.nb = B == 1 ? 1 : (B <= 16 ? 16 : (B <= 32 ? 32 : 64));
   L.bpad = (int)(((B + L.nb - 1) / L.nb) * L.nb);
   L.gxp = std::max(1, (p->nsm * 6) / ((B + L.nb - 1) / L.nb));
+  // BF16 modes: the projection runs on the tensor cores for the whole batch
+  L.tcp = (mixed && p->phi_dtype == SDF_BF16 && B <= 256) ? 1 : 0;
+  L.nbp = B <= 16 ? 16 : (B <= 32 ? 32 : (B <= 64 ? 64 : (B <= 128 ? 128 : 256)));
+  if (L.tcp) {
+    L.bpad = L.nbp;
+    L.gxp = (int)std::min<long long>(p->nsm * (L.nbp <= 64 ? 8 : 4), (N + 63) / 64);
+  }
   if (max_blocks > 0) L.gxp = std::min(L.gxp, max_blocks);
   L.v = take(mixed ? sizeof(float) * (size_t)N * B : 8);
   L.xlo = take(mixed ? sizeof(float) * (size_t)N * B : 8);
   L.cvec = take(sizeof(float) * (size_t)B * KM);
   L.ppart = take(mixed ? sizeof(double) * (size_t)L.gxp * L.bpad * KM : 8);
+  // tensor-core expansion: BF16 modes, and its shared-memory tiles must fit
+  L.kp = (std::max(k, 1) + 15) / 16 * 16;
+  L.tce = (L.tcp && expand_tc_smem(L.nbp, L.kp) <= 200 * 1024) ? 1 : 0;
+  L.phin = take(L.tce ? sizeof(uint16_t) * (size_t)N * L.kp : 8);
   L.total = o;
   return L;
 }
@@ -1830,8 +2153,53 @@ sdf_status solve_mixed(sdf_problem *p, const double *inst, int B, const double *
   const double rtol2 = o.rtol * o.rtol;
   int live = B;
   int par = 0;
+  __nv_bfloat16 *phin = (__nv_bfloat16 *)(ws + L.phin);
+  const size_t xsm = expand_tc_smem(L.nbp, L.kp);
+  const int gxt = (int)std::max<long long>(1, std::min<long long>((N + 127) / 128, p->nsm * 6LL));
+  if constexpr (std::is_same<PhiT, __nv_bfloat16>::value) {
+    if (L.tce && defl) {
+      k_phi_node_major<<<p->nsm * 8, NT, 0, s>>>(Phi, ld, k, N, L.kp, phin);
+      CKL("k_phi_node_major");
+      cudaError_t e = cudaSuccess;
+      switch (L.nbp) {
+        case 16: e = cudaFuncSetAttribute(k_expand_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm); break;
+        case 32: e = cudaFuncSetAttribute(k_expand_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm); break;
+        case 64: e = cudaFuncSetAttribute(k_expand_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm); break;
+        case 128: e = cudaFuncSetAttribute(k_expand_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm); break;
+        default: e = cudaFuncSetAttribute(k_expand_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)xsm); break;
+      }
+      CK(e);
+    }
+    if (L.tcp && defl) {  // the larger batch tiles need more than 48 KB of shared memory
+      const int sm = tc::GM * tc::GK * 2 + 3 * L.nbp * tc::GK * 2;
+      cudaError_t e = cudaSuccess;
+      switch (L.nbp) {
+        case 16: e = cudaFuncSetAttribute(k_proj_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm); break;
+        case 32: e = cudaFuncSetAttribute(k_proj_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm); break;
+        case 64: e = cudaFuncSetAttribute(k_proj_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm); break;
+        case 128: e = cudaFuncSetAttribute(k_proj_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm); break;
+        default: e = cudaFuncSetAttribute(k_proj_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm); break;
+      }
+      CK(e);
+    }
+  }
   auto project = [&](const float *src) -> sdf_status {  // cvec <- csign E^-1 Phi_I^T src
     if (!defl) return SDF_OK;
+    if constexpr (std::is_same<PhiT, __nv_bfloat16>::value) {
+      if (L.tcp) {
+        const size_t sm = (size_t)tc::GM * tc::GK * 2 + 3 * (size_t)L.nbp * tc::GK * 2;
+        switch (L.nbp) {
+          case 16: k_proj_tc<16><<<L.gxp, tc::GTH, sm, s>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad, KMAX); break;
+          case 32: k_proj_tc<32><<<L.gxp, tc::GTH, sm, s>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad, KMAX); break;
+          case 64: k_proj_tc<64><<<L.gxp, tc::GTH, sm, s>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad, KMAX); break;
+          case 128: k_proj_tc<128><<<L.gxp, tc::GTH, sm, s>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad, KMAX); break;
+          default: k_proj_tc<256><<<L.gxp, tc::GTH, sm, s>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad, KMAX); break;
+        }
+        k_proj_reduce<KMAX><<<B, KMAX, 0, s>>>(ppart, L.gxp, L.bpad, k, st, Einv, cvec);
+        p->prof.launches += 2;
+        return SDF_OK;
+      }
+    }
     if (L.nb == 1)
       k_proj_gemm<KMAX, 1, PhiT><<<gP, NT, 0, s>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad);
     else if (L.nb == 16)
@@ -1846,8 +2214,26 @@ sdf_status solve_mixed(sdf_problem *p, const double *inst, int B, const double *
   };
   auto triple = [&](float *dir, bool timed) -> sdf_status {
     if (timed) CK(cudaEventRecord(p->ev[0], s));
-    k_expand_b<KMAX, PhiT><<<gxe, NT, esm, s>>>(Phi, ld, k, N, B, st, cvec, mask, rbuf[par], dinv,
-                                                P.convection, dir);
+    bool expanded = false;
+    if constexpr (std::is_same<PhiT, __nv_bfloat16>::value) {
+      if (L.tce && defl) {
+#define SDF_EXPAND_TC(NB_)                                                                        \
+  k_expand_tc<NB_><<<gxt, tc::GTH, xsm, s>>>(phin, L.kp, N, B, st, cvec, KMAX, mask, rbuf[par], \
+                                             dinv, P.convection, dir)
+        switch (L.nbp) {
+          case 16: SDF_EXPAND_TC(16); break;
+          case 32: SDF_EXPAND_TC(32); break;
+          case 64: SDF_EXPAND_TC(64); break;
+          case 128: SDF_EXPAND_TC(128); break;
+          default: SDF_EXPAND_TC(256); break;
+        }
+#undef SDF_EXPAND_TC
+        expanded = true;
+      }
+    }
+    if (!expanded)
+      k_expand_b<KMAX, PhiT><<<gxe, NT, esm, s>>>(Phi, ld, k, N, B, st, cvec, mask, rbuf[par],
+                                                  dinv, P.convection, dir);
     if (timed) CK(cudaEventRecord(p->ev[1], s));
     if constexpr (DIM == 3) {
       const dim3 gC(B, L.gxc);

@@ -357,3 +357,20 @@ def test_mixed_rejects_fp64_modes_and_fp64_rejects_bf16():
     G.set_modes(phi.to(torch.bfloat16).contiguous())
     with pytest.raises(sdf.SdfError):
         G.solve(t64([inst_row(1.0, (0.5, 0.5))]), t64(np.ones(256)), sdf.default_opts())
+
+
+def test_mixed_3d_bf16_batch_of_37_on_an_odd_grid():
+    # the tensor-core projection with a ragged batch (37 of a 64-wide tile) and
+    # an odd node count (scalar fall-back loads at the last chunk)
+    n3 = (19, 17, 13)
+    P3 = O.Problem(3, n3, alpha=1e-4)
+    Phi3 = O.dense_modes(P3, 16)[0]
+    w3 = W.scaled(W.WORKLOADS["diff3d_128"], 17, instances=37)
+    i3 = W.draw_instances(w3, count=37)
+    i3[5].a = 4.0
+    psi = np.ones(P3.N)
+    orc3 = _orc_solves(P3, [P3.desired_state(i.a, i.c, w3.sigma)[1] for i in i3], psi, Phi3)
+    G3 = sdf.Problem(3, n3, alpha=1e-4, yd_sigma=w3.sigma)
+    G3.set_modes(modes_tensor_as(Phi3, torch.bfloat16))
+    out3 = G3.solve(t64(W.instances_array(i3)), t64(psi), sdf.default_opts(precision=sdf.PREC_MIXED))
+    compare_mixed(out3, orc3)
