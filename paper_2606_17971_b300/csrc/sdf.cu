@@ -1114,6 +1114,19 @@ __global__ void __launch_bounds__(tc::GTH) k_expand_tc(const __nv_bfloat16 *__re
     const float dsh = (!dinv_per_inst && g < N) ? dinv[g] : 0.0f;
 #pragma unroll 1
     for (int cb = 0; cb < NBP; cb += 16) {
+      // every load of the 16 instances first, then the arithmetic
+      uint8_t mk[16];
+      float rv[16], pv[16], dv[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int b = cb + q;
+        const bool on = g < N && b < B && act[b];
+        const long long gb = (long long)b * N + g;
+        mk[q] = on ? mask[gb] : (uint8_t)1;
+        rv[q] = on ? r[gb] : 0.0f;
+        pv[q] = (on && bet[b] != 0.0f) ? p[gb] : 0.0f;
+        dv[q] = on ? (dinv_per_inst ? dinv[gb] : dsh) : 0.0f;
+      }
       float d[16];
       __syncwarp();
       if (all_ok) tc_ld16(lane_addr + (uint32_t)cb, d);
@@ -1122,15 +1135,12 @@ __global__ void __launch_bounds__(tc::GTH) k_expand_tc(const __nv_bfloat16 *__re
         for (int q = 0; q < 16; ++q) {
           const int b = cb + q;
           if (b >= B || !act[b]) continue;
-          const long long gb = (long long)b * N + g;
           float v = 0.0f;
-          if (!mask[gb]) {
-            const float dv = dinv_per_inst ? dinv[gb] : dsh;
-            v = gam[b] * dv * r[gb];
-            if (bet[b] != 0.0f) v = fmaf(bet[b], p[gb], v);
+          if (!mk[q]) {
+            v = fmaf(bet[b], pv[q], gam[b] * dv[q] * rv[q]);
             v = all_ok ? v - d[q] : __int_as_float(0x7fc00000);
           }
-          p[gb] = v;
+          p[(long long)b * N + g] = v;
         }
       }
     }
@@ -1560,12 +1570,17 @@ __global__ void __launch_bounds__(tc::GTH) k_proj_tc(const __nv_bfloat16 *__rest
   const long long nch = (N + GK - 1) / GK;
   const long long c_lo = nch * blockIdx.x / gridDim.x, c_hi = nch * (blockIdx.x + 1) / gridDim.x;
   const bool vphi = (ld % 8) == 0, vv = (N % 4) == 0;
-  bool all_ok = true;
-  uint32_t phase = 0;
-  for (long long ch = c_lo; ch < c_hi; ++ch) {
+  // The next chunk's global loads are issued into registers before this
+  // chunk's MMAs are awaited (the instance rows too when NBP <= 64).
+  constexpr int AIT = GM * (GK / 8) / GTH, BIT = NBP * (GK / 8) / GTH;
+  constexpr bool PFB = NBP <= 64;
+  uint4 pa[AIT];
+  float pb[PFB ? BIT : 1][8];
+  auto fetch_a = [&](long long ch) {
     const long long g0 = ch * GK;
-    for (int e = tid; e < GM * (GK / 8); e += GTH) {  // modes
-      const int j = e >> 3, kg = (e & 7) * 8;
+#pragma unroll
+    for (int it = 0; it < AIT; ++it) {
+      const int e = tid + it * GTH, j = e >> 3, kg = (e & 7) * 8;
       const long long g = g0 + kg;
       uint4 val = make_uint4(0, 0, 0, 0);
       if (j < k && g < N) {
@@ -1575,42 +1590,78 @@ __global__ void __launch_bounds__(tc::GTH) k_proj_tc(const __nv_bfloat16 *__rest
         } else {
           __nv_bfloat16 h[8];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) h[i] = g + i < N ? src[i] : __float2bfloat16_rn(0.0f);
+          for (int q = 0; q < 8; ++q) h[q] = g + q < N ? src[q] : __float2bfloat16_rn(0.0f);
           val = *reinterpret_cast<const uint4 *>(h);
         }
       }
-      *reinterpret_cast<uint4 *>(sa + cm_off(j, kg)) = val;
+      pa[it] = val;
     }
-    for (int e = tid; e < NBP * (GK / 8); e += GTH) {  // instances, three BF16 terms
-      const int b = e >> 3, kg = (e & 7) * 8;
-      const long long g = g0 + kg;
-      float f[8];
+  };
+  auto fetch_b = [&](long long ch, int it, float (&f)[8]) {
+    const int e = tid + it * GTH, b = e >> 3, kg = (e & 7) * 8;
+    const long long g = ch * GK + kg;
 #pragma unroll
-      for (int i = 0; i < 8; ++i) f[i] = 0.0f;
-      if (run[b] && g < N) {
-        const float *src = v + (long long)b * N + g;
-        if (vv && g + 8 <= N) {
-          const float4 a = *reinterpret_cast<const float4 *>(src);
-          const float4 c = *reinterpret_cast<const float4 *>(src + 4);
-          f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w;
-          f[4] = c.x; f[5] = c.y; f[6] = c.z; f[7] = c.w;
-        } else {
+    for (int q = 0; q < 8; ++q) f[q] = 0.0f;
+    if (run[b] && g < N) {
+      const float *src = v + (long long)b * N + g;
+      if (vv && g + 8 <= N) {
+        const float4 a = *reinterpret_cast<const float4 *>(src);
+        const float4 c = *reinterpret_cast<const float4 *>(src + 4);
+        f[0] = a.x; f[1] = a.y; f[2] = a.z; f[3] = a.w;
+        f[4] = c.x; f[5] = c.y; f[6] = c.z; f[7] = c.w;
+      } else {
 #pragma unroll
-          for (int i = 0; i < 8; ++i) f[i] = g + i < N ? src[i] : 0.0f;
-        }
+        for (int q = 0; q < 8; ++q) f[q] = g + q < N ? src[q] : 0.0f;
       }
-      __nv_bfloat16 h1[8], h2[8], h3[8];
+    }
+  };
+  auto put_b = [&](int it, const float (&f)[8]) {  // three BF16 terms of 8 values
+    const int e = tid + it * GTH, b = e >> 3, kg = (e & 7) * 8;
+    __nv_bfloat16 h1[8], h2[8], h3[8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        h1[i] = __float2bfloat16_rn(f[i]);
-        const float r1 = f[i] - __bfloat162float(h1[i]);
-        h2[i] = __float2bfloat16_rn(r1);
-        h3[i] = __float2bfloat16_rn(r1 - __bfloat162float(h2[i]));
+    for (int q = 0; q < 8; ++q) {
+      h1[q] = __float2bfloat16_rn(f[q]);
+      const float r1 = f[q] - __bfloat162float(h1[q]);
+      h2[q] = __float2bfloat16_rn(r1);
+      h3[q] = __float2bfloat16_rn(r1 - __bfloat162float(h2[q]));
+    }
+    const uint32_t o = cm_off(b, kg);
+    *reinterpret_cast<uint4 *>(sb + o) = *reinterpret_cast<const uint4 *>(h1);
+    *reinterpret_cast<uint4 *>(sb + NBP * 128 + o) = *reinterpret_cast<const uint4 *>(h2);
+    *reinterpret_cast<uint4 *>(sb + 2 * NBP * 128 + o) = *reinterpret_cast<const uint4 *>(h3);
+  };
+  if (c_lo < c_hi) {
+    fetch_a(c_lo);
+    if constexpr (PFB) {
+#pragma unroll
+      for (int it = 0; it < BIT; ++it) fetch_b(c_lo, it, pb[it]);
+    }
+  }
+  bool all_ok = true;
+  uint32_t phase = 0;
+  for (long long ch = c_lo; ch < c_hi; ++ch) {
+    // the tiles are free: the previous chunk's MMAs have completed
+#pragma unroll
+    for (int it = 0; it < AIT; ++it) {
+      const int e = tid + it * GTH;
+      *reinterpret_cast<uint4 *>(sa + cm_off(e >> 3, (e & 7) * 8)) = pa[it];
+    }
+    if constexpr (PFB) {
+#pragma unroll
+      for (int it = 0; it < BIT; ++it) put_b(it, pb[it]);
+    } else {
+      for (int it = 0; it < BIT; ++it) {
+        float f[8];
+        fetch_b(ch, it, f);
+        put_b(it, f);
       }
-      const uint32_t o = cm_off(b, kg);
-      *reinterpret_cast<uint4 *>(sb + o) = *reinterpret_cast<const uint4 *>(h1);
-      *reinterpret_cast<uint4 *>(sb + NBP * 128 + o) = *reinterpret_cast<const uint4 *>(h2);
-      *reinterpret_cast<uint4 *>(sb + 2 * NBP * 128 + o) = *reinterpret_cast<const uint4 *>(h3);
+    }
+    if (ch + 1 < c_hi) {
+      fetch_a(ch + 1);
+      if constexpr (PFB) {
+#pragma unroll
+        for (int it = 0; it < BIT; ++it) fetch_b(ch + 1, it, pb[it]);
+      }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
@@ -1664,16 +1715,31 @@ __global__ void __launch_bounds__(tc::GTH) k_proj_tc(const __nv_bfloat16 *__rest
 // Sum the projection partials of each instance in block order and form the
 // coarse coefficients c_b = csign_b E_raw,b^-1 t_b (FP64), stored as FP32.
 template <int KMAX>
-__global__ void k_proj_reduce(const double *part, int GXp, int Bpad, int k, const InstState *st,
-                              const double *Einv, float *cvec) {
+__global__ void __launch_bounds__(NT) k_proj_reduce(const double *part, int GXp, int Bpad, int k,
+                                                    const InstState *st, const double *Einv,
+                                                    float *cvec) {
+  // NT threads: mode j = tid % KMAX, block slice q = tid / KMAX sums the
+  // partials g = q, q + Q, ... (eight loads in flight), then the Q slice sums
+  // of each mode are added in slice order (deterministic)
+  constexpr int Q = NT / KMAX > 0 ? NT / KMAX : 1;
   __shared__ double t[KMAX];
+  __shared__ double sl[Q][KMAX];
   const int b = blockIdx.x;
   const InstState &S = st[b];
   if (S.outer_done || S.cg_done) return;
+  for (int e = threadIdx.x; e < Q * KMAX; e += blockDim.x) {
+    const int j = e % KMAX, q = e / KMAX;
+    double s = 0.0;
+    if (j < k && S.deflate) {
+#pragma unroll 8
+      for (int g = q; g < GXp; g += Q) s += part[((long long)g * Bpad + b) * KMAX + j];
+    }
+    sl[q][j] = s;
+  }
+  __syncthreads();
   for (int j = threadIdx.x; j < KMAX; j += blockDim.x) {
     double s = 0.0;
-    if (j < k && S.deflate)
-      for (int g = 0; g < GXp; ++g) s += part[((long long)g * Bpad + b) * KMAX + j];
+    for (int q = 0; q < Q; ++q) s += sl[q][j];
     t[j] = s;
   }
   __syncthreads();
@@ -1926,8 +1992,12 @@ Layout make_layout(const sdf_problem *p, int B, int max_blocks = 0, int mixed = 
   L.tcp = (mixed && p->phi_dtype == SDF_BF16 && B <= 256) ? 1 : 0;
   L.nbp = B <= 16 ? 16 : (B <= 32 ? 32 : (B <= 64 ? 64 : (B <= 128 ? 128 : 256)));
   if (L.tcp) {
+    // one wave: as many blocks per SM as shared memory admits (at most 6)
+    // (the 64-wide tile holds its prefetched rows in 128 registers: 4 blocks)
+    const int occ = std::max(1, std::min(L.nbp == 64 ? 4 : 6,
+                                         (int)((220 * 1024) / (16384 + 3 * 128 * L.nbp + 2048))));
     L.bpad = L.nbp;
-    L.gxp = (int)std::min<long long>(p->nsm * (L.nbp <= 64 ? 8 : 4), (N + 63) / 64);
+    L.gxp = (int)std::min<long long>((long long)p->nsm * occ, (N + 63) / 64);
   }
   if (max_blocks > 0) L.gxp = std::min(L.gxp, max_blocks);
   L.v = take(mixed ? sizeof(float) * (size_t)N * B : 8);
@@ -2195,7 +2265,7 @@ sdf_status solve_mixed(sdf_problem *p, const double *inst, int B, const double *
           case 128: k_proj_tc<128><<<L.gxp, tc::GTH, sm, s>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad, KMAX); break;
           default: k_proj_tc<256><<<L.gxp, tc::GTH, sm, s>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad, KMAX); break;
         }
-        k_proj_reduce<KMAX><<<B, KMAX, 0, s>>>(ppart, L.gxp, L.bpad, k, st, Einv, cvec);
+        k_proj_reduce<KMAX><<<B, NT, 0, s>>>(ppart, L.gxp, L.bpad, k, st, Einv, cvec);
         p->prof.launches += 2;
         return SDF_OK;
       }
@@ -2208,7 +2278,7 @@ sdf_status solve_mixed(sdf_problem *p, const double *inst, int B, const double *
       k_proj_gemm<KMAX, 32, PhiT><<<gP, NT, 0, s>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad);
     else
       k_proj_gemm<KMAX, 64, PhiT><<<gP, NT, 0, s>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad);
-    k_proj_reduce<KMAX><<<B, KMAX, 0, s>>>(ppart, L.gxp, L.bpad, k, st, Einv, cvec);
+    k_proj_reduce<KMAX><<<B, NT, 0, s>>>(ppart, L.gxp, L.bpad, k, st, Einv, cvec);
     p->prof.launches += 2;
     return SDF_OK;
   };
