@@ -293,6 +293,44 @@ const char *sdf_last_error(const sdf_problem *p);
 /* Release the host handle (device buffers stay the caller's). */
 void sdf_problem_destroy(sdf_problem *p);
 
+/* Reference eigensolve (Sec. 2.2.3, where the paper uses ARPACK): the k
+ * smallest eigenpairs of A (no convection: A symmetric), which are those of
+ * S with lambda_S = mass + wgt lambda_A^2, by Chebyshev-filtered subspace
+ * iteration (Zhou & Saad's scaled filter on [a, b], a = the largest Ritz
+ * value of the block, b = a Gershgorin bound of A) with Cholesky-QR
+ * orthonormalisation (twice) and Rayleigh-Ritz; all vector work in FP64 on
+ * the GPU, the (k + guard)^2 factorisations on the host.  The start block is
+ * SplitMix64 of (seed, index).
+ *   tol       stop when every wanted pair has ||A phi - lambda phi|| <=
+ *             tol |lambda|
+ *   degree    Chebyshev degree per filter pass
+ *   guard     extra block vectors (0: max(16, k / 2)); k + guard <= 320
+ *   max_iter  filter passes
+ * phi_dev: k orthonormal columns of N doubles with leading dimension ld
+ * (device); lambda_S_host / lambda_A_host (k, ascending, may be NULL).
+ * SDF_ERR_UNSUPPORTED with convection; SDF_ERR_CG_MAXIT if not converged (the
+ * best block so far is written). */
+typedef struct {
+  double tol;
+  int32_t degree;
+  int32_t guard;
+  int32_t max_iter;
+  uint64_t seed;
+} sdf_eig_opts;
+typedef struct {
+  int32_t iters;
+  int32_t converged;
+  double max_rel_resid;
+  int64_t matvecs;
+  double seconds;
+} sdf_eig_stats;
+void sdf_default_eig_opts(sdf_eig_opts *o);
+sdf_status sdf_eig_workspace_size(const sdf_problem *p, int k, const sdf_eig_opts *o,
+                                  size_t *bytes);
+sdf_status sdf_reference_modes_eig(sdf_problem *p, int k, const sdf_eig_opts *o, double *phi_dev,
+                                   int64_t ld, double *lambda_S_host, double *lambda_A_host,
+                                   sdf_eig_stats *stats, void *ws, size_t ws_bytes, void *stream);
+
 /* ==========================================================================
  * Learned warm start (no counterpart in the paper, which lists learned
  * initialisations only as related work).  A multilayer perceptron maps the

@@ -14,8 +14,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsdf_b300.so")
-SOURCES = ["sdf.cu", "warm.cu"]
-HEADERS = ["sdf_device.cuh", "tc_device.cuh"]
+SOURCES = ["sdf.cu", "warm.cu", "eig.cu"]
+HEADERS = ["sdf_device.cuh", "tc_device.cuh", "host_linalg.h"]
 
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",

@@ -2479,6 +2479,17 @@ size_t problem_bytes(const sdf_problem *p) {
 
 }  // namespace
 
+// Accessors for the eigensolver translation unit (not part of the C ABI).
+const sdf::OpParams *sdf_internal_op(const sdf_problem *p, int *nsm, int *convection) {
+  if (!p || !p->bound) return nullptr;
+  if (nsm) *nsm = p->nsm;
+  if (convection) *convection = p->d.convection;
+  return &p->P;
+}
+void sdf_internal_set_error(sdf_problem *p, const char *msg) {
+  if (p) p->err = msg;
+}
+
 // ===========================================================================
 // C ABI
 

@@ -659,7 +659,7 @@ __device__ __forceinline__ bool last_block(int *counter, int nblocks, int *flag_
 // for f < nf, summed in block order g = 0..ng-1 (fixed order, identical on
 // every run).  Uses all threads: field f is split over `split` threads whose
 // partial sums are then combined in order.
-__device__ void reduce_fields(const double *part, int ng, int stride, int nf, double *out,
+inline __device__ void reduce_fields(const double *part, int ng, int stride, int nf, double *out,
                               double *scratch /* >= NT doubles */) {
   int split = NT / nf;
   if (split < 1) split = 1;

@@ -20,6 +20,7 @@
 
 #include "../../include/sdf.h"
 #include "tc_device.cuh"
+#include "host_linalg.h"
 
 namespace {
 
@@ -467,59 +468,6 @@ __global__ void k_coef_bf16(const float *cstd, int B, int r, const float *cmean,
   }
 }
 
-// host: cyclic Jacobi eigen-decomposition of a symmetric m x m matrix
-// (row-major); eigenvalues descending in w, eigenvectors as columns of V
-void jacobi_eig(int n, std::vector<double> &A, std::vector<double> &w, std::vector<double> &V) {
-  V.assign((size_t)n * n, 0.0);
-  for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
-  for (int sweep = 0; sweep < 100; ++sweep) {
-    double off = 0.0, tot = 0.0;
-    for (int i = 0; i < n; ++i)
-      for (int j = 0; j < n; ++j) {
-        const double a = A[(size_t)i * n + j];
-        tot += a * a;
-        if (i != j) off += a * a;
-      }
-    if (off <= 1e-30 * tot) break;
-    for (int p = 0; p < n - 1; ++p)
-      for (int q = p + 1; q < n; ++q) {
-        const double apq = A[(size_t)p * n + q];
-        if (apq == 0.0) continue;
-        const double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
-        const double theta = (aqq - app) / (2.0 * apq);
-        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
-        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
-        for (int k = 0; k < n; ++k) {
-          const double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
-          A[(size_t)k * n + p] = c * akp - s * akq;
-          A[(size_t)k * n + q] = s * akp + c * akq;
-        }
-        for (int k = 0; k < n; ++k) {
-          const double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
-          A[(size_t)p * n + k] = c * apk - s * aqk;
-          A[(size_t)q * n + k] = s * apk + c * aqk;
-        }
-        for (int k = 0; k < n; ++k) {
-          const double vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
-          V[(size_t)k * n + p] = c * vkp - s * vkq;
-          V[(size_t)k * n + q] = s * vkp + c * vkq;
-        }
-      }
-  }
-  std::vector<int> ord(n);
-  for (int i = 0; i < n; ++i) ord[i] = i;
-  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) {
-    return A[(size_t)a * n + a] > A[(size_t)b * n + b];
-  });
-  std::vector<double> V2((size_t)n * n);
-  w.resize(n);
-  for (int j = 0; j < n; ++j) {
-    w[j] = A[(size_t)ord[j] * n + ord[j]];
-    for (int i = 0; i < n; ++i) V2[(size_t)i * n + j] = V[(size_t)i * n + ord[j]];
-  }
-  V.swap(V2);
-}
-
 // ---------------------------------------------------------------------------
 // MLP workspace layout (batch m, padded rows mp = roundup(m, 128), padded
 // widths p_l = roundup(width_l, 16)).
@@ -875,7 +823,7 @@ sdf_status sdf_pod(const double *Y_dev, int m, int64_t n, int r, double *ybar_de
   std::vector<double> Ch((size_t)m * m), wv, V;
   WCK(cudaMemcpyAsync(Ch.data(), C, sizeof(double) * m * m, cudaMemcpyDeviceToHost, s));
   WCK(cudaStreamSynchronize(s));
-  jacobi_eig(m, Ch, wv, V);
+  hla::jacobi_eig(m, Ch, wv, V);
   if (!(wv[r - 1] > 0.0)) return wfail(SDF_ERR_NOT_SPD, "POD: fewer than r positive singular values");
   std::vector<double> vs((size_t)m * r);
   for (int j = 0; j < r; ++j) {

@@ -52,6 +52,17 @@ PROFILE_NAMES = ("expand", "spmv", "update", "setup", "coarse", "active", "lambd
 PREC_F64, PREC_MIXED = 0, 1
 
 
+class EigOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("degree", ctypes.c_int32), ("guard", ctypes.c_int32),
+                ("max_iter", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+class EigStats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("max_rel_resid", ctypes.c_double), ("matvecs", ctypes.c_int64),
+                ("seconds", ctypes.c_double)]
+
+
 class Profile(ctypes.Structure):
     _fields_ = [("ms", ctypes.c_double * SDF_NPROF), ("samples", ctypes.c_int64 * SDF_NPROF),
                 ("launches", ctypes.c_int64)]
@@ -105,6 +116,9 @@ _sigs = {
     "sdf_warm_fit": (_i32, [_vp, _vp, _vp, _i32, _i32, ctypes.c_float, _vp, _vp, _sz, _vp]),
     "sdf_warm_predict_workspace_size": (_i32, [_vp, _i32, ctypes.POINTER(_sz)]),
     "sdf_warm_predict": (_i32, [_vp, _vp, _i32, _vp, _vp, _sz, _vp]),
+    "sdf_default_eig_opts": (None, [_vp]),
+    "sdf_eig_workspace_size": (_i32, [_vp, _i32, _vp, ctypes.POINTER(_sz)]),
+    "sdf_reference_modes_eig": (_i32, [_vp, _i32, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _sz, _vp]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(_lib, _name)
@@ -199,6 +213,29 @@ class Problem:
         self._check(_lib.sdf_analytic_modes(self._h, k, _ptr(phi), self.N, dtype,
                                             ev.ctypes.data, _stream()))
         return phi, ev
+
+    def eig_modes(self, k, **kw):
+        """k smallest eigenpairs of A (those of S) by Chebyshev-filtered
+        subspace iteration (sdf_reference_modes_eig): returns Phi (k, N)
+        float64 (row j = mode j), lambda_S, lambda_A and the solver stats."""
+        o = EigOpts()
+        _lib.sdf_default_eig_opts(ctypes.byref(o))
+        for key, v in kw.items():
+            setattr(o, key, v)
+        nb = _sz()
+        self._check(_lib.sdf_eig_workspace_size(self._h, k, ctypes.byref(o), ctypes.byref(nb)))
+        ws = torch.empty(int(nb.value), dtype=torch.uint8, device=self.device)
+        phi = torch.empty((k, self.N), dtype=torch.float64, device=self.device)
+        ls, la = np.zeros(k), np.zeros(k)
+        st = EigStats()
+        rc = _lib.sdf_reference_modes_eig(self._h, k, ctypes.byref(o), _ptr(phi), self.N,
+                                          ls.ctypes.data, la.ctypes.data, ctypes.byref(st),
+                                          _ptr(ws), ws.numel(), _stream())
+        if rc not in (0, 5):
+            self._check(rc)
+        stats = dict(iters=st.iters, converged=bool(st.converged), max_rel_resid=st.max_rel_resid,
+                     matvecs=st.matvecs, seconds=st.seconds, status=rc)
+        return phi, ls, la, stats
 
     # workspace --------------------------------------------------------------
     def workspace(self, batch, opts=None, host_io=False):
