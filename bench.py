@@ -253,6 +253,9 @@ def main():
     ap.add_argument("--train", type=int, default=128,
                     help="training instances of the learned warm start (first solves)")
     ap.add_argument("--epochs", type=int, default=2000, help="Adam epochs of the warm-start MLP")
+    ap.add_argument("--eig", default="", help="also time the reference eigensolve (Sec. 2.2.3) "
+                    "of this variable-kappa workload, separately (e.g. block2d_1024)")
+    ap.add_argument("--eig-degree", type=int, default=240)
     args = ap.parse_args()
 
     from paper_2606_17971_b300 import workloads as W
@@ -495,6 +498,21 @@ def main():
                        f"solve truncated at 20 CG iterations (set-up {ts:.2f} s, {ti * 1e3:.1f} ms "
                        f"per iteration); instances/s = 1/(outer*t_setup + iters*t_iter) with this "
                        f"run's mean outer={np.mean(outer):.2f}, iters={np.mean(cg):.0f}")}
+    if args.eig and rank == 0:
+        # the offline eigensolve, timed on its own (not part of the metric)
+        we = W.WORKLOADS[args.eig]
+        Ge = sdf.Problem(we.dim, we.n, alpha=we.alpha, kappa=W.kappa_field(we), yd_sigma=we.sigma,
+                         device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, ls, la, est = Ge.eig_modes(we.k, degree=args.eig_degree, max_iter=2000)
+        torch.cuda.synchronize()
+        line["eigensolve"] = {"workload": we.name, "k": we.k, "N": we.N,
+                              "seconds": time.perf_counter() - t0, "passes": est["iters"],
+                              "converged": est["converged"], "max_rel_resid": est["max_rel_resid"],
+                              "block_matvecs": est["matvecs"],
+                              "method": "Chebyshev-filtered subspace iteration on A, FP64"}
+        del Ge
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
