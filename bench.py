@@ -322,6 +322,9 @@ def main():
                       "note": "first (unconstrained) solves of separate training instances; "
                               "not part of the timed region"}
 
+    # autotuned column depth of the stencil kernels (short capped solves, untimed)
+    tuned_zc = G.autotune(inst_t[0], psi, opts) if mixed else 0
+
     def one_step(inst):
         if model is not None:
             x0 = model.predict(inst)
@@ -459,7 +462,8 @@ def main():
                    "modes": "closed-form sines on the GPU (Sec. 2.2.7)",
                    "l2": "inputs larger than L2: Phi is %.2f GB, read twice per CG iteration"
                          % (w.N * w.k * phi_bytes / 1e9),
-                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+                   "autotuned_column_depth": tuned_zc},
         "cg_iters_per_instance": float(np.mean(cg)), "outer_iters_per_instance": float(np.mean(outer)),
         "statuses": sorted(set(s["status"] for s in stats)),
         "roofline": roof, "clocks": clk.summary(), "e2e": e2e,

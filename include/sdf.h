@@ -214,6 +214,16 @@ sdf_status sdf_solve_batch_x0(sdf_problem *p, const double *inst_dev, int batch,
                               void *ws, size_t ws_bytes, void *stream, double *y_dev,
                               double *lambda_dev, uint8_t *active_dev, sdf_stats *stats_host);
 
+/* Autotuner of the batched mixed 3D path: for this batch size, time a short
+ * capped solve (40 CG iterations) of these instances with each candidate
+ * column depth of the stencil kernels (8, 16, 32, 64 planes per block) and
+ * keep the fastest for later solves of this handle with the same batch size
+ * (*choice receives it; 0 when nothing is tuned for this problem).  Outputs
+ * y_dev / active_dev are scratch here.  No counterpart in the paper. */
+sdf_status sdf_autotune(sdf_problem *p, const double *inst_dev, int batch, const double *psi_dev,
+                        const sdf_opts *opts, void *ws, size_t ws_bytes, void *stream,
+                        double *y_dev, uint8_t *active_dev, int *choice);
+
 /* The same solve with every input and output in HOST memory: the instance
  * array and psi are copied to the device inside the call and y, lambda (if not
  * NULL) and active are copied back; the workspace (device) must be at least

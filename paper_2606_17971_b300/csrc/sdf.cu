@@ -31,6 +31,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <map>
 #include <type_traits>
 #include <cmath>
 #include <cstdio>
@@ -1572,7 +1573,11 @@ __global__ void __launch_bounds__(tc::GTH) k_proj_tc(const __nv_bfloat16 *__rest
   const bool vphi = (ld % 8) == 0, vv = (N % 4) == 0;
   // The next chunk's global loads are issued into registers before this
   // chunk's MMAs are awaited (the instance rows too when NBP <= 64).
+  // only the k real mode rows are staged per chunk; rows k..127 are zeroed once
   constexpr int AIT = GM * (GK / 8) / GTH, BIT = NBP * (GK / 8) / GTH;
+  const int a_items = k * (GK / 8);
+  for (int e = a_items + tid; e < GM * (GK / 8); e += GTH)
+    *reinterpret_cast<uint4 *>(sa + cm_off(e >> 3, (e & 7) * 8)) = make_uint4(0, 0, 0, 0);
   constexpr bool PFB = NBP <= 64;
   uint4 pa[AIT];
   float pb[PFB ? BIT : 1][8];
@@ -1583,7 +1588,7 @@ __global__ void __launch_bounds__(tc::GTH) k_proj_tc(const __nv_bfloat16 *__rest
       const int e = tid + it * GTH, j = e >> 3, kg = (e & 7) * 8;
       const long long g = g0 + kg;
       uint4 val = make_uint4(0, 0, 0, 0);
-      if (j < k && g < N) {
+      if (e < a_items && g < N) {
         const __nv_bfloat16 *src = Phi + (long long)j * ld + g;
         if (vphi && g + 8 <= N) {
           val = *reinterpret_cast<const uint4 *>(src);
@@ -1644,7 +1649,7 @@ __global__ void __launch_bounds__(tc::GTH) k_proj_tc(const __nv_bfloat16 *__rest
 #pragma unroll
     for (int it = 0; it < AIT; ++it) {
       const int e = tid + it * GTH;
-      *reinterpret_cast<uint4 *>(sa + cm_off(e >> 3, (e & 7) * 8)) = pa[it];
+      if (e < a_items) *reinterpret_cast<uint4 *>(sa + cm_off(e >> 3, (e & 7) * 8)) = pa[it];
     }
     if constexpr (PFB) {
 #pragma unroll
@@ -1901,6 +1906,9 @@ struct sdf_problem {
   cudaEvent_t ev[8] = {};
   bool ev_ready = false;
   const double *x0 = nullptr;  // start of every inner solve (set for one call)
+  // autotuned column depth of the 3D mixed kernels, keyed by batch size
+  std::map<int, int> tuned_zc;
+  int force_zc = 0;  // set by sdf_autotune while it times one candidate
 };
 
 namespace {
@@ -1968,17 +1976,27 @@ Layout make_layout(const sdf_problem *p, int B, int max_blocks = 0, int mixed = 
   L.Eraw = take(kk * B);
   L.G = take(kk * B);
   L.coarse = take(kk * B * 5);
-  // 3D column traversal of the mixed path: z-chunks of zc planes
+  // 3D column traversal of the mixed path: z-chunks of zc planes (an
+  // autotuned depth when sdf_autotune has measured this batch size)
   L.zc = B >= 8 ? 32 : (B >= 2 ? 16 : 8);
+  {
+    auto it = p->tuned_zc.find(B);
+    if (it != p->tuned_zc.end()) L.zc = it->second;
+    if (p->force_zc > 0) L.zc = p->force_zc;
+  }
   L.gxc = 1;
+  int gxc_max = 1;  // the partial buffers fit every candidate depth (8 planes)
   if (p->d.dim == 3) {
     long long items = col_items(p->P.nx, p->P.ny, p->P.nz, L.zc);
     // one column item per block: the hardware block scheduler balances the
     // items of all instances across the SMs
     L.gxc = (int)std::max<long long>(1, std::min<long long>(items, 65535));
     if (max_blocks > 0) L.gxc = std::min(L.gxc, max_blocks);
+    gxc_max = (int)std::max<long long>(
+        1, std::min<long long>(col_items(p->P.nx, p->P.ny, p->P.nz, 8), 65535));
+    gxc_max = std::max(gxc_max, L.gxc);
   }
-  int gmax = std::max(std::max(L.gx, L.gxc), std::max(L.gxa, 1));
+  int gmax = std::max(std::max(L.gx, gxc_max), std::max(L.gxa, 1));
   L.part = take(sizeof(double) * (size_t)B * gmax * (KM + 4));
   L.gpart = take(sizeof(double) * (size_t)L.gxg * k * k);
   L.state = take(sizeof(InstState) * (size_t)B);
@@ -2787,6 +2805,53 @@ sdf_status sdf_solve_batch_x0(sdf_problem *p, const double *inst_dev, int batch,
                                   lambda_dev, active_dev, stats_host);
   p->x0 = nullptr;
   return st;
+}
+
+sdf_status sdf_autotune(sdf_problem *p, const double *inst_dev, int batch, const double *psi_dev,
+                        const sdf_opts *opts, void *ws, size_t ws_bytes, void *stream,
+                        double *y_dev, uint8_t *active_dev, int *choice) {
+  if (!p || !opts) return SDF_ERR_INVALID_ARG;
+  sdf_status st = check_solve_args(p, batch, opts, ws, ws_bytes);
+  if (st != SDF_OK) return st;
+  if (!inst_dev || !psi_dev || !y_dev || !active_dev)
+    return fail(p, SDF_ERR_INVALID_ARG, "NULL input or output pointer");
+  int best = 0;
+  if (p->d.dim == 3 && opts->precision == SDF_PREC_MIXED) {
+    cudaStream_t s = (cudaStream_t)stream;
+    sdf_opts o = *opts;
+    o.max_cg = 40;  // a short, capped solve per candidate
+    o.profile = 0;
+    float best_ms = 0.0f;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int zc : {8, 16, 32, 64}) {
+      p->force_zc = zc;
+      for (int rep = 0; rep < 2; ++rep) {  // the first run warms up
+        CK(cudaEventRecord(e0, s));
+        st = sdf_solve_batch(p, inst_dev, batch, psi_dev, &o, ws, ws_bytes, stream, y_dev,
+                             nullptr, active_dev, nullptr);
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        if (st != SDF_OK && st != SDF_ERR_CG_MAXIT) {
+          p->force_zc = 0;
+          return st;
+        }
+      }
+      float ms = 0.0f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (best == 0 || ms < best_ms) {
+        best = zc;
+        best_ms = ms;
+      }
+    }
+    p->force_zc = 0;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->tuned_zc[batch] = best;
+  }
+  if (choice) *choice = best;
+  return SDF_OK;
 }
 
 sdf_status sdf_solve_batch_host(sdf_problem *p, const double *inst_host, int batch,

@@ -198,7 +198,7 @@ __host__ __device__ inline long long num_tiles(int nx, int ny, int nz) {
 // warp takes whole rows and its lanes the x index, so the row's coordinates,
 // global base index and bounds are computed once per row, and shared-memory
 // neighbours are fixed offsets from the row base.
-template <int DIM, class T, bool VARK, class Load, class Store>
+template <int DIM, class T, bool VARK, bool CONV, class Load, class Store>
 __device__ __forceinline__ void tile_S_rows(const OpParams &P, const T cb[3], const T cd[3], T mass,
                                             T wgt, int ox, int oy, int oz, TileSmem<DIM, T> &sm,
                                             Load &load, Store &store) {
@@ -250,13 +250,15 @@ __device__ __forceinline__ void tile_S_rows(const OpParams &P, const T cb[3], co
           zp = uc[DU_Z];
           sacc += fb * (c - zm) + ft * (c - zp);
         }
-        if (cb[0] > (T)0) sacc += cb[0] * (c - um);
-        else if (cb[0] < (T)0) sacc -= cb[0] * (c - up);
-        if (cb[1] > (T)0) sacc += cb[1] * (c - vm);
-        else if (cb[1] < (T)0) sacc -= cb[1] * (c - vp);
-        if (DIM == 3) {
-          if (cb[2] > (T)0) sacc += cb[2] * (c - zm);
-          else if (cb[2] < (T)0) sacc -= cb[2] * (c - zp);
+        if constexpr (CONV) {
+          if (cb[0] > (T)0) sacc += cb[0] * (c - um);
+          else if (cb[0] < (T)0) sacc -= cb[0] * (c - up);
+          if (cb[1] > (T)0) sacc += cb[1] * (c - vm);
+          else if (cb[1] < (T)0) sacc -= cb[1] * (c - vp);
+          if (DIM == 3) {
+            if (cb[2] > (T)0) sacc += cb[2] * (c - zm);
+            else if (cb[2] < (T)0) sacc -= cb[2] * (c - zp);
+          }
         }
         val = sacc;
       }
@@ -299,14 +301,15 @@ __device__ __forceinline__ void tile_S_rows(const OpParams &P, const T cb[3], co
         zp = wc[DW_Z];
         sacc += fb * (c - zm) + ft * (c - zp);
       }
-      // transposed upwind part
-      if (cb[0] > (T)0) sacc += cb[0] * (c - wp);
-      else if (cb[0] < (T)0) sacc -= cb[0] * (c - wm);
-      if (cb[1] > (T)0) sacc += cb[1] * (c - vp);
-      else if (cb[1] < (T)0) sacc -= cb[1] * (c - vm);
-      if (DIM == 3) {
-        if (cb[2] > (T)0) sacc += cb[2] * (c - zp);
-        else if (cb[2] < (T)0) sacc -= cb[2] * (c - zm);
+      if constexpr (CONV) {  // transposed upwind part
+        if (cb[0] > (T)0) sacc += cb[0] * (c - wp);
+        else if (cb[0] < (T)0) sacc -= cb[0] * (c - wm);
+        if (cb[1] > (T)0) sacc += cb[1] * (c - vp);
+        else if (cb[1] < (T)0) sacc -= cb[1] * (c - vm);
+        if (DIM == 3) {
+          if (cb[2] > (T)0) sacc += cb[2] * (c - zp);
+          else if (cb[2] < (T)0) sacc -= cb[2] * (c - zm);
+        }
       }
       store(e, gx, gy, gz, g0 + lx, mass * ubase[lx] + wgt * sacc);
     }
@@ -320,10 +323,19 @@ __device__ void tile_S(const OpParams &P, const double cb64[3], int ox, int oy, 
   const T cb[3] = {(T)cb64[0], (T)cb64[1], (T)cb64[2]};
   const T cd[3] = {OpT<T>::cd(P, 0), OpT<T>::cd(P, 1), OpT<T>::cd(P, 2)};
   const T mass = OpT<T>::mass(P), wgt = OpT<T>::wgt(P);
-  if (P.fx)
-    tile_S_rows<DIM, T, true>(P, cb, cd, mass, wgt, ox, oy, oz, sm, load, store);
-  else
-    tile_S_rows<DIM, T, false>(P, cb, cd, mass, wgt, ox, oy, oz, sm, load, store);
+  // the upwind terms are compiled only for problems with convection (their
+  // per-point compares cost as much as the stencil on the FP64 pipe)
+  if (P.convection) {
+    if (P.fx)
+      tile_S_rows<DIM, T, true, true>(P, cb, cd, mass, wgt, ox, oy, oz, sm, load, store);
+    else
+      tile_S_rows<DIM, T, false, true>(P, cb, cd, mass, wgt, ox, oy, oz, sm, load, store);
+  } else {
+    if (P.fx)
+      tile_S_rows<DIM, T, true, false>(P, cb, cd, mass, wgt, ox, oy, oz, sm, load, store);
+    else
+      tile_S_rows<DIM, T, false, false>(P, cb, cd, mass, wgt, ox, oy, oz, sm, load, store);
+  }
 }
 
 // ---------------------------------------------------------------------------

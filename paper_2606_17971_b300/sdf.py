@@ -116,6 +116,8 @@ _sigs = {
     "sdf_warm_fit": (_i32, [_vp, _vp, _vp, _i32, _i32, ctypes.c_float, _vp, _vp, _sz, _vp]),
     "sdf_warm_predict_workspace_size": (_i32, [_vp, _i32, ctypes.POINTER(_sz)]),
     "sdf_warm_predict": (_i32, [_vp, _vp, _i32, _vp, _vp, _sz, _vp]),
+    "sdf_autotune": (_i32, [_vp, _vp, _i32, _vp, ctypes.POINTER(Opts), _vp, _sz, _vp, _vp, _vp,
+                            ctypes.POINTER(_i32)]),
     "sdf_default_eig_opts": (None, [_vp]),
     "sdf_eig_workspace_size": (_i32, [_vp, _i32, _vp, ctypes.POINTER(_sz)]),
     "sdf_reference_modes_eig": (_i32, [_vp, _i32, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _sz, _vp]),
@@ -273,6 +275,20 @@ class Problem:
         out["status"] = st
         out["stats"] = [stats_dict(s) for s in stats]
         return out
+
+    def autotune(self, inst: torch.Tensor, psi: torch.Tensor, opts=None):
+        """sdf_autotune: pick the column depth of the mixed 3D kernels for
+        this batch size by timing short solves; returns the choice (0: none)."""
+        opts = opts or default_opts()
+        B = inst.shape[0]
+        ws = self.workspace(B, opts)
+        y = torch.empty((B, self.N), dtype=torch.float64, device=self.device)
+        a = torch.empty((B, self.N), dtype=torch.uint8, device=self.device)
+        ch = ctypes.c_int(0)
+        self._check(_lib.sdf_autotune(self._h, _ptr(inst), B, _ptr(psi), ctypes.byref(opts),
+                                      _ptr(ws), ws.numel(), _stream(), _ptr(y), _ptr(a),
+                                      ctypes.byref(ch)))
+        return ch.value
 
     def solve_x0(self, inst: torch.Tensor, psi: torch.Tensor, x0: torch.Tensor, opts=None,
                  want_lambda=False, out=None):

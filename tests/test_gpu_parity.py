@@ -374,3 +374,22 @@ def test_mixed_3d_bf16_batch_of_37_on_an_odd_grid():
     G3.set_modes(modes_tensor_as(Phi3, torch.bfloat16))
     out3 = G3.solve(t64(W.instances_array(i3)), t64(psi), sdf.default_opts(precision=sdf.PREC_MIXED))
     compare_mixed(out3, orc3)
+
+
+def test_autotuned_column_depth_keeps_the_solution():
+    n3 = (24, 20, 36)
+    w3 = W.scaled(W.WORKLOADS["diff3d_128"], 20, instances=6)
+    insts = W.draw_instances(w3, count=6)
+    G = sdf.Problem(3, n3, alpha=1e-4, yd_sigma=w3.sigma)
+    phi, _ = G.analytic_modes(12, sdf.BF16)
+    G.set_modes(phi)
+    psi = t64(np.ones(G.N))
+    inst = t64(W.instances_array(insts))
+    o = sdf.default_opts(precision=sdf.PREC_MIXED)
+    before = G.solve(inst, psi, o, want_lambda=False)
+    zc = G.autotune(inst, psi, o)
+    assert zc in (8, 16, 32, 64)
+    after = G.solve(inst, psi, o, want_lambda=False)
+    assert torch.equal(before["active"], after["active"])
+    assert (before["y"] - after["y"]).abs().max().item() <= 1e-7 * before["y"].abs().max().item()
+    assert all(s["status"] == 0 for s in after["stats"])
