@@ -244,7 +244,7 @@ def main():
                     help="plain: FP64 A-DEF2 per instance; mixed: FP32/BF16 with FP64 refinement")
     ap.add_argument("--phi", default="bf16", choices=["f32", "bf16"], help="mode storage (mixed)")
     ap.add_argument("--batch", type=int, default=0,
-                    help="instances per step and GPU (default: 32 mixed, 1 plain)")
+                    help="instances per step and GPU (default: 64 mixed, 1 plain)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-path comparison")
@@ -280,7 +280,7 @@ def main():
     mixed = args.path == "mixed"
     phi_dt = (sdf.BF16 if args.phi == "bf16" else sdf.F32) if mixed else sdf.F64
     G, phi = make_problem(w, sdf, dev, phi_dt)
-    B = args.batch or (32 if mixed else 1)
+    B = args.batch or (64 if mixed else 1)
     steps, warm = args.steps, args.warmup
     insts = W.draw_instances(w, count=(steps + warm) * B * world)
     mine = insts[rank::world]

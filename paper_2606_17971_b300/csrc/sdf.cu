@@ -1307,29 +1307,36 @@ __device__ __forceinline__ void sigma_epilogue(InstState &S, int b, double sg, d
 
 // Column-stencil sources and outputs of the two mixed-path kernels.
 struct ColSrcP {  // u = p
+  static constexpr bool AUX = false;
   const float *p;
   using Raw = float;
-  __device__ __forceinline__ Raw fetch(long long g) const { return p[g]; }
+  __device__ __forceinline__ Raw fetch(int g) const { return p[g]; }
   __device__ __forceinline__ float value(Raw r) const { return r; }
+  __device__ __forceinline__ float aux(Raw) const { return 0.0f; }
 };
 struct ColOutQ {  // q = S_II p (zero on the active set), sigma = (p, q)
   const uint8_t *mk;
   float *q;
   KahanF sg;
   struct Pre { uint8_t m; };
-  __device__ __forceinline__ Pre fetch(long long g) const { return Pre{mk[g]}; }
-  __device__ __forceinline__ void store(long long g, float su, float uc, const Pre &pr) {
+  __device__ __forceinline__ Pre fetch(int g) const { return Pre{mk[g]}; }
+  __device__ __forceinline__ void store(int g, float su, float uc, float, const Pre &pr) {
     const float qv = pr.m ? 0.0f : su;
     q[g] = qv;
     sg.add(uc * qv);
   }
 };
-struct ColSrcZ {  // u = z = D^-1 (r - alpha q); r and q vanish on the active set
+// u = z = D^-1 (r - alpha q) (r and q vanish on the active set).  (Carrying
+// r - alpha q in a second shared ring for the output nodes instead of
+// reloading r and q there measured slower on this part.)
+struct ColSrcZ {
+  static constexpr bool AUX = false;
   const float *r, *q, *dinv;
   float alpha;
   struct Raw { float r, q, d; };
-  __device__ __forceinline__ Raw fetch(long long g) const { return Raw{r[g], q[g], dinv[g]}; }
-  __device__ __forceinline__ float value(const Raw &a) const { return a.d * (a.r - alpha * a.q); }
+  __device__ __forceinline__ Raw fetch(int g) const { return Raw{r[g], q[g], dinv[g]}; }
+  __device__ __forceinline__ float aux(const Raw &a) const { return a.r - alpha * a.q; }
+  __device__ __forceinline__ float value(const Raw &a) const { return a.d * aux(a); }
 };
 // FOLD: correction pass, which folds x_lo into the FP64 iterate.  A separate
 // instantiation keeps the FP64 arithmetic (1/64 of the FP32 rate on this part)
@@ -1343,8 +1350,8 @@ template <bool FOLD> struct ColOutUpd {  // r, x, v = S z - r and the CG dot pro
   double alpha64;
   KahanF rho, rr;
   struct Pre { float r, q, p, xl; uint8_t m; };
-  __device__ __forceinline__ Pre fetch(long long g) const { return Pre{r[g], q[g], p[g], xl[g], mk[g]}; }
-  __device__ __forceinline__ void store(long long g, float su, float z, const Pre &a) {
+  __device__ __forceinline__ Pre fetch(int g) const { return Pre{r[g], q[g], p[g], xl[g], mk[g]}; }
+  __device__ __forceinline__ void store(int g, float su, float z, float, const Pre &a) {
     if (a.m) {
       rw[g] = 0.0f;
       v[g] = 0.0f;
@@ -2772,6 +2779,8 @@ static sdf_status check_solve_args(sdf_problem *p, int batch, const sdf_opts *op
                 "the mixed path is not validated for convection (FP32 attainable accuracy above "
                 "rtol stalls its refinement loop); use SDF_PREC_F64");
   if (opts->replace_every < 0) return fail(p, SDF_ERR_INVALID_ARG, "replace_every < 0");
+  if (opts->precision == SDF_PREC_MIXED && p->P.N > 2147483647LL)
+    return fail(p, SDF_ERR_UNSUPPORTED, "the mixed path indexes one instance with 32 bits");
   size_t need = make_layout(p, batch, opts->max_blocks, opts->precision == SDF_PREC_MIXED).total;
   if (ws_bytes < need) return fail(p, SDF_ERR_WORKSPACE, "workspace too small");
   return SDF_OK;

@@ -353,23 +353,30 @@ constexpr int CNU = CUX * CUY, CNW = CWX * CWY, CNO = CX * CY;
 constexpr int CSU = (CNU + NT - 1) / NT, CSW = (CNW + NT - 1) / NT, CSO = CNO / NT;
 static_assert(CNO % NT == 0, "whole output slots per thread");
 
-template <class T> struct ColSmem {
+// NA = 1: a second ring of five planes carries an auxiliary value of each u
+// node (Src::AUX), read back at the output nodes; NA = 0 reserves nothing.
+template <class T, int NA = 0> struct ColSmem {
   T u[5][CNU];
   T w[3][CNW];
+  T a[NA ? 5 : 1][NA ? CNU : 1];
 };
 
-// Src: `Raw fetch(g)` issues the global loads of u at grid node g and
-// `T value(const Raw &)` turns them into u.  Out: `Pre fetch(g)` loads the
-// per-node operands of the output at g, `store(g, Su, u_g, pre)` receives S u.
-// CONV = false drops the upwind terms (all convection coefficients zero).
-template <class T, bool VARK, bool CONV, class Src, class Out>
+// Src: `Raw fetch(g)` issues the global loads of u at grid node g (index
+// within the instance, 32-bit) and `T value(const Raw &)` turns them into u;
+// with Src::AUX, `T aux(const Raw &)` is kept beside u.  Out: `Pre fetch(g)`
+// loads the per-node operands of the output at g, and `store(g, Su, u_g,
+// aux_g, pre)` receives S u.  CONV = false drops the upwind terms.
+template <class T, bool VARK, bool CONV, class Src, class Out, int NA>
 __device__ __forceinline__ void col_S3_impl(const OpParams &P, const T cb[3], const T cd[3], T mass,
                                             T wgt, int x0, int y0, int z0, int z1,
-                                            ColSmem<T> &sm, const Src &src, Out &out) {
+                                            ColSmem<T, NA> &sm, const Src &src, Out &out) {
   using Raw = typename Src::Raw;
   using Pre = typename Out::Pre;
+  constexpr bool AUX = Src::AUX;
+  static_assert(!AUX || NA == 1, "auxiliary ring");
   const int nx = P.nx, ny = P.ny, nz = P.nz;
-  const long long nxy = (long long)nx * ny, base = (long long)y0 * nx + x0;
+  // node indices within one instance fit in 32 bits (checked by the host)
+  const int nxy = nx * ny, base = y0 * nx + x0;
   // u slots: shared index (-1: idle), in-grid flag, xy offset from the tile origin
   int ue[CSU], uoff[CSU];
   bool uok[CSU];
@@ -407,7 +414,7 @@ __device__ __forceinline__ void col_S3_impl(const OpParams &P, const T cb[3], co
 
   auto fetch = [&](int z, Raw (&raw)[CSU]) {
     const bool zin = z >= 0 && z < nz;
-    const long long zb = (long long)z * nxy + base;
+    const int zb = z * nxy + base;
 #pragma unroll
     for (int q = 0; q < CSU; ++q) raw[q] = (zin && uok[q]) ? src.fetch(zb + uoff[q]) : Raw{};
   };
@@ -416,10 +423,14 @@ __device__ __forceinline__ void col_S3_impl(const OpParams &P, const T cb[3], co
     T *up = sm.u[slot];
 #pragma unroll
     for (int q = 0; q < CSU; ++q)
-      if (ue[q] >= 0) up[ue[q]] = (zin && uok[q]) ? src.value(raw[q]) : (T)0;
+      if (ue[q] >= 0) {
+        const bool on = zin && uok[q];
+        up[ue[q]] = on ? src.value(raw[q]) : (T)0;
+        if constexpr (AUX) sm.a[slot][ue[q]] = on ? src.aux(raw[q]) : (T)0;
+      }
   };
   auto prefetch = [&](int z, Pre (&pr)[CSO]) {
-    const long long zb = (long long)z * nxy + base;
+    const int zb = z * nxy + base;
 #pragma unroll
     for (int q = 0; q < CSO; ++q) pr[q] = ook[q] ? out.fetch(zb + ooff[q]) : Pre{};
   };
@@ -464,7 +475,7 @@ __device__ __forceinline__ void col_S3_impl(const OpParams &P, const T cb[3], co
   // S u = mass u + wgt A^T w at plane z
   auto outputs = [&](int z, int wsm, int ws0, int wsp, int us0, const Pre (&pr)[CSO]) {
     const T *wm = sm.w[wsm], *wc = sm.w[ws0], *wpl = sm.w[wsp], *uc = sm.u[us0];
-    const long long zb = (long long)z * nxy + base;
+    const int zb = z * nxy + base;
 #pragma unroll
     for (int q = 0; q < CSO; ++q) {
       if (!ook[q]) continue;
@@ -493,7 +504,9 @@ __device__ __forceinline__ void col_S3_impl(const OpParams &P, const T cb[3], co
         else if (cb[2] < (T)0) acc -= cb[2] * (c - zm);
       }
       const T u0 = uc[ouc[q]];
-      out.store(zb + ooff[q], mass * u0 + wgt * acc, u0, pr[q]);
+      T ax = (T)0;
+      if constexpr (AUX) ax = sm.a[us0][ouc[q]];
+      out.store(zb + ooff[q], mass * u0 + wgt * acc, u0, ax, pr[q]);
     }
   };
 
@@ -539,9 +552,10 @@ __device__ __forceinline__ void col_S3_impl(const OpParams &P, const T cb[3], co
 
 // Entry of the column stencil for kernels compiled per coefficient kind
 // (VARK: face coefficients from kappa; CONV: upwind convection present).
-template <class T, bool VARK, bool CONV, class Src, class Out>
+template <class T, bool VARK, bool CONV, class Src, class Out, int NA>
 __device__ __forceinline__ void col_S3(const OpParams &P, const double cb64[3], int x0, int y0,
-                                       int z0, int z1, ColSmem<T> &sm, const Src &src, Out &out) {
+                                       int z0, int z1, ColSmem<T, NA> &sm, const Src &src,
+                                       Out &out) {
   const T cb[3] = {(T)cb64[0], (T)cb64[1], (T)cb64[2]};
   const T cd[3] = {OpT<T>::cd(P, 0), OpT<T>::cd(P, 1), OpT<T>::cd(P, 2)};
   col_S3_impl<T, VARK, CONV>(P, cb, cd, OpT<T>::mass(P), OpT<T>::wgt(P), x0, y0, z0, z1, sm, src,
