@@ -166,7 +166,7 @@ def make_problem(w, sdf, device, phi_dtype=0):
     kap = W.kappa_field(w)
     G = sdf.Problem(w.dim, w.n, alpha=w.alpha, kappa=kap, diff_scale=w.diff_scale,
                     convection=w.convection, yd_sigma=w.sigma, device=device)
-    phi, _ = G.analytic_modes(w.k, phi_dtype)  # closed-form reference modes on the GPU (Sec. 2.2.7)
+    phi, _ = G.analytic_modes(w.k, phi_dtype)  # closed-form reference modes on the GPU (Sec. 2.2.8)
     G.set_modes(phi)
     return G, phi
 
@@ -253,7 +253,7 @@ def main():
     ap.add_argument("--train", type=int, default=128,
                     help="training instances of the learned warm start (first solves)")
     ap.add_argument("--epochs", type=int, default=2000, help="Adam epochs of the warm-start MLP")
-    ap.add_argument("--eig", default="", help="also time the reference eigensolve (Sec. 2.2.3) "
+    ap.add_argument("--eig", default="", help="also time the reference eigensolve (Sec. 2.2.2) "
                     "of this variable-kappa workload, separately (e.g. block2d_1024)")
     ap.add_argument("--eig-degree", type=int, default=240)
     args = ap.parse_args()
@@ -459,7 +459,7 @@ def main():
                             % args.phi if mixed else "plain FP64 A-DEF2 per instance")
                            + (", learned warm start" if learned else "")
                            + " (primal active-set loop)",
-                   "modes": "closed-form sines on the GPU (Sec. 2.2.7)",
+                   "modes": "closed-form sines on the GPU (Sec. 2.2.8)",
                    "l2": "inputs larger than L2: Phi is %.2f GB, read twice per CG iteration"
                          % (w.N * w.k * phi_bytes / 1e9),
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",

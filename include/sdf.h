@@ -172,7 +172,7 @@ sdf_status sdf_set_reference_modes(sdf_problem *p, const void *phi_dev, int k, i
                                    sdf_dtype dtype);
 
 /* Closed-form reference modes for a constant-coefficient diffusion reference
- * S_ref = mass I + w (diff_scale L_h)^2 (Sec. 2.2.7): the k smallest Kronecker
+ * S_ref = mass I + w (diff_scale L_h)^2 (Sec. 2.2.8): the k smallest Kronecker
  * sine modes, ties broken lexicographically by (i_d, ..., i_1).  Writes
  * phi_dev (N x k column-major, ld, dtype) on the device and, if eigvals_host
  * is not NULL, the k eigenvalues of S_ref to host memory.  Does not register
@@ -303,7 +303,7 @@ const char *sdf_last_error(const sdf_problem *p);
 /* Release the host handle (device buffers stay the caller's). */
 void sdf_problem_destroy(sdf_problem *p);
 
-/* Reference eigensolve (Sec. 2.2.3, where the paper uses ARPACK): the k
+/* Reference eigensolve (Sec. 2.2.2, where the paper uses ARPACK): the k
  * smallest eigenpairs of A (no convection: A symmetric), which are those of
  * S with lambda_S = mass + wgt lambda_A^2, by Chebyshev-filtered subspace
  * iteration (Zhou & Saad's scaled filter on [a, b], a = the largest Ritz
@@ -345,7 +345,7 @@ sdf_status sdf_reference_modes_eig(sdf_problem *p, int k, const sdf_eig_opts *o,
  * Learned warm start (no counterpart in the paper, which lists learned
  * initialisations only as related work).  A multilayer perceptron maps the
  * instance parameters to the coefficients of a POD basis of solved states
- * (the paper's POD, Sec. 2.2.5, mean-centred); the expansion
+ * (the paper's POD, Sec. 2.2.4, mean-centred); the expansion
  * x0 = ybar + Psi c is the start of every inner solve (sdf_solve_batch_x0).
  * The MLP's products run on the tensor cores (tcgen05.mma, BF16 operands,
  * FP32 accumulation in tensor memory); everything else is FP32 (MLP) or FP64

@@ -27,7 +27,7 @@ def main(count=2, name="diff3d_128"):
     rng = np.random.default_rng(12345)
     sample = np.sort(rng.choice(w.N, size=64, replace=False))
     out_path = os.path.join(ROOT, "tests", "golden", f"{name}_oracle.json")
-    res = {"workload": name, "rtol": 1e-8, "k": w.k, "modes": "closed-form sines (Sec. 2.2.7)",
+    res = {"workload": name, "rtol": 1e-8, "k": w.k, "modes": "closed-form sines (Sec. 2.2.8)",
            "sample_index": sample.tolist(), "instances": []}
     for i, ins in enumerate(W.draw_instances(w, count=count)):
         _, rhs = P.desired_state(ins.a, ins.c[: w.dim], w.sigma)

@@ -14,7 +14,7 @@ What lives here:
     Jacobi-PCG (App. B.2) and A-DEF2 (Sec. 2.2.1 Algorithm adef2 in the cited
     standard form).
   * ``analytic_modes``: closed-form Kronecker sine eigenmodes of
-    alpha L^2 + I on a tensor grid (Sec. 2.2.7).
+    alpha L^2 + I on a tensor grid (Sec. 2.2.8).
   * ``dense_modes``: the k smallest eigenpairs of a (small) S by a dense
     symmetric eigensolver (Sec. 2.2.2 Eq. eig, with LAPACK in place of ARPACK).
 """
@@ -256,7 +256,7 @@ class Problem:
 
 def analytic_modes(dim, n, k, alpha=1e-4, diff_scale=1.0):
     """The k smallest eigenpairs of S_ref = alpha (diff_scale L_h)^2 + I on an
-    n^dim interior grid (Sec. 2.2.7, with the node index in place of x_l):
+    n^dim interior grid (Sec. 2.2.8, with the node index in place of x_l):
 
         phi_{i_1..i_d}(j_1..j_d) = prod_l sqrt(2/(n+1)) sin(i_l pi j_l / (n+1)),
         lambda = alpha (diff_scale sum_l mu_{i_l})^2 + 1,

@@ -8,13 +8,14 @@ The paper has no learned component (its introduction lists learned
 initialisations as related work only); the warm start is the target
 configuration's fourth part, read as follows:
 
-* POD of solved states (the paper's own POD, Sec. 2.2.5 "Online POD
+* POD of solved states (the paper's own POD, Sec. 2.2.4 "Online POD
   enrichment", mean-centred): y_i = ybar + Psi c_i, Psi the leading left
   singular vectors of the centred snapshot matrix.
 * MLP mu -> c with widths 4-256-256-256-64, exact GELU
   g(z) = z/2 (1 + erf(z / sqrt 2)) between layers, identity after the last.
-  Inputs min-max scaled to [-1, 1] over the parameter box, targets
-  standardised per coefficient.
+  Inputs min-max scaled to [-1, 1] over the parameter box; the targets (the
+  fit's business, not this module's) are the coefficients centred per
+  coefficient and divided by one common scale.
 * Loss: mean squared error over the batch and the coefficients.  Adam with
   bias correction (Kingma & Ba), learning rate given per step.
 * Precision: the kernels multiply BF16 operands (weights, layer inputs and

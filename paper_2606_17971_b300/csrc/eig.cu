@@ -4,8 +4,8 @@
 // lambda_A^2 (Sec. 2.1.2 Eq. schur), by Chebyshev-filtered subspace iteration
 // (Zhou & Saad, 2007: a scaled Chebyshev filter that damps the unwanted
 // interval [a, b] of the spectrum, Rayleigh-Ritz on the filtered block).
-// The paper computes its reference modes with ARPACK (Sec. 2.2.3) or in
-// closed form on tensor-product grids (Sec. 2.2.7); this replaces the former.
+// The paper computes its reference modes with ARPACK (Sec. 2.2.2) or in
+// closed form on tensor-product grids (Sec. 2.2.8); this replaces the former.
 //
 // Every vector operation is FP64 on the GPU; the m x m Rayleigh-Ritz and
 // Cholesky factorisations run on the host (m = k + guard <= 320).

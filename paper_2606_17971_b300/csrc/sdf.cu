@@ -1865,7 +1865,7 @@ __global__ void __launch_bounds__(NT) k_apply(OpParams P, const double *inst,
   }
 }
 
-// Kronecker sine modes (Sec. 2.2.7): Phi_c(j) = prod_l sqrt(2/(n_l+1)) sin(i_l pi j_l/(n_l+1)).
+// Kronecker sine modes (Sec. 2.2.8): Phi_c(j) = prod_l sqrt(2/(n_l+1)) sin(i_l pi j_l/(n_l+1)).
 struct ModeIdx {
   int v[3 * SDF_MAX_K];
 };

@@ -4,7 +4,7 @@
 // states, and the expansion x0 = ybar + Psi c that seeds the inner solves.
 //
 // The paper has no learned component; the method follows the reading stated
-// in the header (include/sdf.h): POD as in Sec. 2.2.5 (mean-centred), an MLP
+// in the header (include/sdf.h): POD as in Sec. 2.2.4 (mean-centred), an MLP
 // with exact GELU, MSE on standardised coefficients, Adam with bias
 // correction.
 #include <cuda_runtime.h>

@@ -26,7 +26,7 @@ def lap1d(n):
 
 
 def laplacian_kron(dim, n):
-    """L_h as a Kronecker sum of 1D second differences (App. A, Sec. 2.2.7)."""
+    """L_h as a Kronecker sum of 1D second differences (App. A, Sec. 2.2.8)."""
     L1, I = lap1d(n), np.eye(n)
     if dim == 2:
         return np.kron(I, L1) + np.kron(L1, I)
