@@ -256,6 +256,8 @@ def main():
     ap.add_argument("--eig", default="", help="also time the reference eigensolve (Sec. 2.2.2) "
                     "of this variable-kappa workload, separately (e.g. block2d_1024)")
     ap.add_argument("--eig-degree", type=int, default=240)
+    ap.add_argument("--eig-coarse", type=int, default=2,
+                    help="also time the coarse-grid basis (Sec. 2.2.7) with this factor (0: off)")
     args = ap.parse_args()
 
     from paper_2606_17971_b300 import workloads as W
@@ -516,6 +518,16 @@ def main():
                               "converged": est["converged"], "max_rel_resid": est["max_rel_resid"],
                               "block_matvecs": est["matvecs"],
                               "method": "Chebyshev-filtered subspace iteration on A, FP64"}
+        if args.eig_coarse >= 2:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            phc, _, cst = Ge.coarse_modes(args.eig_coarse, we.k, degree=args.eig_degree,
+                                          max_iter=2000)
+            torch.cuda.synchronize()
+            line["eigensolve"]["coarse_grid"] = {
+                "factor": args.eig_coarse, "seconds": time.perf_counter() - t0,
+                "columns_kept": int(phc.shape[0]), "coarse_passes": cst["iters"],
+                "method": "eigenpairs on the grid coarsened by the factor, linear prolongation, QR"}
         del Ge
     if rank == 0:
         print(json.dumps(line))

@@ -341,6 +341,24 @@ sdf_status sdf_reference_modes_eig(sdf_problem *p, int k, const sdf_eig_opts *o,
                                    int64_t ld, double *lambda_S_host, double *lambda_A_host,
                                    sdf_eig_stats *stats, void *ws, size_t ws_bytes, void *stream);
 
+/* Coarse-grid reference basis (Sec. 2.2.7, Algorithm coarse): the r_pool
+ * smallest eigenpairs of the same problem on a grid of n_d / c interior nodes
+ * per direction (kappa injected at the fine node nearest to each coarse node;
+ * sdf_reference_modes_eig with the options o), prolongated to the fine grid by
+ * (bi/tri)linear interpolation with zero boundary values (Eq. prolong), then
+ * orthonormalised by a QR that discards every column whose R_jj is below
+ * tau_sv times the largest column norm.  phi_dev receives *r_out <= r_pool
+ * orthonormal columns (N doubles, leading dimension ld, device);
+ * lambda_c_host (r_pool, may be NULL) the coarse eigenvalues of S_c; stats
+ * those of the coarse eigensolve.  c >= 2; SDF_ERR_UNSUPPORTED with
+ * convection. */
+sdf_status sdf_coarse_modes_workspace_size(const sdf_problem *p, int c, int r_pool,
+                                           const sdf_eig_opts *o, size_t *bytes);
+sdf_status sdf_reference_modes_coarse(sdf_problem *p, int c, int r_pool, const sdf_eig_opts *o,
+                                      double tau_sv, double *phi_dev, int64_t ld, int *r_out,
+                                      double *lambda_c_host, sdf_eig_stats *stats, void *ws,
+                                      size_t ws_bytes, void *stream);
+
 /* ==========================================================================
  * Learned warm start (no counterpart in the paper, which lists learned
  * initialisations only as related work).  A multilayer perceptron maps the

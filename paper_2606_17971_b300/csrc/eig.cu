@@ -25,6 +25,7 @@
 // defined in sdf.cu: the operator parameters of a bound problem
 const sdf::OpParams *sdf_internal_op(const sdf_problem *p, int *nsm, int *convection);
 void sdf_internal_set_error(sdf_problem *p, const char *msg);
+const sdf_problem_desc *sdf_internal_desc(const sdf_problem *p, const double **kappa_host);
 
 namespace {
 
@@ -208,9 +209,92 @@ __global__ void k_resid_norms(const double *AX, const double *X, const double *t
   if (threadIdx.x == 0) part[(long long)j * nchunk + blockIdx.x] = red[0];
 }
 
-struct EigWs {
-  double *X, *Y, *Z, *AX, *part, *small, *theta;
+// Prolongation of r coarse vectors (column-major, Nc rows) to the fine grid:
+// each fine node takes the (bi/tri)linear interpolant of the coarse values,
+// the coarse node j of a direction sitting at (j + 1) / (nc + 1) and the
+// boundary values being zero (Sec. 2.2.7 Eq. prolong).
+__global__ void k_prolong(int dim, int nx, int ny, int nz, int cx, int cy, int cz,
+                          const double *Xc, int r, double *Xf) {
+  const long long N = (long long)nx * ny * nz, Nc = (long long)cx * cy * cz;
+  const int j = blockIdx.y;
+  for (long long g = blockIdx.x * (long long)ET + threadIdx.x; g < N;
+       g += (long long)gridDim.x * ET) {
+    const int i = (int)(g % nx);
+    const long long t = g / nx;
+    const int jj = (int)(t % ny), l = (int)(t / ny);
+    int c0[3];
+    double w1[3];
+    const int fi[3] = {i, jj, l}, fn[3] = {nx, ny, nz}, cn[3] = {cx, cy, cz};
+    for (int d = 0; d < 3; ++d) {
+      if (d < dim) {
+        const double tc = (double)(fi[d] + 1) / (double)(fn[d] + 1) * (double)(cn[d] + 1) - 1.0;
+        c0[d] = (int)floor(tc);
+        w1[d] = tc - c0[d];
+      } else {
+        c0[d] = 0;
+        w1[d] = 0.0;
+      }
+    }
+    double acc = 0.0;
+    for (int corner = 0; corner < (1 << dim); ++corner) {
+      double wt = 1.0;
+      long long idx = 0, stride = 1;
+      bool in = true;
+      for (int d = 0; d < dim; ++d) {
+        const int a = (corner >> d) & 1;
+        const int cidx = c0[d] + a;
+        wt *= a ? w1[d] : 1.0 - w1[d];
+        in = in && cidx >= 0 && cidx < cn[d];
+        idx += (long long)cidx * stride;
+        stride *= cn[d];
+      }
+      if (in && wt != 0.0) acc = fma(wt, Xc[(long long)j * Nc + idx], acc);
+    }
+    Xf[(long long)j * N + g] = acc;
+  }
+}
+
+// Block operations on column-major N x m blocks: Gram matrices X^T Y (FP64
+// partials per node chunk, summed in chunk order) and rotations X W by a
+// small host matrix (in column chunks that fit in shared memory).
+struct BlockOps {
+  sdf_problem *p;
+  cudaStream_t s;
+  long long N;
   int nchunk;
+  double *part;   // nchunk * m * m doubles
+  double *small;  // 2 * m * m doubles
+  int mmax;
+
+  sdf_status gram(const double *Xa, const double *Ya, int m, std::vector<double> &C) {
+    const int tiles = (m + GT - 1) / GT;
+    k_gram2<<<dim3(nchunk, tiles, tiles), 256, 0, s>>>(Xa, Ya, N, m, nchunk, part);
+    k_gram2_reduce<<<64, 256, 0, s>>>(part, nchunk, m, small);
+    ECK(cudaGetLastError());
+    C.resize((size_t)m * m);
+    ECK(cudaMemcpyAsync(C.data(), small, sizeof(double) * m * m, cudaMemcpyDeviceToHost, s));
+    ECK(cudaStreamSynchronize(s));
+    return SDF_OK;
+  }
+  sdf_status rotate(const double *Xa, const std::vector<double> &W, int m, int mo, double *Yo) {
+    const int mc = std::max(8, std::min(mo, (int)((160 * 1024) / (sizeof(double) * m)) / 8 * 8));
+    ECK(cudaFuncSetAttribute(k_rotate, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(double) * (size_t)m * mc)));
+    for (int j0 = 0; j0 < mo; j0 += mc) {
+      const int w = std::min(mc, mo - j0);
+      std::vector<double> Wc((size_t)m * w);
+      for (int i = 0; i < m; ++i)
+        for (int j = 0; j < w; ++j) Wc[(size_t)i * w + j] = W[(size_t)i * mo + j0 + j];
+      double *wd = small + (size_t)mmax * mmax;
+      ECK(cudaMemcpyAsync(wd, Wc.data(), sizeof(double) * m * w, cudaMemcpyHostToDevice, s));
+      k_rotate<<<(unsigned)((N + 127) / 128), 128, sizeof(double) * (size_t)m * w, s>>>(
+          Xa, wd, N, m, w, Yo + (size_t)j0 * N);
+      ECK(cudaGetLastError());
+      // the host block is reused by the next chunk: wait for this copy
+      ECK(cudaStreamSynchronize(s));
+    }
+    return SDF_OK;
+  }
 };
 
 }  // namespace
@@ -289,8 +373,6 @@ sdf_status sdf_reference_modes_eig(sdf_problem *p, int k, const sdf_eig_opts *o,
   double *part = (double *)take(sizeof(double) * (size_t)nchunk * m * m);
   double *small = (double *)take(sizeof(double) * (size_t)m * m * 2);
   double *theta_d = (double *)take(sizeof(double) * (size_t)m);
-  const int tiles = (m + GT - 1) / GT;
-  const dim3 gblk((unsigned)std::min<long long>((N + ET - 1) / ET, nsm * 4LL), m);
   int64_t matvecs = 0;
 
   auto apply = [&](const double *Xp, const double *Xc, double *Xn, int cols, double a, double b,
@@ -301,36 +383,12 @@ sdf_status sdf_reference_modes_eig(sdf_problem *p, int k, const sdf_eig_opts *o,
     matvecs += cols;
     return SDF_OK;
   };
-  // C (m x m, host) = X^T Y
-  auto gram = [&](const double *Xa, const double *Ya, std::vector<double> &C) -> sdf_status {
-    k_gram2<<<dim3(nchunk, tiles, tiles), 256, 0, s>>>(Xa, Ya, N, m, nchunk, part);
-    k_gram2_reduce<<<64, 256, 0, s>>>(part, nchunk, m, small);
-    ECK(cudaGetLastError());
-    C.resize((size_t)m * m);
-    ECK(cudaMemcpyAsync(C.data(), small, sizeof(double) * m * m, cudaMemcpyDeviceToHost, s));
-    ECK(cudaStreamSynchronize(s));
-    return SDF_OK;
+  BlockOps ops{p, s, N, nchunk, part, small, m};
+  auto gram = [&](const double *Xa, const double *Ya, std::vector<double> &C) {
+    return ops.gram(Xa, Ya, m, C);
   };
-  // Yo = Xa W (W m x mo row-major, host), in column chunks whose m x mc
-  // block of W fits in shared memory
-  const int mc = std::max(8, std::min(m, (int)((160 * 1024) / (sizeof(double) * m)) / 8 * 8));
-  ECK(cudaFuncSetAttribute(k_rotate, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(sizeof(double) * (size_t)m * mc)));
-  auto rotate = [&](const double *Xa, const std::vector<double> &W, int mo, double *Yo) -> sdf_status {
-    for (int j0 = 0; j0 < mo; j0 += mc) {
-      const int w = std::min(mc, mo - j0);
-      std::vector<double> Wc((size_t)m * w);
-      for (int i = 0; i < m; ++i)
-        for (int j = 0; j < w; ++j) Wc[(size_t)i * w + j] = W[(size_t)i * mo + j0 + j];
-      double *wd = small + (size_t)m * m;
-      ECK(cudaMemcpyAsync(wd, Wc.data(), sizeof(double) * m * w, cudaMemcpyHostToDevice, s));
-      k_rotate<<<(unsigned)((N + 127) / 128), 128, sizeof(double) * (size_t)m * w, s>>>(
-          Xa, wd, N, m, w, Yo + (size_t)j0 * N);
-      ECK(cudaGetLastError());
-      // the host block is reused by the next chunk: wait for this copy
-      ECK(cudaStreamSynchronize(s));
-    }
-    return SDF_OK;
+  auto rotate = [&](const double *Xa, const std::vector<double> &W, int mo, double *Yo) {
+    return ops.rotate(Xa, W, m, mo, Yo);
   };
   // orthonormalise the columns of *A in place: shifted Cholesky-QR, then
   // Cholesky-QR twice (Fukaya et al., "shifted CholeskyQR3"); the shift
@@ -475,6 +533,184 @@ sdf_status sdf_reference_modes_eig(sdf_problem *p, int k, const sdf_eig_opts *o,
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
   }
   return converged ? SDF_OK : efail(p, SDF_ERR_CG_MAXIT, "eig: not converged within max_iter");
+}
+
+static void coarse_sizes(const sdf_problem_desc *d, int c, int nc[3], long long *Nc) {
+  for (int i = 0; i < 3; ++i) nc[i] = i < d->dim ? d->n[i] / c : 1;
+  *Nc = (long long)nc[0] * nc[1] * nc[2];
+}
+
+sdf_status sdf_coarse_modes_workspace_size(const sdf_problem *p, int c, int r_pool,
+                                           const sdf_eig_opts *o, size_t *bytes) {
+  if (!p || !o || !bytes || c < 2 || r_pool < 1 || r_pool > SDF_MAX_K) return SDF_ERR_INVALID_ARG;
+  const sdf_problem_desc *d = sdf_internal_desc(p, nullptr);
+  int nsm = 148, conv = 0;
+  const OpParams *P = sdf_internal_op(p, &nsm, &conv);
+  if (!d || !P) return SDF_ERR_INVALID_ARG;
+  int nc[3];
+  long long Nc;
+  coarse_sizes(d, c, nc, &Nc);
+  if (Nc < 2 * (long long)r_pool) return SDF_ERR_INVALID_ARG;
+  sdf_problem_desc dc = *d;
+  for (int i = 0; i < 3; ++i) dc.n[i] = nc[i];
+  std::vector<double> kap(d->has_kappa ? Nc : 0, 1.0);
+  sdf_problem *pc = nullptr;
+  if (sdf_problem_create(&dc, d->has_kappa ? kap.data() : nullptr, &pc) != SDF_OK)
+    return SDF_ERR_INVALID_ARG;
+  size_t pb = 0;
+  sdf_problem_device_bytes(pc, &pb);
+  sdf_problem_destroy(pc);
+  // the coarse eigensolve's own workspace: the same block layout on Nc nodes
+  const int m = r_pool + (o->guard > 0 ? o->guard : std::max(16, r_pool / 2));
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  const int nchunk = 2 * nsm;
+  size_t eb = 4 * al(sizeof(double) * (size_t)Nc * m) + al(sizeof(double) * (size_t)nchunk * m * m) +
+              al(sizeof(double) * (size_t)m * m * 2) + al(sizeof(double) * m);
+  const long long N = P->N;
+  size_t b = al(pb) + eb + al(sizeof(double) * (size_t)Nc * r_pool) +
+             2 * al(sizeof(double) * (size_t)N * r_pool) +
+             al(sizeof(double) * (size_t)nchunk * r_pool * r_pool) +
+             al(sizeof(double) * (size_t)r_pool * r_pool * 2);
+  *bytes = b;
+  return SDF_OK;
+}
+
+sdf_status sdf_reference_modes_coarse(sdf_problem *p, int c, int r_pool, const sdf_eig_opts *o,
+                                      double tau_sv, double *phi_dev, int64_t ld, int *r_out,
+                                      double *lambda_c_host, sdf_eig_stats *stats, void *ws,
+                                      size_t ws_bytes, void *stream) {
+  if (!p) return SDF_ERR_INVALID_ARG;
+  sdf_eig_opts def;
+  sdf_default_eig_opts(&def);
+  if (!o) o = &def;
+  size_t need = 0;
+  if (sdf_coarse_modes_workspace_size(p, c, r_pool, o, &need) != SDF_OK)
+    return efail(p, SDF_ERR_INVALID_ARG, "coarse modes: bad factor, pool size or problem");
+  int nsm = 148, conv = 0;
+  const OpParams P = *sdf_internal_op(p, &nsm, &conv);
+  if (conv) return efail(p, SDF_ERR_UNSUPPORTED, "coarse modes: A with convection is not symmetric");
+  if (!phi_dev || ld < P.N || !ws || ((uintptr_t)ws & 255) != 0 || !(tau_sv >= 0.0))
+    return efail(p, SDF_ERR_INVALID_ARG, "coarse modes: bad output, workspace or tau_sv");
+  if (ws_bytes < need) return efail(p, SDF_ERR_WORKSPACE, "coarse modes: workspace too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  const double *kap_f = nullptr;
+  const sdf_problem_desc *d = sdf_internal_desc(p, &kap_f);
+  int nc[3];
+  long long Nc;
+  coarse_sizes(d, c, nc, &Nc);
+  // coarse problem: the same operator law, kappa injected at the nearest fine node
+  sdf_problem_desc dc = *d;
+  for (int i = 0; i < 3; ++i) dc.n[i] = nc[i];
+  std::vector<double> kap_c;
+  if (d->has_kappa) {
+    kap_c.resize(Nc);
+    const int nf[3] = {d->n[0], d->n[1], d->dim == 3 ? d->n[2] : 1};
+    auto near = [&](int j, int m_c, int m_f) {
+      int i = (int)std::lround((double)(j + 1) / (m_c + 1) * (m_f + 1)) - 1;
+      return std::min(std::max(i, 0), m_f - 1);
+    };
+    for (int l = 0; l < nc[2]; ++l)
+      for (int j = 0; j < nc[1]; ++j)
+        for (int i = 0; i < nc[0]; ++i) {
+          const int fi = near(i, nc[0], nf[0]), fj = near(j, nc[1], nf[1]),
+                    fl = d->dim == 3 ? near(l, nc[2], nf[2]) : 0;
+          kap_c[i + (size_t)nc[0] * (j + (size_t)nc[1] * l)] =
+              kap_f[fi + (size_t)nf[0] * (fj + (size_t)nf[1] * fl)];
+        }
+  }
+  sdf_problem *pc = nullptr;
+  if (sdf_problem_create(&dc, d->has_kappa ? kap_c.data() : nullptr, &pc) != SDF_OK)
+    return efail(p, SDF_ERR_INVALID_ARG, "coarse modes: coarse problem rejected");
+  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  size_t pb = 0;
+  sdf_problem_device_bytes(pc, &pb);
+  char *w = (char *)ws;
+  size_t off = 0;
+  char *pbuf = w + off;
+  off += al(pb);
+  sdf_status st = sdf_problem_bind(pc, pbuf, pb, stream);
+  if (st != SDF_OK) {
+    sdf_problem_destroy(pc);
+    return efail(p, st, "coarse modes: binding the coarse problem failed");
+  }
+  size_t eb = 0;
+  sdf_eig_workspace_size(pc, r_pool, o, &eb);
+  char *ews = w + off;
+  off += al(eb);
+  double *Xc = (double *)(w + off);
+  off += al(sizeof(double) * (size_t)Nc * r_pool);
+  double *Xf = (double *)(w + off);
+  off += al(sizeof(double) * (size_t)P.N * r_pool);
+  double *Xg = (double *)(w + off);
+  off += al(sizeof(double) * (size_t)P.N * r_pool);
+  const int nchunk = 2 * nsm;
+  double *part = (double *)(w + off);
+  off += al(sizeof(double) * (size_t)nchunk * r_pool * r_pool);
+  double *small = (double *)(w + off);
+  // 1-2. coarse eigenpairs
+  std::vector<double> lam_c(r_pool);
+  st = sdf_reference_modes_eig(pc, r_pool, o, Xc, Nc, lambda_c_host ? lambda_c_host : lam_c.data(),
+                               nullptr, stats, ews, eb, stream);
+  if (st != SDF_OK) {
+    const std::string msg = std::string("coarse modes: ") + sdf_last_error(pc);
+    sdf_problem_destroy(pc);
+    return efail(p, st, msg.c_str());
+  }
+  sdf_problem_destroy(pc);
+  // 3. prolongation
+  k_prolong<<<dim3((unsigned)std::min<long long>((P.N + ET - 1) / ET, nsm * 4LL), r_pool), ET, 0,
+              s>>>(d->dim, P.nx, P.ny, P.nz, nc[0], nc[1], nc[2], Xc, r_pool, Xf);
+  ECK(cudaGetLastError());
+  // 4. QR with column discard: Cholesky of the Gram matrix that skips a column
+  //    whose pivot R_jj is below tau_sv times the largest column norm
+  BlockOps ops{p, s, P.N, nchunk, part, small, r_pool};
+  std::vector<double> G;
+  st = ops.gram(Xf, Xf, r_pool, G);
+  if (st != SDF_OK) return st;
+  double gmax = 0.0;
+  for (int j = 0; j < r_pool; ++j) gmax = std::max(gmax, G[(size_t)j * r_pool + j]);
+  const double thr = tau_sv * tau_sv * gmax;
+  std::vector<int> kept;
+  std::vector<double> L;  // rows of the lower factor over the kept columns
+  for (int j = 0; j < r_pool; ++j) {
+    const int q = (int)kept.size();
+    std::vector<double> row(q + 1, 0.0);
+    for (int a = 0; a < q; ++a) {
+      double v = G[(size_t)kept[a] * r_pool + j];
+      for (int b = 0; b < a; ++b) v -= L[(size_t)a * r_pool + b] * row[b];
+      row[a] = v / L[(size_t)a * r_pool + a];
+    }
+    double dj = G[(size_t)j * r_pool + j];
+    for (int a = 0; a < q; ++a) dj -= row[a] * row[a];
+    if (!(dj > thr)) continue;  // dependent column: discarded
+    row[q] = std::sqrt(dj);
+    L.resize((size_t)(q + 1) * r_pool, 0.0);
+    for (int a = 0; a <= q; ++a) L[(size_t)q * r_pool + a] = row[a];
+    kept.push_back(j);
+  }
+  const int rk = (int)kept.size();
+  if (rk == 0) return efail(p, SDF_ERR_NOT_SPD, "coarse modes: every column discarded");
+  std::vector<double> Lk((size_t)rk * rk), Wk, W((size_t)r_pool * rk, 0.0);
+  for (int a = 0; a < rk; ++a)
+    for (int b = 0; b <= a; ++b) Lk[(size_t)a * rk + b] = L[(size_t)a * r_pool + b];
+  hla::inv_lower_transpose(rk, Lk, Wk);
+  for (int a = 0; a < rk; ++a)
+    for (int b = 0; b < rk; ++b) W[(size_t)kept[a] * rk + b] = Wk[(size_t)a * rk + b];
+  st = ops.rotate(Xf, W, r_pool, rk, Xg);  // Xg = Xf[:, kept] R^-1
+  if (st != SDF_OK) return st;
+  // a second Cholesky-QR pass restores orthonormality to working precision
+  std::vector<double> G2, L2, W2;
+  st = ops.gram(Xg, Xg, rk, G2);
+  if (st != SDF_OK) return st;
+  if (!hla::cholesky(rk, G2, L2)) return efail(p, SDF_ERR_NOT_SPD, "coarse modes: QR failed");
+  hla::inv_lower_transpose(rk, L2, W2);
+  st = ops.rotate(Xg, W2, rk, rk, Xf);
+  if (st != SDF_OK) return st;
+  ECK(cudaMemcpy2DAsync(phi_dev, sizeof(double) * ld, Xf, sizeof(double) * P.N,
+                        sizeof(double) * P.N, rk, cudaMemcpyDeviceToDevice, s));
+  ECK(cudaStreamSynchronize(s));
+  if (r_out) *r_out = rk;
+  return SDF_OK;
 }
 
 }  // extern "C"

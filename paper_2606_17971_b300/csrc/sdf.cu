@@ -2514,6 +2514,11 @@ const sdf::OpParams *sdf_internal_op(const sdf_problem *p, int *nsm, int *convec
 void sdf_internal_set_error(sdf_problem *p, const char *msg) {
   if (p) p->err = msg;
 }
+const sdf_problem_desc *sdf_internal_desc(const sdf_problem *p, const double **kappa_host) {
+  if (!p) return nullptr;
+  if (kappa_host) *kappa_host = p->kappa.empty() ? nullptr : p->kappa.data();
+  return &p->d;
+}
 
 // ===========================================================================
 // C ABI

@@ -121,6 +121,9 @@ _sigs = {
     "sdf_default_eig_opts": (None, [_vp]),
     "sdf_eig_workspace_size": (_i32, [_vp, _i32, _vp, ctypes.POINTER(_sz)]),
     "sdf_reference_modes_eig": (_i32, [_vp, _i32, _vp, _vp, _i64, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "sdf_coarse_modes_workspace_size": (_i32, [_vp, _i32, _i32, _vp, ctypes.POINTER(_sz)]),
+    "sdf_reference_modes_coarse": (_i32, [_vp, _i32, _i32, _vp, ctypes.c_double, _vp, _i64,
+                                          ctypes.POINTER(_i32), _vp, _vp, _vp, _sz, _vp]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(_lib, _name)
@@ -238,6 +241,30 @@ class Problem:
         stats = dict(iters=st.iters, converged=bool(st.converged), max_rel_resid=st.max_rel_resid,
                      matvecs=st.matvecs, seconds=st.seconds, status=rc)
         return phi, ls, la, stats
+
+    def coarse_modes(self, c, r_pool, tau_sv=1e-8, **kw):
+        """Coarse-grid reference basis (sdf_reference_modes_coarse): returns
+        Phi (r, N) float64 with r <= r_pool kept columns, the coarse
+        eigenvalues of S_c and the coarse eigensolve's stats."""
+        o = EigOpts()
+        _lib.sdf_default_eig_opts(ctypes.byref(o))
+        for key, v in kw.items():
+            setattr(o, key, v)
+        nb = _sz()
+        self._check(_lib.sdf_coarse_modes_workspace_size(self._h, c, r_pool, ctypes.byref(o),
+                                                         ctypes.byref(nb)))
+        ws = torch.empty(int(nb.value), dtype=torch.uint8, device=self.device)
+        phi = torch.empty((r_pool, self.N), dtype=torch.float64, device=self.device)
+        lam = np.zeros(r_pool)
+        r = ctypes.c_int(0)
+        st = EigStats()
+        self._check(_lib.sdf_reference_modes_coarse(self._h, c, r_pool, ctypes.byref(o), tau_sv,
+                                                    _ptr(phi), self.N, ctypes.byref(r),
+                                                    lam.ctypes.data, ctypes.byref(st), _ptr(ws),
+                                                    ws.numel(), _stream()))
+        stats = dict(iters=st.iters, converged=bool(st.converged), max_rel_resid=st.max_rel_resid,
+                     matvecs=st.matvecs, seconds=st.seconds)
+        return phi[:r.value].contiguous(), lam, stats
 
     # workspace --------------------------------------------------------------
     def workspace(self, batch, opts=None, host_io=False):

@@ -89,3 +89,31 @@ def test_convection_is_refused(sdf):
     G = sdf.Problem(2, 24, alpha=1e-4, diff_scale=1e-2, convection=True, yd_sigma=0.1)
     with pytest.raises(sdf.SdfError):
         G.eig_modes(4)
+
+
+def test_coarse_grid_basis_matches_oracle_and_deflates(sdf):
+    from oracle import coarse_oracle as C
+    n = (48, 40)
+    w = W.scaled(W.WORKLOADS["block2d_1024"], 48)
+    kap = np.ascontiguousarray(W.kappa_field(w).reshape(48, 48)[:40, :]).ravel()
+    r_pool = 12
+    Q_o, lam_o = C.coarse_modes(2, n, 2, r_pool, kappa=kap, alpha=w.alpha)
+    G = sdf.Problem(2, n, alpha=w.alpha, kappa=kap, yd_sigma=w.sigma)
+    phi, lam_c, st = G.coarse_modes(2, r_pool, tol=1e-10)
+    assert st["converged"]
+    np.testing.assert_allclose(lam_c, np.sort(lam_o)[:r_pool], rtol=1e-9)
+    Pg = phi.cpu().numpy().T
+    assert Pg.shape == Q_o.shape
+    np.testing.assert_allclose(Pg.T @ Pg, np.eye(r_pool), atol=1e-12)
+    assert _sin_max_angle(Pg, Q_o) < 1e-6
+    # a 3D grid with every column kept deflates the fine solve
+    G3 = sdf.Problem(3, (30, 28, 26), alpha=1e-4, yd_sigma=0.1)
+    phi3, _, _ = G3.coarse_modes(2, 16)
+    assert phi3.shape[0] == 16
+    G3.set_modes(phi3)
+    inst = torch.as_tensor([[2.0, 0.45, 0.5, 0.55, 0, 0, 0]], dtype=torch.float64, device="cuda")
+    psi = torch.full((G3.N,), 10.0, dtype=torch.float64, device="cuda")
+    defl = G3.solve(inst, psi, want_lambda=False)
+    plain = G3.solve(inst, psi, sdf.default_opts(deflate=0), want_lambda=False)
+    assert defl["stats"][0]["cg_iters"][0] < 0.8 * plain["stats"][0]["cg_iters"][0]
+    assert (defl["y"] - plain["y"]).abs().max().item() < 1e-6 * plain["y"].abs().max().item()
