@@ -199,6 +199,12 @@ class Problem:
         lib().orc_desired_state(self._h, float(a), _dp(c), float(sigma), _dp(yd), _dp(rhs))
         return yd, rhs
 
+    @staticmethod
+    def set_ritz(r: int):
+        """Ritz re-selection (Sec. 2.2.3) in every later A-DEF2 solve: the r
+        smallest Ritz vectors of the restricted pool (0: off)."""
+        lib().orc_set_ritz(int(r))
+
     def inner_solve(self, active, rhs, psi, Phi=None, deflate=True, rtol=1e-8,
                     maxit=100000, tau_cond=1e10, x0=None):
         """Solve S_II x_I = rhs_I - S_IA psi_A on the given active set."""

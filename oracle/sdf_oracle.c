@@ -547,6 +547,73 @@ static void jacobi_eigenvalues(int k, const double *Ain, double *ev) {
   free(A);
 }
 
+/* Eigenpairs of a symmetric k x k column-major matrix by cyclic Jacobi:
+ * eigenvalues ascending in ev, eigenvectors as the columns of V. */
+static void jacobi_eigen(int k, const double *Ain, double *ev, double *V) {
+  double *A = (double *)malloc(sizeof(double) * k * k);
+  double *W = (double *)malloc(sizeof(double) * k * k);
+  memcpy(A, Ain, sizeof(double) * k * k);
+  for (int i = 0; i < k * k; ++i) W[i] = 0.0;
+  for (int i = 0; i < k; ++i) W[i + i * k] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int j = 0; j < k; ++j)
+      for (int i = 0; i < k; ++i) {
+        tot += A[i + j * k] * A[i + j * k];
+        if (i != j) off += A[i + j * k] * A[i + j * k];
+      }
+    if (off <= 1e-30 * tot) break;
+    for (int p = 0; p < k - 1; ++p)
+      for (int q = p + 1; q < k; ++q) {
+        double apq = A[p + q * k];
+        if (apq == 0.0) continue;
+        double app = A[p + p * k], aqq = A[q + q * k];
+        double theta = (aqq - app) / (2.0 * apq);
+        double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+        double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+        for (int r = 0; r < k; ++r) {
+          double arp = A[r + p * k], arq = A[r + q * k];
+          A[r + p * k] = c * arp - s * arq;
+          A[r + q * k] = s * arp + c * arq;
+        }
+        for (int r = 0; r < k; ++r) {
+          double apr = A[p + r * k], aqr = A[q + r * k];
+          A[p + r * k] = c * apr - s * aqr;
+          A[q + r * k] = s * apr + c * aqr;
+        }
+        for (int r = 0; r < k; ++r) {
+          double wrp = W[r + p * k], wrq = W[r + q * k];
+          W[r + p * k] = c * wrp - s * wrq;
+          W[r + q * k] = s * wrp + c * wrq;
+        }
+      }
+  }
+  /* selection sort of the eigenpairs, ascending */
+  int *ord = (int *)malloc(sizeof(int) * k);
+  for (int i = 0; i < k; ++i) ord[i] = i;
+  for (int i = 0; i < k; ++i)
+    for (int j = i + 1; j < k; ++j)
+      if (A[ord[j] + ord[j] * k] < A[ord[i] + ord[i] * k]) {
+        int t = ord[i];
+        ord[i] = ord[j];
+        ord[j] = t;
+      }
+  for (int j = 0; j < k; ++j) {
+    ev[j] = A[ord[j] + ord[j] * k];
+    for (int i = 0; i < k; ++i) V[i + j * k] = W[i + ord[j] * k];
+  }
+  free(ord);
+  free(W);
+  free(A);
+}
+
+/* Ritz re-selection (Sec. 2.2.3): when 0 < r < k, the A-DEF2 deflation space
+ * is the span of the r Ritz vectors of S_II with the smallest Ritz values in
+ * the restricted, orthonormalised pool Z (eigenpairs of E = Z^T S_II Z).
+ * 0 (default): the pool itself. */
+static int g_ritz_r = 0;
+void orc_set_ritz(int r) { g_ritz_r = r; }
+
 /* Householder QR of the n x k column-major matrix X (n >= k): on return Q
  * (n x k, orthonormal columns) overwrites X and rdiag holds |R_jj|. */
 static int householder_qr(int n, int k, double *X, double *rdiag) {
@@ -715,6 +782,42 @@ static int adef2_core(const csr_t *S, const double *b, double *x,
       E[i + j * k] = s;
       E[j + i * k] = s;
     }
+  double *Zsel = NULL;
+  if (g_ritz_r > 0 && g_ritz_r < k) {
+    /* Ritz re-selection: Z <- Z C_r, S Z <- (S Z) C_r with C_r the
+     * eigenvectors of E for its r smallest eigenvalues; E <- C_r^T E C_r */
+    int r = g_ritz_r;
+    double *V = (double *)malloc(sizeof(double) * k * k);
+    double *mu = (double *)malloc(sizeof(double) * k);
+    jacobi_eigen(k, E, mu, V);
+    Zsel = (double *)malloc(sizeof(double) * (size_t)n * r);
+    double *SZsel = (double *)malloc(sizeof(double) * (size_t)n * r);
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < r; ++j) {
+        double a = 0.0, bsz = 0.0;
+        for (int q = 0; q < k; ++q) {
+          a += ZI[(size_t)q * n + i] * V[q + j * k];
+          bsz += SZ[(size_t)q * n + i] * V[q + j * k];
+        }
+        Zsel[(size_t)j * n + i] = a;
+        SZsel[(size_t)j * n + i] = bsz;
+      }
+    for (int j = 0; j < r; ++j)
+      for (int i = 0; i < r; ++i) E[i + j * r] = dot(n, Zsel + (size_t)i * n, SZsel + (size_t)j * n);
+    for (int j = 0; j < r; ++j)
+      for (int i = 0; i < j; ++i) {
+        double sy = 0.5 * (E[i + j * r] + E[j + i * r]);
+        E[i + j * r] = sy;
+        E[j + i * r] = sy;
+      }
+    free(SZ);
+    SZ = SZsel;
+    ZI = Zsel;
+    k = r;
+    free(V);
+    free(mu);
+  }
   jacobi_eigenvalues(k, E, ev);
   double emin = ev[0], emax = ev[0];
   for (int i = 1; i < k; ++i) {
@@ -725,6 +828,7 @@ static int adef2_core(const csr_t *S, const double *b, double *x,
   memcpy(L, E, sizeof(double) * k * k);
   if (!(*condE <= tau_cond) || cholesky(k, L)) {
     *fallback = 1;
+    free(Zsel);
     free(SZ);
     free(E);
     free(L);
@@ -806,6 +910,7 @@ static int adef2_core(const csr_t *S, const double *b, double *x,
   g_t_loop_end = now_s();
   *iters = it;
   *relres = bn > 0 ? rn / bn : 0.0;
+  free(Zsel);
   free(SZ);
   free(E);
   free(L);

@@ -419,3 +419,27 @@ def test_raw_eig100_deflated_iterations_match_paper_table():
         r = P.solve(f(p), psi, Phi, deflate=True, rtol=1e-10, max_cg=3000)
         its.append(r["cg_iters"][-1])
     assert abs(np.median(its) - gold) <= 0.1 * gold
+
+
+def test_ritz_reselection_recovers_the_exact_modes_in_a_pool():
+    # pool = the 8 lowest eigenvectors of S (A = {}) plus 8 random vectors:
+    # the 8 smallest Ritz values of the pool are the 8 smallest eigenvalues
+    # (Cauchy interlacing, attained on the exact vectors), so Ritz
+    # re-selection must deflate exactly as the 8 exact modes do
+    P = O.Problem(2, (24, 20), alpha=1e-4)
+    V, lam = O.dense_modes(P, 8)
+    rng = np.random.default_rng(11)
+    pool = np.asfortranarray(np.column_stack([V, rng.standard_normal((P.N, 8))]))
+    _, rhs = P.desired_state(2.0, (0.45, 0.55), 0.1)
+    act = np.zeros(P.N, np.uint8)
+    psi = np.full(P.N, 10.0)
+    exact = P.inner_solve(act, rhs, psi, V)
+    try:
+        O.Problem.set_ritz(8)
+        ritz = P.inner_solve(act, rhs, psi, pool)
+    finally:
+        O.Problem.set_ritz(0)
+    assert abs(ritz["iters"] - exact["iters"]) <= 1, (ritz["iters"], exact["iters"])
+    np.testing.assert_allclose(ritz["x"], exact["x"], rtol=0, atol=1e-7 * np.abs(exact["x"]).max())
+    # the guard sees the selected Galerkin matrix: cond = lambda_8 / lambda_1
+    np.testing.assert_allclose(ritz["cond_E"], lam[-1] / lam[0], rtol=1e-6)
