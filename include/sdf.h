@@ -116,7 +116,11 @@ typedef struct {
  *   replace_every mixed path: CG iterations between FP64 residual
  *                replacements (0 = 100)                           [100]
  *   max_launches host watchdog: total iteration launches per solve call
- *                before SDF_ERR_TIMEOUT (0 = 4 * max_cg)          [0]        */
+ *                before SDF_ERR_TIMEOUT (0 = 4 * max_cg)          [0]
+ *   ritz_r       Ritz re-selection (Sec. 2.2.3): 0 < ritz_r < k deflates
+ *                with the ritz_r Ritz vectors of S_II of smallest Ritz value
+ *                in the restricted pool of the k registered modes; the
+ *                guard then applies to their Galerkin matrix      [0: off]   */
 typedef struct {
   double rtol;
   double tau;
@@ -130,6 +134,7 @@ typedef struct {
   int32_t precision;
   int32_t replace_every;
   int64_t max_launches;
+  int32_t ritz_r;
 } sdf_opts;
 
 /* Per-instance statistics (host struct filled at the end of a solve). */

@@ -42,6 +42,7 @@
 
 #include "sdf_device.cuh"
 #include "tc_device.cuh"
+#include "host_linalg.h"
 
 using namespace sdf;
 
@@ -2045,6 +2046,62 @@ const PhiT *phi_as(const sdf_problem *p) { return static_cast<const PhiT *>(p->p
 // The solve, templated on dimension, mode-count bucket, Phi type and vector
 // precision V (double: FP64 path; float: mixed path with FP64 x, b,
 // reductions, coarse operator and periodic FP64 residual replacement).
+// Ritz re-selection (Sec. 2.2.3) after k_coarse: for each deflating
+// instance, the eigenpairs (mu, C) of E = Lg^-1 E_raw Lg^-T (the Galerkin
+// matrix of the orthonormalised pool Phi_I Lg^-T) on the host; the r
+// smallest are kept, the guard is applied to mu_r / mu_1, and the coarse
+// inverse becomes Einv = Lg^-T C_r diag(1/mu) C_r^T Lg^-1, i.e. the A-DEF2
+// projector of Z = Phi_I Lg^-T C_r.  coarse holds (Lg, Lg^-1, T, E, Le^-1)
+// per instance, row-major.
+sdf_status ritz_select(sdf_problem *p, int B, int k, int r, InstState *st_d, const double *coarse_d,
+                       double *Einv_d, double tau_cond, cudaStream_t s) {
+  const size_t kk = (size_t)k * k;
+  std::vector<InstState> st(B);
+  std::vector<double> cs((size_t)B * 5 * kk);
+  CK(cudaMemcpyAsync(st.data(), st_d, sizeof(InstState) * B, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(cs.data(), coarse_d, sizeof(double) * cs.size(), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  std::vector<double> Ei(kk);
+  for (int b = 0; b < B; ++b) {
+    InstState &S = st[b];
+    if (S.outer_done || !S.deflate) continue;
+    const double *Lgi = cs.data() + (size_t)b * 5 * kk + kk;
+    std::vector<double> E(cs.begin() + (size_t)b * 5 * kk + 3 * kk,
+                          cs.begin() + (size_t)b * 5 * kk + 4 * kk), w, Vd;
+    hla::jacobi_eig(k, E, w, Vd);  // descending
+    const double mu1 = w[k - 1], mur = w[k - r];
+    const double cond = mu1 > 0.0 ? mur / mu1 : INFINITY;
+    S.stats.cond_E[S.outer] = cond;
+    if (!(cond <= tau_cond)) {
+      S.deflate = 0;
+      S.stats.fallback[S.outer] = 1;
+      continue;
+    }
+    // Y = C_r^T Lg^-1 (r x k); Einv = Y^T diag(1 / mu) Y
+    std::vector<double> Y((size_t)r * k, 0.0);
+    for (int a = 0; a < r; ++a) {
+      const int col = k - 1 - a;  // a-th smallest
+      for (int j = 0; j < k; ++j) {
+        double v = 0.0;
+        for (int q = 0; q < k; ++q) v += Vd[(size_t)q * k + col] * Lgi[(size_t)q * k + j];
+        Y[(size_t)a * k + j] = v;
+      }
+    }
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) {
+        double v = 0.0;
+        for (int a = 0; a < r; ++a) v += Y[(size_t)a * k + i] * Y[(size_t)a * k + j] / w[k - 1 - a];
+        Ei[(size_t)i * k + j] = v;
+      }
+    CK(cudaMemcpyAsync(Einv_d + (size_t)b * kk, Ei.data(), sizeof(double) * kk,
+                       cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  CK(cudaMemcpyAsync(st_d, st.data(), sizeof(InstState) * B, cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  return SDF_OK;
+}
+
 template <int DIM, int KMAX, class PhiT, class V>
 sdf_status solve_impl(sdf_problem *p, const double *inst, int B, const double *psi,
                       const sdf_opts &o, char *ws, cudaStream_t s, double *y, double *lam,
@@ -2126,8 +2183,15 @@ sdf_status solve_impl(sdf_problem *p, const double *inst, int B, const double *p
       if (nset < B)
         k_coarse_copy<<<B - 1, NT, 0, s>>>(k, Eraw, G);
       CKL("coarse setup");
-      k_coarse<<<B, NT, 0, s>>>(k, st, G, Eraw, Einv, coarse, o.tau_cond);
-      CKL("k_coarse");
+      {
+        const bool ritz = o.ritz_r > 0 && o.ritz_r < k;
+        k_coarse<<<B, NT, 0, s>>>(k, st, G, Eraw, Einv, coarse, ritz ? INFINITY : o.tau_cond);
+        CKL("k_coarse");
+        if (ritz) {
+          sdf_status e = ritz_select(p, B, k, o.ritz_r, st, coarse, Einv, o.tau_cond, s);
+          if (e != SDF_OK) return e;
+        }
+      }
       k_project<KMAX, PhiT, V><<<gA, NT, 0, s>>>(Phi, ld, k, N, mask, rbuf[0], st, nullptr, part,
                                                  cnt, L.gxa);
       CKL("k_project");
@@ -2381,8 +2445,15 @@ sdf_status solve_mixed(sdf_problem *p, const double *inst, int B, const double *
       if (nset < B)
         k_coarse_copy<<<B - 1, NT, 0, s>>>(k, Eraw, G);
       CKL("coarse setup");
-      k_coarse<<<B, NT, 0, s>>>(k, st, G, Eraw, Einv, coarse, o.tau_cond);
-      CKL("k_coarse");
+      {
+        const bool ritz = o.ritz_r > 0 && o.ritz_r < k;
+        k_coarse<<<B, NT, 0, s>>>(k, st, G, Eraw, Einv, coarse, ritz ? INFINITY : o.tau_cond);
+        CKL("k_coarse");
+        if (ritz) {
+          sdf_status e = ritz_select(p, B, k, o.ritz_r, st, coarse, Einv, o.tau_cond, s);
+          if (e != SDF_OK) return e;
+        }
+      }
       p->prof.launches += 5LL * nset + (nset < B ? 1 : 0) + 1;
       sdf_status e = project(rbuf[0]);  // coarse-corrected start: c = -E^-1 Phi_I^T b
       if (e != SDF_OK) return e;
@@ -2539,6 +2610,7 @@ void sdf_default_opts(sdf_opts *o) {
   o->precision = SDF_PREC_F64;
   o->replace_every = 100;
   o->max_launches = 0;
+  o->ritz_r = 0;
 }
 
 sdf_status sdf_problem_create(const sdf_problem_desc *desc, const double *kappa_host,

@@ -43,7 +43,7 @@ class Opts(ctypes.Structure):
                 ("deflate", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("max_blocks", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("replace_every", ctypes.c_int32),
-                ("max_launches", ctypes.c_int64)]
+                ("max_launches", ctypes.c_int64), ("ritz_r", ctypes.c_int32)]
 
 
 SDF_NPROF = 9

@@ -393,3 +393,42 @@ def test_autotuned_column_depth_keeps_the_solution():
     assert torch.equal(before["active"], after["active"])
     assert (before["y"] - after["y"]).abs().max().item() <= 1e-7 * before["y"].abs().max().item()
     assert all(s["status"] == 0 for s in after["stats"])
+
+
+def test_ritz_reselection_matches_oracle():
+    # a pool of the 8 lowest modes of S plus 8 random directions: Ritz
+    # re-selection (r = 8) must deflate as the exact modes do, on both sides
+    n = (24, 20)
+    P = O.Problem(2, n, alpha=1e-4)
+    V, lam = O.dense_modes(P, 8)
+    rng = np.random.default_rng(11)
+    pool = np.asfortranarray(np.column_stack([V, rng.standard_normal((P.N, 8))]))
+    pool = np.asfortranarray(pool / np.linalg.norm(pool, axis=0))
+    w = W.scaled(W.WORKLOADS["diff2d_32"], 24)
+    insts = W.draw_instances(w, count=4)
+    psi = np.ones(P.N)
+    try:
+        O.Problem.set_ritz(8)
+        orc = _orc_solves(P, [P.desired_state(i.a, i.c[:2], w.sigma)[1] for i in insts], psi, pool)
+    finally:
+        O.Problem.set_ritz(0)
+    G = sdf.Problem(2, n, alpha=1e-4, yd_sigma=w.sigma)
+    G.set_modes(torch.as_tensor(np.ascontiguousarray(pool.T), device="cuda"))
+    out = G.solve(t64(W.instances_array(insts)), t64(psi), sdf.default_opts(ritz_r=8))
+    for b, r in enumerate(orc):
+        st = out["stats"][b]
+        assert st["status"] == 0 and st["outer_iters"] == r["outer_iters"]
+        assert np.array_equal(out["active"][b].cpu().numpy().astype(bool), r["active"])
+        for ig, io in zip(st["cg_iters"], r["cg_iters"]):
+            assert abs(ig - io) <= max(3, 0.02 * io), (st["cg_iters"], r["cg_iters"])
+        y = out["y"][b].cpu().numpy()
+        assert np.linalg.norm(y - r["y"]) <= 1e-6 * np.linalg.norm(r["y"])
+        np.testing.assert_allclose(st["cond_E"], r["cond_E"], rtol=1e-6)
+    # the mixed path with the same pool (FP32)
+    G.set_modes(torch.as_tensor(np.ascontiguousarray(pool.T), device="cuda").float().contiguous())
+    om = G.solve(t64(W.instances_array(insts)), t64(psi),
+                 sdf.default_opts(ritz_r=8, precision=sdf.PREC_MIXED))
+    for b, r in enumerate(orc):
+        assert np.array_equal(om["active"][b].cpu().numpy().astype(bool), r["active"])
+        y = om["y"][b].cpu().numpy()
+        assert np.linalg.norm(y - r["y"]) <= 1e-5 * np.linalg.norm(r["y"])
