@@ -161,6 +161,26 @@ class ClockSampler:
 
 # ---------------------------------------------------------------------------
 
+# ---------------------------------------------------------------------------
+# multi-process aggregation (one process per GPU, instances sharded by rank)
+
+def shard(items, rank, world):
+    """The instances of this rank: every world-th one, starting at rank (no
+    collective in the data path: ranks solve disjoint instances)."""
+    return items[rank::world]
+
+
+def max_over_ranks(value, device, world):
+    """The largest of the ranks' values (the job's wall time is the slowest
+    rank's); world == 1 returns the value itself."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_problem(w, sdf, device, phi_dtype=0):
     from paper_2606_17971_b300 import workloads as W
     kap = W.kappa_field(w)
@@ -285,7 +305,7 @@ def main():
     B = args.batch or (64 if mixed else 1)
     steps, warm = args.steps, args.warmup
     insts = W.draw_instances(w, count=(steps + warm) * B * world)
-    mine = insts[rank::world]
+    mine = shard(insts, rank, world)
     inst_t = [torch.as_tensor(W.instances_array(mine[i * B:(i + 1) * B]), device=dev)
               for i in range(steps + warm)]
     psi = torch.full((w.N,), w.psi, dtype=torch.float64, device=dev)
@@ -355,12 +375,8 @@ def main():
         torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    ms = e0.elapsed_time(e1)
     prof = G.profile()
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dev, world)
     value = steps * B * world / (ms * 1e-3)
 
     # ---- e2e: host buffers in, host buffers out, copies inside the timed region ----
@@ -395,10 +411,8 @@ def main():
         for i in range(steps):
             e2e_step(warm + i)
         torch.cuda.synchronize()
-        te = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = {"value": steps * B * world / float(te.item()), "unit": UNIT,
+        te = max_over_ranks(time.perf_counter() - t0, dev, world)
+        e2e = {"value": steps * B * world / te, "unit": UNIT,
                "h2d_bytes_per_step": int(inst_h[0].numel() * 8 + psi_h.numel() * 8),
                "d2h_bytes_per_step": int(y_h.numel() * 8 + a_h.numel()),
                "path": "learned pipeline through the Python binding" if model is not None
