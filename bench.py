@@ -367,12 +367,15 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
+        # NVTX range: lets a profiler capture exactly the timed launches
+        torch.cuda.nvtx.range_push("timed_region")
         e0.record(stream)
         for i in range(steps):
             res = one_step(inst_t[warm + i])
             stats.extend(res["stats"])
         e1.record(stream)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
     if world > 1:
         dist.barrier()
     prof = G.profile()
