@@ -120,7 +120,15 @@ typedef struct {
  *   ritz_r       Ritz re-selection (Sec. 2.2.3): 0 < ritz_r < k deflates
  *                with the ritz_r Ritz vectors of S_II of smallest Ritz value
  *                in the restricted pool of the k registered modes; the
- *                guard then applies to their Galerkin matrix      [0: off]   */
+ *                guard then applies to their Galerkin matrix      [0: off]
+ *   safe_r       conditioning-based safe merge (Sec. 2.2.5, Algorithm safe):
+ *                0 < safe_r < k takes the first safe_r registered modes as
+ *                the eigenmode part and the rest, in order, as POD
+ *                candidates; each candidate is orthogonalised against the
+ *                basis so far (skipped if its norm < tau_dep) and accepted
+ *                while cond(Z^T S_II Z) <= tau_safe (the first violation ends
+ *                the merge).  Takes precedence over ritz_r        [0: off]
+ *   tau_safe, tau_dep  thresholds of the safe merge          [1e4, 1e-10] */
 typedef struct {
   double rtol;
   double tau;
@@ -135,6 +143,9 @@ typedef struct {
   int32_t replace_every;
   int64_t max_launches;
   int32_t ritz_r;
+  int32_t safe_r;
+  double tau_safe;
+  double tau_dep;
 } sdf_opts;
 
 /* Per-instance statistics (host struct filled at the end of a solve). */

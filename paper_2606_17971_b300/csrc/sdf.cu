@@ -475,9 +475,11 @@ __device__ double dev_power(const double *E, const double *Li, int k, int op, do
   return lam;
 }
 
+// host_decides = 1: the deflation decision is left to a host step that works
+// from G and E_raw alone (the safe merge); the factorisations may then fail.
 __global__ void __launch_bounds__(NT) k_coarse(int k, InstState *st, const double *G,
                                                const double *Eraw, double *Einv, double *wk,
-                                               double tau_cond) {
+                                               double tau_cond, int host_decides) {
   __shared__ double red[NWARP];
   __shared__ int ok;
   __shared__ double vv[SDF_MAX_K], ww[SDF_MAX_K];
@@ -530,7 +532,7 @@ __global__ void __launch_bounds__(NT) k_coarse(int k, InstState *st, const doubl
     }
   }
   if (threadIdx.x == 0) {
-    S.deflate = good ? 1 : 0;
+    S.deflate = (good || host_decides) ? 1 : 0;
     S.stats.cond_E[S.outer] = cond;
     S.stats.fallback[S.outer] = good ? 0 : 1;
   }
@@ -2046,6 +2048,139 @@ const PhiT *phi_as(const sdf_problem *p) { return static_cast<const PhiT *>(p->p
 // The solve, templated on dimension, mode-count bucket, Phi type and vector
 // precision V (double: FP64 path; float: mixed path with FP64 x, b,
 // reductions, coarse operator and periodic FP64 residual replacement).
+// Conditioning-based safe merge (Sec. 2.2.5, Algorithm safe) after k_coarse,
+// in the coordinates of the registered pool [eigenmodes (first r) | POD
+// candidates]: a basis column is a coefficient vector t with Z = Phi_I t, so
+// inner products are t^T G t (G = Phi_I^T Phi_I) and the Galerkin matrix is
+// T^T E_raw T.  Per deflating instance, on the host: the eigen part is
+// orthonormalised (T = [L_r^-T; 0] with G_rr = L_r L_r^T); each candidate e_j
+// is orthogonalised against T twice, skipped if its norm is below tau_dep,
+// normalised, and accepted while cond(E_trial) <= tau_safe (the first
+// violation ends the merge).  The coarse inverse becomes T E_Z^-1 T^T; the
+// guard applies to cond(E_Z).
+sdf_status safe_merge_select(sdf_problem *p, int B, int k, int r, InstState *st_d,
+                             const double *G_d, const double *Eraw_d, double *Einv_d,
+                             double tau_safe, double tau_dep, double tau_cond, cudaStream_t s) {
+  const size_t kk = (size_t)k * k;
+  std::vector<InstState> st(B);
+  std::vector<double> Gh((size_t)B * kk), Eh((size_t)B * kk);
+  CK(cudaMemcpyAsync(st.data(), st_d, sizeof(InstState) * B, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(Gh.data(), G_d, sizeof(double) * Gh.size(), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(Eh.data(), Eraw_d, sizeof(double) * Eh.size(), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  auto galerkin = [&](const double *E, const std::vector<std::vector<double>> &T) {
+    const int m = (int)T.size();
+    std::vector<double> out((size_t)m * m, 0.0);
+    for (int a = 0; a < m; ++a)
+      for (int b2 = 0; b2 < m; ++b2) {
+        double v = 0.0;
+        for (int i = 0; i < k; ++i) {
+          if (T[a][i] == 0.0) continue;
+          double w = 0.0;
+          for (int j = 0; j < k; ++j) w += E[(size_t)i * k + j] * T[b2][j];
+          v += T[a][i] * w;
+        }
+        out[(size_t)a * m + b2] = v;
+      }
+    for (int a = 0; a < m; ++a)
+      for (int b2 = a + 1; b2 < m; ++b2) {
+        const double sy = 0.5 * (out[(size_t)a * m + b2] + out[(size_t)b2 * m + a]);
+        out[(size_t)a * m + b2] = out[(size_t)b2 * m + a] = sy;
+      }
+    return out;
+  };
+  auto cond_of = [&](std::vector<double> E, int m) {
+    std::vector<double> w, V;
+    hla::jacobi_eig(m, E, w, V);  // descending
+    return w[m - 1] > 0.0 ? w[0] / w[m - 1] : INFINITY;
+  };
+  std::vector<double> Ei(kk);
+  for (int b = 0; b < B; ++b) {
+    InstState &S = st[b];
+    if (S.outer_done || !S.deflate) continue;
+    const double *G = Gh.data() + (size_t)b * kk, *E = Eh.data() + (size_t)b * kk;
+    auto Gdot = [&](const std::vector<double> &x, const std::vector<double> &y) {
+      double v = 0.0;
+      for (int i = 0; i < k; ++i) {
+        if (x[i] == 0.0) continue;
+        double w = 0.0;
+        for (int j = 0; j < k; ++j) w += G[(size_t)i * k + j] * y[j];
+        v += x[i] * w;
+      }
+      return v;
+    };
+    // eigen part: T = [L_r^-T; 0]
+    std::vector<double> Grr((size_t)r * r), Lr, Wr;
+    for (int i = 0; i < r; ++i)
+      for (int j = 0; j < r; ++j) Grr[(size_t)i * r + j] = G[(size_t)i * k + j];
+    bool good = hla::cholesky(r, Grr, Lr);
+    std::vector<std::vector<double>> T;
+    if (good) {
+      hla::inv_lower_transpose(r, Lr, Wr);
+      for (int c = 0; c < r; ++c) {
+        std::vector<double> t(k, 0.0);
+        for (int i = 0; i < r; ++i) t[i] = Wr[(size_t)i * r + c];
+        T.push_back(t);
+      }
+      for (int j = r; j < k; ++j) {
+        std::vector<double> c(k, 0.0);
+        c[j] = 1.0;
+        for (int rep = 0; rep < 2; ++rep) {
+          std::vector<double> proj(T.size());
+          for (size_t a = 0; a < T.size(); ++a) proj[a] = Gdot(T[a], c);
+          for (size_t a = 0; a < T.size(); ++a)
+            for (int i = 0; i < k; ++i) c[i] -= proj[a] * T[a][i];
+        }
+        const double nrm = std::sqrt(std::max(0.0, Gdot(c, c)));
+        if (nrm < tau_dep) continue;
+        for (int i = 0; i < k; ++i) c[i] /= nrm;
+        T.push_back(c);
+        const std::vector<double> Et = galerkin(E, T);
+        if (!(cond_of(Et, (int)T.size()) <= tau_safe)) {
+          T.pop_back();
+          break;
+        }
+      }
+    }
+    const int m = (int)T.size();
+    double cond = INFINITY;
+    std::vector<double> EZ, L, Winv;
+    if (good) {
+      EZ = galerkin(E, T);
+      cond = cond_of(EZ, m);
+      good = cond <= tau_cond && hla::cholesky(m, EZ, L);
+    }
+    S.stats.cond_E[S.outer] = cond;
+    if (!good) {
+      S.deflate = 0;
+      S.stats.fallback[S.outer] = 1;
+      continue;
+    }
+    S.stats.fallback[S.outer] = 0;
+    // Einv = T E_Z^-1 T^T with E_Z^-1 = W W^T, W = L^-T
+    hla::inv_lower_transpose(m, L, Winv);
+    std::vector<double> TW((size_t)k * m, 0.0);  // T W (k x m)
+    for (int i = 0; i < k; ++i)
+      for (int c = 0; c < m; ++c) {
+        double v = 0.0;
+        for (int a = 0; a < m; ++a) v += T[a][i] * Winv[(size_t)a * m + c];
+        TW[(size_t)i * m + c] = v;
+      }
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < k; ++j) {
+        double v = 0.0;
+        for (int c = 0; c < m; ++c) v += TW[(size_t)i * m + c] * TW[(size_t)j * m + c];
+        Ei[(size_t)i * k + j] = v;
+      }
+    CK(cudaMemcpyAsync(Einv_d + (size_t)b * kk, Ei.data(), sizeof(double) * kk,
+                       cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  CK(cudaMemcpyAsync(st_d, st.data(), sizeof(InstState) * B, cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  return SDF_OK;
+}
+
 // Ritz re-selection (Sec. 2.2.3) after k_coarse: for each deflating
 // instance, the eigenpairs (mu, C) of E = Lg^-1 E_raw Lg^-T (the Galerkin
 // matrix of the orthonormalised pool Phi_I Lg^-T) on the host; the r
@@ -2184,10 +2319,16 @@ sdf_status solve_impl(sdf_problem *p, const double *inst, int B, const double *p
         k_coarse_copy<<<B - 1, NT, 0, s>>>(k, Eraw, G);
       CKL("coarse setup");
       {
-        const bool ritz = o.ritz_r > 0 && o.ritz_r < k;
-        k_coarse<<<B, NT, 0, s>>>(k, st, G, Eraw, Einv, coarse, ritz ? INFINITY : o.tau_cond);
+        const bool merge = o.safe_r > 0 && o.safe_r < k;
+        const bool ritz = !merge && o.ritz_r > 0 && o.ritz_r < k;
+        k_coarse<<<B, NT, 0, s>>>(k, st, G, Eraw, Einv, coarse,
+                                  (ritz || merge) ? INFINITY : o.tau_cond, merge ? 1 : 0);
         CKL("k_coarse");
-        if (ritz) {
+        if (merge) {
+          sdf_status e = safe_merge_select(p, B, k, o.safe_r, st, G, Eraw, Einv, o.tau_safe,
+                                           o.tau_dep, o.tau_cond, s);
+          if (e != SDF_OK) return e;
+        } else if (ritz) {
           sdf_status e = ritz_select(p, B, k, o.ritz_r, st, coarse, Einv, o.tau_cond, s);
           if (e != SDF_OK) return e;
         }
@@ -2446,10 +2587,16 @@ sdf_status solve_mixed(sdf_problem *p, const double *inst, int B, const double *
         k_coarse_copy<<<B - 1, NT, 0, s>>>(k, Eraw, G);
       CKL("coarse setup");
       {
-        const bool ritz = o.ritz_r > 0 && o.ritz_r < k;
-        k_coarse<<<B, NT, 0, s>>>(k, st, G, Eraw, Einv, coarse, ritz ? INFINITY : o.tau_cond);
+        const bool merge = o.safe_r > 0 && o.safe_r < k;
+        const bool ritz = !merge && o.ritz_r > 0 && o.ritz_r < k;
+        k_coarse<<<B, NT, 0, s>>>(k, st, G, Eraw, Einv, coarse,
+                                  (ritz || merge) ? INFINITY : o.tau_cond, merge ? 1 : 0);
         CKL("k_coarse");
-        if (ritz) {
+        if (merge) {
+          sdf_status e = safe_merge_select(p, B, k, o.safe_r, st, G, Eraw, Einv, o.tau_safe,
+                                           o.tau_dep, o.tau_cond, s);
+          if (e != SDF_OK) return e;
+        } else if (ritz) {
           sdf_status e = ritz_select(p, B, k, o.ritz_r, st, coarse, Einv, o.tau_cond, s);
           if (e != SDF_OK) return e;
         }
@@ -2611,6 +2758,9 @@ void sdf_default_opts(sdf_opts *o) {
   o->replace_every = 100;
   o->max_launches = 0;
   o->ritz_r = 0;
+  o->safe_r = 0;
+  o->tau_safe = 1e4;
+  o->tau_dep = 1e-10;
 }
 
 sdf_status sdf_problem_create(const sdf_problem_desc *desc, const double *kappa_host,

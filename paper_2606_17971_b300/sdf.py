@@ -43,7 +43,9 @@ class Opts(ctypes.Structure):
                 ("deflate", ctypes.c_int32), ("check_every", ctypes.c_int32),
                 ("profile", ctypes.c_int32), ("max_blocks", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("replace_every", ctypes.c_int32),
-                ("max_launches", ctypes.c_int64), ("ritz_r", ctypes.c_int32)]
+                ("max_launches", ctypes.c_int64), ("ritz_r", ctypes.c_int32),
+                ("safe_r", ctypes.c_int32), ("tau_safe", ctypes.c_double),
+                ("tau_dep", ctypes.c_double)]
 
 
 SDF_NPROF = 9

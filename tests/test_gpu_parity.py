@@ -432,3 +432,44 @@ def test_ritz_reselection_matches_oracle():
         assert np.array_equal(om["active"][b].cpu().numpy().astype(bool), r["active"])
         y = om["y"][b].cpu().numpy()
         assert np.linalg.norm(y - r["y"]) <= 1e-5 * np.linalg.norm(r["y"])
+
+
+def test_safe_merge_matches_oracle():
+    # eigen part: the 6 lowest modes of S; POD candidates: a duplicate of an
+    # eigenmode (skipped), two useful smooth directions, the top mode of S
+    # (ill-conditioning: ends the merge) and one more smooth direction (never
+    # considered).  The oracle runs Algorithm safe on the restricted vectors.
+    from oracle import merge_oracle as M
+    n = (24, 20)
+    P = O.Problem(2, n, alpha=1e-4)
+    S = P.dense_S()
+    lam, V = np.linalg.eigh(S)
+    eig = V[:, :6]
+    rng = np.random.default_rng(5)
+    smooth = np.linalg.qr(V[:, 6:9] + 0.1 * rng.standard_normal((P.N, 3)))[0]
+    pod = np.column_stack([V[:, 2], smooth[:, 0], smooth[:, 1], V[:, -1], smooth[:, 2]])
+    pool = np.asfortranarray(np.column_stack([eig, pod]))
+    w = W.scaled(W.WORKLOADS["diff2d_32"], 24)
+    insts = W.draw_instances(w, count=3)
+    psi = np.ones(P.N)
+    G = sdf.Problem(2, n, alpha=1e-4, yd_sigma=w.sigma)
+    G.set_modes(torch.as_tensor(np.ascontiguousarray(pool.T), device="cuda"))
+    out = G.solve(t64(W.instances_array(insts)), t64(psi), sdf.default_opts(safe_r=6))
+    for b, inst in enumerate(insts):
+        rhs = P.desired_state(inst.a, inst.c[:2], w.sigma)[1]
+        st = out["stats"][b]
+        # replay the outer loop on the oracle with the merged basis of each solve
+        act = np.zeros(P.N, np.uint8)
+        for it in range(st["outer_iters"]):
+            S_II, idx = M.restricted(P, act)
+            Z, acc = M.safe_merge(S_II, eig[idx], pod[idx])
+            Ez = Z.T @ S_II @ Z
+            ev = np.linalg.eigvalsh(0.5 * (Ez + Ez.T))
+            np.testing.assert_allclose(st["cond_E"][it], ev[-1] / ev[0], rtol=1e-6)
+            r = P.inner_solve(act, rhs, psi, M.to_full(Z, idx, P.N))
+            assert abs(st["cg_iters"][it] - r["iters"]) <= max(3, 0.02 * r["iters"])
+            y = np.where(act == 1, psi, r["x"])
+            act = (y > psi - 1e-10).astype(np.uint8) | act
+        assert np.array_equal(out["active"][b].cpu().numpy(), act)
+        ref = P.solve(rhs, psi, eig)
+        assert np.linalg.norm(out["y"][b].cpu().numpy() - ref["y"]) <= 1e-6 * np.linalg.norm(ref["y"])
