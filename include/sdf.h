@@ -376,6 +376,86 @@ sdf_status sdf_reference_modes_coarse(sdf_problem *p, int c, int r_pool, const s
                                       size_t ws_bytes, void *stream);
 
 /* ==========================================================================
+ * Spectral diagnostics (App. A.1 sources of spectral variation, Sec. 4.1 and
+ * App. D spectral-coherence diagnostics).  Off the solve path: tooling that
+ * explains iteration counts.  Each call synchronises its stream before it
+ * returns, and results land in host memory.
+ * ========================================================================== */
+
+/* Active-set distances of B instances from one reference active set:
+ *   sym_diff_host[b] = |A_ref sym-diff A_b|, delta_host[b] = sym_diff / N (Eq. delta),
+ *   n_active_host[b] = |A_b|,               rho_host[b]   = n_active / N (Eq. rho),
+ *   delta_w_host[b]  = sum_j w_j |A_ref(j) - A_b(j)| / sum_j w_j with
+ *                      w_j = sum_{q<r} phi_q(j)^2 over the registered
+ *                      reference modes (the eigenmode-weighted distance of
+ *                      App. D.6); r = 0 skips it (delta_w_host may be NULL),
+ *                      r > 0 needs registered modes with r <= k.
+ * active_ref_dev: N bytes; active_dev: B x N bytes (1 = active), device.
+ * The counts are exact.  delta_w is FP64 and summed in a fixed order, so it
+ * is deterministic.  Any host output may be NULL.  ws: device, 256-byte
+ * aligned, at least sdf_diag_sets_workspace_size bytes. */
+sdf_status sdf_diag_sets_workspace_size(const sdf_problem *p, int B, size_t *bytes);
+sdf_status sdf_diag_active_sets(sdf_problem *p, const uint8_t *active_ref_dev,
+                                const uint8_t *active_dev, int B, int r, int64_t *sym_diff_host,
+                                int64_t *n_active_host, double *delta_host, double *rho_host,
+                                double *delta_w_host, void *ws, size_t ws_bytes, void *stream);
+
+/* Operator drift (Eq. epsilon) of the full-domain Schur complements:
+ *   eps_host[b] = ||S(ref) - S(b)||_2 / ||S(ref)||_2,
+ * with S(ref) and S(b) the operators of the reference instance inst_ref_dev
+ * (SDF_INSTANCE_DOUBLES, device) and of the B instances inst_dev
+ * (B x SDF_INSTANCE_DOUBLES, device).  They differ through the per-instance
+ * convection velocity, the only instance-dependent part of S.  Each 2-norm
+ * is the largest |eigenvalue| of a symmetric operator.  It is computed by
+ * `steps` Lanczos steps with full reorthogonalisation from a fixed
+ * SplitMix64 start vector, each step applying S through sdf_apply_S.  The
+ * result is a lower bound that becomes exact once steps reaches the
+ * dimension, or earlier on an invariant subspace.  A zero difference gives
+ * eps = 0 exactly.  norm_ref_host (may be NULL) receives ||S(ref)||_2.
+ * 1 <= steps <= 1024.  ws: at least sdf_diag_drift_workspace_size bytes. */
+sdf_status sdf_diag_drift_workspace_size(const sdf_problem *p, int steps, size_t *bytes);
+sdf_status sdf_diag_drift(sdf_problem *p, const double *inst_ref_dev, const double *inst_dev,
+                          int B, int steps, double *eps_host, double *norm_ref_host, void *ws,
+                          size_t ws_bytes, void *stream);
+
+/* The k smallest eigenpairs of the restricted operator S_II (App. A.2, whose
+ * spectrum interlaces that of S).  S_II is taken on the inactive set of
+ * active_dev (N bytes, device) for the instance inst_dev (device), as
+ * sdf_apply_S mode 0 applies it; convection is allowed, because S is
+ * symmetric either way.  Method: Chebyshev-filtered subspace iteration as in
+ * sdf_reference_modes_eig, on S_II itself, with the spectrum bounded above by
+ * mass + wgt (Gershgorin bound of A)^2.  The block stays zero on A.
+ * phi_dev receives k orthonormal columns (N doubles, leading dimension ld,
+ * zero on A), lambda_host (k) their eigenvalues in ascending order.  Needs
+ * |I| >= k + guard; SDF_ERR_CG_MAXIT if not converged within o->max_iter.
+ * ws: at least sdf_restricted_eig_workspace_size bytes. */
+sdf_status sdf_restricted_eig_workspace_size(const sdf_problem *p, int k, const sdf_eig_opts *o,
+                                             size_t *bytes);
+sdf_status sdf_restricted_modes_eig(sdf_problem *p, const double *inst_dev,
+                                    const uint8_t *active_dev, int k, const sdf_eig_opts *o,
+                                    double *phi_dev, int64_t ld, double *lambda_host,
+                                    sdf_eig_stats *stats, void *ws, size_t ws_bytes,
+                                    void *stream);
+
+/* Principal angles at every deflation cutoff (Prop. dk, App. A.3, with
+ * S = {1..r}): theta_host[r-1], r = 1..k, is the largest principal angle in
+ * radians between span(Phi_I[:, :r]) and span(V[:, :r]).  Phi_I is the first
+ * r registered reference modes with their rows on the active set of
+ * active_dev zeroed.  V_dev is N x k FP64, column-major, leading dimension
+ * ldv, device: for instance the eigenvectors of S_II from
+ * sdf_restricted_modes_eig.  Both bases are orthonormalised by Cholesky-QR,
+ * which keeps the nested spans.  cos theta_r is the smallest singular value
+ * of the leading r x r block of Q_Phi^T Q_V.  Because the angle is taken
+ * from its cosine, angles below about 1e-7 rad are resolved only to about
+ * that.  SDF_ERR_NOT_SPD if either restricted basis is numerically rank
+ * deficient.  k <= the number of registered modes.
+ * ws: at least sdf_diag_angles_workspace_size bytes. */
+sdf_status sdf_diag_angles_workspace_size(const sdf_problem *p, int k, size_t *bytes);
+sdf_status sdf_diag_angles(sdf_problem *p, const uint8_t *active_dev, const double *V_dev,
+                           int64_t ldv, int k, double *theta_host, void *ws, size_t ws_bytes,
+                           void *stream);
+
+/* ==========================================================================
  * Learned warm start (no counterpart in the paper, which lists learned
  * initialisations only as related work).  A multilayer perceptron maps the
  * instance parameters to the coefficients of a POD basis of solved states

@@ -7,14 +7,22 @@
 // The paper computes its reference modes with ARPACK (Sec. 2.2.2) or in
 // closed form on tensor-product grids (Sec. 2.2.8); this replaces the former.
 //
+// The same driver computes the k smallest eigenpairs of the restricted
+// operator S_II (App. A.2), applied through the solver's own stencil; the
+// file also holds the spectral diagnostics of App. A.1, Sec. 4.1 and App. D
+// (active-set distances, operator drift by Lanczos, principal angles) and
+// the coarse-grid basis of Sec. 2.2.7.
+//
 // Every vector operation is FP64 on the GPU; the m x m Rayleigh-Ritz and
 // Cholesky factorisations run on the host (m = k + guard <= 320).
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -26,6 +34,7 @@
 const sdf::OpParams *sdf_internal_op(const sdf_problem *p, int *nsm, int *convection);
 void sdf_internal_set_error(sdf_problem *p, const char *msg);
 const sdf_problem_desc *sdf_internal_desc(const sdf_problem *p, const double **kappa_host);
+const void *sdf_internal_modes(const sdf_problem *p, int *k, long long *ld, sdf_dtype *dtype);
 
 namespace {
 
@@ -297,73 +306,194 @@ struct BlockOps {
   }
 };
 
-}  // namespace
 
-extern "C" {
+size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-void sdf_default_eig_opts(sdf_eig_opts *o) {
-  if (!o) return;
-  o->tol = 1e-6;
-  o->degree = 60;
-  o->guard = 0;
-  o->max_iter = 400;
-  o->seed = 20260;
-}
-
-static int eig_block(int k, const sdf_eig_opts *o) {
+int eig_block(int k, const sdf_eig_opts *o) {
   const int guard = o->guard > 0 ? o->guard : std::max(16, k / 2);
   return k + guard;
 }
 
-sdf_status sdf_eig_workspace_size(const sdf_problem *p, int k, const sdf_eig_opts *o,
-                                  size_t *bytes) {
-  if (!p || !o || !bytes || k < 1 || k > SDF_MAX_K) return SDF_ERR_INVALID_ARG;
-  int nsm = 148, conv = 0;
-  const OpParams *P = sdf_internal_op(p, &nsm, &conv);
-  if (!P) return SDF_ERR_INVALID_ARG;
-  const int m = eig_block(k, o);
-  if (m > 320) return SDF_ERR_INVALID_ARG;
-  const long long N = P->N;
-  const int nchunk = 2 * nsm;
-  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
-  size_t b = 4 * al(sizeof(double) * (size_t)N * m);
-  b += al(sizeof(double) * (size_t)nchunk * m * m);
-  b += al(sizeof(double) * (size_t)m * m * 2);
-  b += al(sizeof(double) * (size_t)m);
-  *bytes = b;
+// Xn = a Xn + b Xc + c Xp elementwise over n entries (Xn holds Op Xc on
+// entry; Xp is read only when c != 0)
+__global__ void k_comb(double *Xn, const double *Xc, const double *Xp, long long n, double a,
+                       double b, double c) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    double v = fma(a, Xn[e], b * Xc[e]);
+    if (c != 0.0) v = fma(c, Xp[e], v);
+    Xn[e] = v;
+  }
+}
+
+// zero the rows on the active set of the m columns of X (column-major N x m)
+__global__ void k_mask_rows(double *X, long long N, int m, const uint8_t *mask) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N * m;
+       e += (long long)gridDim.x * blockDim.x)
+    if (mask[e % N]) X[e] = 0.0;
+}
+
+// number of inactive nodes (integer atomics: exact and order-independent)
+__global__ void k_count_inactive(const uint8_t *mask, long long N, unsigned long long *cnt) {
+  unsigned long long c = 0;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N;
+       g += (long long)gridDim.x * blockDim.x)
+    c += mask[g] == 0;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(cnt, c);
+}
+
+// Dot products c_j = V_j . x for the first `cols` columns of V (column-major,
+// leading dimension N): partial sums per node chunk, part[j * nchunk + chunk]
+__global__ void __launch_bounds__(ET) k_vtw(const double *V, long long N, const double *x,
+                                            int nchunk, double *part) {
+  __shared__ double red[ET / 32];
+  const int j = blockIdx.y;
+  const long long per = (N + nchunk - 1) / nchunk;
+  const long long g0 = blockIdx.x * per, g1 = min(N, g0 + per);
+  const double *v = V + (long long)j * N;
+  double s = 0.0;
+  for (long long g = g0 + threadIdx.x; g < g1; g += ET) s = fma(v[g], x[g], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < ET / 32; ++q) t += red[q];
+    part[(long long)j * nchunk + blockIdx.x] = t;
+  }
+}
+
+// x -= V c over the first `cols` columns (c in device memory)
+__global__ void k_vsub(const double *V, long long N, int cols, const double *c, double *x) {
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N;
+       g += (long long)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int j = 0; j < cols; ++j) acc = fma(V[(long long)j * N + g], c[j], acc);
+    x[g] -= acc;
+  }
+}
+
+// y = a x + b y (b = 0: y is not read, so it may hold anything)
+__global__ void k_axpby(double *y, const double *x, long long N, double a, double b) {
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N;
+       g += (long long)gridDim.x * blockDim.x)
+    y[g] = b == 0.0 ? a * x[g] : fma(a, x[g], b * y[g]);
+}
+
+// the first k modes (dtype T, leading dimension ld) in FP64 with their rows
+// on the active set zeroed: Phi_I in full-grid layout
+template <class T> __device__ __forceinline__ double to_f64(T v) { return (double)v; }
+template <> __device__ __forceinline__ double to_f64<__nv_bfloat16>(__nv_bfloat16 v) {
+  return (double)__bfloat162float(v);
+}
+template <class T>
+__global__ void k_restrict_modes(const T *phi, long long ld, int k, long long N,
+                                 const uint8_t *mask, double *out) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N * k;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long j = e / N, g = e - j * N;
+    out[e] = (mask && mask[g]) ? 0.0 : to_f64(phi[j * ld + g]);
+  }
+}
+
+// Per instance b (blockIdx.y) and node chunk (blockIdx.x): |A_ref sym-diff
+// A_b|, |A_b|, sum_j w_j [A_ref(j) != A_b(j)] and sum_j w_j, with
+// w_j = sum_{q<r} phi_q(j)^2.  The counts are integers held in doubles
+// (exact below 2^53).
+template <class T>
+__global__ void __launch_bounds__(ET) k_diag_sets(const uint8_t *aref, const uint8_t *act,
+                                                  long long N, const T *phi, long long ld, int r,
+                                                  int nchunk, double *part) {
+  __shared__ double red[4][ET / 32];
+  const int b = blockIdx.y;
+  const uint8_t *ab = act + (long long)b * N;
+  const long long per = (N + nchunk - 1) / nchunk;
+  const long long g0 = blockIdx.x * per, g1 = min(N, g0 + per);
+  double sym = 0.0, na = 0.0, wd = 0.0, ws = 0.0;
+  for (long long g = g0 + threadIdx.x; g < g1; g += ET) {
+    const bool x = aref[g] != 0, y = ab[g] != 0;
+    sym += (x != y);
+    na += y;
+    if (r > 0) {
+      double w = 0.0;
+      for (int q = 0; q < r; ++q) {
+        const double v = to_f64(phi[(long long)q * ld + g]);
+        w = fma(v, v, w);
+      }
+      ws += w;
+      if (x != y) wd += w;
+    }
+  }
+  double v[4] = {sym, na, wd, ws};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
+    if ((threadIdx.x & 31) == 0) red[i][threadIdx.x >> 5] = v[i];
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double t = 0.0;
+    for (int q = 0; q < ET / 32; ++q) t += red[threadIdx.x][q];
+    part[((long long)b * nchunk + blockIdx.x) * 4 + threadIdx.x] = t;
+  }
+}
+
+// Orthonormalise the m columns of *A in place: shifted Cholesky-QR, then
+// Cholesky-QR twice (Fukaya et al., "shifted CholeskyQR3"); the shift
+// 11 (N m + m (m + 1)) u ||A||_F^2 keeps the first factorisation defined
+// however ill-conditioned the block is (shift = false: plain CholeskyQR
+// three times, which fails on a numerically rank-deficient block).  The
+// factor is triangular, so span(Q[:, :r]) = span(A[:, :r]) for every r.
+// *tmp is scratch; the two pointers may be swapped.
+sdf_status cholqr3(BlockOps &ops, double *&A, double *&tmp, int m, bool shift, const char *what) {
+  sdf_problem *p = ops.p;
+  for (int rep = 0; rep < 3; ++rep) {
+    std::vector<double> G, L, Wt;
+    sdf_status e = ops.gram(A, A, m, G);
+    if (e != SDF_OK) return e;
+    if (rep == 0 && shift) {
+      double tr = 0.0;
+      for (int i = 0; i < m; ++i) tr += G[(size_t)i * m + i];
+      const double sh = 11.0 * ((double)ops.N * m + (double)m * (m + 1)) * 1.1102230246251565e-16 * tr;
+      for (int i = 0; i < m; ++i) G[(size_t)i * m + i] += sh;
+    }
+    if (!hla::cholesky(m, G, L)) return efail(p, SDF_ERR_NOT_SPD, what);
+    hla::inv_lower_transpose(m, L, Wt);
+    e = ops.rotate(A, Wt, m, m, tmp);
+    if (e != SDF_OK) return e;
+    std::swap(A, tmp);
+  }
   return SDF_OK;
 }
 
-sdf_status sdf_reference_modes_eig(sdf_problem *p, int k, const sdf_eig_opts *o, double *phi_dev,
-                                   int64_t ld, double *lambda_S_host, double *lambda_A_host,
-                                   sdf_eig_stats *stats, void *ws, size_t ws_bytes, void *stream) {
-  if (!p) return SDF_ERR_INVALID_ARG;
-  sdf_eig_opts def;
-  sdf_default_eig_opts(&def);
-  if (!o) o = &def;
-  size_t need = 0;
-  if (sdf_eig_workspace_size(p, k, o, &need) != SDF_OK)
-    return efail(p, SDF_ERR_INVALID_ARG, "eig: bad k, options or problem (k + guard <= 320)");
-  int nsm = 148, conv = 0;
-  const OpParams *Pp = sdf_internal_op(p, &nsm, &conv);
-  const OpParams P = *Pp;
-  if (conv) return efail(p, SDF_ERR_UNSUPPORTED, "eig: A with convection is not symmetric");
-  if (!phi_dev || ld < P.N || !ws || ((uintptr_t)ws & 255) != 0)
-    return efail(p, SDF_ERR_INVALID_ARG, "eig: bad output or workspace pointer");
-  if (ws_bytes < need) return efail(p, SDF_ERR_WORKSPACE, "eig: workspace too small");
-  if (o->degree < 2 || o->max_iter < 1 || !(o->tol > 0))
-    return efail(p, SDF_ERR_INVALID_ARG, "eig: bad options");
-  const auto t_start = std::chrono::steady_clock::now();
-  cudaStream_t s = (cudaStream_t)stream;
-  const long long N = P.N;
+// Xn = a Op(Xc) + b Xc + c Xp on `cols` columns (c = 0: Xp is not read)
+using ApplyFn = std::function<sdf_status(const double *Xp, const double *Xc, double *Xn, int cols,
+                                         double a, double b, double c)>;
+
+struct ChebResult {
+  std::vector<double> theta;  // Ritz values of the block, ascending
+  int iters = 0, converged = 0;
+  double maxrel = INFINITY;
+  int64_t matvecs = 0;
+};
+
+// Chebyshev-filtered subspace iteration (Zhou & Saad) for the k smallest
+// eigenpairs of a symmetric positive semi-definite operator whose spectrum
+// lies in [0, bmax]: block of m = k + guard columns, adaptive filter degree,
+// shifted CholeskyQR3, Rayleigh-Ritz on the host.  With `mask`, the start
+// block is zero on the masked rows and the operator keeps it so.  The k
+// wanted vectors are copied to phi_dev (leading dimension ld).
+sdf_status cheb_eigs(sdf_problem *p, cudaStream_t s, long long N, int nsm, int k,
+                     const sdf_eig_opts *o, const ApplyFn &op, double bmax, const uint8_t *mask,
+                     void *ws, double *phi_dev, int64_t ld, ChebResult &res) {
   const int m = eig_block(k, o);
   const int nchunk = 2 * nsm;
-  auto al = [](size_t v) { return (v + 255) & ~(size_t)255; };
   char *w = (char *)ws;
   size_t off = 0;
   auto take = [&](size_t b) {
     char *at = w + off;
-    off += al(b);
+    off += al256(b);
     return at;
   };
   double *X = (double *)take(sizeof(double) * (size_t)N * m);
@@ -373,53 +503,21 @@ sdf_status sdf_reference_modes_eig(sdf_problem *p, int k, const sdf_eig_opts *o,
   double *part = (double *)take(sizeof(double) * (size_t)nchunk * m * m);
   double *small = (double *)take(sizeof(double) * (size_t)m * m * 2);
   double *theta_d = (double *)take(sizeof(double) * (size_t)m);
-  int64_t matvecs = 0;
-
   auto apply = [&](const double *Xp, const double *Xc, double *Xn, int cols, double a, double b,
                    double c) -> sdf_status {
-    const dim3 g((unsigned)std::min<long long>((N + ET - 1) / ET, nsm * 4LL), cols);
-    k_cheb<<<g, ET, 0, s>>>(P, Xp, Xc, Xn, N, a, b, c);
-    ECK(cudaGetLastError());
-    matvecs += cols;
-    return SDF_OK;
+    res.matvecs += cols;
+    return op(Xp, Xc, Xn, cols, a, b, c);
   };
   BlockOps ops{p, s, N, nchunk, part, small, m};
-  auto gram = [&](const double *Xa, const double *Ya, std::vector<double> &C) {
-    return ops.gram(Xa, Ya, m, C);
-  };
-  auto rotate = [&](const double *Xa, const std::vector<double> &W, int mo, double *Yo) {
-    return ops.rotate(Xa, W, m, mo, Yo);
-  };
-  // orthonormalise the columns of *A in place: shifted Cholesky-QR, then
-  // Cholesky-QR twice (Fukaya et al., "shifted CholeskyQR3"); the shift
-  // 11 (N m + m (m + 1)) u ||A||^2 keeps the first factorisation defined
-  // however ill-conditioned the filtered block is; *tmp is scratch
-  auto cholqr2 = [&](double *&A, double *&tmp) -> sdf_status {
-    for (int rep = 0; rep < 3; ++rep) {
-      std::vector<double> G, L, Wt;
-      sdf_status e = gram(A, A, G);
-      if (e != SDF_OK) return e;
-      if (rep == 0) {
-        double tr = 0.0;
-        for (int i = 0; i < m; ++i) tr += G[(size_t)i * m + i];
-        const double shift = 11.0 * ((double)N * m + (double)m * (m + 1)) * 1.1102230246251565e-16 * tr;
-        for (int i = 0; i < m; ++i) G[(size_t)i * m + i] += shift;
-      }
-      if (!hla::cholesky(m, G, L)) return efail(p, SDF_ERR_NOT_SPD, "eig: block lost rank");
-      hla::inv_lower_transpose(m, L, Wt);
-      e = rotate(A, Wt, m, tmp);
-      if (e != SDF_OK) return e;
-      std::swap(A, tmp);
-    }
-    return SDF_OK;
-  };
-  std::vector<double> theta(m), V, H;
-  // Rayleigh-Ritz on the orthonormal block *Xb: *Xb <- Xb V, AX = A Xb,
+  std::vector<double> &theta = res.theta;
+  theta.assign(m, 0.0);
+  std::vector<double> V, H;
+  // Rayleigh-Ritz on the orthonormal block *Xb: *Xb <- Xb V, AX = Op Xb,
   // theta ascending
   auto rayleigh_ritz = [&](double *&Xb, double *&tmp) -> sdf_status {
     sdf_status e = apply(nullptr, Xb, AX, m, 1.0, 0.0, 0.0);
     if (e != SDF_OK) return e;
-    e = gram(Xb, AX, H);
+    e = ops.gram(Xb, AX, m, H);
     if (e != SDF_OK) return e;
     for (int i = 0; i < m; ++i)  // symmetrise the rounding
       for (int j = i + 1; j < m; ++j) {
@@ -433,33 +531,25 @@ sdf_status sdf_reference_modes_eig(sdf_problem *p, int k, const sdf_eig_opts *o,
       theta[j] = wv[m - 1 - j];
       for (int i = 0; i < m; ++i) V[(size_t)i * m + j] = Vd[(size_t)i * m + (m - 1 - j)];
     }
-    e = rotate(Xb, V, m, tmp);
+    e = ops.rotate(Xb, V, m, m, tmp);
     if (e != SDF_OK) return e;
     std::swap(Xb, tmp);
-    e = rotate(AX, V, m, tmp);  // A (Xb V) = (A Xb) V
+    e = ops.rotate(AX, V, m, m, tmp);  // Op (Xb V) = (Op Xb) V
     if (e != SDF_OK) return e;
     ECK(cudaMemcpyAsync(AX, tmp, sizeof(double) * (size_t)N * m, cudaMemcpyDeviceToDevice, s));
     return SDF_OK;
   };
 
-  // spectrum bound
-  k_gershgorin<<<nchunk, ET, 0, s>>>(P, N, part);
-  ECK(cudaGetLastError());
-  std::vector<double> gp(nchunk);
-  ECK(cudaMemcpyAsync(gp.data(), part, sizeof(double) * nchunk, cudaMemcpyDeviceToHost, s));
-  ECK(cudaStreamSynchronize(s));
-  const double bmax = 1.01 * *std::max_element(gp.begin(), gp.end());
-
   // start block
   k_rand_block<<<nsm * 8, ET, 0, s>>>(X, N, m, o->seed);
+  if (mask) k_mask_rows<<<nsm * 8, ET, 0, s>>>(X, N, m, mask);
   ECK(cudaGetLastError());
   double *Xb = X, *T1 = Y, *T2 = Z;
-  sdf_status e = cholqr2(Xb, T1);
+  sdf_status e = cholqr3(ops, Xb, T1, m, true, "eig: block lost rank");
   if (e != SDF_OK) return e;
   e = rayleigh_ritz(Xb, T1);
   if (e != SDF_OK) return e;
-  int it = 0, converged = 0;
-  double maxrel = INFINITY;
+  int it = 0;
   std::vector<double> rn(k);
   for (it = 1; it <= o->max_iter; ++it) {
     // scaled Chebyshev filter on [a, bmax], scaled at a0 (Zhou & Saad)
@@ -475,7 +565,7 @@ sdf_status sdf_reference_modes_eig(sdf_problem *p, int k, const sdf_eig_opts *o,
                               : o->degree;
     double sigma = ee / (a0 - cc);
     const double tau = 2.0 / sigma;
-    // T1 = (sigma / e) (A Xb - c Xb)
+    // T1 = (sigma / e) (Op Xb - c Xb)
     e = apply(nullptr, Xb, T1, m, sigma / ee, -cc * sigma / ee, 0.0);
     if (e != SDF_OK) return e;
     double *prev = Xb, *cur = T1, *nxt = T2;
@@ -493,7 +583,7 @@ sdf_status sdf_reference_modes_eig(sdf_problem *p, int k, const sdf_eig_opts *o,
     Xb = cur;
     T1 = prev;
     T2 = nxt;
-    e = cholqr2(Xb, T1);
+    e = cholqr3(ops, Xb, T1, m, true, "eig: block lost rank");
     if (e != SDF_OK) return e;
     e = rayleigh_ritz(Xb, T1);
     if (e != SDF_OK) return e;
@@ -504,35 +594,507 @@ sdf_status sdf_reference_modes_eig(sdf_problem *p, int k, const sdf_eig_opts *o,
     std::vector<double> rp((size_t)k * nchunk);
     ECK(cudaMemcpyAsync(rp.data(), part, sizeof(double) * k * nchunk, cudaMemcpyDeviceToHost, s));
     ECK(cudaStreamSynchronize(s));
-    maxrel = 0.0;
+    res.maxrel = 0.0;
     for (int j = 0; j < k; ++j) {
       double r2 = 0.0;
       for (int c = 0; c < nchunk; ++c) r2 += rp[(size_t)j * nchunk + c];
       rn[j] = std::sqrt(r2);
-      maxrel = std::max(maxrel, rn[j] / std::fabs(theta[j]));
+      res.maxrel = std::max(res.maxrel, rn[j] / std::fabs(theta[j]));
     }
-    if (maxrel <= o->tol) {
-      converged = 1;
+    if (res.maxrel <= o->tol) {
+      res.converged = 1;
       break;
     }
   }
+  res.iters = std::min(it, o->max_iter);
   // output: the k wanted vectors (unit norm, column-major with leading dim ld)
   ECK(cudaMemcpy2DAsync(phi_dev, sizeof(double) * ld, Xb, sizeof(double) * N, sizeof(double) * N, k,
                         cudaMemcpyDeviceToDevice, s));
   ECK(cudaStreamSynchronize(s));
+  return SDF_OK;
+}
+
+// Number of eigenvalues below x of the symmetric tridiagonal T (diagonal al,
+// off-diagonal be), by the signs of the pivots of T - x I (Sturm sequence;
+// Golub & Van Loan, Sec. 8.4); a zero pivot is replaced by a tiny one.
+int sturm_count(const std::vector<double> &al, const std::vector<double> &be, double x) {
+  int cnt = 0;
+  double q = 1.0;
+  for (size_t i = 0; i < al.size(); ++i) {
+    const double b2 = i > 0 ? be[i - 1] * be[i - 1] : 0.0;
+    q = (al[i] - x) - (i > 0 ? b2 / q : 0.0);
+    if (q == 0.0) q = -1e-300;
+    if (q < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+// The smallest and largest eigenvalues of T by bisection on the Sturm count
+// inside the Gershgorin interval (to the spacing of doubles).
+void tridiag_extremes(const std::vector<double> &al, const std::vector<double> &be, double &lo_out,
+                      double &hi_out) {
+  const size_t m = al.size();
+  double lo = INFINITY, hi = -INFINITY;
+  for (size_t i = 0; i < m; ++i) {
+    const double r = (i > 0 ? std::fabs(be[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(be[i]) : 0.0);
+    lo = std::min(lo, al[i] - r);
+    hi = std::max(hi, al[i] + r);
+  }
+  auto bisect = [&](int target) {  // the smallest x with count(x) > target
+    double a = lo, b = hi;
+    for (int it = 0; it < 200 && b - a > 0.0; ++it) {
+      const double c = 0.5 * (a + b);
+      if (c <= a || c >= b) break;
+      if (sturm_count(al, be, c) > target) b = c;
+      else a = c;
+    }
+    return 0.5 * (a + b);
+  };
+  lo_out = bisect(0);
+  hi_out = bisect((int)m - 1);
+}
+
+// Largest |eigenvalue| of a symmetric operator on N-vectors by Lanczos with
+// full reorthogonalisation (classical Gram-Schmidt applied twice per step),
+// from the SplitMix64 start vector `seed`.  Stops after `steps` steps, at N,
+// or when the new residual norm beta falls to 1e-14 of the largest
+// coefficient seen (an invariant subspace).  V holds steps + 1 columns of N;
+// x is one N-vector of scratch; cdev at least steps + 1 doubles.
+sdf_status lanczos_absmax(sdf_problem *p, cudaStream_t s, long long N, int nsm, int steps,
+                          uint64_t seed, const std::function<sdf_status(const double *, double *)> &op,
+                          double *V, double *x, double *part, double *cdev, double &out) {
+  const int nchunk = 2 * nsm;
+  const unsigned grid = (unsigned)std::min<long long>((N + ET - 1) / ET, nsm * 8LL);
+  auto dots = [&](const double *Vb, int cols, const double *y, std::vector<double> &c) -> sdf_status {
+    k_vtw<<<dim3(nchunk, cols), ET, 0, s>>>(Vb, N, y, nchunk, part);
+    ECK(cudaGetLastError());
+    std::vector<double> pp((size_t)cols * nchunk);
+    ECK(cudaMemcpyAsync(pp.data(), part, sizeof(double) * pp.size(), cudaMemcpyDeviceToHost, s));
+    ECK(cudaStreamSynchronize(s));
+    c.assign(cols, 0.0);
+    for (int j = 0; j < cols; ++j)
+      for (int q = 0; q < nchunk; ++q) c[j] += pp[(size_t)j * nchunk + q];
+    return SDF_OK;
+  };
+  k_rand_block<<<grid, ET, 0, s>>>(V, N, 1, seed);
+  ECK(cudaGetLastError());
+  std::vector<double> c, c2;
+  sdf_status e = dots(V, 1, V, c);
+  if (e != SDF_OK) return e;
+  k_axpby<<<grid, ET, 0, s>>>(V, V, N, 1.0 / std::sqrt(c[0]), 0.0);
+  std::vector<double> al, be;
+  double scale = 0.0;
+  const int jmax = (int)std::min<long long>(steps, N);
+  for (int j = 0; j < jmax; ++j) {
+    double *vj = V + (size_t)j * N;
+    e = op(vj, x);
+    if (e != SDF_OK) return e;
+    double alpha = 0.0;
+    for (int pass = 0; pass < 2; ++pass) {
+      e = dots(V, j + 1, x, c);
+      if (e != SDF_OK) return e;
+      alpha += c[j];
+      ECK(cudaMemcpyAsync(cdev, c.data(), sizeof(double) * (j + 1), cudaMemcpyHostToDevice, s));
+      k_vsub<<<grid, ET, 0, s>>>(V, N, j + 1, cdev, x);
+      ECK(cudaGetLastError());
+    }
+    e = dots(x, 1, x, c2);
+    if (e != SDF_OK) return e;
+    const double beta = std::sqrt(c2[0]);
+    al.push_back(alpha);
+    scale = std::max(scale, std::max(std::fabs(alpha), beta));
+    if (j + 1 == jmax || beta <= 1e-14 * scale) break;
+    be.push_back(beta);
+    k_axpby<<<grid, ET, 0, s>>>(V + (size_t)(j + 1) * N, x, N, 1.0 / beta, 0.0);
+    ECK(cudaGetLastError());
+  }
+  double lo = 0.0, hi = 0.0;
+  tridiag_extremes(al, be, lo, hi);
+  out = std::max(std::fabs(lo), std::fabs(hi));
+  return SDF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void sdf_default_eig_opts(sdf_eig_opts *o) {
+  if (!o) return;
+  o->tol = 1e-6;
+  o->degree = 60;
+  o->guard = 0;
+  o->max_iter = 400;
+  o->seed = 20260;
+}
+
+sdf_status sdf_eig_workspace_size(const sdf_problem *p, int k, const sdf_eig_opts *o,
+                                  size_t *bytes) {
+  if (!p || !o || !bytes || k < 1 || k > SDF_MAX_K) return SDF_ERR_INVALID_ARG;
+  int nsm = 148, conv = 0;
+  const OpParams *P = sdf_internal_op(p, &nsm, &conv);
+  if (!P) return SDF_ERR_INVALID_ARG;
+  const int m = eig_block(k, o);
+  if (m > 320) return SDF_ERR_INVALID_ARG;
+  const long long N = P->N;
+  const int nchunk = 2 * nsm;
+  size_t b = 4 * al256(sizeof(double) * (size_t)N * m);
+  b += al256(sizeof(double) * (size_t)nchunk * m * m);
+  b += al256(sizeof(double) * (size_t)m * m * 2);
+  b += al256(sizeof(double) * (size_t)m);
+  *bytes = b;
+  return SDF_OK;
+}
+
+static void fill_eig_stats(sdf_eig_stats *stats, const ChebResult &r,
+                           std::chrono::steady_clock::time_point t0) {
+  if (!stats) return;
+  stats->iters = r.iters;
+  stats->converged = r.converged;
+  stats->max_rel_resid = r.maxrel;
+  stats->matvecs = r.matvecs;
+  stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+sdf_status sdf_reference_modes_eig(sdf_problem *p, int k, const sdf_eig_opts *o, double *phi_dev,
+                                   int64_t ld, double *lambda_S_host, double *lambda_A_host,
+                                   sdf_eig_stats *stats, void *ws, size_t ws_bytes, void *stream) {
+  if (!p) return SDF_ERR_INVALID_ARG;
+  sdf_eig_opts def;
+  sdf_default_eig_opts(&def);
+  if (!o) o = &def;
+  size_t need = 0;
+  if (sdf_eig_workspace_size(p, k, o, &need) != SDF_OK)
+    return efail(p, SDF_ERR_INVALID_ARG, "eig: bad k, options or problem (k + guard <= 320)");
+  int nsm = 148, conv = 0;
+  const OpParams P = *sdf_internal_op(p, &nsm, &conv);
+  if (conv) return efail(p, SDF_ERR_UNSUPPORTED, "eig: A with convection is not symmetric");
+  if (!phi_dev || ld < P.N || !ws || ((uintptr_t)ws & 255) != 0)
+    return efail(p, SDF_ERR_INVALID_ARG, "eig: bad output or workspace pointer");
+  if (ws_bytes < need) return efail(p, SDF_ERR_WORKSPACE, "eig: workspace too small");
+  if (o->degree < 2 || o->max_iter < 1 || !(o->tol > 0))
+    return efail(p, SDF_ERR_INVALID_ARG, "eig: bad options");
+  const auto t_start = std::chrono::steady_clock::now();
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long N = P.N;
+  const int nchunk = 2 * nsm;
+  // spectrum bound of A (Gershgorin), into the partials area of the workspace
+  double *gpart = (double *)((char *)ws + 4 * al256(sizeof(double) * (size_t)N * eig_block(k, o)));
+  k_gershgorin<<<nchunk, ET, 0, s>>>(P, N, gpart);
+  ECK(cudaGetLastError());
+  std::vector<double> gp(nchunk);
+  ECK(cudaMemcpyAsync(gp.data(), gpart, sizeof(double) * nchunk, cudaMemcpyDeviceToHost, s));
+  ECK(cudaStreamSynchronize(s));
+  const double bmax = 1.01 * *std::max_element(gp.begin(), gp.end());
+  // the operator: A by its stencil (the eigenvectors of S are those of A)
+  ApplyFn opA = [&](const double *Xp, const double *Xc, double *Xn, int cols, double a, double b,
+                    double c) -> sdf_status {
+    const dim3 g((unsigned)std::min<long long>((N + ET - 1) / ET, nsm * 4LL), cols);
+    k_cheb<<<g, ET, 0, s>>>(P, Xp, Xc, Xn, N, a, b, c);
+    ECK(cudaGetLastError());
+    return SDF_OK;
+  };
+  ChebResult r;
+  sdf_status e = cheb_eigs(p, s, N, nsm, k, o, opA, bmax, nullptr, ws, phi_dev, ld, r);
+  if (e != SDF_OK) return e;
   for (int j = 0; j < k; ++j) {
-    if (lambda_A_host) lambda_A_host[j] = theta[j];
-    if (lambda_S_host) lambda_S_host[j] = P.mass + P.wgt * theta[j] * theta[j];
+    if (lambda_A_host) lambda_A_host[j] = r.theta[j];
+    if (lambda_S_host) lambda_S_host[j] = P.mass + P.wgt * r.theta[j] * r.theta[j];
   }
-  if (stats) {
-    stats->iters = std::min(it, o->max_iter);
-    stats->converged = converged;
-    stats->max_rel_resid = maxrel;
-    stats->matvecs = matvecs;
-    stats->seconds =
-        std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  fill_eig_stats(stats, r, t_start);
+  return r.converged ? SDF_OK : efail(p, SDF_ERR_CG_MAXIT, "eig: not converged within max_iter");
+}
+
+sdf_status sdf_restricted_eig_workspace_size(const sdf_problem *p, int k, const sdf_eig_opts *o,
+                                             size_t *bytes) {
+  size_t b = 0;
+  const sdf_status e = sdf_eig_workspace_size(p, k, o, &b);
+  if (e != SDF_OK) return e;
+  *bytes = b + al256(sizeof(unsigned long long));
+  return SDF_OK;
+}
+
+sdf_status sdf_restricted_modes_eig(sdf_problem *p, const double *inst_dev,
+                                    const uint8_t *active_dev, int k, const sdf_eig_opts *o,
+                                    double *phi_dev, int64_t ld, double *lambda_host,
+                                    sdf_eig_stats *stats, void *ws, size_t ws_bytes,
+                                    void *stream) {
+  if (!p) return SDF_ERR_INVALID_ARG;
+  sdf_eig_opts def;
+  sdf_default_eig_opts(&def);
+  if (!o) o = &def;
+  size_t need = 0;
+  if (sdf_restricted_eig_workspace_size(p, k, o, &need) != SDF_OK)
+    return efail(p, SDF_ERR_INVALID_ARG, "restricted eig: bad k, options or problem");
+  int nsm = 148, conv = 0;
+  const OpParams P = *sdf_internal_op(p, &nsm, &conv);
+  if (!inst_dev || !active_dev || !phi_dev || ld < P.N || !ws || ((uintptr_t)ws & 255) != 0)
+    return efail(p, SDF_ERR_INVALID_ARG, "restricted eig: bad pointer");
+  if (ws_bytes < need) return efail(p, SDF_ERR_WORKSPACE, "restricted eig: workspace too small");
+  if (o->degree < 2 || o->max_iter < 1 || !(o->tol > 0))
+    return efail(p, SDF_ERR_INVALID_ARG, "restricted eig: bad options");
+  const auto t_start = std::chrono::steady_clock::now();
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long N = P.N;
+  const int m = eig_block(k, o);
+  const int nchunk = 2 * nsm;
+  size_t eb = 0;
+  sdf_eig_workspace_size(p, k, o, &eb);
+  unsigned long long *cnt = (unsigned long long *)((char *)ws + eb);
+  // |I| >= m, or the block cannot stay of full rank on I
+  ECK(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s));
+  k_count_inactive<<<nsm * 4, ET, 0, s>>>(active_dev, N, cnt);
+  ECK(cudaGetLastError());
+  unsigned long long nI = 0;
+  ECK(cudaMemcpyAsync(&nI, cnt, sizeof(nI), cudaMemcpyDeviceToHost, s));
+  // spectrum bound: ||A||_2 <= max row sum of |A| (and column sum, the same
+  // bound here): twice the diffusion face sum (Gershgorin kernel) plus
+  // 2 sum_d |b_d| / h_d for the upwind convection of this instance
+  double *gpart = (double *)((char *)ws + 4 * al256(sizeof(double) * (size_t)N * m));
+  k_gershgorin<<<nchunk, ET, 0, s>>>(P, N, gpart);
+  ECK(cudaGetLastError());
+  std::vector<double> gp(nchunk);
+  double inst_h[SDF_INSTANCE_DOUBLES];
+  ECK(cudaMemcpyAsync(gp.data(), gpart, sizeof(double) * nchunk, cudaMemcpyDeviceToHost, s));
+  ECK(cudaMemcpyAsync(inst_h, inst_dev, sizeof(inst_h), cudaMemcpyDeviceToHost, s));
+  ECK(cudaStreamSynchronize(s));
+  if ((long long)nI < m)
+    return efail(p, SDF_ERR_INVALID_ARG, "restricted eig: fewer inactive nodes than k + guard");
+  double bA = *std::max_element(gp.begin(), gp.end());
+  if (conv)
+    for (int d = 0; d < P.dim; ++d) bA += 2.0 * std::fabs(inst_h[4 + d]) * P.inv_h[d];
+  const double bmax = 1.01 * (P.mass + P.wgt * bA * bA);
+  // the operator: S_II through the solver's own stencil (mode 0), column by
+  // column, then the three-term combination
+  ApplyFn opS = [&](const double *Xp, const double *Xc, double *Xn, int cols, double a, double b,
+                    double c) -> sdf_status {
+    for (int j = 0; j < cols; ++j) {
+      const sdf_status e = sdf_apply_S(p, inst_dev, active_dev, Xc + (size_t)j * N,
+                                       Xn + (size_t)j * N, 0, nullptr, 0, stream);
+      if (e != SDF_OK) return e;
+    }
+    if (a != 1.0 || b != 0.0 || c != 0.0) {
+      k_comb<<<nsm * 8, ET, 0, s>>>(Xn, Xc, Xp, N * cols, a, b, c);
+      ECK(cudaGetLastError());
+    }
+    return SDF_OK;
+  };
+  ChebResult r;
+  sdf_status e = cheb_eigs(p, s, N, nsm, k, o, opS, bmax, active_dev, ws, phi_dev, ld, r);
+  if (e != SDF_OK) return e;
+  if (lambda_host)
+    for (int j = 0; j < k; ++j) lambda_host[j] = r.theta[j];
+  fill_eig_stats(stats, r, t_start);
+  return r.converged ? SDF_OK
+                     : efail(p, SDF_ERR_CG_MAXIT, "restricted eig: not converged within max_iter");
+}
+
+static int diag_chunks(long long N, int nsm) {
+  return (int)std::max<long long>(1, std::min<long long>((N + 4LL * ET - 1) / (4LL * ET), 2LL * nsm));
+}
+
+sdf_status sdf_diag_sets_workspace_size(const sdf_problem *p, int B, size_t *bytes) {
+  int nsm = 148, conv = 0;
+  const OpParams *P = p ? sdf_internal_op(p, &nsm, &conv) : nullptr;
+  if (!P || !bytes || B < 1) return SDF_ERR_INVALID_ARG;
+  *bytes = al256(sizeof(double) * 4 * (size_t)B * diag_chunks(P->N, nsm));
+  return SDF_OK;
+}
+
+sdf_status sdf_diag_active_sets(sdf_problem *p, const uint8_t *active_ref_dev,
+                                const uint8_t *active_dev, int B, int r, int64_t *sym_diff_host,
+                                int64_t *n_active_host, double *delta_host, double *rho_host,
+                                double *delta_w_host, void *ws, size_t ws_bytes, void *stream) {
+  if (!p) return SDF_ERR_INVALID_ARG;
+  size_t need = 0;
+  if (sdf_diag_sets_workspace_size(p, B, &need) != SDF_OK)
+    return efail(p, SDF_ERR_INVALID_ARG, "diag sets: unbound problem or B < 1");
+  int nsm = 148, conv = 0;
+  const OpParams P = *sdf_internal_op(p, &nsm, &conv);
+  if (!active_ref_dev || !active_dev || !ws || ((uintptr_t)ws & 255) != 0)
+    return efail(p, SDF_ERR_INVALID_ARG, "diag sets: bad pointer");
+  if (ws_bytes < need) return efail(p, SDF_ERR_WORKSPACE, "diag sets: workspace too small");
+  int k = 0;
+  long long ld = 0;
+  sdf_dtype dt = SDF_F64;
+  const void *phi = sdf_internal_modes(p, &k, &ld, &dt);
+  if (r < 0 || (r > 0 && (!phi || r > k)))
+    return efail(p, SDF_ERR_INVALID_ARG, "diag sets: r must be 0 or at most the registered modes");
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long N = P.N;
+  const int nchunk = diag_chunks(N, nsm);
+  double *part = (double *)ws;
+  const dim3 g(nchunk, B);
+  if (r == 0 || dt == SDF_F64)
+    k_diag_sets<double><<<g, ET, 0, s>>>(active_ref_dev, active_dev, N, (const double *)phi, ld, r,
+                                         nchunk, part);
+  else if (dt == SDF_F32)
+    k_diag_sets<float><<<g, ET, 0, s>>>(active_ref_dev, active_dev, N, (const float *)phi, ld, r,
+                                        nchunk, part);
+  else
+    k_diag_sets<__nv_bfloat16><<<g, ET, 0, s>>>(active_ref_dev, active_dev, N,
+                                                (const __nv_bfloat16 *)phi, ld, r, nchunk, part);
+  ECK(cudaGetLastError());
+  std::vector<double> pp((size_t)4 * B * nchunk);
+  ECK(cudaMemcpyAsync(pp.data(), part, sizeof(double) * pp.size(), cudaMemcpyDeviceToHost, s));
+  ECK(cudaStreamSynchronize(s));
+  for (int b = 0; b < B; ++b) {
+    double t[4] = {0, 0, 0, 0};
+    for (int c = 0; c < nchunk; ++c)
+      for (int i = 0; i < 4; ++i) t[i] += pp[((size_t)b * nchunk + c) * 4 + i];
+    if (sym_diff_host) sym_diff_host[b] = (int64_t)t[0];
+    if (n_active_host) n_active_host[b] = (int64_t)t[1];
+    if (delta_host) delta_host[b] = t[0] / (double)N;
+    if (rho_host) rho_host[b] = t[1] / (double)N;
+    if (delta_w_host && r > 0) delta_w_host[b] = t[3] > 0.0 ? t[2] / t[3] : 0.0;
   }
-  return converged ? SDF_OK : efail(p, SDF_ERR_CG_MAXIT, "eig: not converged within max_iter");
+  return SDF_OK;
+}
+
+sdf_status sdf_diag_drift_workspace_size(const sdf_problem *p, int steps, size_t *bytes) {
+  int nsm = 148, conv = 0;
+  const OpParams *P = p ? sdf_internal_op(p, &nsm, &conv) : nullptr;
+  if (!P || !bytes || steps < 1 || steps > 1024) return SDF_ERR_INVALID_ARG;
+  const long long N = P->N;
+  *bytes = al256(sizeof(double) * (size_t)N * (steps + 1)) + 3 * al256(sizeof(double) * (size_t)N) +
+           al256(sizeof(double) * (size_t)2 * nsm * (steps + 1)) +
+           al256(sizeof(double) * (size_t)(steps + 1));
+  return SDF_OK;
+}
+
+sdf_status sdf_diag_drift(sdf_problem *p, const double *inst_ref_dev, const double *inst_dev,
+                          int B, int steps, double *eps_host, double *norm_ref_host, void *ws,
+                          size_t ws_bytes, void *stream) {
+  if (!p) return SDF_ERR_INVALID_ARG;
+  size_t need = 0;
+  if (sdf_diag_drift_workspace_size(p, steps, &need) != SDF_OK)
+    return efail(p, SDF_ERR_INVALID_ARG, "diag drift: unbound problem or steps not in [1, 1024]");
+  int nsm = 148, conv = 0;
+  const OpParams P = *sdf_internal_op(p, &nsm, &conv);
+  if (!inst_ref_dev || (B > 0 && (!inst_dev || !eps_host)) || B < 0 || !ws ||
+      ((uintptr_t)ws & 255) != 0)
+    return efail(p, SDF_ERR_INVALID_ARG, "diag drift: bad pointer or B");
+  if (ws_bytes < need) return efail(p, SDF_ERR_WORKSPACE, "diag drift: workspace too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long N = P.N;
+  char *w = (char *)ws;
+  double *V = (double *)w;
+  w += al256(sizeof(double) * (size_t)N * (steps + 1));
+  double *x = (double *)w;
+  w += al256(sizeof(double) * (size_t)N);
+  double *t1 = (double *)w;
+  w += al256(sizeof(double) * (size_t)N);
+  double *t2 = (double *)w;
+  w += al256(sizeof(double) * (size_t)N);
+  double *part = (double *)w;
+  w += al256(sizeof(double) * (size_t)2 * nsm * (steps + 1));
+  double *cdev = (double *)w;
+  const unsigned grid = (unsigned)std::min<long long>((N + ET - 1) / ET, nsm * 8LL);
+  const uint64_t seed = 0x5dee7ULL;
+  // ||S(ref)||_2: S(ref) is positive definite, its largest eigenvalue
+  double nref = 0.0;
+  sdf_status e = lanczos_absmax(
+      p, s, N, nsm, steps, seed,
+      [&](const double *v, double *y) {
+        return sdf_apply_S(p, inst_ref_dev, nullptr, v, y, 1, nullptr, 0, stream);
+      },
+      V, x, part, cdev, nref);
+  if (e != SDF_OK) return e;
+  if (norm_ref_host) *norm_ref_host = nref;
+  for (int b = 0; b < B; ++b) {
+    const double *ib = inst_dev + (size_t)b * SDF_INSTANCE_DOUBLES;
+    double nd = 0.0;
+    e = lanczos_absmax(
+        p, s, N, nsm, steps, seed,
+        [&](const double *v, double *y) -> sdf_status {
+          sdf_status q = sdf_apply_S(p, inst_ref_dev, nullptr, v, t1, 1, nullptr, 0, stream);
+          if (q != SDF_OK) return q;
+          q = sdf_apply_S(p, ib, nullptr, v, t2, 1, nullptr, 0, stream);
+          if (q != SDF_OK) return q;
+          ECK(cudaMemcpyAsync(y, t1, sizeof(double) * (size_t)N, cudaMemcpyDeviceToDevice, s));
+          k_axpby<<<grid, ET, 0, s>>>(y, t2, N, -1.0, 1.0);
+          ECK(cudaGetLastError());
+          return SDF_OK;
+        },
+        V, x, part, cdev, nd);
+    if (e != SDF_OK) return e;
+    eps_host[b] = nref > 0.0 ? nd / nref : 0.0;
+  }
+  return SDF_OK;
+}
+
+sdf_status sdf_diag_angles_workspace_size(const sdf_problem *p, int k, size_t *bytes) {
+  int nsm = 148, conv = 0;
+  const OpParams *P = p ? sdf_internal_op(p, &nsm, &conv) : nullptr;
+  if (!P || !bytes || k < 1 || k > SDF_MAX_K) return SDF_ERR_INVALID_ARG;
+  const long long N = P->N;
+  *bytes = 3 * al256(sizeof(double) * (size_t)N * k) +
+           al256(sizeof(double) * (size_t)2 * nsm * k * k) + al256(sizeof(double) * (size_t)2 * k * k);
+  return SDF_OK;
+}
+
+sdf_status sdf_diag_angles(sdf_problem *p, const uint8_t *active_dev, const double *V_dev,
+                           int64_t ldv, int k, double *theta_host, void *ws, size_t ws_bytes,
+                           void *stream) {
+  if (!p) return SDF_ERR_INVALID_ARG;
+  size_t need = 0;
+  if (sdf_diag_angles_workspace_size(p, k, &need) != SDF_OK)
+    return efail(p, SDF_ERR_INVALID_ARG, "diag angles: unbound problem or bad k");
+  int nsm = 148, conv = 0;
+  const OpParams P = *sdf_internal_op(p, &nsm, &conv);
+  int kr = 0;
+  long long ld = 0;
+  sdf_dtype dt = SDF_F64;
+  const void *phi = sdf_internal_modes(p, &kr, &ld, &dt);
+  if (!phi || k > kr) return efail(p, SDF_ERR_INVALID_ARG, "diag angles: k above the registered modes");
+  if (!active_dev || !V_dev || ldv < P.N || !theta_host || !ws || ((uintptr_t)ws & 255) != 0)
+    return efail(p, SDF_ERR_INVALID_ARG, "diag angles: bad pointer");
+  if (ws_bytes < need) return efail(p, SDF_ERR_WORKSPACE, "diag angles: workspace too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long N = P.N;
+  const int nchunk = 2 * nsm;
+  char *w = (char *)ws;
+  double *Qp = (double *)w;
+  w += al256(sizeof(double) * (size_t)N * k);
+  double *Qv = (double *)w;
+  w += al256(sizeof(double) * (size_t)N * k);
+  double *T = (double *)w;
+  w += al256(sizeof(double) * (size_t)N * k);
+  double *part = (double *)w;
+  w += al256(sizeof(double) * (size_t)nchunk * k * k);
+  double *small = (double *)w;
+  const unsigned grid = (unsigned)std::min<long long>((N * k + ET - 1) / ET, nsm * 8LL);
+  if (dt == SDF_F64)
+    k_restrict_modes<double><<<grid, ET, 0, s>>>((const double *)phi, ld, k, N, active_dev, Qp);
+  else if (dt == SDF_F32)
+    k_restrict_modes<float><<<grid, ET, 0, s>>>((const float *)phi, ld, k, N, active_dev, Qp);
+  else
+    k_restrict_modes<__nv_bfloat16><<<grid, ET, 0, s>>>((const __nv_bfloat16 *)phi, ld, k, N,
+                                                         active_dev, Qp);
+  ECK(cudaGetLastError());
+  ECK(cudaMemcpy2DAsync(Qv, sizeof(double) * N, V_dev, sizeof(double) * ldv, sizeof(double) * N, k,
+                        cudaMemcpyDeviceToDevice, s));
+  BlockOps ops{p, s, N, nchunk, part, small, k};
+  double *A1 = Qp, *A2 = Qv, *tmp = T;
+  sdf_status e = cholqr3(ops, A1, tmp, k, false, "diag angles: restricted modes rank deficient");
+  if (e != SDF_OK) return e;
+  e = cholqr3(ops, A2, tmp, k, false, "diag angles: V rank deficient");
+  if (e != SDF_OK) return e;
+  std::vector<double> C;
+  e = ops.gram(A1, A2, k, C);  // C[i][j] = q_phi,i . q_v,j
+  if (e != SDF_OK) return e;
+  for (int r = 1; r <= k; ++r) {
+    std::vector<double> M((size_t)r * r, 0.0), wv, Vd;
+    for (int i = 0; i < r; ++i)
+      for (int j = 0; j < r; ++j) {
+        double t = 0.0;
+        for (int q = 0; q < r; ++q) t += C[(size_t)q * k + i] * C[(size_t)q * k + j];
+        M[(size_t)i * r + j] = t;
+      }
+    hla::jacobi_eig(r, M, wv, Vd);  // descending: wv[r - 1] = sigma_min^2
+    const double c = std::sqrt(std::min(1.0, std::max(0.0, wv[r - 1])));
+    theta_host[r - 1] = std::acos(c);
+  }
+  return SDF_OK;
 }
 
 static void coarse_sizes(const sdf_problem_desc *d, int c, int nc[3], long long *Nc) {
@@ -712,5 +1274,6 @@ sdf_status sdf_reference_modes_coarse(sdf_problem *p, int c, int r_pool, const s
   if (r_out) *r_out = rk;
   return SDF_OK;
 }
+
 
 }  // extern "C"

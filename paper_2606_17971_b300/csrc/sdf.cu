@@ -2737,6 +2737,14 @@ const sdf_problem_desc *sdf_internal_desc(const sdf_problem *p, const double **k
   if (kappa_host) *kappa_host = p->kappa.empty() ? nullptr : p->kappa.data();
   return &p->d;
 }
+// the registered reference modes (nullptr when none)
+const void *sdf_internal_modes(const sdf_problem *p, int *k, long long *ld, sdf_dtype *dtype) {
+  if (!p || !p->phi) return nullptr;
+  *k = p->k;
+  *ld = p->ld;
+  *dtype = p->phi_dtype;
+  return p->phi;
+}
 
 // ===========================================================================
 // C ABI

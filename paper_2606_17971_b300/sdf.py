@@ -126,6 +126,16 @@ _sigs = {
     "sdf_coarse_modes_workspace_size": (_i32, [_vp, _i32, _i32, _vp, ctypes.POINTER(_sz)]),
     "sdf_reference_modes_coarse": (_i32, [_vp, _i32, _i32, _vp, ctypes.c_double, _vp, _i64,
                                           ctypes.POINTER(_i32), _vp, _vp, _vp, _sz, _vp]),
+    "sdf_diag_sets_workspace_size": (_i32, [_vp, _i32, ctypes.POINTER(_sz)]),
+    "sdf_diag_active_sets": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _sz,
+                                    _vp]),
+    "sdf_diag_drift_workspace_size": (_i32, [_vp, _i32, ctypes.POINTER(_sz)]),
+    "sdf_diag_drift": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp, _vp, _vp, _sz, _vp]),
+    "sdf_restricted_eig_workspace_size": (_i32, [_vp, _i32, _vp, ctypes.POINTER(_sz)]),
+    "sdf_restricted_modes_eig": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _i64, _vp, _vp, _vp, _sz,
+                                        _vp]),
+    "sdf_diag_angles_workspace_size": (_i32, [_vp, _i32, ctypes.POINTER(_sz)]),
+    "sdf_diag_angles": (_i32, [_vp, _vp, _vp, _i64, _i32, _vp, _vp, _sz, _vp]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(_lib, _name)
@@ -267,6 +277,78 @@ class Problem:
         stats = dict(iters=st.iters, converged=bool(st.converged), max_rel_resid=st.max_rel_resid,
                      matvecs=st.matvecs, seconds=st.seconds)
         return phi[:r.value].contiguous(), lam, stats
+
+    # spectral diagnostics -----------------------------------------------------
+    def _scratch(self, size_fn, *args):
+        nb = _sz()
+        self._check(size_fn(self._h, *args, ctypes.byref(nb)))
+        return torch.empty(max(int(nb.value), 256), dtype=torch.uint8, device=self.device)
+
+    def diag_active_sets(self, active_ref: torch.Tensor, active: torch.Tensor, r=0):
+        """sdf_diag_active_sets: active-set distances (Eq. delta, Eq. rho and
+        the mode-weighted delta_w over the first r registered modes) of the
+        B masks `active` (B, N) uint8 from `active_ref` (N,) uint8."""
+        assert active_ref.dtype == torch.uint8 and active.dtype == torch.uint8
+        act = active.reshape(-1, self.N).contiguous()
+        B = act.shape[0]
+        ws = self._scratch(_lib.sdf_diag_sets_workspace_size, B)
+        sym, na = np.zeros(B, np.int64), np.zeros(B, np.int64)
+        dl, rh, dw = np.zeros(B), np.zeros(B), np.zeros(B)
+        self._check(_lib.sdf_diag_active_sets(self._h, _ptr(active_ref.contiguous()), _ptr(act), B,
+                                              r, sym.ctypes.data, na.ctypes.data, dl.ctypes.data,
+                                              rh.ctypes.data, dw.ctypes.data if r > 0 else None,
+                                              _ptr(ws), ws.numel(), _stream()))
+        return dict(sym_diff=sym, n_active=na, delta=dl, rho=rh, delta_w=dw if r > 0 else None)
+
+    def diag_drift(self, inst_ref: torch.Tensor, inst: torch.Tensor, steps=200):
+        """sdf_diag_drift: eps_b = ||S(ref) - S(b)||_2 / ||S(ref)||_2 (Eq.
+        epsilon) by Lanczos; returns (eps (B,), ||S(ref)||_2)."""
+        inst = inst.reshape(-1, 7).contiguous()
+        B = inst.shape[0]
+        ws = self._scratch(_lib.sdf_diag_drift_workspace_size, steps)
+        eps = np.zeros(B)
+        nref = ctypes.c_double(0.0)
+        self._check(_lib.sdf_diag_drift(self._h, _ptr(inst_ref.contiguous()), _ptr(inst), B, steps,
+                                        eps.ctypes.data, ctypes.byref(nref), _ptr(ws), ws.numel(),
+                                        _stream()))
+        return eps, nref.value
+
+    def restricted_modes(self, inst: torch.Tensor, active: torch.Tensor, k, **kw):
+        """sdf_restricted_modes_eig: the k smallest eigenpairs of S_II on the
+        inactive set of `active` (N,) uint8 for one instance (7,); returns
+        V (k, N) float64 (row j = eigenvector j, zero on A), lambda, stats."""
+        o = EigOpts()
+        _lib.sdf_default_eig_opts(ctypes.byref(o))
+        for key, v in kw.items():
+            setattr(o, key, v)
+        nb = _sz()
+        self._check(_lib.sdf_restricted_eig_workspace_size(self._h, k, ctypes.byref(o),
+                                                           ctypes.byref(nb)))
+        ws = torch.empty(int(nb.value), dtype=torch.uint8, device=self.device)
+        V = torch.empty((k, self.N), dtype=torch.float64, device=self.device)
+        lam = np.zeros(k)
+        st = EigStats()
+        rc = _lib.sdf_restricted_modes_eig(self._h, _ptr(inst.contiguous()),
+                                           _ptr(active.contiguous()), k, ctypes.byref(o), _ptr(V),
+                                           self.N, lam.ctypes.data, ctypes.byref(st), _ptr(ws),
+                                           ws.numel(), _stream())
+        if rc not in (0, 5):
+            self._check(rc)
+        stats = dict(iters=st.iters, converged=bool(st.converged), max_rel_resid=st.max_rel_resid,
+                     matvecs=st.matvecs, seconds=st.seconds, status=rc)
+        return V, lam, stats
+
+    def diag_angles(self, active: torch.Tensor, V: torch.Tensor, k=None):
+        """sdf_diag_angles: theta_r (radians), r = 1..k, the largest principal
+        angle between span(Phi_I[:, :r]) (registered modes restricted to the
+        inactive set) and span(V[:r]) for V (k, N) float64."""
+        k = V.shape[0] if k is None else k
+        assert V.dtype == torch.float64 and V.is_contiguous() and V.shape[1] == self.N
+        ws = self._scratch(_lib.sdf_diag_angles_workspace_size, k)
+        th = np.zeros(k)
+        self._check(_lib.sdf_diag_angles(self._h, _ptr(active.contiguous()), _ptr(V), self.N, k,
+                                         th.ctypes.data, _ptr(ws), ws.numel(), _stream()))
+        return th
 
     # workspace --------------------------------------------------------------
     def workspace(self, batch, opts=None, host_io=False):
