@@ -92,6 +92,8 @@ def lib():
         _lib.orc_create.argtypes = [ctypes.c_int] * 4 + [dp, ctypes.c_double, dp,
                                                           ctypes.c_double, ctypes.c_double,
                                                           ctypes.c_double]
+        _lib.orc_create_csr.restype = P
+        _lib.orc_create_csr.argtypes = [ctypes.c_int, ip, ip, dp]
         _lib.orc_destroy.argtypes = [P]
         for f in ("orc_size", "orc_nnz_A", "orc_nnz_S"):
             getattr(_lib, f).argtypes = [P]
@@ -152,6 +154,25 @@ class Problem:
         if not self._h:
             raise ValueError("orc_create failed")
         self.N = L.orc_size(self._h)
+
+    @classmethod
+    def from_csr(cls, S):
+        """A problem given by its Schur complement S (scipy.sparse, N x N;
+        copied), for operators assembled outside the C file: the solves and
+        the S products only (no grid, no A, no desired state)."""
+        S = S.tocsr()
+        S.sort_indices()
+        rp = np.ascontiguousarray(S.indptr, dtype=np.int32)
+        ci = np.ascontiguousarray(S.indices, dtype=np.int32)
+        v = np.ascontiguousarray(S.data, dtype=np.float64)
+        self = cls.__new__(cls)
+        self._h = lib().orc_create_csr(S.shape[0], _ip(rp), _ip(ci), _dp(v))
+        if not self._h:
+            raise ValueError("orc_create_csr failed")
+        self.dim, self.n, self.N = 1, (S.shape[0],), S.shape[0]
+        self.kappa = self.b = None
+        self.mass, self.alpha, self.kscale = 1.0, None, 1.0
+        return self
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:

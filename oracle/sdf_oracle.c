@@ -367,6 +367,38 @@ void *orc_create(int dim, int nx, int ny, int nz, const double *kappa,
   return P;
 }
 
+/* A problem given by its Schur complement S itself (CSR, FP64, N rows,
+ * copied): for operators assembled outside this file, such as the
+ * space-time S_st = alpha F^T F + I of App. E.2.  A is left empty (no
+ * entries) and the desired state is unavailable; the solves, the S products
+ * and the S rows use S alone. */
+void *orc_create_csr(int N, const int *rp, const int *ci, const double *v) {
+  if (N < 1 || !rp || !ci || !v || rp[0] != 0) return NULL;
+  orc_problem *P = (orc_problem *)calloc(1, sizeof(orc_problem));
+  if (!P) return NULL;
+  P->dim = 1;
+  P->nx = N;
+  P->ny = P->nz = 1;
+  P->N = N;
+  P->h[0] = 1.0 / (N + 1);
+  P->h[1] = P->h[2] = 1.0;
+  P->alpha = P->mass = P->kscale = 1.0;
+  const int nnz = rp[N];
+  P->A.n = P->S.n = N;
+  P->A.rp = (int *)calloc((size_t)N + 1, sizeof(int));
+  P->S.rp = (int *)malloc(sizeof(int) * ((size_t)N + 1));
+  P->S.ci = (int *)malloc(sizeof(int) * ((size_t)nnz + 1));
+  P->S.v = (double *)malloc(sizeof(double) * ((size_t)nnz + 1));
+  if (!P->A.rp || !P->S.rp || !P->S.ci || !P->S.v) {
+    orc_destroy(P);
+    return NULL;
+  }
+  memcpy(P->S.rp, rp, sizeof(int) * ((size_t)N + 1));
+  memcpy(P->S.ci, ci, sizeof(int) * (size_t)nnz);
+  memcpy(P->S.v, v, sizeof(double) * (size_t)nnz);
+  return P;
+}
+
 int orc_size(void *h) { return ((orc_problem *)h)->N; }
 int orc_nnz_A(void *h) { return ((orc_problem *)h)->A.rp[((orc_problem *)h)->N]; }
 int orc_nnz_S(void *h) { return ((orc_problem *)h)->S.rp[((orc_problem *)h)->N]; }
