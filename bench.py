@@ -204,6 +204,46 @@ def cpu_sample(w, inst, m_iters=20):
     return r["t_setup"], r["t_loop"] / max(1, r["iters"]), os.cpu_count()
 
 
+def spacetime_leg(w, sdf, dev):
+    """The space-time workload (App. E.2) on the FP64 path: one batch of
+    its instances with the Kronecker basis I_nt (x) Z_s, with the
+    constant-in-time lift 1_nt (x) Z_s / sqrt(n_t), and with plain PCG, each
+    timed with CUDA events after one warm-up solve (not part of the metric)."""
+    import torch
+    from paper_2606_17971_b300 import workloads as W
+    n_t = w.extra["n_t"]
+    G = sdf.Problem(3, (w.n, w.n, n_t), alpha=w.alpha, yd_sigma=w.sigma, time_axis=True,
+                    t_final=w.extra["t_final"], ramp_tau=w.extra["ramp_tau"], device=dev)
+    zs, _ = sdf.Problem(2, w.n, alpha=w.alpha, yd_sigma=w.sigma, device=dev).analytic_modes(w.k)
+    kron = G.spacetime_kron_modes(zs)
+    lift = (zs / np.sqrt(n_t)).repeat(1, n_t).contiguous()  # row j: mode j on every step
+    inst = torch.as_tensor(W.instances_array(W.draw_instances(w, count=w.batch)), device=dev)
+    psi = torch.full((G.N,), w.psi, dtype=torch.float64, device=dev)
+    res = {"workload": w.name, "grid": [w.n, w.n], "n_t": n_t, "N": G.N, "instances": w.batch,
+           "spatial_modes": w.k, "path": "FP64 A-DEF2 (primal active-set loop)"}
+    stream = torch.cuda.current_stream()
+    for name, phi in (("kronecker", kron), ("constant_lift", lift), ("plain", None)):
+        o = sdf.default_opts(check_every=128, deflate=int(phi is not None))
+        if phi is not None:
+            G.set_modes(phi)
+        G.solve(inst[:1].contiguous(), psi, o, want_lambda=False)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        r = G.solve(inst, psi, o, want_lambda=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[name] = {"instances_per_s": w.batch / (e0.elapsed_time(e1) * 1e-3),
+                     "cg_iters_per_instance": float(np.mean([sum(s["cg_iters"]) for s in r["stats"]])),
+                     "outer_iters_per_instance": float(np.mean([s["outer_iters"] for s in r["stats"]])),
+                     "rank": 0 if phi is None else int(phi.shape[0]),
+                     "statuses": sorted(set(s["status"] for s in r["stats"]))}
+    c0 = res["plain"]["cg_iters_per_instance"]
+    res["iteration_reduction"] = {k: 1.0 - res[k]["cg_iters_per_instance"] / c0
+                                  for k in ("kronecker", "constant_lift")}
+    return res
+
+
 def oracle_counts(name):
     path = os.path.join(ROOT, "tests", "golden", f"{name}_oracle.json")
     if not os.path.exists(path):
@@ -278,6 +318,11 @@ def main():
     ap.add_argument("--eig-degree", type=int, default=240)
     ap.add_argument("--eig-coarse", type=int, default=2,
                     help="also time the coarse-grid basis (Sec. 2.2.7) with this factor (0: off)")
+    ap.add_argument("--spacetime", default="spacetime2d_64",
+                    help="also time the space-time workload (App. E.2) with the Kronecker "
+                         "basis, the constant-in-time lift and plain PCG ('' : off)")
+    ap.add_argument("--no-diag", action="store_true",
+                    help="skip timing the active-set diagnostics on the last batch")
     args = ap.parse_args()
 
     from paper_2606_17971_b300 import workloads as W
@@ -546,6 +591,23 @@ def main():
                 "columns_kept": int(phc.shape[0]), "coarse_passes": cst["iters"],
                 "method": "eigenpairs on the grid coarsened by the factor, linear prolongation, QR"}
         del Ge
+    if not args.no_diag and rank == 0:
+        # Eq. delta / Eq. rho / the mode-weighted distance of the last timed
+        # batch's active sets from its first instance's (not part of the metric)
+        ref = out["active"][0].clone()
+        G.diag_active_sets(ref, out["active"], r=w.k)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        dg = G.diag_active_sets(ref, out["active"], r=w.k)
+        td = time.perf_counter() - t0
+        line["diagnostics"] = {
+            "active_sets": B, "N": w.N, "r": w.k, "ms": 1e3 * td,
+            "mask_and_mode_gb_per_s": (B * w.N + w.N + w.N * w.k * phi_bytes * ((B + 7) // 8))
+                                      / td / 1e9,
+            "delta_max": float(dg["delta"].max()), "rho_mean": float(dg["rho"].mean()),
+            "note": "sdf_diag_active_sets, host round trip included"}
+    if args.spacetime and rank == 0:
+        line["spacetime"] = spacetime_leg(W.WORKLOADS[args.spacetime], sdf, dev)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

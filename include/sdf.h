@@ -86,7 +86,24 @@ typedef struct sdf_problem sdf_problem;
  *   has_kappa    1: node diffusivity given to sdf_problem_create, 0: kappa = 1
  *   convection   1: each instance carries its upwind convection velocity b
  *   yd_sigma     width of the Gaussian desired state
- *                y_d(x) = a exp(-|x - c|^2 / (2 yd_sigma^2)), rhs = mass y_d */
+ *                y_d(x) = a exp(-|x - c|^2 / (2 yd_sigma^2)), rhs = mass y_d
+ *   time_axis    1: the all-at-once space-time problem (App. E.2) of the
+ *                parabolic state equation y_t + A_x y = u, y(., 0) = 0, on
+ *                (0, t_final] with implicit Euler.  Needs dim = 3: axes 0 and
+ *                1 are space (unit square, n[0] x n[1] interior nodes),
+ *                axis 2 is time with n[2] steps of dt = t_final / n[2].  The
+ *                forward operator F (block lower bidiagonal: I/dt + A_x on
+ *                the diagonal, -I/dt below) takes the place of A, so
+ *                S = mass I + wgt F^T F; there is no diffusion along time
+ *                (time faces of kappa are unused), and an instance's
+ *                convection velocity, if any, acts in space only (b_z is
+ *                ignored).  The desired state is ramped in time (App. F.5):
+ *                y_d(x, t_l) = (1 - exp(-t_l / ramp_tau)) a exp(-|x - c|^2 /
+ *                (2 yd_sigma^2)), x in space, t_l = (l + 1) dt.
+ *                FP64 path only (SDF_PREC_MIXED is refused, as for
+ *                convection).  0: the steady problem (t_final, ramp_tau
+ *                unused).
+ *   t_final, ramp_tau  (> 0 when time_axis = 1) */
 typedef struct {
   int32_t dim;
   int32_t n[3];
@@ -97,6 +114,9 @@ typedef struct {
   int32_t has_kappa;
   int32_t convection;
   double yd_sigma;
+  int32_t time_axis;
+  double t_final;
+  double ramp_tau;
 } sdf_problem_desc;
 
 /* Solve options (defaults from sdf_default_opts).
@@ -195,6 +215,32 @@ sdf_status sdf_set_reference_modes(sdf_problem *p, const void *phi_dev, int k, i
  * the modes (call sdf_set_reference_modes). */
 sdf_status sdf_analytic_modes(sdf_problem *p, int k, void *phi_dev, int64_t ld, sdf_dtype dtype,
                               double *eigvals_host, void *stream);
+
+/* Space-time Kronecker deflation basis (App. E.2.1 Eq. kron_basis):
+ * Phi_st = I_{n_t} (x) Z_s for a problem with time_axis = 1.  Z_s (device,
+ * N_s = n[0] n[1] rows, r columns, leading dimension ldz, dtype) is a
+ * spatial basis, e.g. sdf_analytic_modes of the 2D problem on the same
+ * spatial grid.  phi_dev (device, N rows, r n_t columns, leading dimension
+ * ld, the same dtype) receives column l r + j = Z_s[:, j] on time step l
+ * and zero elsewhere.  r n_t <= SDF_MAX_K. */
+sdf_status sdf_spacetime_kron_modes(sdf_problem *p, const void *zs_dev, int r, int64_t ldz,
+                                    sdf_dtype dtype, void *phi_dev, int64_t ld, void *stream);
+
+/* A general temporal factor (App. E.2.1): Phi_st = W_t (x) Z_s with W_t
+ * (host, n_t x r_t, column-major, FP64) and Z_s as above; column a r + j is
+ * spatial mode j scaled by W_t[l, a] on time step l (the product in FP64,
+ * rounded once to dtype).  W_t = I gives the Kronecker basis, the DCT-II
+ * columns of sdf_dct2_basis the paper's cosine basis.  n_t r_t <= 1024,
+ * r r_t <= SDF_MAX_K. */
+sdf_status sdf_spacetime_modes(sdf_problem *p, const double *wt_host, int rt, const void *zs_dev,
+                               int r, int64_t ldz, sdf_dtype dtype, void *phi_dev, int64_t ld,
+                               void *stream);
+
+/* The first r orthonormal DCT-II basis vectors of length n as the columns
+ * of w_host (n x r, column-major):
+ * w[l, a] = sqrt((2 - [a = 0]) / n) cos(pi (l + 1/2) a / n).  1 <= r <= n;
+ * other arguments leave w_host untouched.  Host only. */
+void sdf_dct2_basis(int n, int r, double *w_host);
 
 /* Workspace bytes for a batch of `batch` instances under `opts`. */
 sdf_status sdf_workspace_size(const sdf_problem *p, int batch, const sdf_opts *opts,
@@ -428,7 +474,12 @@ sdf_status sdf_diag_drift(sdf_problem *p, const double *inst_ref_dev, const doub
  * phi_dev receives k orthonormal columns (N doubles, leading dimension ld,
  * zero on A), lambda_host (k) their eigenvalues in ascending order.  Needs
  * |I| >= k + guard; SDF_ERR_CG_MAXIT if not converged within o->max_iter.
- * ws: at least sdf_restricted_eig_workspace_size bytes. */
+ * o = NULL takes sdf_default_restricted_eig_opts: degree 200, guard
+ * max(32, k/2), tol 1e-8 (the low spectrum of S_II is that of A squared, so
+ * a filter degree gains about the square root of what it gains on A, and
+ * the attainable relative residual is about 1e-16 ||S|| / lambda_1).
+ * ws: at least sdf_restricted_eig_workspace_size bytes (o may be NULL). */
+void sdf_default_restricted_eig_opts(int k, sdf_eig_opts *o);
 sdf_status sdf_restricted_eig_workspace_size(const sdf_problem *p, int k, const sdf_eig_opts *o,
                                              size_t *bytes);
 sdf_status sdf_restricted_modes_eig(sdf_problem *p, const double *inst_dev,

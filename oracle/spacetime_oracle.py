@@ -16,8 +16,9 @@ App. E.2 and App. F.5 (space-time), written out from their definitions:
   y_d(x, t_l) = (1 - exp(-t_l / tau)) a exp(-|x - c|^2 / (2 sigma^2)) at the
   interior nodes x_j = (j + 1) h and t_l = l dt, l = 1..n_t; rhs = mass y_d.
 * Deflation bases (App. E.2.1): the Kronecker expansion
-  Z_st = I_{n_t} (x) Z_s (Eq. kron_basis) and the constant-in-time lift
-  1_{n_t} (x) Z_s / sqrt(n_t).
+  Z_st = I_{n_t} (x) Z_s (Eq. kron_basis), the cosine basis W_t (x) Z_s with
+  W_t the first r_t columns of the orthonormal DCT-II matrix, and the
+  constant-in-time lift 1_{n_t} (x) Z_s / sqrt(n_t).
 * The primal active-set loop and A-DEF2 are the C oracle's (the same
   algorithm as the steady problem), run on S_st given as CSR.
 
@@ -87,6 +88,20 @@ def kron_basis(Z_s, n_t):
     """Z_st = I_{n_t} (x) Z_s (Eq. kron_basis): column l r + j is spatial
     mode j on time step l."""
     return np.asfortranarray(np.kron(np.identity(n_t), np.asarray(Z_s, np.float64)))
+
+
+def dct2_basis(n_t, r_t):
+    """The first r_t orthonormal DCT-II basis vectors of length n_t (columns):
+    W[l, a] = sqrt((2 - [a = 0]) / n_t) cos(pi (l + 1/2) a / n_t)."""
+    l = np.arange(n_t)[:, None] + 0.5
+    a = np.arange(r_t)[None, :]
+    return np.sqrt(np.where(a == 0, 1.0, 2.0) / n_t) * np.cos(np.pi * l * a / n_t)
+
+
+def temporal_basis(W_t, Z_s):
+    """W_t (x) Z_s: column a r + j is spatial mode j weighted by W_t[l, a] on
+    time step l (the Kronecker basis is W_t = I, the cosine basis the DCT-II)."""
+    return np.asfortranarray(np.kron(np.asarray(W_t, np.float64), np.asarray(Z_s, np.float64)))
 
 
 def constant_lift(Z_s, n_t):

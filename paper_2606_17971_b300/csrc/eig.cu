@@ -397,45 +397,59 @@ __global__ void k_restrict_modes(const T *phi, long long ld, int k, long long N,
   }
 }
 
-// Per instance b (blockIdx.y) and node chunk (blockIdx.x): |A_ref sym-diff
-// A_b|, |A_b|, sum_j w_j [A_ref(j) != A_b(j)] and sum_j w_j, with
-// w_j = sum_{q<r} phi_q(j)^2.  The counts are integers held in doubles
-// (exact below 2^53).
+// Per node chunk (blockIdx.x) and group of DSB instances (blockIdx.y):
+// |A_ref sym-diff A_b|, |A_b|, sum_j w_j [A_ref(j) != A_b(j)] and sum_j w_j,
+// with w_j = sum_{q<r} phi_q(j)^2 computed once per node for the group (the
+// modes are read B / DSB times, the masks once).  The counts are integers
+// held in doubles (exact below 2^53).  part[(b nchunk + chunk) 4 + i].
+constexpr int DSB = 8;
 template <class T>
-__global__ void __launch_bounds__(ET) k_diag_sets(const uint8_t *aref, const uint8_t *act,
+__global__ void __launch_bounds__(ET) k_diag_sets(const uint8_t *aref, const uint8_t *act, int B,
                                                   long long N, const T *phi, long long ld, int r,
                                                   int nchunk, double *part) {
-  __shared__ double red[4][ET / 32];
-  const int b = blockIdx.y;
-  const uint8_t *ab = act + (long long)b * N;
+  constexpr int NV = 3 * DSB + 1;
+  __shared__ double red[NV][ET / 32];
+  const int b0 = blockIdx.y * DSB;
+  const int nb = min(DSB, B - b0);
   const long long per = (N + nchunk - 1) / nchunk;
   const long long g0 = blockIdx.x * per, g1 = min(N, g0 + per);
-  double sym = 0.0, na = 0.0, wd = 0.0, ws = 0.0;
+  double v[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) v[i] = 0.0;
   for (long long g = g0 + threadIdx.x; g < g1; g += ET) {
-    const bool x = aref[g] != 0, y = ab[g] != 0;
-    sym += (x != y);
-    na += y;
-    if (r > 0) {
-      double w = 0.0;
-      for (int q = 0; q < r; ++q) {
-        const double v = to_f64(phi[(long long)q * ld + g]);
-        w = fma(v, v, w);
+    const bool x = aref[g] != 0;
+    double w = 0.0;
+    for (int q = 0; q < r; ++q) {
+      const double f = to_f64(phi[(long long)q * ld + g]);
+      w = fma(f, f, w);
+    }
+    v[3 * DSB] += w;
+#pragma unroll
+    for (int bb = 0; bb < DSB; ++bb) {
+      if (bb < nb) {
+        const bool y = act[(long long)(b0 + bb) * N + g] != 0;
+        v[3 * bb] += (x != y);
+        v[3 * bb + 1] += y;
+        if (x != y) v[3 * bb + 2] += w;
       }
-      ws += w;
-      if (x != y) wd += w;
     }
   }
-  double v[4] = {sym, na, wd, ws};
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < NV; ++i) {
     for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
     if ((threadIdx.x & 31) == 0) red[i][threadIdx.x >> 5] = v[i];
   }
   __syncthreads();
-  if (threadIdx.x < 4) {
-    double t = 0.0;
-    for (int q = 0; q < ET / 32; ++q) t += red[threadIdx.x][q];
-    part[((long long)b * nchunk + blockIdx.x) * 4 + threadIdx.x] = t;
+  if (threadIdx.x < 3 * nb) {
+    const int bb = threadIdx.x / 3, i = threadIdx.x % 3;
+    double t = 0.0, ws = 0.0;
+    for (int q = 0; q < ET / 32; ++q) {
+      t += red[threadIdx.x][q];
+      ws += red[3 * DSB][q];
+    }
+    double *o = part + ((long long)(b0 + bb) * nchunk + blockIdx.x) * 4;
+    o[i] = t;
+    if (i == 0) o[3] = ws;
   }
 }
 
@@ -804,8 +818,22 @@ sdf_status sdf_reference_modes_eig(sdf_problem *p, int k, const sdf_eig_opts *o,
   return r.converged ? SDF_OK : efail(p, SDF_ERR_CG_MAXIT, "eig: not converged within max_iter");
 }
 
+void sdf_default_restricted_eig_opts(int k, sdf_eig_opts *o) {
+  if (!o) return;
+  sdf_default_eig_opts(o);
+  // S_II's low spectrum is that of A squared and compressed against a bound
+  // of wgt ||A||^2, so each filter degree gains about the square root of
+  // what it gains on A: a longer filter and a wider guard
+  o->degree = 200;
+  o->guard = std::max(32, k / 2);
+  o->tol = 1e-8;
+}
+
 sdf_status sdf_restricted_eig_workspace_size(const sdf_problem *p, int k, const sdf_eig_opts *o,
                                              size_t *bytes) {
+  sdf_eig_opts def;
+  sdf_default_restricted_eig_opts(k, &def);
+  if (!o) o = &def;
   size_t b = 0;
   const sdf_status e = sdf_eig_workspace_size(p, k, o, &b);
   if (e != SDF_OK) return e;
@@ -820,7 +848,7 @@ sdf_status sdf_restricted_modes_eig(sdf_problem *p, const double *inst_dev,
                                     void *stream) {
   if (!p) return SDF_ERR_INVALID_ARG;
   sdf_eig_opts def;
-  sdf_default_eig_opts(&def);
+  sdf_default_restricted_eig_opts(k, &def);
   if (!o) o = &def;
   size_t need = 0;
   if (sdf_restricted_eig_workspace_size(p, k, o, &need) != SDF_OK)
@@ -848,7 +876,8 @@ sdf_status sdf_restricted_modes_eig(sdf_problem *p, const double *inst_dev,
   ECK(cudaMemcpyAsync(&nI, cnt, sizeof(nI), cudaMemcpyDeviceToHost, s));
   // spectrum bound: ||A||_2 <= max row sum of |A| (and column sum, the same
   // bound here): twice the diffusion face sum (Gershgorin kernel) plus
-  // 2 sum_d |b_d| / h_d for the upwind convection of this instance
+  // 2 sum_d |b_d| / h_d for the upwind convection of this instance, and
+  // 2 / dt along the time axis of a space-time problem
   double *gpart = (double *)((char *)ws + 4 * al256(sizeof(double) * (size_t)N * m));
   k_gershgorin<<<nchunk, ET, 0, s>>>(P, N, gpart);
   ECK(cudaGetLastError());
@@ -860,8 +889,10 @@ sdf_status sdf_restricted_modes_eig(sdf_problem *p, const double *inst_dev,
   if ((long long)nI < m)
     return efail(p, SDF_ERR_INVALID_ARG, "restricted eig: fewer inactive nodes than k + guard");
   double bA = *std::max_element(gp.begin(), gp.end());
-  if (conv)
-    for (int d = 0; d < P.dim; ++d) bA += 2.0 * std::fabs(inst_h[4 + d]) * P.inv_h[d];
+  for (int d = 0; d < P.dim; ++d) {
+    if (P.time_axis && d == 2) bA += 2.0 * P.cb_t;  // the implicit Euler difference
+    else if (P.inst_conv) bA += 2.0 * std::fabs(inst_h[4 + d]) * P.inv_h[d];
+  }
   const double bmax = 1.01 * (P.mass + P.wgt * bA * bA);
   // the operator: S_II through the solver's own stencil (mode 0), column by
   // column, then the three-term combination
@@ -923,15 +954,15 @@ sdf_status sdf_diag_active_sets(sdf_problem *p, const uint8_t *active_ref_dev,
   const long long N = P.N;
   const int nchunk = diag_chunks(N, nsm);
   double *part = (double *)ws;
-  const dim3 g(nchunk, B);
+  const dim3 g(nchunk, (B + DSB - 1) / DSB);
   if (r == 0 || dt == SDF_F64)
-    k_diag_sets<double><<<g, ET, 0, s>>>(active_ref_dev, active_dev, N, (const double *)phi, ld, r,
-                                         nchunk, part);
+    k_diag_sets<double><<<g, ET, 0, s>>>(active_ref_dev, active_dev, B, N, (const double *)phi, ld,
+                                         r, nchunk, part);
   else if (dt == SDF_F32)
-    k_diag_sets<float><<<g, ET, 0, s>>>(active_ref_dev, active_dev, N, (const float *)phi, ld, r,
-                                        nchunk, part);
+    k_diag_sets<float><<<g, ET, 0, s>>>(active_ref_dev, active_dev, B, N, (const float *)phi, ld,
+                                        r, nchunk, part);
   else
-    k_diag_sets<__nv_bfloat16><<<g, ET, 0, s>>>(active_ref_dev, active_dev, N,
+    k_diag_sets<__nv_bfloat16><<<g, ET, 0, s>>>(active_ref_dev, active_dev, B, N,
                                                 (const __nv_bfloat16 *)phi, ld, r, nchunk, part);
   ECK(cudaGetLastError());
   std::vector<double> pp((size_t)4 * B * nchunk);

@@ -96,8 +96,11 @@ inline size_t expand_tc_smem(int nbp, int kp) {
 // ---------------------------------------------------------------------------
 // helpers
 
+// Upwind coefficients b_d / h_d of an instance; on a space-time problem the
+// time axis takes 1 / dt instead (implicit Euler, App. E.2), whatever b_z is.
 __device__ __forceinline__ void inst_cb(const OpParams &P, const double *inst, double cb[3]) {
-  for (int d = 0; d < 3; ++d) cb[d] = (P.convection && d < P.dim) ? inst[4 + d] * P.inv_h[d] : 0.0;
+  for (int d = 0; d < 3; ++d) cb[d] = (P.inst_conv && d < P.dim) ? inst[4 + d] * P.inv_h[d] : 0.0;
+  if (P.time_axis) cb[2] = P.cb_t;
 }
 
 __device__ __forceinline__ double desired(const OpParams &P, const double *inst, int gx, int gy,
@@ -105,6 +108,10 @@ __device__ __forceinline__ double desired(const OpParams &P, const double *inst,
   double dx = (gx + 1) * P.h[0] - inst[1];
   double dy = (gy + 1) * P.h[1] - inst[2];
   double r2 = dx * dx + dy * dy;
+  if (P.time_axis) {  // App. F.5: the spatial Gaussian ramped in time
+    const double t = (gz + 1) * P.dt;
+    return (1.0 - exp(-t / P.ramp_tau)) * inst[0] * exp(-r2 / (2.0 * P.yd_sigma * P.yd_sigma));
+  }
   if (P.dim == 3) {
     double dz = (gz + 1) * P.h[2] - inst[3];
     r2 += dz * dz;
@@ -145,7 +152,8 @@ __global__ void k_faces(OpParams P, const double *kappa, double diff_scale, doub
       long long t = f / P.nx;
       int j = (int)(t % P.ny), l = (int)(t / P.ny);
       double kf = l == 0 ? kap(i, j, 0) : l == P.nz ? kap(i, j, P.nz - 1) : hm(kap(i, j, l - 1), kap(i, j, l));
-      fz[f] = diff_scale * kf * P.inv_h[2] * P.inv_h[2];
+      // no diffusion along the time axis of a space-time problem
+      fz[f] = P.time_axis ? 0.0 : diff_scale * kf * P.inv_h[2] * P.inv_h[2];
       fzf[f] = (float)fz[f];
     }
   }
@@ -1868,6 +1876,44 @@ __global__ void __launch_bounds__(NT) k_apply(OpParams P, const double *inst,
   }
 }
 
+// Space-time Kronecker basis (App. E.2.1 Eq. kron_basis): column
+// c = l r + j of Phi (N rows, leading dimension ld) is spatial mode j
+// (zs, Ns rows, leading dimension ldz) on time step l, zero elsewhere.
+template <class T>
+__global__ void k_kron_time(const T *zs, long long ldz, int r, long long Ns, int nt, T *phi,
+                            long long ld) {
+  const long long N = Ns * nt, total = N * (long long)r * nt;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long c = e / N, g = e - c * N;
+    const int l = (int)(c / r), j = (int)(c - (long long)l * r);
+    const long long slab = g / Ns;
+    phi[c * ld + g] = slab == l ? zs[j * ldz + (g - slab * Ns)] : T(0.0f);
+  }
+}
+
+// Space-time basis W_t (x) Z_s (App. E.2.1): column c = a r + j of Phi is
+// spatial mode j times W_t[l, a] on time step l.  W_t (n_t x r_t,
+// column-major) travels in the kernel's parameters.
+constexpr int SDF_TB_MAX = 1024;
+struct TemporalBasis {
+  int nt, rt;
+  double w[SDF_TB_MAX];
+};
+template <class T>
+__global__ void k_time_basis(const TemporalBasis tb, const T *zs, long long ldz, int r, long long Ns,
+                             T *phi, long long ld) {
+  const long long N = Ns * tb.nt, total = N * (long long)r * tb.rt;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long c = e / N, g = e - c * N;
+    const int a = (int)(c / r), j = (int)(c - (long long)a * r);
+    const int l = (int)(g / Ns);
+    const double v = tb.w[l + a * tb.nt] * (double)zs[j * ldz + (g - (long long)l * Ns)];
+    phi[c * ld + g] = (T)v;
+  }
+}
+
 // Kronecker sine modes (Sec. 2.2.8): Phi_c(j) = prod_l sqrt(2/(n_l+1)) sin(i_l pi j_l/(n_l+1)).
 struct ModeIdx {
   int v[3 * SDF_MAX_K];
@@ -1978,7 +2024,7 @@ Layout make_layout(const sdf_problem *p, int B, int max_blocks = 0, int mixed = 
   L.p = take(vecv);
   L.q = take(vecv);
   L.w = take(mixed ? vecv : 8);
-  L.dinv = take(p->d.convection ? vecv : 8);
+  L.dinv = take(p->P.convection ? vecv : 8);
   L.mask = take((size_t)N * B);
   L.W = take(sizeof(double) * (size_t)N * k);
   size_t kk = sizeof(double) * (size_t)k * k;
@@ -2726,7 +2772,7 @@ size_t problem_bytes(const sdf_problem *p) {
 const sdf::OpParams *sdf_internal_op(const sdf_problem *p, int *nsm, int *convection) {
   if (!p || !p->bound) return nullptr;
   if (nsm) *nsm = p->nsm;
-  if (convection) *convection = p->d.convection;
+  if (convection) *convection = p->P.convection;
   return &p->P;
 }
 void sdf_internal_set_error(sdf_problem *p, const char *msg) {
@@ -2783,6 +2829,8 @@ sdf_status sdf_problem_create(const sdf_problem_desc *desc, const double *kappa_
       !(d.yd_sigma > 0))
     return SDF_ERR_INVALID_ARG;
   if (d.has_kappa && !kappa_host) return SDF_ERR_INVALID_ARG;
+  if (d.time_axis && (d.dim != 3 || !(d.t_final > 0) || !(d.ramp_tau > 0)))
+    return SDF_ERR_INVALID_ARG;
   long long nz = d.dim == 3 ? d.n[2] : 1;
   long long N = (long long)d.n[0] * d.n[1] * nz;
   if (N > (1LL << 31)) return SDF_ERR_INVALID_ARG;
@@ -2815,7 +2863,19 @@ sdf_status sdf_problem_create(const sdf_problem_desc *desc, const double *kappa_
   P.massf = (float)P.mass;
   P.wgtf = (float)P.wgt;
   P.convection = d.convection;
+  P.inst_conv = d.convection;
   P.yd_sigma = d.yd_sigma;
+  if (d.time_axis) {
+    // axis 2 is time: no diffusion along it, the implicit Euler difference
+    // as an upwind term (the convection code path), dt = t_final / n_t
+    P.time_axis = 1;
+    P.convection = 1;
+    P.dt = d.t_final / (double)nz;
+    P.cb_t = 1.0 / P.dt;
+    P.ramp_tau = d.ramp_tau;
+    P.cdiff[2] = 0.0;
+    P.cdf[2] = 0.0f;
+  }
   int dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess) {
     int v = 0;
@@ -2915,6 +2975,10 @@ sdf_status sdf_analytic_modes(sdf_problem *p, int k, void *phi_dev, int64_t ld, 
   if (!p) return SDF_ERR_INVALID_ARG;
   if (!phi_dev || k < 1 || ld < p->P.N) return fail(p, SDF_ERR_INVALID_ARG, "bad arguments");
   if (k > SDF_MAX_K) return fail(p, SDF_ERR_UNSUPPORTED, "k > SDF_MAX_K");
+  if (p->P.time_axis)
+    return fail(p, SDF_ERR_UNSUPPORTED,
+                "no closed-form modes on a space-time problem: build I_nt (x) Z_s with "
+                "sdf_spacetime_kron_modes");
   const int dim = p->d.dim;
   int n[3] = {p->P.nx, p->P.ny, p->P.nz};
   // enumerate multi-indices with small eigenvalue sums; mu_q per direction
@@ -3009,7 +3073,7 @@ static sdf_status check_solve_args(sdf_problem *p, int batch, const sdf_opts *op
     return fail(p, SDF_ERR_INVALID_ARG, "workspace must be a 256-byte aligned device pointer");
   if (opts->precision != SDF_PREC_F64 && opts->precision != SDF_PREC_MIXED)
     return fail(p, SDF_ERR_INVALID_ARG, "unknown precision");
-  if (opts->precision == SDF_PREC_MIXED && p->d.convection)
+  if (opts->precision == SDF_PREC_MIXED && p->P.convection)
     return fail(p, SDF_ERR_UNSUPPORTED,
                 "the mixed path is not validated for convection (FP32 attainable accuracy above "
                 "rtol stalls its refinement loop); use SDF_PREC_F64");
@@ -3136,6 +3200,72 @@ sdf_status sdf_solve_batch_host(sdf_problem *p, const double *inst_host, int bat
   CK(cudaMemcpyAsync(active_host, act_d, (size_t)N * batch, cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   return st;
+}
+
+sdf_status sdf_spacetime_kron_modes(sdf_problem *p, const void *zs_dev, int r, int64_t ldz,
+                                    sdf_dtype dtype, void *phi_dev, int64_t ld, void *stream) {
+  if (!p) return SDF_ERR_INVALID_ARG;
+  if (!p->P.time_axis) return fail(p, SDF_ERR_INVALID_ARG, "not a space-time problem");
+  const long long Ns = (long long)p->P.nx * p->P.ny;
+  const int nt = p->P.nz;
+  if (!zs_dev || !phi_dev || r < 1 || ldz < Ns || ld < p->P.N)
+    return fail(p, SDF_ERR_INVALID_ARG, "bad arguments");
+  if ((long long)r * nt > SDF_MAX_K) return fail(p, SDF_ERR_UNSUPPORTED, "r n_t > SDF_MAX_K");
+  cudaStream_t s = (cudaStream_t)stream;
+  const unsigned g = (unsigned)p->nsm * 8;
+  if (dtype == SDF_F64)
+    k_kron_time<double><<<g, NT, 0, s>>>((const double *)zs_dev, ldz, r, Ns, nt, (double *)phi_dev, ld);
+  else if (dtype == SDF_F32)
+    k_kron_time<float><<<g, NT, 0, s>>>((const float *)zs_dev, ldz, r, Ns, nt, (float *)phi_dev, ld);
+  else if (dtype == SDF_BF16)
+    k_kron_time<__nv_bfloat16><<<g, NT, 0, s>>>((const __nv_bfloat16 *)zs_dev, ldz, r, Ns, nt,
+                                                 (__nv_bfloat16 *)phi_dev, ld);
+  else
+    return fail(p, SDF_ERR_INVALID_ARG, "unknown dtype");
+  CKL("k_kron_time");
+  p->prof.launches += 1;
+  return SDF_OK;
+}
+
+void sdf_dct2_basis(int n, int r, double *w_host) {
+  if (!w_host || n < 1 || r < 1 || r > n) return;
+  const double pi = 3.14159265358979323846;
+  for (int a = 0; a < r; ++a)
+    for (int l = 0; l < n; ++l)
+      w_host[l + (size_t)a * n] =
+          std::sqrt((a == 0 ? 1.0 : 2.0) / n) * std::cos(pi * (l + 0.5) * a / n);
+}
+
+sdf_status sdf_spacetime_modes(sdf_problem *p, const double *wt_host, int rt, const void *zs_dev,
+                               int r, int64_t ldz, sdf_dtype dtype, void *phi_dev, int64_t ld,
+                               void *stream) {
+  if (!p) return SDF_ERR_INVALID_ARG;
+  if (!p->P.time_axis) return fail(p, SDF_ERR_INVALID_ARG, "not a space-time problem");
+  const long long Ns = (long long)p->P.nx * p->P.ny;
+  const int nt = p->P.nz;
+  if (!wt_host || !zs_dev || !phi_dev || r < 1 || rt < 1 || ldz < Ns || ld < p->P.N)
+    return fail(p, SDF_ERR_INVALID_ARG, "bad arguments");
+  if ((long long)nt * rt > SDF_TB_MAX)
+    return fail(p, SDF_ERR_UNSUPPORTED, "n_t r_t above 1024");
+  if ((long long)r * rt > SDF_MAX_K) return fail(p, SDF_ERR_UNSUPPORTED, "r r_t > SDF_MAX_K");
+  TemporalBasis tb{};
+  tb.nt = nt;
+  tb.rt = rt;
+  for (long long e = 0; e < (long long)nt * rt; ++e) tb.w[e] = wt_host[e];
+  cudaStream_t s = (cudaStream_t)stream;
+  const unsigned g = (unsigned)p->nsm * 8;
+  if (dtype == SDF_F64)
+    k_time_basis<double><<<g, NT, 0, s>>>(tb, (const double *)zs_dev, ldz, r, Ns, (double *)phi_dev, ld);
+  else if (dtype == SDF_F32)
+    k_time_basis<float><<<g, NT, 0, s>>>(tb, (const float *)zs_dev, ldz, r, Ns, (float *)phi_dev, ld);
+  else if (dtype == SDF_BF16)
+    k_time_basis<__nv_bfloat16><<<g, NT, 0, s>>>(tb, (const __nv_bfloat16 *)zs_dev, ldz, r, Ns,
+                                                  (__nv_bfloat16 *)phi_dev, ld);
+  else
+    return fail(p, SDF_ERR_INVALID_ARG, "unknown dtype");
+  CKL("k_time_basis");
+  p->prof.launches += 1;
+  return SDF_OK;
 }
 
 sdf_status sdf_apply_S(sdf_problem *p, const double *inst_dev, const uint8_t *active_dev,

@@ -31,6 +31,12 @@ struct OpParams {
   // FP64 pipe, 1/64 of the FP32 rate on this part)
   float cdf[3], massf, wgtf;
   const float *fxf, *fyf, *fzf;  // face coefficients in FP32 or null
+  // space-time problems (App. E.2): axis 2 is time, the backward difference
+  // (u_l - u_{l-1}) / dt enters A as an upwind term of coefficient
+  // cb_t = 1 / dt; y_d carries the ramp 1 - exp(-t / ramp_tau)
+  int time_axis;
+  double cb_t, dt, ramp_tau;
+  int inst_conv;  // instances' convection velocities are applied (in space)
 };
 
 // Operator constants and face arrays in arithmetic type T.

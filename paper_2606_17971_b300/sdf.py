@@ -34,7 +34,9 @@ class ProblemDesc(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int32), ("n", ctypes.c_int32 * 3), ("alpha", ctypes.c_double),
                 ("mass", ctypes.c_double), ("kscale", ctypes.c_double),
                 ("diff_scale", ctypes.c_double), ("has_kappa", ctypes.c_int32),
-                ("convection", ctypes.c_int32), ("yd_sigma", ctypes.c_double)]
+                ("convection", ctypes.c_int32), ("yd_sigma", ctypes.c_double),
+                ("time_axis", ctypes.c_int32), ("t_final", ctypes.c_double),
+                ("ramp_tau", ctypes.c_double)]
 
 
 class Opts(ctypes.Structure):
@@ -126,11 +128,15 @@ _sigs = {
     "sdf_coarse_modes_workspace_size": (_i32, [_vp, _i32, _i32, _vp, ctypes.POINTER(_sz)]),
     "sdf_reference_modes_coarse": (_i32, [_vp, _i32, _i32, _vp, ctypes.c_double, _vp, _i64,
                                           ctypes.POINTER(_i32), _vp, _vp, _vp, _sz, _vp]),
+    "sdf_spacetime_kron_modes": (_i32, [_vp, _vp, _i32, _i64, _i32, _vp, _i64, _vp]),
+    "sdf_spacetime_modes": (_i32, [_vp, _vp, _i32, _vp, _i32, _i64, _i32, _vp, _i64, _vp]),
+    "sdf_dct2_basis": (None, [_i32, _i32, _vp]),
     "sdf_diag_sets_workspace_size": (_i32, [_vp, _i32, ctypes.POINTER(_sz)]),
     "sdf_diag_active_sets": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _sz,
                                     _vp]),
     "sdf_diag_drift_workspace_size": (_i32, [_vp, _i32, ctypes.POINTER(_sz)]),
     "sdf_diag_drift": (_i32, [_vp, _vp, _vp, _i32, _i32, _vp, _vp, _vp, _sz, _vp]),
+    "sdf_default_restricted_eig_opts": (None, [_i32, _vp]),
     "sdf_restricted_eig_workspace_size": (_i32, [_vp, _i32, _vp, ctypes.POINTER(_sz)]),
     "sdf_restricted_modes_eig": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _i64, _vp, _vp, _vp, _sz,
                                         _vp]),
@@ -178,13 +184,17 @@ class Problem:
     """Handle over sdf_problem: operator data bound to a device tensor."""
 
     def __init__(self, dim, n, alpha=1e-4, kappa=None, mass=1.0, kscale=1.0, diff_scale=1.0,
-                 convection=False, yd_sigma=0.1, device="cuda"):
+                 convection=False, yd_sigma=0.1, time_axis=False, t_final=1.0, ramp_tau=0.2,
+                 device="cuda"):
+        """time_axis=True: the space-time problem on an (n_x, n_y, n_t) grid
+        (dim = 3; sdf_problem_desc.time_axis)."""
         n = list(n) if hasattr(n, "__len__") else [n] * dim
         while len(n) < 3:
             n.append(1)
         d = ProblemDesc(dim=dim, alpha=alpha, mass=mass, kscale=kscale, diff_scale=diff_scale,
                         has_kappa=int(kappa is not None), convection=int(bool(convection)),
-                        yd_sigma=yd_sigma)
+                        yd_sigma=yd_sigma, time_axis=int(bool(time_axis)), t_final=t_final,
+                        ramp_tau=ramp_tau)
         for i in range(3):
             d.n[i] = n[i]
         self.dim, self.n = dim, tuple(n[:dim])
@@ -230,6 +240,31 @@ class Problem:
         self._check(_lib.sdf_analytic_modes(self._h, k, _ptr(phi), self.N, dtype,
                                             ev.ctypes.data, _stream()))
         return phi, ev
+
+    def spacetime_kron_modes(self, zs: torch.Tensor):
+        """sdf_spacetime_kron_modes: I_nt (x) Z_s for spatial modes zs
+        (r, N_s) (row j = mode j); returns (r n_t, N) of zs's dtype."""
+        assert zs.is_cuda and zs.is_contiguous()
+        r, Ns = zs.shape
+        nt = self.n[2] if len(self.n) > 2 else 1
+        dt = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}[zs.dtype]
+        phi = torch.empty((r * nt, self.N), dtype=zs.dtype, device=self.device)
+        self._check(_lib.sdf_spacetime_kron_modes(self._h, _ptr(zs), r, Ns, dt, _ptr(phi),
+                                                  self.N, _stream()))
+        return phi
+
+    def spacetime_modes(self, wt: np.ndarray, zs: torch.Tensor):
+        """sdf_spacetime_modes: W_t (x) Z_s for a temporal factor wt (n_t, r_t)
+        (host) and spatial modes zs (r, N_s); returns (r_t r, N) of zs's dtype."""
+        assert zs.is_cuda and zs.is_contiguous()
+        wt = np.asfortranarray(wt, dtype=np.float64)
+        r, Ns = zs.shape
+        rt = wt.shape[1]
+        dt = {torch.float64: F64, torch.float32: F32, torch.bfloat16: BF16}[zs.dtype]
+        phi = torch.empty((rt * r, self.N), dtype=zs.dtype, device=self.device)
+        self._check(_lib.sdf_spacetime_modes(self._h, wt.ctypes.data, rt, _ptr(zs), r, Ns, dt,
+                                             _ptr(phi), self.N, _stream()))
+        return phi
 
     def eig_modes(self, k, **kw):
         """k smallest eigenpairs of A (those of S) by Chebyshev-filtered
@@ -318,7 +353,7 @@ class Problem:
         inactive set of `active` (N,) uint8 for one instance (7,); returns
         V (k, N) float64 (row j = eigenvector j, zero on A), lambda, stats."""
         o = EigOpts()
-        _lib.sdf_default_eig_opts(ctypes.byref(o))
+        _lib.sdf_default_restricted_eig_opts(k, ctypes.byref(o))
         for key, v in kw.items():
             setattr(o, key, v)
         nb = _sz()
@@ -536,6 +571,14 @@ class Mlp:
                                           B, _ptr(grad), _ptr(loss), _ptr(ws), ws.numel(),
                                           _stream()))
         return loss, grad
+
+
+def dct2_basis(n, r):
+    """sdf_dct2_basis: the first r orthonormal DCT-II vectors of length n,
+    as an (n, r) float64 array."""
+    w = np.zeros((n, r), order="F")
+    _lib.sdf_dct2_basis(n, r, w.ctypes.data)
+    return w
 
 
 def adam_step(theta, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):

@@ -22,6 +22,12 @@ Workloads (grid, operator, parameter law, instance count, number of modes k):
   ``diff3d_128``       128^3, kappa = 1, mu = (a, cx, cy, cz), a ~ U[1,3],
                        c ~ U[0.25,0.75]^3, 2000 training + 1024 held-out
                        instances, evaluated in batches of 128, k = 60.
+  ``spacetime2d_64``   the all-at-once parabolic problem on a 64^2 spatial
+                       grid with n_t = 16 implicit Euler steps on (0, 1]
+                       (N = 65,536), kappa = 1, y_d ramped in time with
+                       tau = 0.2, sigma = 0.12, a ~ U[1,3],
+                       c ~ U[0.25,0.75]^2, 32 instances; k = 8 spatial modes,
+                       Kronecker basis of rank 8 n_t = 128.
 
 Every generator takes an explicit seed (numpy PCG64).  Parameters are drawn in
 the order a, c, theta for each instance, instance by instance.
@@ -66,6 +72,8 @@ WORKLOADS = {
                                  seed=20263),
     "diff3d_128": Workload("diff3d_128", 3, 128, 60, 3024, batch=128, seed=20264,
                            extra={"train": 2000, "held_out": 1024}),
+    "spacetime2d_64": Workload("spacetime2d_64", 2, 64, 8, 32, sigma=0.12, batch=32, seed=20265,
+                               extra={"n_t": 16, "t_final": 1.0, "ramp_tau": 0.2}),
 }
 
 

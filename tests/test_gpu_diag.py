@@ -132,7 +132,7 @@ def test_restricted_modes_match_dense_eigh_and_interlace(sdf, conv):
         inst = torch.as_tensor([1.0, 0.5, 0.5, 0, 0, 0, 0], dtype=torch.float64, device=DEV)
     act = _disc(n, (0.6, 0.4), 0.03)
     k = 12
-    V, lam, st = G.restricted_modes(inst, torch.as_tensor(act, device=DEV), k, tol=1e-8)
+    V, lam, st = G.restricted_modes(inst, torch.as_tensor(act, device=DEV), k)
     assert st["converged"], st
     S = P.dense_S()
     lam_o, V_o = D.restricted_modes(S, act, k)
@@ -161,7 +161,7 @@ def test_cutoff_angles_match_oracle(sdf):
     inst = torch.as_tensor([1.0, 0.5, 0.5, 0, 0, 0, 0], dtype=torch.float64, device=DEV)
     for act in (np.zeros(P.N, np.uint8), _disc(n, (0.6, 0.4), 0.03), _disc(n, (0.4, 0.5), 0.08)):
         a_t = torch.as_tensor(act, device=DEV)
-        V, _, st = G.restricted_modes(inst, a_t, k, tol=1e-8)
+        V, _, st = G.restricted_modes(inst, a_t, k)
         assert st["converged"]
         th = G.diag_angles(a_t, V)
         th_o = D.cutoff_angles(D.restrict(phi.cpu().numpy().T, act), V.cpu().numpy().T)

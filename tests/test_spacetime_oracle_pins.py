@@ -159,3 +159,31 @@ def test_desired_state_slabs_are_the_steady_desired_state_ramped():
     for l in range(n_t):
         np.testing.assert_allclose(yd[l * n * n:(l + 1) * n * n],
                                    (1.0 - np.exp(-t[l] / tau)) * steady, rtol=1e-13, atol=1e-300)
+
+
+def test_dct2_basis_is_scipys_orthonormal_dct():
+    from scipy.fft import dct
+    for n_t, r_t in ((8, 8), (16, 5), (7, 3)):
+        W = ST.dct2_basis(n_t, r_t)
+        # the orthonormal DCT-II of the identity: row a is basis vector a
+        ref = dct(np.eye(n_t), type=2, norm="ortho", axis=0)[:r_t].T
+        np.testing.assert_allclose(W, ref, atol=1e-14)
+        np.testing.assert_allclose(W.T @ W, np.eye(r_t), atol=1e-14)
+
+
+def test_full_cosine_basis_equals_kronecker_and_truncation_degrades():
+    # App. E.2.1: W_t (x) Z_s with r_t = n_t spans the Kronecker basis' space,
+    # so A-DEF2 (invariant under Z -> Z G) takes the same iterations; with
+    # r_t < n_t it deflates less
+    n, n_t, r = 16, 8, 16
+    P, _ = ST.problem(n, n_t, 1e-4)
+    yd, rhs = ST.desired_state(n, n_t, 2.0, (0.5, 0.5))
+    psi = np.full(P.N, 10.0)
+    Z_s = O.analytic_modes(2, n, r, 1e-4)[0]
+    kron = P.solve(rhs, psi, ST.kron_basis(Z_s, n_t))
+    full = P.solve(rhs, psi, ST.temporal_basis(ST.dct2_basis(n_t, n_t), Z_s))
+    half = P.solve(rhs, psi, ST.temporal_basis(ST.dct2_basis(n_t, n_t // 2), Z_s))
+    assert abs(full["cg_iters"][0] - kron["cg_iters"][0]) <= 1
+    assert np.linalg.norm(full["y"] - kron["y"]) <= 1e-7 * np.linalg.norm(kron["y"])
+    assert half["cg_iters"][0] > kron["cg_iters"][0] + 5
+    np.testing.assert_array_equal(ST.temporal_basis(np.eye(n_t), Z_s), ST.kron_basis(Z_s, n_t))
