@@ -244,6 +244,65 @@ def spacetime_leg(w, sdf, dev):
     return res
 
 
+def diag_sweep_leg(n, count, sdf, dev, K=40, r=20, psi_value=0.5):
+    """The spectral-coherence sweep of Sec. 4.1 on the GPU: instances of the
+    2D diffusion family on an n x n grid with psi = psi_value (calibrated for
+    a sizeable active set, as the paper calibrates psi), each solved with r
+    reference modes and cold; then delta and rho against the first
+    instance's active set, the K lowest eigenpairs of S_II, and the
+    principal angles between them and the K restricted reference modes
+    (theta_r the r-th smallest, theta_max the largest, and the nested angle
+    of Prop. dk at r).  Timed per stage; not part of the metric."""
+    import torch
+    from paper_2606_17971_b300 import workloads as W
+    w = W.scaled(W.WORKLOADS["diff2d_32"], n)
+    G = sdf.Problem(2, n, alpha=w.alpha, yd_sigma=w.sigma, device=dev)
+    phiK, _ = G.analytic_modes(K)
+    phir = phiK[:r].contiguous()
+    insts = W.draw_instances(w, count=count)
+    inst = torch.as_tensor(W.instances_array(insts), device=dev)
+    psi = torch.full((G.N,), psi_value, dtype=torch.float64, device=dev)
+    t = {}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    G.set_modes(phir)
+    defl = G.solve(inst, psi, want_lambda=False)
+    cold = G.solve(inst, psi, sdf.default_opts(deflate=0), want_lambda=False)
+    torch.cuda.synchronize()
+    t["solves_s"] = time.perf_counter() - t0
+    G.set_modes(phiK)
+    t0 = time.perf_counter()
+    sets = G.diag_active_sets(defl["active"][0].clone(), defl["active"], r=r)
+    t["sets_s"] = time.perf_counter() - t0
+    rows, t_eig, t_ang = [], 0.0, 0.0
+    for b in range(count):
+        act = defl["active"][b].contiguous()
+        t0 = time.perf_counter()
+        V, _, est = G.restricted_modes(inst[b], act, K)
+        t_eig += time.perf_counter() - t0
+        t0 = time.perf_counter()
+        nested, srt = G.diag_angles(act, V, sorted_angles=True)
+        t_ang += time.perf_counter() - t0
+        n_d = sum(defl["stats"][b]["cg_iters"])
+        n_c = sum(cold["stats"][b]["cg_iters"])
+        rows.append({"a": insts[b].a, "delta": float(sets["delta"][b]), "rho": float(sets["rho"][b]),
+                     "theta_r_deg": float(np.degrees(srt[r - 1])),
+                     "theta_max_deg": float(np.degrees(srt[-1])),
+                     "nested_theta_r_deg": float(np.degrees(nested[r - 1])),
+                     "cg_deflated": n_d, "cg_cold": n_c, "eff": 1.0 - n_d / n_c,
+                     "eig_converged": bool(est["converged"]), "eig_passes": est["iters"]})
+    t["restricted_eig_s"] = t_eig
+    t["angles_s"] = t_ang
+    d = np.array([x["delta"] for x in rows])
+    e = np.array([x["eff"] for x in rows])
+    return {"grid": [n, n], "instances": count, "psi": psi_value, "K": K, "r": r, "seconds": t,
+            "delta_max": float(d.max()), "theta_r_max_deg": max(x["theta_r_deg"] for x in rows),
+            "theta_max_min_deg": min(x["theta_max_deg"] for x in rows),
+            "eff_mean": float(e.mean()), "eff_std": float(e.std()),
+            "corr_delta_eff": float(np.corrcoef(d, e)[0, 1]) if d.std() > 0 and e.std() > 0 else None,
+            "rows": rows}
+
+
 def oracle_counts(name):
     path = os.path.join(ROOT, "tests", "golden", f"{name}_oracle.json")
     if not os.path.exists(path):
@@ -323,6 +382,10 @@ def main():
                          "basis, the constant-in-time lift and plain PCG ('' : off)")
     ap.add_argument("--no-diag", action="store_true",
                     help="skip timing the active-set diagnostics on the last batch")
+    ap.add_argument("--diag-sweep", type=int, default=0,
+                    help="also run the spectral-coherence sweep of Sec. 4.1 over this many "
+                         "instances of the 2D diffusion family (0: off)")
+    ap.add_argument("--diag-n", type=int, default=128, help="grid of the diagnostics sweep")
     args = ap.parse_args()
 
     from paper_2606_17971_b300 import workloads as W
@@ -608,6 +671,8 @@ def main():
             "note": "sdf_diag_active_sets, host round trip included"}
     if args.spacetime and rank == 0:
         line["spacetime"] = spacetime_leg(W.WORKLOADS[args.spacetime], sdf, dev)
+    if args.diag_sweep and rank == 0:
+        line["diagnostics_sweep"] = diag_sweep_leg(args.diag_n, args.diag_sweep, sdf, dev)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

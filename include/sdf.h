@@ -488,9 +488,14 @@ sdf_status sdf_restricted_modes_eig(sdf_problem *p, const double *inst_dev,
                                     sdf_eig_stats *stats, void *ws, size_t ws_bytes,
                                     void *stream);
 
-/* Principal angles at every deflation cutoff (Prop. dk, App. A.3, with
- * S = {1..r}): theta_host[r-1], r = 1..k, is the largest principal angle in
- * radians between span(Phi_I[:, :r]) and span(V[:, :r]).  Phi_I is the first
+/* Principal angles between the restricted reference modes and V, in two
+ * readings.  sorted_host[i] (k values, may be NULL): the principal angles in
+ * radians between the k-dimensional spans of Phi_I[:, :k] and V[:, :k],
+ * ascending; the paper's diagnostic theta_r (Sec. 4.1, App. D, "the
+ * principal angle at the deflation cutoff") is sorted_host[r-1] and
+ * theta_max the last.  theta_host[r-1], r = 1..k: the nested angle of
+ * Prop. dk (App. A.3) with S = {1..r}, the largest principal angle between
+ * span(Phi_I[:, :r]) and span(V[:, :r]).  Phi_I is the first
  * r registered reference modes with their rows on the active set of
  * active_dev zeroed.  V_dev is N x k FP64, column-major, leading dimension
  * ldv, device: for instance the eigenvectors of S_II from
@@ -503,8 +508,8 @@ sdf_status sdf_restricted_modes_eig(sdf_problem *p, const double *inst_dev,
  * ws: at least sdf_diag_angles_workspace_size bytes. */
 sdf_status sdf_diag_angles_workspace_size(const sdf_problem *p, int k, size_t *bytes);
 sdf_status sdf_diag_angles(sdf_problem *p, const uint8_t *active_dev, const double *V_dev,
-                           int64_t ldv, int k, double *theta_host, void *ws, size_t ws_bytes,
-                           void *stream);
+                           int64_t ldv, int k, double *theta_host, double *sorted_host, void *ws,
+                           size_t ws_bytes, void *stream);
 
 /* ==========================================================================
  * Learned warm start (no counterpart in the paper, which lists learned

@@ -35,6 +35,9 @@ const sdf::OpParams *sdf_internal_op(const sdf_problem *p, int *nsm, int *convec
 void sdf_internal_set_error(sdf_problem *p, const char *msg);
 const sdf_problem_desc *sdf_internal_desc(const sdf_problem *p, const double **kappa_host);
 const void *sdf_internal_modes(const sdf_problem *p, int *k, long long *ld, sdf_dtype *dtype);
+sdf_status sdf_internal_apply_S_cols(sdf_problem *p, const double *inst_dev,
+                                     const uint8_t *active_dev, const double *u, double *out,
+                                     int cols, int mode, cudaStream_t s);
 
 namespace {
 
@@ -894,15 +897,12 @@ sdf_status sdf_restricted_modes_eig(sdf_problem *p, const double *inst_dev,
     else if (P.inst_conv) bA += 2.0 * std::fabs(inst_h[4 + d]) * P.inv_h[d];
   }
   const double bmax = 1.01 * (P.mass + P.wgt * bA * bA);
-  // the operator: S_II through the solver's own stencil (mode 0), column by
-  // column, then the three-term combination
+  // the operator: S_II through the solver's own stencil (mode 0) on the
+  // whole block in one launch, then the three-term combination
   ApplyFn opS = [&](const double *Xp, const double *Xc, double *Xn, int cols, double a, double b,
                     double c) -> sdf_status {
-    for (int j = 0; j < cols; ++j) {
-      const sdf_status e = sdf_apply_S(p, inst_dev, active_dev, Xc + (size_t)j * N,
-                                       Xn + (size_t)j * N, 0, nullptr, 0, stream);
-      if (e != SDF_OK) return e;
-    }
+    const sdf_status e = sdf_internal_apply_S_cols(p, inst_dev, active_dev, Xc, Xn, cols, 0, s);
+    if (e != SDF_OK) return e;
     if (a != 1.0 || b != 0.0 || c != 0.0) {
       k_comb<<<nsm * 8, ET, 0, s>>>(Xn, Xc, Xp, N * cols, a, b, c);
       ECK(cudaGetLastError());
@@ -1064,8 +1064,8 @@ sdf_status sdf_diag_angles_workspace_size(const sdf_problem *p, int k, size_t *b
 }
 
 sdf_status sdf_diag_angles(sdf_problem *p, const uint8_t *active_dev, const double *V_dev,
-                           int64_t ldv, int k, double *theta_host, void *ws, size_t ws_bytes,
-                           void *stream) {
+                           int64_t ldv, int k, double *theta_host, double *sorted_host, void *ws,
+                           size_t ws_bytes, void *stream) {
   if (!p) return SDF_ERR_INVALID_ARG;
   size_t need = 0;
   if (sdf_diag_angles_workspace_size(p, k, &need) != SDF_OK)
@@ -1124,6 +1124,11 @@ sdf_status sdf_diag_angles(sdf_problem *p, const uint8_t *active_dev, const doub
     hla::jacobi_eig(r, M, wv, Vd);  // descending: wv[r - 1] = sigma_min^2
     const double c = std::sqrt(std::min(1.0, std::max(0.0, wv[r - 1])));
     theta_host[r - 1] = std::acos(c);
+    // r = k: the singular values of the whole C give every principal angle
+    // between the k-dimensional spans, ascending with descending sigma
+    if (r == k && sorted_host)
+      for (int i = 0; i < k; ++i)
+        sorted_host[i] = std::acos(std::sqrt(std::min(1.0, std::max(0.0, wv[i]))));
   }
   return SDF_OK;
 }

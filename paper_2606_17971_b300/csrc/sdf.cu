@@ -1855,7 +1855,9 @@ __global__ void __launch_bounds__(NT) k_lambda(OpParams P, const double *inst, c
   }
 }
 
-// sdf_apply_S building block: out = S_II u (mode 0) or S u (mode 1).
+// sdf_apply_S building block: out = S_II u (mode 0) or S u (mode 1), for
+// column blockIdx.y of u and out (column stride P.N; one column from the ABI,
+// a whole block from the restricted eigensolve).
 template <int DIM>
 __global__ void __launch_bounds__(NT) k_apply(OpParams P, const double *inst,
                                               const uint8_t *mask, const double *u, double *out,
@@ -1863,6 +1865,8 @@ __global__ void __launch_bounds__(NT) k_apply(OpParams P, const double *inst,
   __shared__ TileSmem<DIM> sm;
   double cb[3];
   inst_cb(P, inst, cb);
+  u += (long long)blockIdx.y * P.N;
+  out += (long long)blockIdx.y * P.N;
   const long long T = num_tiles<DIM>(P.nx, P.ny, P.nz);
   for (long long t = blockIdx.x; t < T; t += GX) {
     int ox, oy, oz;
@@ -2782,6 +2786,21 @@ const sdf_problem_desc *sdf_internal_desc(const sdf_problem *p, const double **k
   if (!p) return nullptr;
   if (kappa_host) *kappa_host = p->kappa.empty() ? nullptr : p->kappa.data();
   return &p->d;
+}
+// S_II (mode 0) or S (mode 1) applied to `cols` columns of N doubles at once
+// (the restricted eigensolve's block), one launch
+sdf_status sdf_internal_apply_S_cols(sdf_problem *p, const double *inst_dev,
+                                     const uint8_t *active_dev, const double *u, double *out,
+                                     int cols, int mode, cudaStream_t s) {
+  if (cols < 1 || cols > 65535) return fail(p, SDF_ERR_INVALID_ARG, "bad column count");
+  const OpParams &P = p->P;
+  const int GX = std::max(1, p->nsm * 4 / cols);
+  const dim3 g(GX, cols);
+  if (P.dim == 2) k_apply<2><<<g, NT, 0, s>>>(P, inst_dev, active_dev, u, out, mode, GX);
+  else k_apply<3><<<g, NT, 0, s>>>(P, inst_dev, active_dev, u, out, mode, GX);
+  CKL("k_apply");
+  p->prof.launches += 1;
+  return SDF_OK;
 }
 // the registered reference modes (nullptr when none)
 const void *sdf_internal_modes(const sdf_problem *p, int *k, long long *ld, sdf_dtype *dtype) {

@@ -141,7 +141,7 @@ _sigs = {
     "sdf_restricted_modes_eig": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _i64, _vp, _vp, _vp, _sz,
                                         _vp]),
     "sdf_diag_angles_workspace_size": (_i32, [_vp, _i32, ctypes.POINTER(_sz)]),
-    "sdf_diag_angles": (_i32, [_vp, _vp, _vp, _i64, _i32, _vp, _vp, _sz, _vp]),
+    "sdf_diag_angles": (_i32, [_vp, _vp, _vp, _i64, _i32, _vp, _vp, _vp, _sz, _vp]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(_lib, _name)
@@ -373,17 +373,20 @@ class Problem:
                      matvecs=st.matvecs, seconds=st.seconds, status=rc)
         return V, lam, stats
 
-    def diag_angles(self, active: torch.Tensor, V: torch.Tensor, k=None):
-        """sdf_diag_angles: theta_r (radians), r = 1..k, the largest principal
-        angle between span(Phi_I[:, :r]) (registered modes restricted to the
-        inactive set) and span(V[:r]) for V (k, N) float64."""
+    def diag_angles(self, active: torch.Tensor, V: torch.Tensor, k=None, sorted_angles=False):
+        """sdf_diag_angles for V (k, N) float64 against the registered modes
+        restricted to the inactive set: the nested angles theta_r (radians),
+        r = 1..k (Prop. dk with S = {1..r}); with sorted_angles=True also the
+        ascending principal angles between the k-dimensional spans (the
+        paper's theta_r is entry r - 1)."""
         k = V.shape[0] if k is None else k
         assert V.dtype == torch.float64 and V.is_contiguous() and V.shape[1] == self.N
         ws = self._scratch(_lib.sdf_diag_angles_workspace_size, k)
-        th = np.zeros(k)
+        th, srt = np.zeros(k), np.zeros(k)
         self._check(_lib.sdf_diag_angles(self._h, _ptr(active.contiguous()), _ptr(V), self.N, k,
-                                         th.ctypes.data, _ptr(ws), ws.numel(), _stream()))
-        return th
+                                         th.ctypes.data, srt.ctypes.data, _ptr(ws), ws.numel(),
+                                         _stream()))
+        return (th, srt) if sorted_angles else th
 
     # workspace --------------------------------------------------------------
     def workspace(self, batch, opts=None, host_io=False):

@@ -135,3 +135,20 @@ def test_davis_kahan_bound_holds_under_convection_drift():
             gap = lam[r] - lam[r - 1]
             if gap > 1e-9 * nref:
                 assert np.sin(ang[r - 1]) <= eps * nref / gap * (1 + 1e-9), (th, r)
+
+
+def test_sorted_principal_angles_of_known_rotations_and_their_largest_is_the_nested_last():
+    e = np.eye(7)
+    Phi = e[:, :3]
+    t1, t2 = 0.2, 1.1
+    V = np.column_stack([e[:, 0],
+                         np.cos(t1) * e[:, 1] + np.sin(t1) * e[:, 4],
+                         np.cos(t2) * e[:, 2] + np.sin(t2) * e[:, 5]])
+    np.testing.assert_allclose(D.principal_angles(Phi, V), [0.0, t1, t2], atol=1e-12)
+    # the span of a reordered basis is the same set of angles
+    np.testing.assert_allclose(D.principal_angles(Phi[:, ::-1], V[:, [2, 0, 1]]), [0.0, t1, t2],
+                               atol=1e-12)
+    # the largest principal angle between the full spans is the nested angle at r = k
+    rng = np.random.default_rng(8)
+    A, B = rng.standard_normal((30, 6)), rng.standard_normal((30, 6))
+    assert D.principal_angles(A, B)[-1] == pytest.approx(D.cutoff_angles(A, B)[-1], abs=1e-12)

@@ -163,9 +163,12 @@ def test_cutoff_angles_match_oracle(sdf):
         a_t = torch.as_tensor(act, device=DEV)
         V, _, st = G.restricted_modes(inst, a_t, k)
         assert st["converged"]
-        th = G.diag_angles(a_t, V)
-        th_o = D.cutoff_angles(D.restrict(phi.cpu().numpy().T, act), V.cpu().numpy().T)
+        th, srt = G.diag_angles(a_t, V, sorted_angles=True)
+        Phi_I = D.restrict(phi.cpu().numpy().T, act)
+        th_o = D.cutoff_angles(Phi_I, V.cpu().numpy().T)
         np.testing.assert_allclose(th, th_o, atol=2e-6)
+        np.testing.assert_allclose(srt, D.principal_angles(Phi_I, V.cpu().numpy().T), atol=2e-6)
+        assert srt[-1] == pytest.approx(th[-1], abs=2e-6)
         if act.sum() == 0:
             assert th.max() < 1e-5  # the same operator: aligned at every cut
         else:
@@ -186,3 +189,38 @@ def test_diagnostics_refuse_bad_arguments(sdf):
         G.restricted_modes(inst, nearly_all, 4)
     with pytest.raises(sdf.SdfError):  # no registered modes
         G.diag_angles(act, torch.zeros((4, G.N), dtype=torch.float64, device=DEV))
+
+
+def test_two_regime_spectral_coherence_on_a_sweep(sdf):
+    # Sec. 4.1: over instances whose active sets differ by up to ~20 % of the
+    # nodes, the r-th smallest principal angle between the restricted
+    # reference modes and S_II's lowest eigenvectors stays small while the
+    # largest approaches 90 degrees; deflation stays effective
+    n, K, r = 48, 40, 20
+    w = W.scaled(W.WORKLOADS["diff2d_32"], n)
+    G = sdf.Problem(2, n, alpha=w.alpha, yd_sigma=w.sigma)
+    phiK, _ = G.analytic_modes(K)
+    insts = W.draw_instances(w, count=4)
+    inst = torch.as_tensor(W.instances_array(insts), device=DEV)
+    psi = torch.full((G.N,), 0.5, dtype=torch.float64, device=DEV)
+    G.set_modes(phiK[:r].contiguous())
+    defl = G.solve(inst, psi, want_lambda=False)
+    cold = G.solve(inst, psi, sdf.default_opts(deflate=0), want_lambda=False)
+    G.set_modes(phiK)
+    P = O.Problem(2, n, alpha=w.alpha)
+    S = P.dense_S()
+    Phi = phiK.cpu().numpy().T
+    for b in range(4):
+        act = defl["active"][b].contiguous()
+        assert 0 < int(act.sum().item()) < G.N // 4
+        V, _, st = G.restricted_modes(inst[b], act, K)
+        assert st["converged"]
+        _, srt = G.diag_angles(act, V, sorted_angles=True)
+        assert np.degrees(srt[r - 1]) < 5.0 and np.degrees(srt[-1]) > 60.0, np.degrees(srt)
+        # the same angles from the oracle's dense restricted eigenvectors
+        a_np = act.cpu().numpy()
+        _, V_o = D.restricted_modes(S, a_np, K)
+        srt_o = D.principal_angles(D.restrict(Phi, a_np), V_o)
+        assert abs(np.degrees(srt[r - 1]) - np.degrees(srt_o[r - 1])) < 0.05
+        eff = 1 - sum(defl["stats"][b]["cg_iters"]) / sum(cold["stats"][b]["cg_iters"])
+        assert eff > 0.5
