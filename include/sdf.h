@@ -187,6 +187,22 @@ void sdf_default_opts(sdf_opts *o);
 sdf_status sdf_problem_create(const sdf_problem_desc *desc, const double *kappa_host,
                               sdf_problem **out);
 
+/* A problem given by its state operator K instead of a grid (the general
+ * form of Sec. 2.1.2 Eq. schur): K is n x n CSR on the host (rowptr n+1,
+ * col and val rowptr[n] entries, 0-based, FP64; copied), and the library
+ * assembles S = mass I + (alpha kscale^2 / mass) K^T K on the host once
+ * (Gustavson's row-merge product), with its inverse diagonal.  Bind it with
+ * sdf_problem_device_bytes / sdf_problem_bind as any problem; S is then
+ * applied row by row from the assembled CSR in every FP64-path kernel
+ * (sdf_apply_S, the solve, the coarse set-up).  There is no grid: solve
+ * with sdf_solve_batch_rhs; the mixed path, the closed-form modes and the
+ * eigensolves of the grid's A return SDF_ERR_UNSUPPORTED.  n <= 2^30 and
+ * nnz(S) <= INT_MAX; SDF_ERR_INVALID_ARG on a malformed CSR (decreasing
+ * row pointers, a column outside [0, n), a non-finite value). */
+sdf_status sdf_problem_create_csr(int64_t n, const int32_t *rowptr, const int32_t *col,
+                                  const double *val, double mass, double alpha, double kscale,
+                                  sdf_problem **out);
+
 /* Bytes of device memory the problem's operator data needs (face
  * coefficients of A_h); may be 0 for constant kappa. */
 sdf_status sdf_problem_device_bytes(const sdf_problem *p, size_t *bytes);
@@ -275,6 +291,17 @@ sdf_status sdf_solve_batch_x0(sdf_problem *p, const double *inst_dev, int batch,
                               const double *psi_dev, const double *x0_dev, const sdf_opts *opts,
                               void *ws, size_t ws_bytes, void *stream, double *y_dev,
                               double *lambda_dev, uint8_t *active_dev, sdf_stats *stats_host);
+
+/* sdf_solve_batch with caller-given right-hand sides: rhs_dev (batch x N
+ * FP64, device, instance-major) replaces mass y_d of every instance (Sec.
+ * 2.1.2 Eq. reduced then uses rhs_I - S_IA psi_A).  inst_dev may be NULL
+ * when the problem has no per-instance convection (it is read for nothing
+ * else); a problem created by sdf_problem_create_csr must be solved this
+ * way.  Everything else as sdf_solve_batch; lambda = rhs - S y. */
+sdf_status sdf_solve_batch_rhs(sdf_problem *p, const double *inst_dev, const double *rhs_dev,
+                               int batch, const double *psi_dev, const sdf_opts *opts, void *ws,
+                               size_t ws_bytes, void *stream, double *y_dev, double *lambda_dev,
+                               uint8_t *active_dev, sdf_stats *stats_host);
 
 /* Autotuner of the batched mixed 3D path: for this batch size, time a short
  * capped solve (40 CG iterations) of these instances with each candidate

@@ -317,6 +317,16 @@ def analytic_modes(dim, n, k, alpha=1e-4, diff_scale=1.0):
     return np.asfortranarray(Phi), lam, sel + 1
 
 
+def schur_from_operator(K, alpha=1e-4, mass=1.0, kscale=1.0):
+    """S = mass I + (alpha kscale^2 / mass) K^T K for a state operator K
+    given as a scipy.sparse matrix (Sec. 2.1.2 Eq. schur with M = mass I),
+    as a CSR matrix: the operator of a problem given without a grid."""
+    import scipy.sparse as sp
+    K = sp.csr_matrix(K, dtype=np.float64)
+    n = K.shape[0]
+    return (mass * sp.identity(n) + (alpha * kscale * kscale / mass) * (K.T @ K)).tocsr()
+
+
 def dense_modes(prob: Problem, k: int):
     """k smallest eigenpairs of the full S (Eq. eig) by a dense symmetric
     eigensolver; for small N only.  Signs are fixed so that the entry of

@@ -785,6 +785,7 @@ sdf_status sdf_reference_modes_eig(sdf_problem *p, int k, const sdf_eig_opts *o,
   int nsm = 148, conv = 0;
   const OpParams P = *sdf_internal_op(p, &nsm, &conv);
   if (conv) return efail(p, SDF_ERR_UNSUPPORTED, "eig: A with convection is not symmetric");
+  if (P.csr_rp) return efail(p, SDF_ERR_UNSUPPORTED, "eig: the filter runs on the grid's A");
   if (!phi_dev || ld < P.N || !ws || ((uintptr_t)ws & 255) != 0)
     return efail(p, SDF_ERR_INVALID_ARG, "eig: bad output or workspace pointer");
   if (ws_bytes < need) return efail(p, SDF_ERR_WORKSPACE, "eig: workspace too small");
@@ -860,6 +861,8 @@ sdf_status sdf_restricted_modes_eig(sdf_problem *p, const double *inst_dev,
   const OpParams P = *sdf_internal_op(p, &nsm, &conv);
   if (!inst_dev || !active_dev || !phi_dev || ld < P.N || !ws || ((uintptr_t)ws & 255) != 0)
     return efail(p, SDF_ERR_INVALID_ARG, "restricted eig: bad pointer");
+  if (P.csr_rp)
+    return efail(p, SDF_ERR_UNSUPPORTED, "restricted eig: the spectrum bound uses the grid's A");
   if (ws_bytes < need) return efail(p, SDF_ERR_WORKSPACE, "restricted eig: workspace too small");
   if (o->degree < 2 || o->max_iter < 1 || !(o->tol > 0))
     return efail(p, SDF_ERR_INVALID_ARG, "restricted eig: bad options");
@@ -1187,6 +1190,7 @@ sdf_status sdf_reference_modes_coarse(sdf_problem *p, int c, int r_pool, const s
   int nsm = 148, conv = 0;
   const OpParams P = *sdf_internal_op(p, &nsm, &conv);
   if (conv) return efail(p, SDF_ERR_UNSUPPORTED, "coarse modes: A with convection is not symmetric");
+  if (P.csr_rp) return efail(p, SDF_ERR_UNSUPPORTED, "coarse modes: no grid to coarsen");
   if (!phi_dev || ld < P.N || !ws || ((uintptr_t)ws & 255) != 0 || !(tau_sv >= 0.0))
     return efail(p, SDF_ERR_INVALID_ARG, "coarse modes: bad output, workspace or tau_sv");
   if (ws_bytes < need) return efail(p, SDF_ERR_WORKSPACE, "coarse modes: workspace too small");

@@ -31,6 +31,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <climits>
 #include <map>
 #include <type_traits>
 #include <cmath>
@@ -213,7 +214,7 @@ __global__ void __launch_bounds__(NT) k_outer_setup(OpParams P, const double *in
         [&](int, int, int, long long g) { return mk[g] ? psi[g] : 0.0; },
         [&](int, int gx, int gy, int gz, long long g, double su) {
           bool act = mk[g] != 0;
-          double rhs = P.mass * desired(P, ib, gx, gy, gz);
+          double rhs = P.rhs ? P.rhs[b * N + g] : P.mass * desired(P, ib, gx, gy, gz);
           double bv = act ? 0.0 : rhs - su;
           bb64[g] = bv;
           rb[g] = (V)bv;
@@ -682,8 +683,13 @@ __global__ void __launch_bounds__(NT) k_spmv(OpParams P, const double *inst, Ins
         [&](int e, int, int, int, long long g, V su) {
           V qv = mk[g] ? (V)0 : su;
           qb[g] = qv;
-          const V pv = sm.u[uidx<DIM>(e % TileCfg<DIM>::TX, (e / TileCfg<DIM>::TX) % TileCfg<DIM>::TY,
-                                      e / (TileCfg<DIM>::TX * TileCfg<DIM>::TY))];
+          V pv;
+          if constexpr (DIM == 1) {  // CSR rows: no staged halo, p from memory
+            pv = pb[g];
+          } else {
+            pv = sm.u[uidx<DIM>(e % TileCfg<DIM>::TX, (e / TileCfg<DIM>::TX) % TileCfg<DIM>::TY,
+                                e / (TileCfg<DIM>::TX * TileCfg<DIM>::TY))];
+          }
           if constexpr (sizeof(V) == sizeof(float)) sgf.add(pv * qv);
           else sg = fma((double)pv, (double)qv, sg);
         });
@@ -1323,7 +1329,6 @@ struct ColSrcP {  // u = p
   using Raw = float;
   __device__ __forceinline__ Raw fetch(int g) const { return p[g]; }
   __device__ __forceinline__ float value(Raw r) const { return r; }
-  __device__ __forceinline__ float aux(Raw) const { return 0.0f; }
 };
 struct ColOutQ {  // q = S_II p (zero on the active set), sigma = (p, q)
   const uint8_t *mk;
@@ -1850,7 +1855,7 @@ __global__ void __launch_bounds__(NT) k_lambda(OpParams P, const double *inst, c
     tile_S<DIM>(
         P, cb, ox, oy, oz, sm, [&](int, int, int, long long g) { return yb[g]; },
         [&](int, int gx, int gy, int gz, long long g, double su) {
-          lb[g] = P.mass * desired(P, ib, gx, gy, gz) - su;
+          lb[g] = (P.rhs ? P.rhs[b * N + g] : P.mass * desired(P, ib, gx, gy, gz)) - su;
         });
   }
 }
@@ -1969,6 +1974,11 @@ struct sdf_problem {
   // autotuned column depth of the 3D mixed kernels, keyed by batch size
   std::map<int, int> tuned_zc;
   int force_zc = 0;  // set by sdf_autotune while it times one candidate
+  // a problem created from its operator K (sdf_problem_create_csr): the
+  // assembled S = mass I + wgt K^T K and its inverse diagonal, host copies
+  bool csr = false;
+  std::vector<int> srp, sci;
+  std::vector<double> sv, sdinv;
 };
 
 namespace {
@@ -2000,8 +2010,9 @@ Layout make_layout(const sdf_problem *p, int B, int max_blocks = 0, int mixed = 
   Layout L{};
   const long long N = p->P.N;
   const int k = std::max(p->k, 1), KM = kmax_for(k);
-  long long T = p->d.dim == 2 ? num_tiles<2>(p->P.nx, p->P.ny, p->P.nz)
-                              : num_tiles<3>(p->P.nx, p->P.ny, p->P.nz);
+  long long T = p->d.dim == 1   ? num_tiles<1>(p->P.nx, p->P.ny, p->P.nz)
+                : p->d.dim == 2 ? num_tiles<2>(p->P.nx, p->P.ny, p->P.nz)
+                                : num_tiles<3>(p->P.nx, p->P.ny, p->P.nz);
   // FP64 path: two blocks per SM in total (FP64-pipe bound, large partials);
   // mixed path: eight (latency-bound stencil tiles need more resident blocks)
   long long target = (long long)p->nsm * (mixed ? 8 : 2);
@@ -2729,6 +2740,9 @@ sdf_status dispatch_phi(sdf_problem *p, const double *inst, int B, const double 
       return fail(p, SDF_ERR_UNSUPPORTED, "the FP64 path takes FP64 reference modes");
     return solve_impl<DIM, KMAX, double, double>(p, inst, B, psi, o, ws, s, y, lam, active, stats);
   }
+  if constexpr (DIM == 1) {  // refused at entry: a problem given by its operator is FP64 only
+    return fail(p, SDF_ERR_UNSUPPORTED, "no mixed path for a problem given by its operator");
+  } else {
   switch (p->phi_dtype) {
     case SDF_F32: return solve_mixed<DIM, KMAX, float>(p, inst, B, psi, o, ws, s, y, lam, active, stats);
     case SDF_BF16: return solve_mixed<DIM, KMAX, __nv_bfloat16>(p, inst, B, psi, o, ws, s, y, lam, active, stats);
@@ -2736,6 +2750,7 @@ sdf_status dispatch_phi(sdf_problem *p, const double *inst, int B, const double 
       if (p->phi && o.deflate)
         return fail(p, SDF_ERR_UNSUPPORTED, "the mixed path takes FP32 or BF16 reference modes");
       return solve_mixed<DIM, KMAX, float>(p, inst, B, psi, o, ws, s, y, lam, active, stats);
+  }
   }
 }
 
@@ -2752,6 +2767,16 @@ sdf_status dispatch_k(sdf_problem *p, const double *inst, int B, const double *p
 }
 
 size_t problem_bytes(const sdf_problem *p) {
+  if (p->csr) {
+    const long long N = p->P.N, nnz = (long long)p->sci.size();
+    size_t o = 0;
+    o = al(o + sizeof(double) * N);        // inverse diagonal of S
+    o = al(o + sizeof(float) * N);         // its FP32 copy
+    o = al(o + sizeof(int) * (N + 1));     // S row pointers
+    o = al(o + sizeof(int) * nnz);         // S column indices
+    o = al(o + sizeof(double) * nnz);      // S values
+    return o;
+  }
   const auto &d = p->d;
   long long nx = d.n[0], ny = d.n[1], nz = d.dim == 3 ? d.n[2] : 1;
   long long N = nx * ny * nz;
@@ -2796,7 +2821,8 @@ sdf_status sdf_internal_apply_S_cols(sdf_problem *p, const double *inst_dev,
   const OpParams &P = p->P;
   const int GX = std::max(1, p->nsm * 4 / cols);
   const dim3 g(GX, cols);
-  if (P.dim == 2) k_apply<2><<<g, NT, 0, s>>>(P, inst_dev, active_dev, u, out, mode, GX);
+  if (P.dim == 1) k_apply<1><<<g, NT, 0, s>>>(P, inst_dev, active_dev, u, out, mode, GX);
+  else if (P.dim == 2) k_apply<2><<<g, NT, 0, s>>>(P, inst_dev, active_dev, u, out, mode, GX);
   else k_apply<3><<<g, NT, 0, s>>>(P, inst_dev, active_dev, u, out, mode, GX);
   CKL("k_apply");
   p->prof.launches += 1;
@@ -2914,6 +2940,134 @@ sdf_status sdf_problem_create(const sdf_problem_desc *desc, const double *kappa_
   return SDF_OK;
 }
 
+sdf_status sdf_problem_create_csr(int64_t n, const int32_t *rowptr, const int32_t *col,
+                                  const double *val, double mass, double alpha, double kscale,
+                                  sdf_problem **out) {
+  if (!out) return SDF_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n < 1 || n > (1LL << 30) || !rowptr || !col || !val || !(mass > 0) || !(alpha > 0) ||
+      !(kscale > 0) || rowptr[0] != 0)
+    return SDF_ERR_INVALID_ARG;
+  for (int64_t i = 0; i < n; ++i)
+    if (rowptr[i + 1] < rowptr[i]) return SDF_ERR_INVALID_ARG;
+  const int64_t nnz = rowptr[n];
+  for (int64_t q = 0; q < nnz; ++q)
+    if (col[q] < 0 || col[q] >= n || !std::isfinite(val[q])) return SDF_ERR_INVALID_ARG;
+  // K^T by rows (the columns of K), entries in increasing row order
+  std::vector<int> tp(n + 1, 0), ti(nnz);
+  std::vector<double> tv(nnz);
+  for (int64_t q = 0; q < nnz; ++q) ++tp[col[q] + 1];
+  for (int64_t i = 0; i < n; ++i) tp[i + 1] += tp[i];
+  {
+    std::vector<int> fill(tp.begin(), tp.end() - 1);
+    for (int64_t r = 0; r < n; ++r)
+      for (int q = rowptr[r]; q < rowptr[r + 1]; ++q) {
+        const int a = fill[col[q]]++;
+        ti[a] = (int)r;
+        tv[a] = val[q];
+      }
+  }
+  // S = mass I + wgt K^T K row by row (Gustavson): row i of K^T K is the sum
+  // over the entries K_ri of K_ri times row r of K
+  sdf_problem *p = new sdf_problem();
+  p->csr = true;
+  const double wgt = alpha * kscale * kscale / mass;
+  p->srp.assign(n + 1, 0);
+  p->sdinv.assign(n, 0.0);
+  std::vector<int> mark(n, -1), cols;
+  std::vector<double> acc(n, 0.0);
+  for (int64_t i = 0; i < n; ++i) {
+    cols.clear();
+    mark[i] = (int)i;
+    acc[i] = mass;
+    cols.push_back((int)i);
+    for (int a = tp[i]; a < tp[i + 1]; ++a) {
+      const int r = ti[a];
+      const double kri = tv[a];
+      for (int q = rowptr[r]; q < rowptr[r + 1]; ++q) {
+        const int j = col[q];
+        if (mark[j] != (int)i) {
+          mark[j] = (int)i;
+          acc[j] = 0.0;
+          cols.push_back(j);
+        }
+        acc[j] += wgt * kri * val[q];
+      }
+    }
+    std::sort(cols.begin(), cols.end());
+    for (int j : cols) {
+      p->sci.push_back(j);
+      p->sv.push_back(acc[j]);
+    }
+    p->srp[i + 1] = (int)p->sci.size();
+    p->sdinv[i] = 1.0 / acc[i];
+  }
+  if (p->sci.size() > (size_t)INT_MAX) {
+    delete p;
+    return SDF_ERR_UNSUPPORTED;
+  }
+  // DIM = 1: the rows in tiles of 256 consecutive nodes
+  sdf_problem_desc &d = p->d;
+  memset(&d, 0, sizeof(d));
+  d.dim = 1;
+  d.n[0] = (int)n;
+  d.n[1] = 1;
+  d.n[2] = 1;
+  d.alpha = alpha;
+  d.mass = mass;
+  d.kscale = kscale;
+  d.diff_scale = 1.0;
+  d.yd_sigma = 1.0;
+  OpParams &P = p->P;
+  memset(&P, 0, sizeof(P));
+  P.dim = 1;
+  P.nx = (int)n;
+  P.ny = 1;
+  P.nz = 1;
+  P.N = n;
+  P.mass = mass;
+  P.wgt = wgt;
+  P.massf = (float)mass;
+  P.wgtf = (float)wgt;
+  for (int i = 0; i < 3; ++i) {
+    P.h[i] = 1.0;
+    P.inv_h[i] = 1.0;
+  }
+  P.yd_sigma = 1.0;
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      p->nsm = v;
+  }
+  if (cudaHostAlloc((void **)&p->pinned, 4 * sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+    cudaGetLastError();
+    delete p;
+    return SDF_ERR_CUDA;
+  }
+  p->ev_ready = true;
+  for (int i = 0; i < 8; ++i)
+    if (cudaEventCreate(&p->ev[i]) != cudaSuccess) p->ev_ready = false;
+  cudaGetLastError();
+  *out = p;
+  return SDF_OK;
+}
+
+sdf_status sdf_solve_batch_rhs(sdf_problem *p, const double *inst_dev, const double *rhs_dev,
+                               int batch, const double *psi_dev, const sdf_opts *opts, void *ws,
+                               size_t ws_bytes, void *stream, double *y_dev, double *lambda_dev,
+                               uint8_t *active_dev, sdf_stats *stats_host) {
+  if (!p) return SDF_ERR_INVALID_ARG;
+  if (!rhs_dev) return fail(p, SDF_ERR_INVALID_ARG, "NULL rhs");
+  if (!inst_dev && p->P.inst_conv)
+    return fail(p, SDF_ERR_INVALID_ARG, "the instances' convection velocities are needed");
+  p->P.rhs = rhs_dev;
+  sdf_status st = sdf_solve_batch(p, inst_dev, batch, psi_dev, opts, ws, ws_bytes, stream, y_dev,
+                                  lambda_dev, active_dev, stats_host);
+  p->P.rhs = nullptr;
+  return st;
+}
+
 sdf_status sdf_problem_device_bytes(const sdf_problem *p, size_t *bytes) {
   if (!p || !bytes) return SDF_ERR_INVALID_ARG;
   *bytes = problem_bytes(p);
@@ -2936,6 +3090,30 @@ sdf_status sdf_problem_bind(sdf_problem *p, void *dev_buf, size_t bytes, void *s
   o = al(o + sizeof(float) * P.N);
   P.fx = P.fy = P.fz = nullptr;
   P.fxf = P.fyf = P.fzf = nullptr;
+  if (p->csr) {
+    const long long nnz = (long long)p->sci.size();
+    int *rp = (int *)(base + o);
+    o = al(o + sizeof(int) * (P.N + 1));
+    int *ci = (int *)(base + o);
+    o = al(o + sizeof(int) * nnz);
+    double *v = (double *)(base + o);
+    std::vector<float> d32(p->sdinv.begin(), p->sdinv.end());
+    CK(cudaMemcpyAsync(rp, p->srp.data(), sizeof(int) * (P.N + 1), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ci, p->sci.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(v, p->sv.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(p->dinv_shared, p->sdinv.data(), sizeof(double) * P.N,
+                       cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(p->dinv_shared32, d32.data(), sizeof(float) * P.N, cudaMemcpyHostToDevice,
+                       s));
+    CK(cudaStreamSynchronize(s));  // the host copies are pageable and d32 is local
+    P.csr_rp = rp;
+    P.csr_ci = ci;
+    P.csr_v = v;
+    p->dev = dev_buf;
+    p->dev_bytes = bytes;
+    p->bound = true;
+    return SDF_OK;
+  }
   if (p->d.has_kappa) {
     double *kap = (double *)(base + o);
     o = al(o + sizeof(double) * P.N);
@@ -2998,6 +3176,7 @@ sdf_status sdf_analytic_modes(sdf_problem *p, int k, void *phi_dev, int64_t ld, 
     return fail(p, SDF_ERR_UNSUPPORTED,
                 "no closed-form modes on a space-time problem: build I_nt (x) Z_s with "
                 "sdf_spacetime_kron_modes");
+  if (p->csr) return fail(p, SDF_ERR_UNSUPPORTED, "no closed-form modes without a grid");
   const int dim = p->d.dim;
   int n[3] = {p->P.nx, p->P.ny, p->P.nz};
   // enumerate multi-indices with small eigenvalue sums; mu_q per direction
@@ -3092,6 +3271,8 @@ static sdf_status check_solve_args(sdf_problem *p, int batch, const sdf_opts *op
     return fail(p, SDF_ERR_INVALID_ARG, "workspace must be a 256-byte aligned device pointer");
   if (opts->precision != SDF_PREC_F64 && opts->precision != SDF_PREC_MIXED)
     return fail(p, SDF_ERR_INVALID_ARG, "unknown precision");
+  if (opts->precision == SDF_PREC_MIXED && p->csr)
+    return fail(p, SDF_ERR_UNSUPPORTED, "a problem given by its operator runs on the FP64 path");
   if (opts->precision == SDF_PREC_MIXED && p->P.convection)
     return fail(p, SDF_ERR_UNSUPPORTED,
                 "the mixed path is not validated for convection (FP32 attainable accuracy above "
@@ -3110,10 +3291,16 @@ sdf_status sdf_solve_batch(sdf_problem *p, const double *inst_dev, int batch, co
                            sdf_stats *stats_host) {
   sdf_status st = check_solve_args(p, batch, opts, ws, ws_bytes);
   if (st != SDF_OK) return st;
-  if (!inst_dev || !psi_dev || !y_dev || !active_dev)
+  if ((!inst_dev && !p->P.rhs) || !psi_dev || !y_dev || !active_dev)
     return fail(p, SDF_ERR_INVALID_ARG, "NULL input or output pointer");
+  if (p->csr && !p->P.rhs)
+    return fail(p, SDF_ERR_INVALID_ARG,
+                "a problem given by its operator has no desired state: use sdf_solve_batch_rhs");
   p->err.clear();
   cudaStream_t s = (cudaStream_t)stream;
+  if (p->d.dim == 1)
+    return dispatch_k<1>(p, inst_dev, batch, psi_dev, *opts, (char *)ws, s, y_dev, lambda_dev,
+                         active_dev, stats_host);
   if (p->d.dim == 2)
     return dispatch_k<2>(p, inst_dev, batch, psi_dev, *opts, (char *)ws, s, y_dev, lambda_dev,
                          active_dev, stats_host);
@@ -3299,7 +3486,9 @@ sdf_status sdf_apply_S(sdf_problem *p, const double *inst_dev, const uint8_t *ac
   cudaStream_t s = (cudaStream_t)stream;
   const OpParams &P = p->P;
   int GX = p->nsm * 4;
-  if (P.dim == 2) k_apply<2><<<GX, NT, 0, s>>>(P, inst_dev, active_dev, u_dev, out_dev, mode, GX);
+  if (P.dim == 1) k_apply<1><<<GX, NT, 0, s>>>(P, inst_dev, active_dev, u_dev, out_dev, mode, GX);
+  else if (P.dim == 2)
+    k_apply<2><<<GX, NT, 0, s>>>(P, inst_dev, active_dev, u_dev, out_dev, mode, GX);
   else k_apply<3><<<GX, NT, 0, s>>>(P, inst_dev, active_dev, u_dev, out_dev, mode, GX);
   CKL("k_apply");
   p->prof.launches += 1;

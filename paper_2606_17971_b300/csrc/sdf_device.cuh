@@ -37,6 +37,13 @@ struct OpParams {
   int time_axis;
   double cb_t, dt, ramp_tau;
   int inst_conv;  // instances' convection velocities are applied (in space)
+  // a problem given by its operator K (sdf_problem_create_csr): S assembled
+  // as CSR (rows of the pseudo-grid's nodes), applied row by row
+  const int *csr_rp, *csr_ci;
+  const double *csr_v;
+  // caller-given right-hand sides (instance-major, stride N) in place of
+  // mass y_d, for sdf_solve_batch_rhs; null otherwise
+  const double *rhs;
 };
 
 // Operator constants and face arrays in arithmetic type T.
@@ -66,6 +73,10 @@ template <> struct TileCfg<2> {
 template <> struct TileCfg<3> {
   static constexpr int TX = 32, TY = 4, TZ = 4, HZ = 2, HZ1 = 1;
 };
+// DIM = 1: a problem given by its operator (CSR S), tiles of 256 rows
+template <> struct TileCfg<1> {
+  static constexpr int TX = 256, TY = 1, TZ = 1, HZ = 0, HZ1 = 0;
+};
 
 // Shared-memory tile of the stencil in arithmetic type T (double for the FP64
 // path, float for the FP32 part of the mixed path).
@@ -76,6 +87,11 @@ template <int DIM, class T = double> struct TileSmem {
   static constexpr int TILE = C::TX * C::TY * C::TZ;
   T u[UZ * UY * UX];
   T w[WZ * WY * WX];
+  T v[TILE];
+};
+// the CSR tiles keep only the tile-local output vector
+template <class T> struct TileSmem<1, T> {
+  static constexpr int TILE = TileCfg<1>::TX;
   T v[TILE];
 };
 
@@ -323,9 +339,36 @@ __device__ __forceinline__ void tile_S_rows(const OpParams &P, const T cb[3], co
   __syncthreads();
 }
 
+// S u on the rows of a DIM = 1 tile from the assembled CSR S (a problem
+// created from its operator K): one thread per row, the row's entries in
+// order.  Out-of-range slots of sm.v are zeroed, as the stencil does.
 template <int DIM, class T, class Load, class Store>
-__device__ void tile_S(const OpParams &P, const double cb64[3], int ox, int oy, int oz,
-                       TileSmem<DIM, T> &sm, Load load, Store store) {
+__device__ __forceinline__ void tile_S_csr(const OpParams &P, int ox, int oy, int oz,
+                                           TileSmem<DIM, T> &sm, Load &load, Store &store) {
+  using C = TileCfg<DIM>;
+  constexpr int TILE = C::TX * C::TY * C::TZ;
+  for (int e = threadIdx.x; e < TILE; e += blockDim.x) {
+    const int lx = e % C::TX, row = e / C::TX, ly = row % C::TY, lz = row / C::TY;
+    const int gx = ox + lx, gy = oy + ly, gz = oz + lz;
+    if (gx >= P.nx || gy >= P.ny || gz >= P.nz) {
+      sm.v[e] = (T)0;
+      continue;
+    }
+    const long long g = gx + (long long)P.nx * (gy + (long long)P.ny * gz);
+    double acc = 0.0;
+    for (int q = P.csr_rp[g], qe = P.csr_rp[g + 1]; q < qe; ++q) {
+      const int j = P.csr_ci[q];
+      acc = fma(P.csr_v[q], (double)load(0, 0, 0, (long long)j), acc);
+    }
+    store(e, gx, gy, gz, g, (T)acc);
+  }
+  __syncthreads();
+}
+
+template <int DIM, class T, class Load, class Store>
+__device__ __forceinline__ void tile_S_grid(const OpParams &P, const double cb64[3], int ox,
+                                            int oy, int oz, TileSmem<DIM, T> &sm, Load &load,
+                                            Store &store) {
   const T cb[3] = {(T)cb64[0], (T)cb64[1], (T)cb64[2]};
   const T cd[3] = {OpT<T>::cd(P, 0), OpT<T>::cd(P, 1), OpT<T>::cd(P, 2)};
   const T mass = OpT<T>::mass(P), wgt = OpT<T>::wgt(P);
@@ -341,6 +384,18 @@ __device__ void tile_S(const OpParams &P, const double cb64[3], int ox, int oy, 
       tile_S_rows<DIM, T, true, false>(P, cb, cd, mass, wgt, ox, oy, oz, sm, load, store);
     else
       tile_S_rows<DIM, T, false, false>(P, cb, cd, mass, wgt, ox, oy, oz, sm, load, store);
+  }
+}
+
+// S u on the tile with origin (ox, oy, oz): the row-wise CSR product on a
+// problem given by its operator (DIM = 1), the stencil otherwise.
+template <int DIM, class T, class Load, class Store>
+__device__ void tile_S(const OpParams &P, const double cb64[3], int ox, int oy, int oz,
+                       TileSmem<DIM, T> &sm, Load load, Store store) {
+  if constexpr (DIM == 1) {
+    tile_S_csr<DIM, T>(P, ox, oy, oz, sm, load, store);
+  } else {
+    tile_S_grid<DIM, T>(P, cb64, ox, oy, oz, sm, load, store);
   }
 }
 

@@ -87,6 +87,10 @@ _sigs = {
     "sdf_default_opts": (None, [ctypes.POINTER(Opts)]),
     "sdf_problem_create": (_i32, [ctypes.POINTER(ProblemDesc), _vp, ctypes.POINTER(_vp)]),
     "sdf_problem_device_bytes": (_i32, [_vp, ctypes.POINTER(_sz)]),
+    "sdf_problem_create_csr": (_i32, [_i64, _vp, _vp, _vp, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, ctypes.POINTER(_vp)]),
+    "sdf_solve_batch_rhs": (_i32, [_vp, _vp, _vp, _i32, _vp, ctypes.POINTER(Opts), _vp, _sz, _vp,
+                                   _vp, _vp, _vp, _vp]),
     "sdf_problem_bind": (_i32, [_vp, _vp, _sz, _vp]),
     "sdf_set_reference_modes": (_i32, [_vp, _vp, _i32, _i64, _i32]),
     "sdf_analytic_modes": (_i32, [_vp, _i32, _vp, _i64, _i32, _vp, _vp]),
@@ -213,6 +217,33 @@ class Problem:
         self._check(_lib.sdf_problem_bind(self._h, _ptr(self._buf), self._buf.numel(), _stream()))
         self._phi = None
         self._ws = None
+
+    @classmethod
+    def csr(cls, K, alpha=1e-4, mass=1.0, kscale=1.0, device="cuda"):
+        """sdf_problem_create_csr: a problem given by its operator K (a
+        scipy.sparse matrix, n x n); S = mass I + alpha kscale^2/mass K^T K
+        is assembled by the library.  Solve with solve_rhs."""
+        K = K.tocsr()
+        n = K.shape[0]
+        rp = np.ascontiguousarray(K.indptr, dtype=np.int32)
+        ci = np.ascontiguousarray(K.indices, dtype=np.int32)
+        v = np.ascontiguousarray(K.data, dtype=np.float64)
+        self = cls.__new__(cls)
+        h = ctypes.c_void_p()
+        st = _lib.sdf_problem_create_csr(n, rp.ctypes.data, ci.ctypes.data, v.ctypes.data, mass,
+                                         alpha, kscale, ctypes.byref(h))
+        if st != 0:
+            raise SdfError(st, "sdf_problem_create_csr")
+        self._h = h
+        self.dim, self.n, self.N = 0, (n,), n
+        self.device = torch.device(device)
+        nb = _sz()
+        self._check(_lib.sdf_problem_device_bytes(self._h, ctypes.byref(nb)))
+        self._buf = torch.empty(max(int(nb.value), 256), dtype=torch.uint8, device=self.device)
+        self._check(_lib.sdf_problem_bind(self._h, _ptr(self._buf), self._buf.numel(), _stream()))
+        self._phi = None
+        self._ws = None
+        return self
 
     def _check(self, st):
         if st != 0:
@@ -456,6 +487,29 @@ class Problem:
         st = _lib.sdf_solve_batch_x0(self._h, _ptr(inst), B, _ptr(psi), _ptr(x0),
                                      ctypes.byref(opts), _ptr(ws), ws.numel(), _stream(),
                                      _ptr(out["y"]), _ptr(out["lam"]), _ptr(out["active"]), stats)
+        if st not in (0, 5, 6, 7, 8):
+            self._check(st)
+        out["status"] = st
+        out["stats"] = [stats_dict(s) for s in stats]
+        return out
+
+    def solve_rhs(self, rhs: torch.Tensor, psi: torch.Tensor, opts=None, inst=None,
+                  want_lambda=False, out=None):
+        """sdf_solve_batch_rhs: rhs (B, N) float64 device tensor in place of
+        the instances' mass y_d; inst (B, 7) only for per-instance convection."""
+        opts = opts or default_opts()
+        assert rhs.dtype == torch.float64 and rhs.is_contiguous() and rhs.shape[1] == self.N
+        B = rhs.shape[0]
+        ws = self.workspace(B, opts)
+        if out is None:
+            out = dict(y=torch.empty((B, self.N), dtype=torch.float64, device=self.device),
+                       lam=torch.empty((B, self.N), dtype=torch.float64, device=self.device)
+                       if want_lambda else None,
+                       active=torch.empty((B, self.N), dtype=torch.uint8, device=self.device))
+        stats = (Stats * B)()
+        st = _lib.sdf_solve_batch_rhs(self._h, _ptr(inst), _ptr(rhs), B, _ptr(psi),
+                                      ctypes.byref(opts), _ptr(ws), ws.numel(), _stream(),
+                                      _ptr(out["y"]), _ptr(out["lam"]), _ptr(out["active"]), stats)
         if st not in (0, 5, 6, 7, 8):
             self._check(st)
         out["status"] = st

@@ -443,3 +443,17 @@ def test_ritz_reselection_recovers_the_exact_modes_in_a_pool():
     np.testing.assert_allclose(ritz["x"], exact["x"], rtol=0, atol=1e-7 * np.abs(exact["x"]).max())
     # the guard sees the selected Galerkin matrix: cond = lambda_8 / lambda_1
     np.testing.assert_allclose(ritz["cond_E"], lam[-1] / lam[0], rtol=1e-6)
+
+
+def test_schur_from_operator_is_the_grid_assembly():
+    # S from a state operator K (a problem given without a grid) against the
+    # C assembly of the same grid operator, mass and kscale included
+    import scipy.sparse as sp
+    from paper_2606_17971_b300 import workloads as W
+    w = W.scaled(W.WORKLOADS["block2d_1024"], 20)
+    for mass, kscale in ((1.0, 1.0), (2.5, 0.7)):
+        P = O.Problem(2, w.n, kappa=W.kappa_field(w), alpha=1e-3, mass=mass, kscale=kscale)
+        rp, ci, v = P.csr_A()
+        A = sp.csr_matrix((v, ci, rp), shape=(P.N, P.N))
+        S = O.schur_from_operator(A, alpha=1e-3, mass=mass, kscale=kscale).toarray()
+        np.testing.assert_allclose(S, P.dense_S(), rtol=1e-13, atol=1e-10)
