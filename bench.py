@@ -216,7 +216,8 @@ def spacetime_leg(w, sdf, dev):
                     t_final=w.extra["t_final"], ramp_tau=w.extra["ramp_tau"], device=dev)
     zs, _ = sdf.Problem(2, w.n, alpha=w.alpha, yd_sigma=w.sigma, device=dev).analytic_modes(w.k)
     kron = G.spacetime_kron_modes(zs)
-    lift = (zs / np.sqrt(n_t)).repeat(1, n_t).contiguous()  # row j: mode j on every step
+    # the constant-in-time lift is W_t (x) Z_s with W_t = 1_nt / sqrt(n_t)
+    lift = G.spacetime_modes(np.full((n_t, 1), 1.0 / np.sqrt(n_t)), zs)
     inst = torch.as_tensor(W.instances_array(W.draw_instances(w, count=w.batch)), device=dev)
     psi = torch.full((G.N,), w.psi, dtype=torch.float64, device=dev)
     res = {"workload": w.name, "grid": [w.n, w.n], "n_t": n_t, "N": G.N, "instances": w.batch,
