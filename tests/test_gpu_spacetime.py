@@ -190,3 +190,29 @@ def test_full_cosine_basis_deflates_like_kronecker_on_gpu(sdf):
     for b in range(2):
         assert abs(its["full"][b] - its["kron"][b]) <= max(3, 0.02 * its["kron"][b]), its
         assert its["half"][b] > its["kron"][b] + 5, its
+
+
+def test_space_time_eigenmodes_span_the_kronecker_basis(sdf):
+    # App. E.2.1 compares eigenmodes of the space-time operator with the
+    # Kronecker basis.  With constant kappa and no convection the spatial
+    # sines diagonalise S_st, and here its r n_t lowest eigenvectors span
+    # I_nt (x) Z_s(r) exactly, so the two bases deflate alike
+    w = W.WORKLOADS["spacetime2d_64"]
+    n, n_t, r = 24, 8, 4
+    G = _gpu_problem(sdf, w, n, n_t)
+    zs, _ = sdf.Problem(2, n, alpha=w.alpha, yd_sigma=w.sigma).analytic_modes(r)
+    kron = G.spacetime_kron_modes(zs)
+    G.set_modes(kron)
+    inst = torch.as_tensor([[2.0, 0.45, 0.55, 0, 0, 0, 0]], dtype=torch.float64, device=DEV)
+    act = torch.zeros(G.N, dtype=torch.uint8, device=DEV)
+    V, lam, st = G.restricted_modes(inst[0], act, r * n_t)
+    assert st["converged"], st
+    _, srt = G.diag_angles(act, V, sorted_angles=True)
+    assert srt.max() < 1e-5, srt.max()
+    _, S = ST.problem(n, n_t, w.alpha, T=w.extra["t_final"])
+    np.testing.assert_allclose(lam, np.linalg.eigvalsh(S.toarray())[:r * n_t], rtol=1e-9)
+    psi = torch.full((G.N,), 10.0, dtype=torch.float64, device=DEV)
+    it_kron = G.solve(inst, psi, want_lambda=False)["stats"][0]["cg_iters"][0]
+    G.set_modes(V)
+    it_eig = G.solve(inst, psi, want_lambda=False)["stats"][0]["cg_iters"][0]
+    assert abs(it_eig - it_kron) <= 3, (it_eig, it_kron)
