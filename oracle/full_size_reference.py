@@ -3,6 +3,9 @@ first instances of the 128^3 diffusion workload (k = 60 closed-form reference
 modes, rtol 1e-8, psi = 1).  Calls only the oracle; takes tens of minutes per
 instance on a few CPU cores, so it is run once and its output committed.
 
+TEST INFRASTRUCTURE ONLY: it writes a stored expected value for tests/ and
+calls nothing outside oracle/ and the seeded input generators.
+
 Usage: python -m oracle.full_size_reference [count]
 """
 import json
