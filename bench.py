@@ -304,6 +304,54 @@ def diag_sweep_leg(n, count, sdf, dev, K=40, r=20, psi_value=0.5):
             "rows": rows}
 
 
+def csr_leg(n, sdf, dev, batch=8, k=16):
+    """A problem given by its operator: K = the 5-point -Laplace on an n x n
+    grid, built here with scipy as a caller would, solved through
+    sdf_problem_create_csr / sdf_solve_batch_rhs, against the grid path on the
+    same operator and the same family of right-hand sides (mass y_d of the
+    same instances, evaluated here as a caller would), FP64, k closed-form
+    modes; not part of the metric."""
+    import scipy.sparse as sp
+    import torch
+    from paper_2606_17971_b300 import workloads as W
+    w = W.scaled(W.WORKLOADS["diff2d_32"], n)
+    h = 1.0 / (n + 1)
+    T1 = sp.diags([-np.ones(n - 1), 2.0 * np.ones(n), -np.ones(n - 1)], [-1, 0, 1]) / h**2
+    K = (sp.kron(sp.identity(n), T1) + sp.kron(T1, sp.identity(n))).tocsr()
+    Gg = sdf.Problem(2, n, alpha=w.alpha, yd_sigma=w.sigma, device=dev)
+    phi, _ = Gg.analytic_modes(k)
+    Gg.set_modes(phi)
+    t0 = time.perf_counter()
+    Gc = sdf.Problem.csr(K, alpha=w.alpha, device=dev)
+    t_create = time.perf_counter() - t0
+    Gc.set_modes(phi)
+    insts = W.draw_instances(w, count=batch)
+    inst = torch.as_tensor(W.instances_array(insts), device=dev)
+    psi = torch.full((Gg.N,), w.psi, dtype=torch.float64, device=dev)
+    # the caller's right-hand sides: the same Gaussian family at the nodes
+    x = (np.arange(n) + 1) * h
+    gy, gx = np.meshgrid(x, x, indexing="ij")
+    rhs = torch.as_tensor(np.stack([
+        i.a * np.exp(-((gx - i.c[0]) ** 2 + (gy - i.c[1]) ** 2).ravel() / (2 * w.sigma**2))
+        for i in insts]), device=dev).contiguous()
+    res = {"grid": [n, n], "instances": batch, "k": k, "nnz_K": int(K.nnz),
+           "host_assembly_s": t_create}
+    stream = torch.cuda.current_stream()
+    for name, run in (("grid", lambda: Gg.solve(inst, psi, want_lambda=False)),
+                      ("csr", lambda: Gc.solve_rhs(rhs, psi))):
+        run()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        r = run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        res[name] = {"instances_per_s": batch / (e0.elapsed_time(e1) * 1e-3),
+                     "cg_iters_per_instance": float(np.mean([sum(s["cg_iters"]) for s in r["stats"]])),
+                     "statuses": sorted(set(s["status"] for s in r["stats"]))}
+    return res
+
+
 def oracle_counts(name):
     path = os.path.join(ROOT, "tests", "golden", f"{name}_oracle.json")
     if not os.path.exists(path):
@@ -387,6 +435,9 @@ def main():
                     help="also run the spectral-coherence sweep of Sec. 4.1 over this many "
                          "instances of the 2D diffusion family (0: off)")
     ap.add_argument("--diag-n", type=int, default=128, help="grid of the diagnostics sweep")
+    ap.add_argument("--csr-n", type=int, default=0,
+                    help="also time the CSR operator path against the grid path on an n x n "
+                         "diffusion problem (0: off)")
     args = ap.parse_args()
 
     from paper_2606_17971_b300 import workloads as W
@@ -672,6 +723,8 @@ def main():
             "note": "sdf_diag_active_sets, host round trip included"}
     if args.spacetime and rank == 0:
         line["spacetime"] = spacetime_leg(W.WORKLOADS[args.spacetime], sdf, dev)
+    if args.csr_n and rank == 0:
+        line["csr_path"] = csr_leg(args.csr_n, sdf, dev)
     if args.diag_sweep and rank == 0:
         line["diagnostics_sweep"] = diag_sweep_leg(args.diag_n, args.diag_sweep, sdf, dev)
     if rank == 0:
