@@ -457,3 +457,10 @@ def test_schur_from_operator_is_the_grid_assembly():
         A = sp.csr_matrix((v, ci, rp), shape=(P.N, P.N))
         S = O.schur_from_operator(A, alpha=1e-3, mass=mass, kscale=kscale).toarray()
         np.testing.assert_allclose(S, P.dense_S(), rtol=1e-13, atol=1e-10)
+    # a nonsymmetric operator (upwind convection): K^T K, not K K^T
+    P = O.Problem(2, 14, diff_scale=1e-2, b=(0.8, -0.6), alpha=1e-3)
+    rp, ci, v = P.csr_A()
+    A = sp.csr_matrix((v, ci, rp), shape=(P.N, P.N))
+    assert abs(A - A.T).max() > 1.0
+    S = O.schur_from_operator(A, alpha=1e-3).toarray()
+    np.testing.assert_allclose(S, P.dense_S(), rtol=1e-13, atol=1e-10)
