@@ -286,7 +286,10 @@ def diag_sweep_leg(n, count, sdf, dev, K=40, r=20, psi_value=0.5):
         t_ang += time.perf_counter() - t0
         n_d = sum(defl["stats"][b]["cg_iters"])
         n_c = sum(cold["stats"][b]["cg_iters"])
+        q = np.array_split(np.degrees(srt), 5)  # mean angle per mode quintile (App. D.6)
         rows.append({"a": insts[b].a, "delta": float(sets["delta"][b]), "rho": float(sets["rho"][b]),
+                     "delta_w": float(sets["delta_w"][b]),
+                     "quintile_mean_deg": [float(x.mean()) for x in q],
                      "theta_r_deg": float(np.degrees(srt[r - 1])),
                      "theta_max_deg": float(np.degrees(srt[-1])),
                      "nested_theta_r_deg": float(np.degrees(nested[r - 1])),
@@ -295,12 +298,19 @@ def diag_sweep_leg(n, count, sdf, dev, K=40, r=20, psi_value=0.5):
     t["restricted_eig_s"] = t_eig
     t["angles_s"] = t_ang
     d = np.array([x["delta"] for x in rows])
+    dw = np.array([x["delta_w"] for x in rows])
     e = np.array([x["eff"] for x in rows])
+
+    def corr(a, c):
+        return float(np.corrcoef(a, c)[0, 1]) if a.std() > 0 and c.std() > 0 else None
+
     return {"grid": [n, n], "instances": count, "psi": psi_value, "K": K, "r": r, "seconds": t,
             "delta_max": float(d.max()), "theta_r_max_deg": max(x["theta_r_deg"] for x in rows),
             "theta_max_min_deg": min(x["theta_max_deg"] for x in rows),
             "eff_mean": float(e.mean()), "eff_std": float(e.std()),
-            "corr_delta_eff": float(np.corrcoef(d, e)[0, 1]) if d.std() > 0 and e.std() > 0 else None,
+            "corr_delta_eff": corr(d, e), "corr_delta_w_eff": corr(dw, e),
+            "quintile_mean_deg": [float(np.mean([x["quintile_mean_deg"][i] for x in rows]))
+                                  for i in range(5)],
             "rows": rows}
 
 
