@@ -534,6 +534,20 @@ sdf_status sdf_restricted_modes_eig(sdf_problem *p, const double *inst_dev,
  * deficient.  k <= the number of registered modes.
  * ws: at least sdf_diag_angles_workspace_size bytes. */
 sdf_status sdf_diag_angles_workspace_size(const sdf_problem *p, int k, size_t *bytes);
+
+/* True relative residual of each instance's final inner solve, from the
+ * outputs of a solve with lambda requested (App. B.2: the solve stops on the
+ * recurrence residual, which can drift from the true one):
+ *   relres_host[b] = ||r_I|| / ||b_I||, r_I = lambda_I (lambda = rhs - S y),
+ *   b_I = rhs_I - S_IA psi_A = r_I + S_II y_I.
+ * y_dev, lambda_dev: B x N FP64; active_dev: B x N bytes (the final active
+ * sets); inst_dev: B x SDF_INSTANCE_DOUBLES, may be NULL without per-instance
+ * convection; all device.  One S_II application per instance.  ws: at
+ * least sdf_diag_relres_workspace_size bytes. */
+sdf_status sdf_diag_relres_workspace_size(const sdf_problem *p, size_t *bytes);
+sdf_status sdf_diag_relres(sdf_problem *p, const double *inst_dev, int B, const double *y_dev,
+                           const double *lambda_dev, const uint8_t *active_dev,
+                           double *relres_host, void *ws, size_t ws_bytes, void *stream);
 sdf_status sdf_diag_angles(sdf_problem *p, const uint8_t *active_dev, const double *V_dev,
                            int64_t ldv, int k, double *theta_host, double *sorted_host, void *ws,
                            size_t ws_bytes, void *stream);

@@ -456,6 +456,37 @@ __global__ void __launch_bounds__(ET) k_diag_sets(const uint8_t *aref, const uin
   }
 }
 
+// Partial sums over node chunks (blockIdx.x) of ||lam_I||^2 and
+// ||lam_I + (S_II y)_I||^2 for one instance: part[2 chunk + {0, 1}]
+__global__ void __launch_bounds__(ET) k_relres_parts(const double *lam, const double *sy,
+                                                     const uint8_t *act, long long N, int nchunk,
+                                                     double *part) {
+  __shared__ double red[2][ET / 32];
+  const long long per = (N + nchunk - 1) / nchunk;
+  const long long g0 = blockIdx.x * per, g1 = min(N, g0 + per);
+  double rr = 0.0, bb = 0.0;
+  for (long long g = g0 + threadIdx.x; g < g1; g += ET) {
+    if (act[g]) continue;
+    const double r = lam[g], b = r + sy[g];
+    rr = fma(r, r, rr);
+    bb = fma(b, b, bb);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    rr += __shfl_down_sync(0xffffffffu, rr, o);
+    bb += __shfl_down_sync(0xffffffffu, bb, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = rr;
+    red[1][threadIdx.x >> 5] = bb;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    double t = 0.0;
+    for (int q = 0; q < ET / 32; ++q) t += red[threadIdx.x][q];
+    part[2 * (long long)blockIdx.x + threadIdx.x] = t;
+  }
+}
+
 // Orthonormalise the m columns of *A in place: shifted Cholesky-QR, then
 // Cholesky-QR twice (Fukaya et al., "shifted CholeskyQR3"); the shift
 // 11 (N m + m (m + 1)) u ||A||_F^2 keeps the first factorisation defined
@@ -1052,6 +1083,55 @@ sdf_status sdf_diag_drift(sdf_problem *p, const double *inst_ref_dev, const doub
         V, x, part, cdev, nd);
     if (e != SDF_OK) return e;
     eps_host[b] = nref > 0.0 ? nd / nref : 0.0;
+  }
+  return SDF_OK;
+}
+
+sdf_status sdf_diag_relres_workspace_size(const sdf_problem *p, size_t *bytes) {
+  int nsm = 148, conv = 0;
+  const OpParams *P = p ? sdf_internal_op(p, &nsm, &conv) : nullptr;
+  if (!P || !bytes) return SDF_ERR_INVALID_ARG;
+  *bytes = al256(sizeof(double) * (size_t)P->N) + al256(sizeof(double) * 2 * (size_t)2 * nsm);
+  return SDF_OK;
+}
+
+sdf_status sdf_diag_relres(sdf_problem *p, const double *inst_dev, int B, const double *y_dev,
+                           const double *lambda_dev, const uint8_t *active_dev,
+                           double *relres_host, void *ws, size_t ws_bytes, void *stream) {
+  if (!p) return SDF_ERR_INVALID_ARG;
+  size_t need = 0;
+  if (sdf_diag_relres_workspace_size(p, &need) != SDF_OK)
+    return efail(p, SDF_ERR_INVALID_ARG, "diag relres: unbound problem");
+  int nsm = 148, conv = 0;
+  const OpParams P = *sdf_internal_op(p, &nsm, &conv);
+  if (B < 1 || !y_dev || !lambda_dev || !active_dev || !relres_host || !ws ||
+      ((uintptr_t)ws & 255) != 0 || (!inst_dev && P.inst_conv))
+    return efail(p, SDF_ERR_INVALID_ARG, "diag relres: bad pointer or B");
+  if (ws_bytes < need) return efail(p, SDF_ERR_WORKSPACE, "diag relres: workspace too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long N = P.N;
+  const int nchunk = 2 * nsm;
+  double *sy = (double *)ws;
+  double *part = (double *)((char *)ws + al256(sizeof(double) * (size_t)N));
+  std::vector<double> pp(2 * (size_t)nchunk);
+  for (int b = 0; b < B; ++b) {
+    // the instance row is read only for its convection velocity; without
+    // per-instance convection any valid pointer stands in for it
+    const double *ib = inst_dev ? inst_dev + (size_t)b * SDF_INSTANCE_DOUBLES : y_dev;
+    const uint8_t *ab = active_dev + (size_t)b * N;
+    // S_II y_I (mode 0 reads y as zero on A and writes zero there)
+    sdf_status e = sdf_internal_apply_S_cols(p, ib, ab, y_dev + (size_t)b * N, sy, 1, 0, s);
+    if (e != SDF_OK) return e;
+    k_relres_parts<<<nchunk, ET, 0, s>>>(lambda_dev + (size_t)b * N, sy, ab, N, nchunk, part);
+    ECK(cudaGetLastError());
+    ECK(cudaMemcpyAsync(pp.data(), part, sizeof(double) * pp.size(), cudaMemcpyDeviceToHost, s));
+    ECK(cudaStreamSynchronize(s));
+    double rr = 0.0, bb = 0.0;
+    for (int c = 0; c < nchunk; ++c) {
+      rr += pp[2 * (size_t)c];
+      bb += pp[2 * (size_t)c + 1];
+    }
+    relres_host[b] = bb > 0.0 ? std::sqrt(rr / bb) : 0.0;
   }
   return SDF_OK;
 }

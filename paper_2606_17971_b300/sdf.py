@@ -145,6 +145,8 @@ _sigs = {
     "sdf_restricted_modes_eig": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _i64, _vp, _vp, _vp, _sz,
                                         _vp]),
     "sdf_diag_angles_workspace_size": (_i32, [_vp, _i32, ctypes.POINTER(_sz)]),
+    "sdf_diag_relres_workspace_size": (_i32, [_vp, ctypes.POINTER(_sz)]),
+    "sdf_diag_relres": (_i32, [_vp, _vp, _i32, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "sdf_diag_angles": (_i32, [_vp, _vp, _vp, _i64, _i32, _vp, _vp, _vp, _sz, _vp]),
 }
 for _name, (_res, _args) in _sigs.items():
@@ -403,6 +405,21 @@ class Problem:
         stats = dict(iters=st.iters, converged=bool(st.converged), max_rel_resid=st.max_rel_resid,
                      matvecs=st.matvecs, seconds=st.seconds, status=rc)
         return V, lam, stats
+
+    def diag_relres(self, out, inst: torch.Tensor = None):
+        """sdf_diag_relres: the true relative residual of each instance's
+        final inner solve, from a solve's outputs (y, lam, active; lam must
+        have been requested)."""
+        y, lam, act = out["y"], out["lam"], out["active"]
+        assert lam is not None, "solve with want_lambda=True"
+        B = y.shape[0]
+        nb = _sz()
+        self._check(_lib.sdf_diag_relres_workspace_size(self._h, ctypes.byref(nb)))
+        ws = torch.empty(int(nb.value), dtype=torch.uint8, device=self.device)
+        rel = np.zeros(B)
+        self._check(_lib.sdf_diag_relres(self._h, _ptr(inst), B, _ptr(y), _ptr(lam), _ptr(act),
+                                         rel.ctypes.data, _ptr(ws), ws.numel(), _stream()))
+        return rel
 
     def diag_angles(self, active: torch.Tensor, V: torch.Tensor, k=None, sorted_angles=False):
         """sdf_diag_angles for V (k, N) float64 against the registered modes
