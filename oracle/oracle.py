@@ -48,6 +48,8 @@ class Stats(ctypes.Structure):
         ("true_relres", ctypes.c_double),
         ("min_margin", ctypes.c_double),
         ("min_lambda_active", ctypes.c_double),
+        ("true_relres_each", ctypes.c_double * MAX_OUTER),
+        ("relres_floor", ctypes.c_double * MAX_OUTER),
     ]
 
 
@@ -108,6 +110,7 @@ def lib():
                                          ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                          ctypes.c_double, dp, ip, dp, dp, ip]
         _lib.orc_last_timing.argtypes = [dp, dp]
+        _lib.orc_last_residuals.argtypes = [dp, dp]
         _lib.orc_solve.restype = ctypes.c_int
         _lib.orc_solve.argtypes = [P, dp, dp, dp, ctypes.c_int, ctypes.c_int,
                                    ctypes.POINTER(Opts), dp, dp, dp, up,
@@ -247,8 +250,11 @@ class Problem:
                                    ctypes.byref(ce), ctypes.byref(fb))
         ts, tl = ctypes.c_double(0), ctypes.c_double(0)
         lib().orc_last_timing(ctypes.byref(ts), ctypes.byref(tl))
+        tr, fl = ctypes.c_double(0), ctypes.c_double(0)
+        lib().orc_last_residuals(ctypes.byref(tr), ctypes.byref(fl))
         return dict(x=x, status=st, iters=it.value, relres=rr.value, cond_E=ce.value,
-                    fallback=fb.value, t_setup=ts.value, t_loop=tl.value)
+                    fallback=fb.value, t_setup=ts.value, t_loop=tl.value,
+                    true_relres=tr.value, relres_floor=fl.value)
 
     def solve(self, rhs, psi, Phi=None, deflate=True, rtol=1e-8, tau=1e-10,
               tau_cond=1e10, max_outer=30, max_cg=100000, rule=0, pdas_c=1.0,
@@ -278,7 +284,9 @@ class Problem:
             n_active=list(st.n_active[:no]), fallback=list(st.fallback[:no]),
             cond_E=list(st.cond_E[:no]), relres=list(st.relres[:no]),
             true_relres=st.true_relres, min_margin=st.min_margin,
-            min_lambda_active=st.min_lambda_active)
+            min_lambda_active=st.min_lambda_active,
+            true_relres_each=list(st.true_relres_each[:no]),
+            relres_floor=list(st.relres_floor[:no]))
 
 
 def analytic_modes(dim, n, k, alpha=1e-4, diff_scale=1.0):
