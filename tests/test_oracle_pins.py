@@ -464,3 +464,68 @@ def test_schur_from_operator_is_the_grid_assembly():
     assert abs(A - A.T).max() > 1.0
     S = O.schur_from_operator(A, alpha=1e-3).toarray()
     np.testing.assert_allclose(S, P.dense_S(), rtol=1e-13, atol=1e-10)
+
+
+# --------------------------------------------------------------------------
+# true residual and attainable-accuracy floor of an inner solve (App. B.2)
+
+def _restricted_dense(P, active):
+    S = P.dense_S()
+    I = np.flatnonzero(~active)
+    return S, I
+
+
+def test_floor_uses_the_entrywise_absolute_value_of_S_II():
+    # Independent route to || |S_II| |x| ||: A is an M-matrix that couples
+    # nearest neighbours only, so every entry of S = I + alpha A^T A has the
+    # checkerboard sign s_i s_j and |S| = D S D with D = diag(s).  A planted
+    # |S| x (no absolute value on S) or S |x| fails this on a convective,
+    # variable-kappa operator with a non-empty active set.
+    n = 14
+    rng = np.random.default_rng(8)
+    kappa = 10.0 ** rng.uniform(-1, 1, n * n)
+    P = O.Problem(2, n, kappa=kappa, b=np.array([0.7, -0.4]), alpha=1e-4)
+    rhs = P.desired_state(3.0, (0.4, 0.6), 0.12)[1]
+    psi = np.full(P.N, 0.6)
+    r = P.solve(rhs, psi, None, deflate=False, rtol=1e-10)
+    assert r["status"] == 0 and r["outer_iters"] >= 2
+    active = r["active"]
+    # the last inner solve ran on the final active set (no change at exit)
+    S, I = _restricted_dense(P, active)
+    jj, ii = np.divmod(np.arange(P.N), n)
+    d = np.where((ii + jj) % 2 == 0, 1.0, -1.0)
+    SII = S[np.ix_(I, I)]
+    x = r["y"][I]
+    via_signs = (d[I][:, None] * SII * d[I][None, :]) @ np.abs(x)
+    assert np.allclose(via_signs, np.abs(SII) @ np.abs(x), rtol=1e-14, atol=0)
+    b = rhs[I] - S[np.ix_(I, np.flatnonzero(active))] @ psi[active]
+    want = 10.0 * 2.0 ** -53 * np.linalg.norm(via_signs) / np.linalg.norm(b)
+    assert r["relres_floor"][-1] == pytest.approx(want, rel=1e-12)
+    assert r["true_relres_each"][-1] == pytest.approx(
+        np.linalg.norm(b - SII @ x) / np.linalg.norm(b), rel=1e-6)
+
+
+def test_floor_is_where_the_fp64_residual_of_the_exact_solution_lies():
+    # The exact solution of S y = b, found by iterative refinement with
+    # residuals in extended precision and rounded to FP64, has an FP64 true
+    # residual that no FP64 method can beat.  It lies below the floor
+    # 10 u || |S||y| || / ||b|| and within two decades of it (a floor of the
+    # right size: neither vacuous nor unattainable).
+    n = 22
+    w = W.scaled(W.WORKLOADS["lognormal2d_2048"], n)
+    P = O.Problem(2, n, kappa=W.kappa_field(w), alpha=1e-4)
+    rhs = P.desired_state(2.0, (0.5, 0.5), 0.1)[1]
+    S = P.dense_S()
+    Sl = S.astype(np.longdouble)
+    y = np.linalg.solve(S, rhs)
+    for _ in range(6):
+        res = rhs.astype(np.longdouble) - Sl @ y.astype(np.longdouble)
+        y = (y.astype(np.longdouble) + np.linalg.solve(S, res.astype(np.float64))).astype(np.float64)
+    r64 = np.linalg.norm(rhs - P.apply_S(y)) / np.linalg.norm(rhs)
+    floor = 10.0 * 2.0 ** -53 * np.linalg.norm(np.abs(S) @ np.abs(y)) / np.linalg.norm(rhs)
+    assert floor > 1e-13  # an ill-conditioned case: the floor is far above u
+    assert floor / 100.0 <= r64 <= floor
+    # the oracle's plain solve at a tight rtol reports that floor for its own y
+    r = P.solve(rhs, np.full(P.N, 1e30), None, deflate=False, rtol=1e-14, max_cg=20000)
+    assert r["relres_floor"][0] == pytest.approx(floor, rel=1e-6)
+    assert r["true_relres_each"][0] <= 2 * floor
