@@ -63,7 +63,11 @@ typedef enum { SDF_F64 = 0, SDF_F32 = 1, SDF_BF16 = 2 } sdf_dtype;
  *                   set-up stay FP64, and every `replace_every` iterations
  *                   the residual is recomputed as b - S_II x with the FP64
  *                   stencil and the coarse correction x += Q r is applied;
- *                   convergence is declared only on that FP64 residual.
+ *                   convergence is declared only on that FP64 residual:
+ *                   ||b - S_II x|| <= max(rtol ||b||, floor_c u || |S_II||x| ||)
+ *                   (the second term, the attainable accuracy of an FP64
+ *                   residual, is evaluated when the recurrence has met rtol
+ *                   or the true residual has stopped falling; see sdf_stats).
  *                   Not available with per-instance convection
  *                   (SDF_ERR_UNSUPPORTED). */
 typedef enum { SDF_PREC_F64 = 0, SDF_PREC_MIXED = 1 } sdf_precision;
@@ -148,7 +152,12 @@ typedef struct {
  *                basis so far (skipped if its norm < tau_dep) and accepted
  *                while cond(Z^T S_II Z) <= tau_safe (the first violation ends
  *                the merge).  Takes precedence over ritz_r        [0: off]
- *   tau_safe, tau_dep  thresholds of the safe merge          [1e4, 1e-10] */
+ *   tau_safe, tau_dep  thresholds of the safe merge          [1e4, 1e-10]
+ *   floor_c      constant of the attainable-accuracy floor (sdf_stats); the
+ *                mixed path stops on max(rtol, floor); 0: rtol only  [10]
+ *   column_depth mixed 3D path: z planes per column item of the stencil
+ *                kernels, 8, 16, 32 or 64 (0: the depth sdf_autotune chose
+ *                for this batch size, else 32 for batches of 8 or more) [0] */
 typedef struct {
   double rtol;
   double tau;
@@ -166,17 +175,31 @@ typedef struct {
   int32_t safe_r;
   double tau_safe;
   double tau_dep;
+  double floor_c;
+  int32_t column_depth;
 } sdf_opts;
 
-/* Per-instance statistics (host struct filled at the end of a solve). */
+/* Per-instance statistics (host struct filled at the end of a solve).
+ * true_relres and relres_floor are taken in FP64 on each inner solve's final
+ * iterate x_I (App. B.2: the stopping rule tests the recurrence residual,
+ * which can drift from the true one):
+ *   true_relres  = ||b_I - S_II x_I|| / ||b_I||,
+ *   relres_floor = floor_c u || |S_II| |x_I| || / ||b_I||, u = 2^-53, the
+ *                  attainable accuracy of an FP64 residual (|S_II| is the
+ *                  entrywise absolute value; both are 0 when b_I = 0). */
 typedef struct {
   int32_t status;                     /* sdf_status of this instance          */
   int32_t outer_iters;                /* inner solves performed               */
   int32_t cg_iters[SDF_MAX_OUTER];    /* CG iterations of each inner solve    */
   int32_t n_active[SDF_MAX_OUTER];    /* |A| in force during each solve       */
   int32_t fallback[SDF_MAX_OUTER];    /* 1: guard fired, plain PCG used       */
+  int32_t floor_stop[SDF_MAX_OUTER];  /* mixed path: 1 when the solve was
+                                         declared converged on the floor
+                                         (rtol not attainable), 0 on rtol     */
   double cond_E[SDF_MAX_OUTER];       /* estimated cond(E) (0 if plain)       */
   double relres[SDF_MAX_OUTER];       /* recurrence ||r||/||b|| at exit       */
+  double true_relres[SDF_MAX_OUTER];  /* FP64 ||b - S_II x||/||b|| at exit    */
+  double relres_floor[SDF_MAX_OUTER]; /* attainable-accuracy floor (above)    */
 } sdf_stats;
 
 void sdf_default_opts(sdf_opts *o);
@@ -351,7 +374,13 @@ sdf_status sdf_project(sdf_problem *p, const uint8_t *active_dev, const double *
  * SDF_ERR_UNSUPPORTED with a message; FP64 modes only.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.  Later calls reuse the address.
+ *     before any stream capture.  Later calls reuse the address.  The array's
+ *     memory is reserved when CUDA loads the library's module on that device:
+ *     at context creation, or with lazy module loading at the latest during
+ *     that first call -- one more reason to make it before any capture.
+ *   - Call it with the device current on which the problem was bound
+ *     (sdf_problem_bind); another current device is refused with
+ *     SDF_ERR_INVALID_ARG.
  *   - The array is shared by all calls in the process and keeps the last
  *     call's contents; the call clears the counters it needs, so results do
  *     not depend on earlier calls.  Calls that overlap on the GPU (different

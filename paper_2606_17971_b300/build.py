@@ -8,6 +8,7 @@ from __future__ import annotations
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
@@ -20,7 +21,7 @@ HEADERS = ["sdf_device.cuh", "tc_device.cuh", "host_linalg.h"]
 NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",
     "-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "--extended-lambda",
-    "-Xcompiler", "-fPIC", "-shared", "-Xptxas", "-v",
+    "-Xcompiler", "-fPIC", "-Xptxas", "-v",
 ]
 
 
@@ -35,22 +36,38 @@ def _stale() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile each source to an object (in parallel), then link the library."""
     if not force and not _stale():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
     nvcc = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
-    tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = [nvcc, *NVCC_FLAGS, "-I", os.path.join(ROOT, "include"), "-o", tmp,
-           *[os.path.join(CSRC, f) for f in SOURCES]]
-    res = subprocess.run(cmd, capture_output=True, text=True)
+    inc = ["-I", os.path.join(ROOT, "include")]
+
+    def compile_one(src):
+        obj = os.path.join(OUT_DIR, os.path.splitext(src)[0] + ".o")
+        cmd = [nvcc, *NVCC_FLAGS, *inc, "-c", "-o", obj, os.path.join(CSRC, src)]
+        res = subprocess.run(cmd, capture_output=True, text=True)
+        return obj, res
+
+    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+        results = list(ex.map(compile_one, SOURCES))
     log = os.path.join(OUT_DIR, "ptxas.log")
     with open(log, "w") as f:
-        f.write(res.stdout + res.stderr)
+        for _, res in results:
+            f.write(res.stdout + res.stderr)
+    bad = [res for _, res in results if res.returncode != 0]
+    if bad:
+        sys.stderr.write("".join(r.stdout + r.stderr for r in bad))
+        raise RuntimeError("nvcc failed; see " + log)
+    tmp = LIB + ".tmp%d" % os.getpid()
+    link = [nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", tmp,
+            *[obj for obj, _ in results]]
+    res = subprocess.run(link, capture_output=True, text=True)
     if res.returncode != 0:
         sys.stderr.write(res.stdout + res.stderr)
-        raise RuntimeError("nvcc failed; see " + log)
+        raise RuntimeError("nvcc link failed")
     if verbose:
-        sys.stdout.write(res.stderr)
+        sys.stdout.write("".join(r.stderr for _, r in results))
     os.replace(tmp, LIB)
     return LIB
 

@@ -54,6 +54,8 @@ struct InstState {
   double rho, sigma, alpha, beta, gamma, csign;
   double rnorm2, bnorm2;
   double rho_prev;     // rho before the last CG iteration (correction-pass beta)
+  double floor2;       // mixed path: (floor_c u || |S_II||x| ||)^2 when last evaluated, else 0
+  double rt2_prev;     // mixed path: true ||r||^2 at the previous residual replacement
   int32_t phase;       // 1: the coarse-correction pass is the next K_B/K_C
   int32_t cg_done;     // current inner solve finished (or failed)
   int32_t outer_done;  // instance finished
@@ -63,7 +65,7 @@ struct InstState {
   int32_t changes;     // active-set changes of the last update
   int32_t empty_I;     // every node active: nothing to solve
   int32_t await;       // mixed path: recurrence residual met rtol, waiting for the FP64 check
-  int32_t pad2;
+  int32_t stall;       // mixed path: the true residual fell less than 2x at the last replacement
   double t[SDF_MAX_K]; // reduced projection Phi_I^T v
   sdf_stats stats;
 };
@@ -83,6 +85,7 @@ struct Layout {
   int tcp, nbp;  // tensor-core projection (BF16 modes, batch <= 256) and its padded batch
   int tce, kp;   // tensor-core expansion and the padded mode count of its node-major copy
   size_t phin;   // node-major BF16 copy of the modes (tensor-core expansion)
+  int fb;        // FP64 path with the shared-Phi batch kernels (batch >= kFp64BatchMin)
 };
 
 inline size_t al(size_t v) { return (v + 255) & ~size_t(255); }
@@ -241,6 +244,9 @@ __global__ void __launch_bounds__(NT) k_outer_setup(OpParams P, const double *in
     S.phase = 1;
     S.cg_done = 0;
     S.await = 0;
+    S.stall = 0;
+    S.floor2 = 0.0;
+    S.rt2_prev = INFINITY;
     S.iters = 0;
     S.gamma = 0.0;
     S.beta = 0.0;
@@ -718,7 +724,7 @@ __global__ void __launch_bounds__(NT) k_spmv(OpParams P, const double *inst, Ins
   }
 }
 
-// Kernel C: x += alpha p (x in FP64), r -= alpha q, z = D^-1 r, v = S_II z,
+// Kernel C: x += alpha p (x in FP64), r -= alpha q, z = D^-1 r, v = S_II z - r,
 // t = Phi_I^T v, rho = (r, z), ||r||^2 (FP64 accumulation); the last block
 // tests convergence (App. B.2) and prepares beta for kernel A.  r is read
 // (with its halo) from r_in and written to r_out: blocks read neighbouring
@@ -733,7 +739,7 @@ __global__ void __launch_bounds__(NT) k_update(OpParams P, const double *inst, c
                                                const uint8_t *mask, const V *r_in, V *r_out,
                                                const V *q, const V *p, double *x, const V *dinv,
                                                double *part, int *cnt, Ctrl *ctrl, int GX,
-                                               double rtol2, int max_cg, int mixed) {
+                                               double rtol2, int max_cg, int mixed, V *vout) {
   __shared__ TileSmem<DIM, V> sm;
   __shared__ double red[NWARP];
   __shared__ double scratch[NT];
@@ -745,7 +751,10 @@ __global__ void __launch_bounds__(NT) k_update(OpParams P, const double *inst, c
   const long long N = P.N;
   const double alpha64 = S.alpha;
   const V alpha = (V)alpha64;
-  const int defl = S.deflate;
+  // vout: v = S z - r is written for the batch projection GEMM instead of
+  // being projected here (shared-Phi batch kernels)
+  const int defl = vout ? 0 : S.deflate;
+  V *vb = vout ? vout + b * N : nullptr;
   double cb[3];
   inst_cb(P, inst + 7 * b, cb);
   const uint8_t *mk = mask + b * N;
@@ -779,6 +788,7 @@ __global__ void __launch_bounds__(NT) k_update(OpParams P, const double *inst, c
           if (mk[g]) {
             sm.v[e] = (V)0;
             rw[g] = (V)0;
+            if (vb) vb[g] = (V)0;
             return;
           }
           V rn = rb[g] - alpha * qb[g];
@@ -787,12 +797,17 @@ __global__ void __launch_bounds__(NT) k_update(OpParams P, const double *inst, c
           rw[g] = rn;
           rho = fma((double)rn, (double)z, rho);
           rr = fma((double)rn, (double)rn, rr);
-          sm.v[e] = su;
+          // A-DEF2 (P^T M^-1 + Q): the next direction is z - Phi E^-1 Phi_I^T (S z - r);
+          // the Q r part vanishes in exact arithmetic but keeps the coarse-space
+          // component that rounding feeds into r out of the iteration
+          sm.v[e] = su - rn;
+          if (vb) vb[g] = su - rn;
           if constexpr (kThreadProj) {
             if (defl) {
 #pragma unroll
               for (int j = 0; j < KMAX; ++j)
-                if (j < k) accf[j] = fmaf((float)Phi[(long long)j * ld + g], (float)su, accf[j]);
+                if (j < k)
+                  accf[j] = fmaf((float)Phi[(long long)j * ld + g], (float)(su - rn), accf[j]);
             }
           }
         });
@@ -862,23 +877,41 @@ __global__ void __launch_bounds__(NT) k_update(OpParams P, const double *inst, c
   }
 }
 
+// Checkerboard sign s_g = (-1)^(i+j+l) of a grid node.  A couples nearest
+// neighbours only (upwind and time terms included), so its graph is
+// bipartite, and it is an M-matrix (positive diagonal, non-positive
+// off-diagonals).  Every entry of S = mass I + w A^T A then has the sign
+// s_i s_j: |S| = D_s S D_s with D_s = diag(s), so the product with the
+// entrywise absolute value is |S_II| |x| = s o (S_II (s o |x|)) and its norm is
+// that of the ordinary (sign-free, cancellation-free) product S_II (s o |x|).
+__device__ __forceinline__ double signed_abs(int gx, int gy, int gz, double v) {
+  return ((gx + gy + gz) & 1) ? -fabs(v) : fabs(v);
+}
+
 // FP64 residual replacement of the mixed path: r = b - S_II x with the FP64
 // stencil on the FP64 iterate and ||r||^2.  The last block declares
-// convergence on this true residual, or arms the coarse correction pass
-// (phase 2: w = Phi E_raw^-1 Phi_I^T r, alpha = 1) whose projection the GEMM
-// computes from the new r.  r is written in place: this kernel reads x, not r.
+// convergence on this true residual when ||r|| <= max(rtol ||b||, floor) with
+// floor = floor_c u || |S_II||x| || (the attainable accuracy of an FP64
+// residual, App. B.2's recurrence stop read for a method whose recurrence runs
+// in FP32), or arms the coarse correction pass (phase 2: w = Phi E_raw^-1
+// Phi_I^T r, alpha = 1) whose projection the GEMM computes from the new r.
+// The floor is evaluated (a second stencil pass on s o |x|) only when the
+// recurrence has met rtol or the true residual fell less than 2x at the last
+// replacement; otherwise the last value stands.  r is written in place: this
+// kernel reads x, not r.
 template <int DIM>
 __global__ void __launch_bounds__(NT) k_resid(OpParams P, const double *inst, InstState *st,
                                               const uint8_t *mask, const double *b64,
                                               const double *x, const float *xlo, float *r,
                                               double *part, int *cnt, Ctrl *ctrl, int GX,
-                                              double rtol2) {
+                                              double rtol2, double floor_cu) {
   __shared__ TileSmem<DIM, double> sm;
   __shared__ double red[NWARP];
   __shared__ int flag;
   const int b = blockIdx.x, gblk = blockIdx.y;
   InstState &S = st[b];
   if (S.outer_done || S.cg_done) return;
+  const bool need_floor = floor_cu > 0.0 && (S.await || S.stall);  // uniform in the block
   const long long N = P.N;
   double cb[3];
   inst_cb(P, inst + 7 * b, cb);
@@ -886,7 +919,7 @@ __global__ void __launch_bounds__(NT) k_resid(OpParams P, const double *inst, In
   const double *xb = x + b * N, *bb = b64 + b * N;
   const float *xl = xlo + b * N;
   float *rb = r + b * N;
-  double rr = 0.0;
+  double rr = 0.0, ff = 0.0;
   const long long T = num_tiles<DIM>(P.nx, P.ny, P.nz);
   for (long long t = gblk; t < T; t += GX) {
     int ox, oy, oz;
@@ -903,34 +936,124 @@ __global__ void __launch_bounds__(NT) k_resid(OpParams P, const double *inst, In
           rb[g] = (float)rt;
           rr = fma(rt, rt, rr);
         });
+    if (need_floor)
+      tile_S<DIM, double>(
+          P, cb, ox, oy, oz, sm,
+          [&](int gx, int gy, int gz, long long g) {
+            return mk[g] ? 0.0 : signed_abs(gx, gy, gz, xb[g] + (double)xl[g]);
+          },
+          [&](int, int, int, int, long long g, double su) {
+            if (!mk[g]) ff = fma(su, su, ff);
+          });
   }
   rr = block_sum(rr, red);
-  if (threadIdx.x == 0) part[(long long)b * GX + gblk] = rr;
+  ff = block_sum(ff, red);
+  if (threadIdx.x == 0) {
+    part[((long long)b * GX + gblk) * 2 + 0] = rr;
+    part[((long long)b * GX + gblk) * 2 + 1] = ff;
+  }
   if (!last_block(cnt + b * NCNT + CNT_UPDATE, GX, &flag)) return;
   __shared__ double scratch[NT];
-  __shared__ double tot1[1];
-  reduce_fields(part + (long long)b * GX, GX, 1, 1, tot1, scratch);
+  __shared__ double tot2[2];
+  reduce_fields(part + (long long)b * GX * 2, GX, 2, 2, tot2, scratch);
   if (threadIdx.x == 0) {
-    const double rn2 = tot1[0];
+    const double rn2 = tot2[0];
     cnt[b * NCNT + CNT_UPDATE] = 0;
     S.rnorm2 = rn2;
+    if (need_floor) S.floor2 = floor_cu * floor_cu * tot2[1];
+    const double rtb = rtol2 * S.bnorm2;
     if (!isfinite(rn2)) {
       S.stats.status = SDF_ERR_NONFINITE;
       S.cg_done = 1;
-    } else if (rn2 <= rtol2 * S.bnorm2) {
+    } else if (rn2 <= fmax(rtb, S.floor2)) {
       S.cg_done = 1;
+      S.stats.floor_stop[S.outer] = rn2 > rtb ? 1 : 0;
     } else {
+      S.stall = rn2 > 0.25 * S.rt2_prev ? 1 : 0;
       S.await = 0;
       S.phase = 2;
       S.gamma = 0.0;
       S.beta = 0.0;
       S.csign = -1.0;
     }
+    S.rt2_prev = rn2;
     if (S.cg_done) {
       S.stats.cg_iters[S.outer] = S.iters;
       S.stats.relres[S.outer] = S.bnorm2 > 0 ? sqrt(rn2 / S.bnorm2) : 0.0;
       atomicSub(&ctrl->running, 1);
     }
+  }
+}
+
+// True residual and attainable-accuracy floor of each instance's final inner
+// solve (App. B.2; see sdf_stats), both paths: ||b - S_II x||^2 and
+// || |S_II||x| ||^2 in FP64 (x = x + x_lo on the mixed path), the latter as
+// S_II (s o |x|) on a grid (signed_abs) and with |S| row by row on a problem
+// given by its operator.
+template <int DIM>
+__global__ void __launch_bounds__(NT) k_exit_resid(OpParams P, const double *inst, InstState *st,
+                                                   const uint8_t *mask, const double *b64,
+                                                   const double *x, const float *xlo,
+                                                   double *part, int *cnt, int GX,
+                                                   double floor_cu) {
+  __shared__ TileSmem<DIM, double> sm;
+  __shared__ double red[NWARP];
+  __shared__ int flag;
+  const int b = blockIdx.x, gblk = blockIdx.y;
+  InstState &S = st[b];
+  if (S.outer_done) return;
+  const long long N = P.N;
+  double cb[3];
+  inst_cb(P, inst + 7 * b, cb);
+  const uint8_t *mk = mask + b * N;
+  const double *xb = x + b * N, *bb = b64 + b * N;
+  const float *xl = xlo ? xlo + b * N : nullptr;
+  auto xval = [&](long long g) { return mk[g] ? 0.0 : (xl ? xb[g] + (double)xl[g] : xb[g]); };
+  double rr = 0.0, ff = 0.0;
+  const long long T = num_tiles<DIM>(P.nx, P.ny, P.nz);
+  for (long long t = gblk; t < T; t += GX) {
+    int ox, oy, oz;
+    tile_origin<DIM>(P, t, ox, oy, oz);
+    tile_S<DIM, double>(
+        P, cb, ox, oy, oz, sm, [&](int, int, int, long long g) { return xval(g); },
+        [&](int, int, int, int, long long g, double su) {
+          if (mk[g]) return;
+          const double rt = bb[g] - su;
+          rr = fma(rt, rt, rr);
+        });
+    if constexpr (DIM == 1) {  // |S| x row by row from the assembled CSR S
+      for (int e = threadIdx.x; e < TileCfg<1>::TX; e += NT) {
+        const long long g = ox + e;
+        if (g >= N || mk[g]) continue;
+        double acc = 0.0;
+        for (int q = P.csr_rp[g], qe = P.csr_rp[g + 1]; q < qe; ++q)
+          acc = fma(fabs(P.csr_v[q]), fabs(xval(P.csr_ci[q])), acc);
+        ff = fma(acc, acc, ff);
+      }
+    } else {
+      tile_S<DIM, double>(
+          P, cb, ox, oy, oz, sm,
+          [&](int gx, int gy, int gz, long long g) { return signed_abs(gx, gy, gz, xval(g)); },
+          [&](int, int, int, int, long long g, double su) {
+            if (!mk[g]) ff = fma(su, su, ff);
+          });
+    }
+  }
+  rr = block_sum(rr, red);
+  ff = block_sum(ff, red);
+  if (threadIdx.x == 0) {
+    part[((long long)b * GX + gblk) * 2 + 0] = rr;
+    part[((long long)b * GX + gblk) * 2 + 1] = ff;
+  }
+  if (!last_block(cnt + b * NCNT + CNT_SETUP, GX, &flag)) return;
+  __shared__ double scratch[NT];
+  __shared__ double tot2[2];
+  reduce_fields(part + (long long)b * GX * 2, GX, 2, 2, tot2, scratch);
+  if (threadIdx.x == 0) {
+    cnt[b * NCNT + CNT_SETUP] = 0;
+    const bool has_b = S.bnorm2 > 0.0;
+    S.stats.true_relres[S.outer] = has_b ? sqrt(tot2[0] / S.bnorm2) : 0.0;
+    S.stats.relres_floor[S.outer] = has_b ? floor_cu * sqrt(tot2[1] / S.bnorm2) : 0.0;
   }
 }
 
@@ -1742,10 +1865,10 @@ __global__ void __launch_bounds__(tc::GTH) k_proj_tc(const __nv_bfloat16 *__rest
 
 // Sum the projection partials of each instance in block order and form the
 // coarse coefficients c_b = csign_b E_raw,b^-1 t_b (FP64), stored as FP32.
-template <int KMAX>
+template <int KMAX, class CT = float>
 __global__ void __launch_bounds__(NT) k_proj_reduce(const double *part, int GXp, int Bpad, int k,
                                                     const InstState *st, const double *Einv,
-                                                    float *cvec) {
+                                                    CT *cvec) {
   // NT threads: mode j = tid % KMAX, block slice q = tid / KMAX sums the
   // partials g = q, q + Q, ... (eight loads in flight), then the Q slice sums
   // of each mode are added in slice order (deterministic)
@@ -1778,7 +1901,153 @@ __global__ void __launch_bounds__(NT) k_proj_reduce(const double *part, int GXp,
       for (int j = 0; j < k; ++j) c = fma(Ei[i * k + j], t[j], c);
       c *= S.csign;
     }
-    cvec[(size_t)b * KMAX + i] = (float)c;
+    cvec[(size_t)b * KMAX + i] = (CT)c;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 path, shared-Phi batch kernels (batches of kFp64BatchMin instances or
+// more): the projection t_b = Phi_I^T v_b of every instance is one
+// tall-skinny GEMM over shared-memory chunks, each mode row read once per tile
+// of NB instances; the expansion p_b = gamma_b D^-1 r_b + beta_b p_b - Phi c_b
+// reads each node's mode values once per group of IG instances.  The
+// arithmetic is the per-instance kernels' (FP64 products and sums, c_b =
+// csign E_raw^-1 t_b from k_proj_reduce); only the order of the partial sums
+// differs.  On this part the FP64 pipe (about 2 FMA per clock per SM) binds
+// these kernels: sharing Phi cuts its reads from 2k to 2k / (tile) doubles per
+// node and instance, the FMA count (k each) stays.
+constexpr int kFp64BatchMin = 8;
+constexpr int kExpandGroup = 32;
+
+template <int KMAX, int NB>
+__global__ void __launch_bounds__(NT) k_proj_gemm64(const double *__restrict__ Phi, long long ld,
+                                                    int k, long long N, int B, const InstState *st,
+                                                    const double *__restrict__ v, double *part,
+                                                    int Bpad) {
+  static_assert(NB >= 16 && NB % 16 == 0 && KMAX % 16 == 0, "thread tile");
+  constexpr int CH = (KMAX * NB >= 128 * 64) ? 16 : 32;
+  constexpr int MT = KMAX / 16, NTN = NB / 16;
+  __shared__ double Ps[CH][KMAX + 1];
+  __shared__ double Vs[CH][NB + 1];
+  __shared__ int run[NB];
+  const int ib = blockIdx.x * NB, gblk = blockIdx.y, GXp = gridDim.y;
+  for (int e = threadIdx.x; e < NB; e += NT) {
+    const int bb = ib + e;
+    run[e] = (bb < B && !st[bb].outer_done && !st[bb].cg_done && st[bb].deflate) ? 1 : 0;
+  }
+  __syncthreads();
+  const long long nch = (N + CH - 1) / CH;
+  const long long c_lo = nch * gblk / GXp, c_hi = nch * (gblk + 1) / GXp;
+  const int ti = threadIdx.x / 16, tj = threadIdx.x % 16;
+  double acc[MT][NTN];
+#pragma unroll
+  for (int a = 0; a < MT; ++a)
+#pragma unroll
+    for (int q = 0; q < NTN; ++q) acc[a][q] = 0.0;
+  for (long long ch = c_lo; ch < c_hi; ++ch) {
+    const long long g0 = ch * CH;
+    for (int e = threadIdx.x; e < CH * KMAX; e += NT) {
+      const int c = e % CH, j = e / CH;
+      const long long g = g0 + c;
+      Ps[c][j] = (j < k && g < N) ? Phi[(long long)j * ld + g] : 0.0;
+    }
+    for (int e = threadIdx.x; e < CH * NB; e += NT) {
+      const int c = e % CH, q = e / CH;
+      const long long g = g0 + c;
+      Vs[c][q] = (run[q] && g < N) ? v[(long long)(ib + q) * N + g] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int c = 0; c < CH; ++c) {
+      double pa[MT], vb[NTN];
+#pragma unroll
+      for (int a = 0; a < MT; ++a) pa[a] = Ps[c][ti + 16 * a];
+#pragma unroll
+      for (int q = 0; q < NTN; ++q) vb[q] = Vs[c][tj + 16 * q];
+#pragma unroll
+      for (int a = 0; a < MT; ++a)
+#pragma unroll
+        for (int q = 0; q < NTN; ++q) acc[a][q] = fma(pa[a], vb[q], acc[a][q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int a = 0; a < MT; ++a)
+#pragma unroll
+    for (int q = 0; q < NTN; ++q) {
+      const int j = ti + 16 * a, bb = ib + tj + 16 * q;
+      if (bb < Bpad) part[((long long)gblk * Bpad + bb) * KMAX + j] = acc[a][q];
+    }
+}
+
+// Grid: x = instance group of IG (fastest, so that the groups of one node
+// range run together and share its mode rows in L2), y = node range.
+template <int KMAX, int IG>
+__global__ void __launch_bounds__(NT) k_expand64_b(const double *__restrict__ Phi, long long ld,
+                                                   int k, long long N, int B, const InstState *st,
+                                                   const double *cvec, const uint8_t *mask,
+                                                   const double *r, const double *dinv,
+                                                   int dinv_per_inst, double *p) {
+  __shared__ double cs[KMAX][IG];  // coefficients, mode-major: a warp reads one broadcast value
+  __shared__ double gam[IG], bet[IG];
+  __shared__ int act[IG];
+  const int b0 = blockIdx.x * IG;
+  for (int q = threadIdx.x; q < IG; q += NT) {
+    const int b = b0 + q;
+    const bool on = b < B && inst_running(st[b]);
+    act[q] = on ? (1 | (st[b].deflate ? 2 : 0)) : 0;
+    gam[q] = on ? st[b].gamma : 0.0;
+    bet[q] = on ? st[b].beta : 0.0;
+  }
+  for (int e = threadIdx.x; e < IG * KMAX; e += NT) {
+    const int q = e / KMAX, j = e % KMAX;
+    cs[j][q] = (b0 + q < B) ? cvec[(size_t)(b0 + q) * KMAX + j] : 0.0;
+  }
+  __syncthreads();
+  bool any = false;
+  for (int q = 0; q < IG; ++q) any = any || act[q];
+  if (!any) return;
+  // sub-groups of 8 instances: 8 accumulators per thread; a node's mode
+  // values are re-read per sub-group from L1
+  constexpr int SG = 8;
+  static_assert(IG % SG == 0, "sub-groups");
+  for (long long g = (long long)blockIdx.y * NT + threadIdx.x; g < N;
+       g += (long long)gridDim.y * NT) {
+    const double d_shared = dinv_per_inst ? 0.0 : dinv[g];
+#pragma unroll 1
+    for (int q0 = 0; q0 < IG; q0 += SG) {
+      int on = 0, dfl = 0;
+#pragma unroll
+      for (int u = 0; u < SG; ++u) {
+        on |= act[q0 + u];
+        dfl |= act[q0 + u] & 2;
+      }
+      if (!on) continue;  // uniform across the block
+      double acc[SG];
+#pragma unroll
+      for (int u = 0; u < SG; ++u) acc[u] = 0.0;
+      if (dfl) {
+        for (int j = 0; j < k; ++j) {
+          const double ph = Phi[(long long)j * ld + g];
+#pragma unroll
+          for (int u = 0; u < SG; ++u) acc[u] = fma(ph, cs[j][q0 + u], acc[u]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < SG; ++u) {
+        const int q = q0 + u;
+        if (!act[q]) continue;
+        const long long gb = (long long)(b0 + q) * N + g;
+        double val = 0.0;
+        if (!mask[gb]) {
+          const double dv = dinv_per_inst ? dinv[gb] : d_shared;
+          val = gam[q] * dv * r[gb];
+          if (bet[q] != 0.0) val = fma(bet[q], p[gb], val);
+          if (act[q] & 2) val -= acc[u];
+        }
+        p[gb] = val;
+      }
+    }
   }
 }
 
@@ -1956,6 +2225,7 @@ struct sdf_problem {
   std::vector<double> kappa;
   OpParams P;
   bool bound = false;
+  int device = -1;  // CUDA device current when the problem buffer was bound
   void *dev = nullptr;
   size_t dev_bytes = 0;
   double *dinv_shared = nullptr;
@@ -2006,7 +2276,8 @@ sdf_status cuda_check(sdf_problem *p, cudaError_t e, const char *what) {
 
 int kmax_for(int k) { return k <= 16 ? 16 : k <= 32 ? 32 : k <= 64 ? 64 : 128; }
 
-Layout make_layout(const sdf_problem *p, int B, int max_blocks = 0, int mixed = 0) {
+Layout make_layout(const sdf_problem *p, int B, int max_blocks = 0, int mixed = 0,
+                   int column_depth = 0) {
   Layout L{};
   const long long N = p->P.N;
   const int k = std::max(p->k, 1), KM = kmax_for(k);
@@ -2054,6 +2325,7 @@ Layout make_layout(const sdf_problem *p, int B, int max_blocks = 0, int mixed = 
     auto it = p->tuned_zc.find(B);
     if (it != p->tuned_zc.end()) L.zc = it->second;
     if (p->force_zc > 0) L.zc = p->force_zc;
+    if (column_depth > 0) L.zc = column_depth;
   }
   L.gxc = 1;
   int gxc_max = 1;  // the partial buffers fit every candidate depth (8 planes)
@@ -2089,10 +2361,11 @@ Layout make_layout(const sdf_problem *p, int B, int max_blocks = 0, int mixed = 
     L.gxp = (int)std::min<long long>((long long)p->nsm * occ, (N + 63) / 64);
   }
   if (max_blocks > 0) L.gxp = std::min(L.gxp, max_blocks);
-  L.v = take(mixed ? sizeof(float) * (size_t)N * B : 8);
+  L.fb = (!mixed && B >= kFp64BatchMin && p->k > 0) ? 1 : 0;
+  L.v = take(mixed ? sizeof(float) * (size_t)N * B : (L.fb ? sizeof(double) * (size_t)N * B : 8));
   L.xlo = take(mixed ? sizeof(float) * (size_t)N * B : 8);
-  L.cvec = take(sizeof(float) * (size_t)B * KM);
-  L.ppart = take(mixed ? sizeof(double) * (size_t)L.gxp * L.bpad * KM : 8);
+  L.cvec = take((L.fb ? sizeof(double) : sizeof(float)) * (size_t)B * KM);
+  L.ppart = take((mixed || L.fb) ? sizeof(double) * (size_t)L.gxp * L.bpad * KM : 8);
   // tensor-core expansion: BF16 modes, and its shared-memory tiles must fit
   L.kp = (std::max(k, 1) + 15) / 16 * 16;
   L.tce = (L.tcp && expand_tc_smem(L.nbp, L.kp) <= 200 * 1024) ? 1 : 0;
@@ -2322,11 +2595,36 @@ sdf_status solve_impl(sdf_problem *p, const double *inst, int B, const double *p
   const int k = defl ? p->k : 0;
   const PhiT *Phi = phi_as<PhiT>(p);
   const long long ld = p->ld;
+  // shared-Phi batch kernels: v = S z - r written by the update, projected for
+  // the whole batch by one GEMM, expanded per node for groups of instances
+  constexpr bool f64 = std::is_same<PhiT, double>::value && std::is_same<V, double>::value;
+  const bool fb = f64 && defl && L.fb;
+  V *vv = (V *)(ws + L.v);
+  double *cvec64 = (double *)(ws + L.cvec), *ppart64 = (double *)(ws + L.ppart);
+  const dim3 gPb(L.bpad / std::max(L.nb, 1), L.gxp);
+  const int ngrp = (B + kExpandGroup - 1) / kExpandGroup;
+  const dim3 gEb(ngrp, (int)std::max<long long>(
+                           1, std::min<long long>((N + NT - 1) / NT, (p->nsm * 4LL + ngrp - 1) / ngrp)));
 
   CK(cudaMemsetAsync(mask, 0, (size_t)N * B, s));
   CK(cudaMemsetAsync(st, 0, sizeof(InstState) * B, s));
   CK(cudaMemsetAsync(cnt, 0, sizeof(int) * B * NCNT, s));
   CK(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s));
+  if (fb) CK(cudaMemsetAsync(cvec64, 0, sizeof(double) * B * KMAX, s));
+
+  // cvec64 <- csign E^-1 Phi_I^T src for every running instance (batch kernels)
+  auto project64 = [&](const V *src) -> sdf_status {
+    if constexpr (f64) {
+      switch (L.nb) {
+        case 16: k_proj_gemm64<KMAX, 16><<<gPb, NT, 0, s>>>(Phi, ld, k, N, B, st, src, ppart64, L.bpad); break;
+        case 32: k_proj_gemm64<KMAX, 32><<<gPb, NT, 0, s>>>(Phi, ld, k, N, B, st, src, ppart64, L.bpad); break;
+        default: k_proj_gemm64<KMAX, 64><<<gPb, NT, 0, s>>>(Phi, ld, k, N, B, st, src, ppart64, L.bpad); break;
+      }
+      k_proj_reduce<KMAX, double><<<B, NT, 0, s>>>(ppart64, L.gxp, L.bpad, k, st, Einv, cvec64);
+      p->prof.launches += 2;
+    }
+    return SDF_OK;
+  };
 
   const dim3 gT(B, L.gx), gA(B, L.gxa);
   long long launches = 0;
@@ -2334,20 +2632,36 @@ sdf_status solve_impl(sdf_problem *p, const double *inst, int B, const double *p
   // CG iterations between FP64 residual replacements (mixed) or host polls
   const int chunk = std::max(1, mixed ? (o.replace_every > 0 ? o.replace_every : 100) : o.check_every);
   const double rtol2 = o.rtol * o.rtol;
+  const double floor_cu = std::max(o.floor_c, 0.0) * std::ldexp(1.0, -53);
   int live = B;
   int par = 0;
   // one CG-kernel triple: A (expand into `dir`), B (spmv of dir), C (update)
   auto triple = [&](V *dir, bool timed) -> sdf_status {
     if (timed) CK(cudaEventRecord(p->ev[0], s));
-    k_expand<KMAX, PhiT, V><<<gA, NT, 0, s>>>(Phi, ld, k, N, st, Einv, mask, rbuf[par], dinv,
-                                              P.convection, dir, L.gxa);
+    bool expanded = false;
+    if constexpr (f64) {
+      if (fb) {
+        k_expand64_b<KMAX, kExpandGroup><<<gEb, NT, 0, s>>>(Phi, ld, k, N, B, st, cvec64, mask,
+                                                            rbuf[par], dinv, P.convection, dir);
+        expanded = true;
+      }
+    }
+    if (!expanded)
+      k_expand<KMAX, PhiT, V><<<gA, NT, 0, s>>>(Phi, ld, k, N, st, Einv, mask, rbuf[par], dinv,
+                                                P.convection, dir, L.gxa);
     if (timed) CK(cudaEventRecord(p->ev[1], s));
     k_spmv<DIM, V><<<gT, NT, 0, s>>>(P, inst, st, mask, dir, q, part, cnt, ctrl, L.gx);
     if (timed) CK(cudaEventRecord(p->ev[2], s));
     k_update<DIM, KMAX, PhiT, V><<<gT, NT, 0, s>>>(P, inst, Phi, ld, k, st, mask, rbuf[par],
                                                    rbuf[par ^ 1], q, dir, x, dinv, part, cnt,
-                                                   ctrl, L.gx, rtol2, o.max_cg, mixed);
+                                                   ctrl, L.gx, rtol2, o.max_cg, mixed,
+                                                   fb ? vv : nullptr);
     if (timed) CK(cudaEventRecord(p->ev[3], s));
+    if (fb) {
+      sdf_status e = project64(vv);
+      if (e != SDF_OK) return e;
+    }
+    if (timed && fb) CK(cudaEventRecord(p->ev[4], s));
     par ^= 1;
     p->prof.launches += 3;
     return SDF_OK;
@@ -2394,10 +2708,16 @@ sdf_status solve_impl(sdf_problem *p, const double *inst, int B, const double *p
           if (e != SDF_OK) return e;
         }
       }
-      k_project<KMAX, PhiT, V><<<gA, NT, 0, s>>>(Phi, ld, k, N, mask, rbuf[0], st, nullptr, part,
-                                                 cnt, L.gxa);
+      if (fb) {
+        sdf_status e = project64(rbuf[0]);  // coarse-corrected start: c = -E^-1 Phi_I^T b
+        if (e != SDF_OK) return e;
+      } else {
+        k_project<KMAX, PhiT, V><<<gA, NT, 0, s>>>(Phi, ld, k, N, mask, rbuf[0], st, nullptr,
+                                                   part, cnt, L.gxa);
+        p->prof.launches += 1;
+      }
       CKL("k_project");
-      p->prof.launches += 5LL * nset + (nset < B ? 1 : 0) + 2;
+      p->prof.launches += 5LL * nset + (nset < B ? 1 : 0) + 1;
     }
     // coarse-corrected start (phase 1), then CG iterations in chunks; r
     // ping-pongs between its two buffers (uniform across the batch: finished
@@ -2422,6 +2742,8 @@ sdf_status solve_impl(sdf_problem *p, const double *inst, int B, const double *p
         cudaEventElapsedTime(&t1, p->ev[1], p->ev[2]);
         cudaEventElapsedTime(&t2, p->ev[2], p->ev[3]);
         if (mixed) cudaEventElapsedTime(&t3, p->ev[4], p->ev[5]);
+        float t4 = 0;
+        if (fb) cudaEventElapsedTime(&t4, p->ev[3], p->ev[4]);
         // only intervals that still had work count (a poll interval whose first
         // iteration found every instance finished would time empty launches)
         if (p->pinned[0] > 0 || chunk > 1) {
@@ -2435,16 +2757,23 @@ sdf_status solve_impl(sdf_problem *p, const double *inst, int B, const double *p
             p->prof.ms[7] += t3;
             p->prof.samples[7] += 1;
           }
+          if (fb) {
+            p->prof.ms[8] += t4;
+            p->prof.samples[8] += 1;
+          }
         }
       }
       if (p->pinned[0] <= 0) break;
       if (launches > max_launches)
         return fail(p, SDF_ERR_TIMEOUT, "solve exceeded its iteration launch budget");
     }
+    k_exit_resid<DIM><<<gT, NT, 0, s>>>(P, inst, st, mask, b64, x, nullptr, part, cnt, L.gx,
+                                        floor_cu);
+    CKL("k_exit_resid");
     k_active<<<gA, NT, 0, s>>>(N, psi, mask, x, nullptr, y, st, part, cnt, ctrl, L.gxa, o.tau,
                                o.max_outer);
     CKL("k_active");
-    p->prof.launches += 1;
+    p->prof.launches += 2;  // k_exit_resid, k_active
     CK(cudaMemcpyAsync(p->pinned + 1, &ctrl->live, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     live = p->pinned[1];
@@ -2474,7 +2803,7 @@ template <int DIM, int KMAX, class PhiT>
 sdf_status solve_mixed(sdf_problem *p, const double *inst, int B, const double *psi,
                        const sdf_opts &o, char *ws, cudaStream_t s, double *y, double *lam,
                        uint8_t *active, sdf_stats *stats) {
-  const Layout L = make_layout(p, B, o.max_blocks, 1);
+  const Layout L = make_layout(p, B, o.max_blocks, 1, o.column_depth);
   const OpParams &P = p->P;
   const long long N = P.N;
   double *x = (double *)(ws + L.x), *b64 = (double *)(ws + L.b64);
@@ -2512,6 +2841,7 @@ sdf_status solve_mixed(sdf_problem *p, const double *inst, int B, const double *
   const long long max_launches = o.max_launches > 0 ? o.max_launches : 4LL * o.max_cg + 64;
   const int chunk = std::max(1, o.replace_every > 0 ? o.replace_every : 100);
   const double rtol2 = o.rtol * o.rtol;
+  const double floor_cu = std::max(o.floor_c, 0.0) * std::ldexp(1.0, -53);
   int live = B;
   int par = 0;
   __nv_bfloat16 *phin = (__nv_bfloat16 *)(ws + L.phin);
@@ -2678,7 +3008,7 @@ sdf_status solve_mixed(sdf_problem *p, const double *inst, int B, const double *
       }
       if (timed) CK(cudaEventRecord(p->ev[5], s));
       k_resid<DIM><<<gT, NT, 0, s>>>(P, inst, st, mask, b64, x, xlo, rbuf[par], part, cnt, ctrl,
-                                     L.gx, rtol2);
+                                     L.gx, rtol2, floor_cu);
       if (timed) CK(cudaEventRecord(p->ev[6], s));
       p->prof.launches += 1;
       {
@@ -2705,10 +3035,12 @@ sdf_status solve_mixed(sdf_problem *p, const double *inst, int B, const double *
       if (launches > max_launches)
         return fail(p, SDF_ERR_TIMEOUT, "solve exceeded its iteration launch budget");
     }
+    k_exit_resid<DIM><<<gT, NT, 0, s>>>(P, inst, st, mask, b64, x, xlo, part, cnt, L.gx, floor_cu);
+    CKL("k_exit_resid");
     k_active<<<dim3(B, L.gxa), NT, 0, s>>>(N, psi, mask, x, xlo, y, st, part, cnt, ctrl, L.gxa,
                                            o.tau, o.max_outer);
     CKL("k_active");
-    p->prof.launches += 1;
+    p->prof.launches += 2;  // k_exit_resid, k_active
     CK(cudaMemcpyAsync(p->pinned + 1, &ctrl->live, sizeof(int), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     live = p->pinned[1];
@@ -2860,6 +3192,8 @@ void sdf_default_opts(sdf_opts *o) {
   o->safe_r = 0;
   o->tau_safe = 1e4;
   o->tau_dep = 1e-10;
+  o->floor_c = 10.0;
+  o->column_depth = 0;
 }
 
 sdf_status sdf_problem_create(const sdf_problem_desc *desc, const double *kappa_host,
@@ -3081,6 +3415,7 @@ sdf_status sdf_problem_bind(sdf_problem *p, void *dev_buf, size_t bytes, void *s
     return fail(p, SDF_ERR_INVALID_ARG, "problem buffer must be a 256-byte aligned device pointer");
   if (bytes < need) return fail(p, SDF_ERR_WORKSPACE, "problem buffer too small");
   cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaGetDevice(&p->device));
   char *base = (char *)dev_buf;
   OpParams &P = p->P;
   size_t o = 0;
@@ -3278,6 +3613,12 @@ static sdf_status check_solve_args(sdf_problem *p, int batch, const sdf_opts *op
                 "the mixed path is not validated for convection (FP32 attainable accuracy above "
                 "rtol stalls its refinement loop); use SDF_PREC_F64");
   if (opts->replace_every < 0) return fail(p, SDF_ERR_INVALID_ARG, "replace_every < 0");
+  if (!(opts->floor_c >= 0.0)) return fail(p, SDF_ERR_INVALID_ARG, "floor_c < 0");
+  {
+    const int cd = opts->column_depth;
+    if (cd != 0 && cd != 8 && cd != 16 && cd != 32 && cd != 64)
+      return fail(p, SDF_ERR_INVALID_ARG, "column_depth must be 0, 8, 16, 32 or 64");
+  }
   if (opts->precision == SDF_PREC_MIXED && p->P.N > 2147483647LL)
     return fail(p, SDF_ERR_UNSUPPORTED, "the mixed path indexes one instance with 32 bits");
   size_t need = make_layout(p, batch, opts->max_blocks, opts->precision == SDF_PREC_MIXED).total;
@@ -3544,6 +3885,11 @@ static sdf_status noalloc_scratch(sdf_problem *p, double **out) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_check(p, e, "cudaGetDevice");
   if (dev < 0 || dev >= 64) return fail(p, SDF_ERR_UNSUPPORTED, "device index >= 64");
+  // the scratch address is per device: the problem's data (and the modes the
+  // kernel reads) live on the device it was bound on
+  if (p->device >= 0 && dev != p->device)
+    return fail(p, SDF_ERR_INVALID_ARG,
+                "sdf_project_noalloc: the current device is not the one the problem was bound on");
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
   if (!g_noalloc_addr[dev]) {
     void *ptr = nullptr;

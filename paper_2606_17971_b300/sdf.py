@@ -47,7 +47,8 @@ class Opts(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("replace_every", ctypes.c_int32),
                 ("max_launches", ctypes.c_int64), ("ritz_r", ctypes.c_int32),
                 ("safe_r", ctypes.c_int32), ("tau_safe", ctypes.c_double),
-                ("tau_dep", ctypes.c_double)]
+                ("tau_dep", ctypes.c_double), ("floor_c", ctypes.c_double),
+                ("column_depth", ctypes.c_int32)]
 
 
 SDF_NPROF = 9
@@ -77,8 +78,11 @@ class Stats(ctypes.Structure):
                 ("cg_iters", ctypes.c_int32 * SDF_MAX_OUTER),
                 ("n_active", ctypes.c_int32 * SDF_MAX_OUTER),
                 ("fallback", ctypes.c_int32 * SDF_MAX_OUTER),
+                ("floor_stop", ctypes.c_int32 * SDF_MAX_OUTER),
                 ("cond_E", ctypes.c_double * SDF_MAX_OUTER),
-                ("relres", ctypes.c_double * SDF_MAX_OUTER)]
+                ("relres", ctypes.c_double * SDF_MAX_OUTER),
+                ("true_relres", ctypes.c_double * SDF_MAX_OUTER),
+                ("relres_floor", ctypes.c_double * SDF_MAX_OUTER)]
 
 
 _vp, _sz = ctypes.c_void_p, ctypes.c_size_t
@@ -166,7 +170,10 @@ class SdfError(RuntimeError):
 def default_opts(**kw) -> Opts:
     o = Opts()
     _lib.sdf_default_opts(ctypes.byref(o))
+    names = {f[0] for f in Opts._fields_}
     for k, v in kw.items():
+        if k not in names:
+            raise TypeError(f"sdf_opts has no field {k!r}")
         setattr(o, k, v)
     return o
 
@@ -183,7 +190,9 @@ def stats_dict(s: Stats) -> dict:
     n = s.outer_iters
     return dict(status=s.status, outer_iters=n, cg_iters=list(s.cg_iters[:n]),
                 n_active=list(s.n_active[:n]), fallback=list(s.fallback[:n]),
-                cond_E=list(s.cond_E[:n]), relres=list(s.relres[:n]))
+                cond_E=list(s.cond_E[:n]), relres=list(s.relres[:n]),
+                true_relres=list(s.true_relres[:n]), relres_floor=list(s.relres_floor[:n]),
+                floor_stop=list(s.floor_stop[:n]))
 
 
 class Problem:
