@@ -4,14 +4,16 @@ BF16 modes and the autotuned column depth, plus one instance on the plain
 FP64 path.
 
 The oracle's own full-size solves of the first two instances
-(tests/golden/diff3d_128_oracle.json, written by oracle/full_size_reference.py)
-fix the outer iterations, the active sets, the state's norm and its values at
-64 sampled nodes.  Tolerances follow from the residuals: with S = mass I +
-wgt A^T A and the active set empty, ||S^-1|| <= 1/mass = 1, so for two
-approximations with relative residuals r1, r2 of S y = rhs,
-|y1_i - y2_i| <= ||y1 - y2||_2 <= (r1 + r2) ||rhs||.  The true residual on the
-inactive set is recomputed in FP64 through the library's S for sampled
-instances of the batch, and y <= psi + tau holds for all of them."""
+(tests/golden/diff3d_128_oracle.json and diff3d_128_oracle_states.npz, written
+by oracle/full_size_reference.py) fix the outer iterations, the active sets and
+every node of the state (stored in float32: relative rounding 6e-8).  The GPU
+states must be within relative L2 1e-5 (mixed path) and 1e-6 (FP64 path) of
+them over every node (Eq. accuracy_rel_err).  The residual bound stays as a
+second check: with S = mass I + wgt A^T A and the active set empty,
+||S^-1|| <= 1/mass = 1, so for two approximations with relative residuals
+r1, r2 of S y = rhs, |y1_i - y2_i| <= ||y1 - y2||_2 <= (r1 + r2) ||rhs||.  The
+true residual on the inactive set is recomputed in FP64 through the library's
+S for sampled instances of the batch, and y <= psi + tau holds for all of them."""
 import json
 import os
 
@@ -38,6 +40,7 @@ def setup():
     from oracle import oracle as O
     from paper_2606_17971_b300 import workloads as W
     gold = json.load(open(os.path.join(HERE, "golden", "diff3d_128_oracle.json")))
+    states = np.load(os.path.join(HERE, "golden", "diff3d_128_oracle_states.npz"))
     w = W.WORKLOADS["diff3d_128"]
     assert gold["k"] == w.k and gold["rtol"] == 1e-8
     insts = W.draw_instances(w, count=64)
@@ -45,7 +48,19 @@ def setup():
         i = insts[g["index"]]
         assert i.a == g["a"] and list(i.c) == g["c"]
     P = O.Problem(w.dim, w.n, alpha=w.alpha)
-    return dict(W=W, w=w, gold=gold, insts=insts, P=P, psi=W.psi_vector(w))
+    return dict(W=W, w=w, gold=gold, insts=insts, P=P, psi=W.psi_vector(w), states=states)
+
+
+def _check_full_state(states, i, y, active, tol):
+    """Every node: relative L2 error against the oracle's stored state, and the
+    stored active set bit for bit."""
+    ref = states[f"y{i}"].astype(np.float64)
+    yy = y.cpu().numpy()
+    err = np.linalg.norm(yy - ref) / np.linalg.norm(ref)
+    assert err <= tol, (i, err)
+    act_ref = np.unpackbits(states[f"active{i}"])[:ref.size].astype(bool)
+    assert np.array_equal(active.cpu().numpy().astype(bool), act_ref), i
+    return err
 
 
 def _true_relres(G, inst_row, y, active, rhs, psi):
@@ -100,6 +115,7 @@ def test_full_size_batch_matches_the_oracle_solves(sdf, setup):
             # FP32 arithmetic and BF16 modes against FP64: a few percent more
             assert abs(sum(st["cg_iters"]) - sum(g["cg_iters"])) <= 0.05 * sum(g["cg_iters"])
             _check_against_golden(g, out["y"][b], rel, np.linalg.norm(rhs_np), idx)
+            _check_full_state(s["states"], b, out["y"][b], act, 1e-5)
 
 
 def test_full_size_plain_fp64_instance_matches_the_oracle(sdf, setup):
@@ -123,3 +139,4 @@ def test_full_size_plain_fp64_instance_matches_the_oracle(sdf, setup):
     assert rel <= 1.05e-8
     _check_against_golden(g, out["y"][0], rel, np.linalg.norm(rhs_np),
                           torch.as_tensor(np.array(gold["sample_index"]), device=DEV))
+    _check_full_state(s["states"], 0, out["y"][0], out["active"][0], 1e-6)
