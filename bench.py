@@ -409,36 +409,217 @@ def run_reference(args, w):
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+
+
+# ---------------------------------------------------------------------------
+# how each workload is benchmarked (the configurations the metric is quoted on)
+
+MODES = {
+    # config 0: the plain method, FP64, the 20-instance batch
+    "diff2d_32": dict(path="plain", batch=20, modes="eig"),
+    # config 1: FP64, one instance per launch, k = 64 reference eigenmodes
+    "block2d_1024": dict(path="plain", batch=1, modes="eig"),
+    # config 2: FP64, 256 instances in one batched solve, shared k = 48 modes
+    "convdiff2d_512": dict(path="plain", batch=256, modes="analytic"),
+    # config 3: FP32 stencil and projections (FP32 or BF16 modes), FP64
+    # scalars, coarse operator and residual replacement; --path plain for FP64
+    "lognormal2d_2048": dict(path="mixed", phi="f32", batch=32, modes="eig"),
+    # config 4 (the headline): batched + mixed + learned warm start
+    "diff3d_128": dict(path="mixed", phi="bf16", batch=128, modes="analytic", learned=True),
+}
+
+
+def loop_roofline(prof, w, k, mixed, phi_bytes, B, units, chunk=100):
+    """Roofline of the whole CG iteration: the algorithmic bytes (mixed path)
+    or FP64 flops (FP64 path) of one iteration per dof and instance, times
+    the units of one launch, over the summed mean kernel times of one
+    iteration (the FP64 residual replacement amortised over its period).
+    Bytes per unit: x, r, p each read and written once, q written and read
+    once, the active-set mask as bits, and the modes read twice per
+    iteration, shared by the batch: 8 s_v + 1/8 + 2 k s_Phi / B."""
+    names = ("expand", "spmv", "update", "project")
+    ms = sum((prof["mean_ms"][n] or 0.0) for n in names)
+    if mixed:
+        ms += (prof["mean_ms"]["resid"] or 0.0) / chunk
+    sv = 4 if mixed else 8
+    bpu = 8 * sv + 1.0 / 8 + 2.0 * k * phi_bytes / B
+    fpu = 2 * stencil_flops(w.dim) + 20 + 4 * k
+    out = {"ms_per_iter": ms, "units": units, "bytes_per_unit": bpu, "flops_per_unit": fpu,
+           "kernels": [n for n in names if prof["mean_ms"][n]]}
+    if ms <= 0:
+        return out
+    if mixed:
+        hbm = peaks().get("hbm_gbs")
+        ach = bpu * units / (ms * 1e-3) / 1e9
+        out.update({"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                    "frac": ach / hbm if hbm else None,
+                    "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"})
+    else:
+        ach = fpu * units / (ms * 1e-3) / 1e12
+        out.update({"bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP64_PEAK_TFLOPS,
+                    "peak_source": "nominal FP64 rate of the profiling recipe (1.25 TFLOP/s)",
+                    "hbm_gbs_at_algorithmic_bytes": bpu * units / (ms * 1e-3) / 1e9})
+    return out
+
+
+def dominant_roofline(prof, w, k, mixed, phi_bytes, B, units, fb):
+    """The kernel with the largest share of the timed CG time, against its own
+    bound: HBM for the FP32 kernels (algorithmic bytes / CUDA-event mean),
+    the FP64 pipe for the FP64 ones."""
+    names = [n for n in ("expand", "spmv", "update", "project") if prof["samples"][n]]
+    tot = {n: (prof["mean_ms"][n] or 0.0) * prof["samples"][n] for n in names}
+    dom = max(names, key=lambda n: tot[n])
+    mean_s = prof["mean_ms"][dom] * 1e-3
+    hbm = peaks().get("hbm_gbs")
+    if mixed:
+        flops, byts = kernel_work(dom, w.dim, k, phi_bytes, 4, True, B)
+        ach = byts * units / mean_s / 1e9
+        roof = {"kernel": f"k_{dom}", "bound": "hbm", "achieved": ach, "peak": hbm,
+                "unit": "GB/s", "frac": ach / hbm, "traffic": profile_traffic(dom + "_mixed", w.name),
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+    else:
+        flops, byts = kernel_work_fp64(dom, w.dim, k, fb, B)
+        ach = flops * units / mean_s / 1e12
+        roof = {"kernel": f"k_{dom}", "bound": "alu", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                "traffic": profile_traffic(dom + "_fp64", w.name),
+                "peak_source": "nominal FP64 rate of the profiling recipe (1.25 TFLOP/s)"}
+    roof.update({"algorithmic_flops_per_launch": flops * units,
+                 "algorithmic_bytes_per_launch": byts * units,
+                 "hbm_gbs_at_algorithmic_bytes": byts * units / mean_s / 1e9,
+                 "mean_launch_ms": prof["mean_ms"][dom], "timed_launches": prof["samples"][dom],
+                 "kernel_mean_ms": {n: prof["mean_ms"][n] for n in names + ["resid"]},
+                 "units_per_launch": units})
+    return roof
+
+
+def kernel_work_fp64(name, dim, k, batched, B):
+    """(flops, bytes) per dof and instance of one launch of an FP64-path CG
+    kernel.  Batched (8 or more instances): the update writes v = S z - r and
+    one GEMM projects the batch (modes read once per tile of the batch); one
+    instance at a time: the update projects S z - r itself and the expansion
+    reads the modes per instance."""
+    share = B if batched else 1
+    if name == "update":   # r, q, p, x read; r, x written (+ v); mask; stencil
+        f = stencil_flops(dim) + 9 + (0 if batched else 2 * k)
+        b = 7 * 8 + 1 + (8 if batched else k * 8)
+        return f, b
+    if name == "expand":   # r, p read; p written; mask; modes
+        return 2 * k + 4, 3 * 8 + 1 + k * 8 / share
+    if name == "spmv":     # p read, q written, mask
+        return stencil_flops(dim) + 2, 2 * 8 + 1
+    if name == "project":  # v read; modes shared by the batch
+        return 2 * k, 8 + k * 8 / share
+    raise ValueError(name)
+
+
+def reference_modes(w, G, sdf, mode, dtype, args):
+    """Reference modes Phi of the workload on the GPU, as the configuration
+    names them: closed-form sines (Sec. 2.2.8; the b = 0 reference of the
+    convection workload) or the k smallest eigenpairs of A by the library's
+    Chebyshev-filtered subspace iteration (Sec. 2.2.2), timed separately."""
+    import torch
+    info = {"source": mode}
+    if mode == "analytic":
+        phi, _ = G.analytic_modes(w.k, dtype)
+        info["method"] = "closed-form Kronecker sines on the GPU (Sec. 2.2.8)"
+        return phi, info
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    phi, _, _, est = G.eig_modes(w.k, degree=args.eig_degree, max_iter=4000)
+    torch.cuda.synchronize()
+    info.update({"seconds": time.perf_counter() - t0, "passes": est["iters"],
+                 "converged": bool(est["converged"]), "max_rel_resid": est["max_rel_resid"],
+                 "block_matvecs": est["matvecs"],
+                 "method": "Chebyshev-filtered subspace iteration on A, FP64, timed separately"})
+    if dtype == sdf.F32:
+        phi = phi.float().contiguous()
+    elif dtype == sdf.BF16:
+        phi = phi.to(torch.bfloat16).contiguous()
+    return phi, info
+
+
+def timed_steps(G, steps, run_step, world, dev):
+    """Time exactly `steps` calls of run_step(i) on the device: barrier and
+    synchronize on both sides, CUDA events on the solve's stream, clocks
+    sampled meanwhile; returns (ms, per-step results, clock summary)."""
+    import torch
+    import torch.distributed as dist
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    res = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index or 0) as clk:
+        torch.cuda.nvtx.range_push("timed_region")
+        e0.record(stream)
+        for i in range(steps):
+            res.append(run_step(i))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+    if world > 1:
+        dist.barrier()
+    return max_over_ranks(e0.elapsed_time(e1), dev, world), res, clk.summary()
+
+
+def mean_stat(stats, f):
+    return float(np.mean([f(s) for s in stats])) if stats else None
+
+
+def cpu_leg(w, inst, stats):
+    """The oracle on a bounded sample of this workload (one restricted A-DEF2
+    solve at the full size truncated at a few CG iterations, closed-form modes
+    of the same k), scaled to the run's mean outer and CG iterations."""
+    outer = mean_stat(stats, lambda s: s["outer_iters"])
+    iters = mean_stat(stats, lambda s: sum(s["cg_iters"]))
+    m_iters = 20 if w.N * w.k <= 2e8 else 5
+    ts, ti, cores = cpu_sample(w, inst, m_iters)
+    per = outer * ts + iters * ti
+    return {"value": 1.0 / per, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"oracle A-DEF2 at the full {w.n}^{w.dim} size on one instance, one "
+                       f"restricted solve truncated at {m_iters} CG iterations (set-up {ts:.2f} s, "
+                       f"{ti * 1e3:.1f} ms per iteration); instances/s = 1/(outer*t_setup + "
+                       f"iters*t_iter) with this run's mean outer={outer:.2f}, iters={iters:.0f}")}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="diff3d_128")
+    ap.add_argument("--workload", default="diff3d_128", choices=sorted(MODES))
     ap.add_argument("--n", type=int, default=0, help="grid override (profiling captures only)")
     ap.add_argument("--max-cg", type=int, default=0, help="CG cap (profiling captures only)")
-    ap.add_argument("--path", default="mixed", choices=["plain", "mixed"],
-                    help="plain: FP64 A-DEF2 per instance; mixed: FP32/BF16 with FP64 refinement")
-    ap.add_argument("--phi", default="bf16", choices=["f32", "bf16"], help="mode storage (mixed)")
-    ap.add_argument("--batch", type=int, default=0,
-                    help="instances per step and GPU (default: 64 mixed, 1 plain)")
+    ap.add_argument("--path", default="", choices=["", "plain", "mixed"],
+                    help="plain: FP64 A-DEF2; mixed: FP32/BF16 with FP64 refinement "
+                         "(default: the workload's configuration)")
+    ap.add_argument("--phi", default="", choices=["", "f32", "bf16"], help="mode storage (mixed)")
+    ap.add_argument("--modes", default="", choices=["", "analytic", "eig"])
+    ap.add_argument("--eig-degree", type=int, default=240)
+    ap.add_argument("--batch", type=int, default=0, help="instances per step and GPU")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2,
+                    help="steps of the end-to-end (host-buffer) measurement")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-path comparison")
+    ap.add_argument("--plain-instances", type=int, default=8,
+                    help="instances of the plain per-instance FP64 comparison")
     ap.add_argument("--no-learned", action="store_true",
-                    help="mixed path without the learned warm start")
-    ap.add_argument("--train", type=int, default=128,
-                    help="training instances of the learned warm start (first solves)")
+                    help="the headline workload without the learned warm start")
+    ap.add_argument("--train", type=int, default=0,
+                    help="training instances of the learned warm start (default: the workload's)")
+    ap.add_argument("--train-rtol", type=float, default=1e-5,
+                    help="CG tolerance of the training solves")
+    ap.add_argument("--held-out", type=int, default=0,
+                    help="held-out instances cycled by the timed steps (default: the workload's)")
     ap.add_argument("--epochs", type=int, default=2000, help="Adam epochs of the warm-start MLP")
-    ap.add_argument("--eig", default="", help="also time the reference eigensolve (Sec. 2.2.2) "
-                    "of this variable-kappa workload, separately (e.g. block2d_1024)")
-    ap.add_argument("--eig-degree", type=int, default=240)
-    ap.add_argument("--eig-coarse", type=int, default=2,
-                    help="also time the coarse-grid basis (Sec. 2.2.7) with this factor (0: off)")
-    ap.add_argument("--spacetime", default="spacetime2d_64",
-                    help="also time the space-time workload (App. E.2) with the Kronecker "
-                         "basis, the constant-in-time lift and plain PCG ('' : off)")
+    ap.add_argument("--spacetime", default="",
+                    help="also time this space-time workload (App. E.2) with the Kronecker "
+                         "basis, the constant-in-time lift and plain PCG")
     ap.add_argument("--no-diag", action="store_true",
                     help="skip timing the active-set diagnostics on the last batch")
     ap.add_argument("--diag-sweep", type=int, default=0,
@@ -469,278 +650,345 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    mixed = args.path == "mixed"
-    phi_dt = (sdf.BF16 if args.phi == "bf16" else sdf.F32) if mixed else sdf.F64
-    G, phi = make_problem(w, sdf, dev, phi_dt)
-    B = args.batch or (64 if mixed else 1)
+    mode = dict(MODES[args.workload])
+    if args.path:
+        mode["path"] = args.path
+    if args.phi:
+        mode["phi"] = args.phi
+    if args.modes:
+        mode["modes"] = args.modes
+    if args.batch:
+        mode["batch"] = args.batch
+    if args.no_learned:
+        mode["learned"] = False
+    if mode["path"] == "plain":
+        mode["learned"] = False
+    if mode.get("learned"):
+        line = headline_run(args, w, mode, sdf, dev, world, rank)
+    else:
+        line = workload_run(args, w, mode, sdf, dev, world, rank)
+    if rank == 0:
+        if args.spacetime:
+            line["spacetime"] = spacetime_leg(W.WORKLOADS[args.spacetime], sdf, dev)
+        if args.csr_n:
+            line["csr_path"] = csr_leg(args.csr_n, sdf, dev)
+        if args.diag_sweep:
+            line["diagnostics_sweep"] = diag_sweep_leg(args.diag_n, args.diag_sweep, sdf, dev)
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def base_line(w, mode, B, world, steps, warm, ms, mixed):
+    return {
+        "metric": METRIC, "value": steps * B * world / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+        "steps": steps, "warmup": warm, "ms_per_step": ms / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64",
+        "data": "synthetic (seeded draws of the workload's parameter law)"}
+
+
+def workload_run(args, w, mode, sdf, dev, world, rank):
+    """One batch per step of a workload without the learned start: configs 0-3
+    (and the space-time workload), on the FP64 or the mixed path."""
+    import torch
+    from paper_2606_17971_b300 import workloads as W
+    mixed = mode["path"] == "mixed"
+    phi_dt = (sdf.BF16 if mode.get("phi") == "bf16" else sdf.F32) if mixed else sdf.F64
+    phi_bytes = (2 if phi_dt == sdf.BF16 else 4) if mixed else 8
+    B = mode["batch"]
     steps, warm = args.steps, args.warmup
-    insts = W.draw_instances(w, count=(steps + warm) * B * world)
+    kap = W.kappa_field(w)
+    G = sdf.Problem(w.dim, w.n, alpha=w.alpha, kappa=kap, diff_scale=w.diff_scale,
+                    convection=w.convection, yd_sigma=w.sigma, device=dev)
+    phi, modes_info = reference_modes(w, G, sdf, mode["modes"], phi_dt, args)
+    G.set_modes(phi)
+    insts = W.draw_instances(w, count=max(w.instances, (steps + warm) * B * world))
     mine = shard(insts, rank, world)
-    inst_t = [torch.as_tensor(W.instances_array(mine[i * B:(i + 1) * B]), device=dev)
-              for i in range(steps + warm)]
+    batches = [torch.as_tensor(W.instances_array(mine[(i * B) % len(mine):][:B]), device=dev)
+               for i in range(steps + warm)]
     psi = torch.full((w.N,), w.psi, dtype=torch.float64, device=dev)
-    opts = sdf.default_opts(check_every=128, precision=sdf.PREC_MIXED if mixed else sdf.PREC_F64)
-    opts_lambda = False
+    opts = sdf.default_opts(check_every=128, precision=sdf.PREC_MIXED if mixed else sdf.PREC_F64,
+                            max_cg=1000000)
+    if args.max_cg:
+        opts.max_cg = args.max_cg
+    out = {"y": torch.empty((B, w.N), dtype=torch.float64, device=dev), "lam": None,
+           "active": torch.empty((B, w.N), dtype=torch.uint8, device=dev)}
+    tuned = G.autotune(batches[0], psi, opts) if (mixed and w.dim == 3) else 0
+    for i in range(warm):
+        G.solve(batches[i], psi, opts, out=out, want_lambda=False)
+    opts.profile = 1
+    G.reset_profile()
+    ms, res, clk = timed_steps(G, steps, lambda i: G.solve(batches[warm + i], psi, opts, out=out,
+                                                           want_lambda=False), world, dev)
+    prof = G.profile()
+    stats = [s for r in res for s in r["stats"]]
+    line = base_line(w, mode, B, world, steps, warm, ms, mixed)
+    units = w.N * B
+    fb = (not mixed) and B >= 8
+    roof = dominant_roofline(prof, w, w.k, mixed, phi_bytes, B, units, fb)
+    roof["loop"] = loop_roofline(prof, w, w.k, mixed, phi_bytes, B, units)
+    line["config"] = {
+        "workload": w.name, "grid": [w.n] * w.dim, "k": w.k, "alpha": w.alpha,
+        "instances_per_step": B * world, "batch_per_gpu": B,
+        "path": ("mixed FP32 / %s modes, FP64 x, reductions, coarse operator and residual "
+                 "replacement" % mode.get("phi") if mixed else
+                 ("FP64 A-DEF2, shared-Phi batch kernels" if fb else
+                  "FP64 A-DEF2, one instance per launch")) + " (primal active-set loop)",
+        "modes": modes_info, "l2": "inputs larger than L2 (%.2f GB of vectors per batch)"
+                                  % (8 * units * (4 if mixed else 8) / 1e9),
+        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}
+    if tuned:
+        line["config"]["autotuned"] = {"column_depth": tuned,
+                                       "instance_pairs": G.autotune_choice(B)[1]}
+    line.update({
+        "cg_iters_per_instance": mean_stat(stats, lambda s: sum(s["cg_iters"])),
+        "outer_iters_per_instance": mean_stat(stats, lambda s: s["outer_iters"]),
+        "statuses": sorted(set(s["status"] for s in stats)),
+        "floor_stops": int(sum(sum(s["floor_stop"]) for s in stats)),
+        "max_true_relres": float(max(s["true_relres"][-1] for s in stats)),
+        "max_relres_floor": float(max(max(s["relres_floor"]) for s in stats)),
+        "roofline": roof, "clocks": clk, "gpu_launches": int(prof["launches"])})
+    if not args.no_e2e:
+        ne = min(steps, args.e2e_steps)
+        inst_h = [b.cpu().pin_memory() for b in batches[warm:warm + ne]]
+        psi_h = torch.full((w.N,), w.psi, dtype=torch.float64).pin_memory()
+        y_h = torch.empty((B, w.N), dtype=torch.float64).pin_memory()
+        a_h = torch.empty((B, w.N), dtype=torch.uint8).pin_memory()
+        opts.profile = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(ne):
+            G.solve_host(inst_h[i].numpy(), psi_h.numpy(), opts, y=y_h.numpy(), active=a_h.numpy())
+        te = max_over_ranks(time.perf_counter() - t0, dev, world)
+        line["e2e"] = {"value": ne * B * world / te, "unit": UNIT,
+                       "h2d_bytes_per_step": int(inst_h[0].numel() * 8 + psi_h.numel() * 8),
+                       "d2h_bytes_per_step": int(y_h.numel() * 8 + a_h.numel()),
+                       "steps": ne, "path": "sdf_solve_batch_host (C ABI, host buffers)"}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_leg(w, mine[0], stats)
+    return line
+
+
+def headline_run(args, w, mode, sdf, dev, world, rank):
+    """Config 4: the batched + mixed + learned form on held-out batches, against
+    the plain per-instance FP64 path and against the same batches solved
+    cold.  Training (untimed): the first (unconstrained) solve of each
+    training instance by the batched solver, POD of the states, full-batch
+    Adam of the MLP on the tensor cores."""
+    import torch
+    from paper_2606_17971_b300 import workloads as W
+    mixed = True
+    phi_dt = sdf.BF16 if mode.get("phi") == "bf16" else sdf.F32
+    phi_bytes = 2 if phi_dt == sdf.BF16 else 4
+    B = mode["batch"]
+    steps, warm = args.steps, args.warmup
+    G = sdf.Problem(w.dim, w.n, alpha=w.alpha, kappa=W.kappa_field(w), yd_sigma=w.sigma,
+                    device=dev)
+    phi, modes_info = reference_modes(w, G, sdf, mode["modes"], phi_dt, args)
+    G.set_modes(phi)
+    psi = torch.full((w.N,), w.psi, dtype=torch.float64, device=dev)
+    # held-out instances, in batches of B, cycled by the timed steps
+    n_held = args.held_out or w.extra.get("held_out", 1024)
+    held = shard(W.draw_instances(w, count=n_held * world), rank, world)
+    nb = max(1, len(held) // B)
+    batches = [torch.as_tensor(W.instances_array(held[i * B:(i + 1) * B]), device=dev)
+               for i in range(nb)]
+    opts = sdf.default_opts(check_every=128, precision=sdf.PREC_MIXED, max_cg=1000000)
     if args.max_cg:
         opts.max_cg = args.max_cg
     out = {"y": torch.empty((B, w.N), dtype=torch.float64, device=dev), "lam": None,
            "active": torch.empty((B, w.N), dtype=torch.uint8, device=dev)}
 
-    # ---- learned warm start: trained before the timed region ----
-    learned = mixed and not args.no_learned
-    model, train_info = None, None
-    if learned:
-        t0 = time.perf_counter()
-        ntr = args.train
-        tr = W.draw_instances(w, count=ntr, seed=w.seed + 1000 + rank)
-        it_tr = torch.as_tensor(W.instances_array(tr), device=dev)
-        o1 = sdf.default_opts(check_every=128, precision=sdf.PREC_MIXED, max_outer=1)
-        Ytr = torch.empty((ntr, w.N), dtype=torch.float64, device=dev)
-        tb = min(128, ntr)
-        for j in range(0, ntr, tb):
-            Ytr[j:j + tb] = G.solve(it_tr[j:j + tb].contiguous(), psi, o1, want_lambda=False)["y"]
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
-        widths = (1 + w.dim, 256, 256, 256, 64)
-        lo, hi = W.input_box(w)
-        model = sdf.WarmModel(widths, w.N, lo, hi, torch.from_numpy(W.mlp_init(widths)).to(dev))
-        loss = model.fit(Ytr, it_tr, epochs=args.epochs, lr0=1e-3)
-        torch.cuda.synchronize()
-        t2 = time.perf_counter()
-        del Ytr
-        train_info = {"instances": ntr, "solve_s": t1 - t0, "fit_s": t2 - t1,
-                      "epochs": args.epochs, "loss_first": float(loss[0]),
-                      "loss_last": float(loss[-1]), "widths": list(widths), "pod_rank": 64,
-                      "note": "first (unconstrained) solves of separate training instances; "
-                              "not part of the timed region"}
-
-    # autotuned column depth of the stencil kernels (short capped solves, untimed)
-    tuned_zc = G.autotune(inst_t[0], psi, opts) if mixed else 0
-
-    def one_step(inst):
-        if model is not None:
-            x0 = model.predict(inst)
-            return G.solve_x0(inst, psi, x0, opts, out=out, want_lambda=opts_lambda)
-        return G.solve(inst, psi, opts, out=out, want_lambda=opts_lambda)
-
-    for i in range(warm):
-        one_step(inst_t[i])
+    # ---- training (untimed) ----
+    t0 = time.perf_counter()
+    ntr = args.train or w.extra.get("train", 2000)
+    tr = W.draw_instances(w, count=ntr, seed=w.seed + 1000 + rank)
+    it_tr = torch.as_tensor(W.instances_array(tr), device=dev)
+    o1 = sdf.default_opts(check_every=128, precision=sdf.PREC_MIXED, max_outer=1,
+                          rtol=args.train_rtol)
+    Ytr = torch.empty((ntr, w.N), dtype=torch.float64, device=dev)
+    for j in range(0, ntr, B):
+        Ytr[j:j + B] = G.solve(it_tr[j:j + B].contiguous(), psi, o1, want_lambda=False)["y"]
     torch.cuda.synchronize()
-
-    # ---- timed region (device-resident inputs) ----
-    opts.profile = 1
-    G.reset_profile()
-    stats = []
-    stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if world > 1:
-        dist.barrier()
+    t1 = time.perf_counter()
+    widths = (1 + w.dim, 256, 256, 256, 64)
+    lo, hi = W.input_box(w)
+    model = sdf.WarmModel(widths, w.N, lo, hi, torch.from_numpy(W.mlp_init(widths)).to(dev))
+    loss = model.fit(Ytr, it_tr, epochs=args.epochs, lr0=1e-3)
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        # NVTX range: lets a profiler capture exactly the timed launches
-        torch.cuda.nvtx.range_push("timed_region")
+    t2 = time.perf_counter()
+    del Ytr
+    torch.cuda.empty_cache()
+    train_info = {"instances": ntr, "rtol": args.train_rtol, "solve_s": t1 - t0, "fit_s": t2 - t1,
+                  "epochs": args.epochs, "loss_first": float(loss[0]), "loss_last": float(loss[-1]),
+                  "widths": list(widths), "pod_rank": 64, "pod_snapshots": min(ntr, 384),
+                  "note": "first (unconstrained) solves of separate training instances; "
+                          "not part of the timed region"}
+
+    # ---- plain per-instance FP64 path on the first held-out instances ----
+    plain = None
+    if not args.no_plain:
+        Gp = sdf.Problem(w.dim, w.n, alpha=w.alpha, kappa=W.kappa_field(w), yd_sigma=w.sigma,
+                         device=dev)
+        php, _ = reference_modes(w, Gp, sdf, mode["modes"], sdf.F64, args)
+        Gp.set_modes(php)
+        op = sdf.default_opts(check_every=128, max_cg=1000000)
+        npl = min(args.plain_instances, B)
+        Gp.solve(batches[0][:1].contiguous(), psi, op, want_lambda=False)  # warm-up instance
+        stream = torch.cuda.current_stream()
+        ep0, ep1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ep0.record(stream)
+        pst = []
+        for i in range(npl):
+            pst += Gp.solve(batches[0][i:i + 1].contiguous(), psi, op, want_lambda=False)["stats"]
+        ep1.record(stream)
+        torch.cuda.synchronize()
+        plain = {"value": npl / (ep0.elapsed_time(ep1) * 1e-3), "unit": UNIT,
+                 "instances_timed": npl,
+                 "cg_iters_per_instance": mean_stat(pst, lambda s: sum(s["cg_iters"])),
+                 "statuses": sorted(set(s["status"] for s in pst)),
+                 "note": "same workload and held-out instances, one instance per launch, "
+                         "after one warm-up instance"}
+        del Gp, php
+        torch.cuda.empty_cache()
+
+    tuned = G.autotune(batches[0], psi, opts)
+
+    def learned_step(inst):
+        x0 = model.predict(inst)
+        return G.solve_x0(inst, psi, x0, opts, out=out, want_lambda=False)
+
+    def timed_solve(fn):
+        stream = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for i in range(steps):
-            res = one_step(inst_t[warm + i])
-            stats.extend(res["stats"])
+        r = fn()
         e1.record(stream)
         torch.cuda.synchronize()
-        torch.cuda.nvtx.range_pop()
-    if world > 1:
-        dist.barrier()
-    prof = G.profile()
-    ms = max_over_ranks(e0.elapsed_time(e1), dev, world)
-    value = steps * B * world / (ms * 1e-3)
+        return e0.elapsed_time(e1), r
 
-    # ---- e2e: host buffers in, host buffers out, copies inside the timed region ----
-    e2e = None
+    # ---- warm-up: one learned step, then cold solves of held-out batches
+    # (each held-out batch is solved cold once, for the comparison) ----
+    cold = {}
+    learned_step(batches[0])
+    for i in range(warm - 1):
+        b = i % nb
+        if b not in cold:
+            cold[b] = timed_solve(lambda: G.solve(batches[b], psi, opts, out=out,
+                                                  want_lambda=False))
+        else:
+            learned_step(batches[b])
+    torch.cuda.synchronize()
+
+    # ---- timed region: learned steps over the held-out batches ----
+    opts.profile = 1
+    G.reset_profile()
+    ms, res, clk = timed_steps(G, steps, lambda i: learned_step(batches[i % nb]), world, dev)
+    prof = G.profile()
+    opts.profile = 0
+    stats = [s for r in res for s in r["stats"]]
+
+    # ---- the remaining cold solves of held-out batches (untimed) ----
+    for b in range(nb):
+        if b not in cold:
+            cold[b] = timed_solve(lambda: G.solve(batches[b], psi, opts, out=out,
+                                                  want_lambda=False))
+    # learned ms and iterations per held-out batch (one timed step each)
+    per_batch = []
+    for b in range(nb):
+        i = next((i for i in range(steps) if i % nb == b), None)
+        lrn_it = mean_stat(res[i]["stats"], lambda s: sum(s["cg_iters"])) if i is not None else None
+        lrn_ms = None
+        if i is None:
+            lrn_ms, rl = timed_solve(lambda: learned_step(batches[b]))
+            lrn_it = mean_stat(rl["stats"], lambda s: sum(s["cg_iters"]))
+        cms, rc = cold[b]
+        lst = res[i]["stats"] if i is not None else rl["stats"]
+        # the learned start changes the CG iterations only: the outer
+        # iterations and the active-set sizes of every solve equal the cold ones
+        same = all(a["outer_iters"] == c["outer_iters"] and a["n_active"] == c["n_active"]
+                   for a, c in zip(lst, rc["stats"]))
+        per_batch.append({"batch": b, "cold_ms": cms,
+                          "cold_cg_iters": mean_stat(rc["stats"], lambda s: sum(s["cg_iters"])),
+                          "learned_cg_iters": lrn_it, "learned_ms": lrn_ms,
+                          "outer_and_active_sizes_equal": same})
+    # prediction error after the coarse-corrected start, on the first batch
+    first = G.solve(batches[0], psi, sdf.default_opts(precision=sdf.PREC_MIXED, max_outer=1),
+                    want_lambda=False)["y"]
+    x0 = model.predict(batches[0])
+    pred_err = ((x0 - first).norm() / first.norm()).item()
+
+    line = base_line(w, mode, B, world, steps, warm, ms, mixed)
+    units = w.N * B
+    roof = dominant_roofline(prof, w, w.k, True, phi_bytes, B, units, False)
+    roof["loop"] = loop_roofline(prof, w, w.k, True, phi_bytes, B, units)
+    line["config"] = {
+        "workload": w.name, "grid": [w.n] * w.dim, "k": w.k, "alpha": w.alpha,
+        "instances_per_step": B * world, "batch_per_gpu": B, "held_out": len(held),
+        "held_out_batches": nb,
+        "path": "mixed FP32 / %s modes, FP64 x, reductions, coarse operator and residual "
+                "replacement, learned warm start (primal active-set loop)" % mode.get("phi"),
+        "modes": modes_info,
+        "l2": "inputs larger than L2: Phi is %.2f GB and each vector %.2f GB"
+              % (w.N * w.k * phi_bytes / 1e9, units * 4 / 1e9),
+        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+        "autotuned": {"column_depth": tuned, "instance_pairs": G.autotune_choice(B)[1]}}
+    cold_ms = float(np.mean([c[0] for c in cold.values()]))
+    cold_it = float(np.mean([p["cold_cg_iters"] for p in per_batch]))
+    lrn_it = mean_stat(stats, lambda s: sum(s["cg_iters"]))
+    line.update({
+        "cg_iters_per_instance": lrn_it,
+        "outer_iters_per_instance": mean_stat(stats, lambda s: s["outer_iters"]),
+        "statuses": sorted(set(s["status"] for s in stats)),
+        "floor_stops": int(sum(sum(s["floor_stop"]) for s in stats)),
+        "max_true_relres": float(max(s["true_relres"][-1] for s in stats)),
+        "roofline": roof, "clocks": clk,
+        # the solver's launches plus the prediction's per step: per layer one
+        # weight conversion and one product, then input conversion, input
+        # scaling and the expansion
+        "gpu_launches": int(prof["launches"]) + steps * (2 * 4 + 3),
+        "learned": {"training": train_info,
+                    "cold": {"ms_per_batch": cold_ms, "cg_iters_per_instance": cold_it,
+                             "instances_per_s": B / (cold_ms * 1e-3)},
+                    "learned_vs_cold": {"cg_iters": lrn_it / cold_it,
+                                        "ms": (ms / steps) / cold_ms},
+                    "prediction_rel_error_first_solve": pred_err,
+                    "per_batch": per_batch}})
+    if plain:
+        line["plain_fp64_per_instance"] = plain
+        line["speedup_vs_plain"] = line["value"] / plain["value"]
     if not args.no_e2e:
-        opts.profile = 0
-        inst_h = [torch.from_numpy(W.instances_array(mine[i * B:(i + 1) * B])).pin_memory()
-                  for i in range(steps + warm)]
+        ne = min(steps, args.e2e_steps)
+        inst_h = [batches[i % nb].cpu().pin_memory() for i in range(ne)]
         psi_h = torch.full((w.N,), w.psi, dtype=torch.float64).pin_memory()
         y_h = torch.empty((B, w.N), dtype=torch.float64).pin_memory()
         a_h = torch.empty((B, w.N), dtype=torch.uint8).pin_memory()
-        if model is None:
-            def e2e_step(i):
-                G.solve_host(inst_h[i].numpy(), psi_h.numpy(), opts, y=y_h.numpy(),
-                             active=a_h.numpy())
-        else:
-            # the learned pipeline through the binding: copy mu and psi in, predict
-            # x0 (tensor-core MLP + FP64 expansion), solve, copy y and A out
-            def e2e_step(i):
-                inst_d = inst_h[i].to(dev, non_blocking=True)
-                psi_d = psi_h.to(dev, non_blocking=True)
-                x0 = model.predict(inst_d)
-                r = G.solve_x0(inst_d, psi_d, x0, opts, out=out, want_lambda=False)
-                y_h.copy_(r["y"], non_blocking=True)
-                a_h.copy_(r["active"], non_blocking=True)
-                torch.cuda.current_stream().synchronize()
-        e2e_step(0)
-        if world > 1:
-            dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for i in range(steps):
-            e2e_step(warm + i)
-        torch.cuda.synchronize()
+        for i in range(ne):
+            G.solve_learned_host(model, inst_h[i].numpy(), psi_h.numpy(), opts, y=y_h.numpy(),
+                                 active=a_h.numpy())
         te = max_over_ranks(time.perf_counter() - t0, dev, world)
-        e2e = {"value": steps * B * world / te, "unit": UNIT,
-               "h2d_bytes_per_step": int(inst_h[0].numel() * 8 + psi_h.numel() * 8),
-               "d2h_bytes_per_step": int(y_h.numel() * 8 + a_h.numel()),
-               "path": "learned pipeline through the Python binding" if model is not None
-               else "sdf_solve_batch_host"}
-
-    # ---- the same batch without the learned start (untimed comparison) ----
-    cold_cmp = None
-    if model is not None:
-        opts.profile = 0
-        ec0, ec1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ec0.record(stream)
-        rc = G.solve(inst_t[warm], psi, opts, out=out, want_lambda=False)
-        ec1.record(stream)
-        torch.cuda.synchronize()
-        cold_cmp = {"ms": ec0.elapsed_time(ec1),
-                    "cg_iters_per_instance": float(np.mean([sum(s["cg_iters"]) for s in rc["stats"]])),
-                    "learned_cg_iters_per_instance":
-                        float(np.mean([sum(s["cg_iters"]) for s in stats[:B]])),
-                    "note": "first timed batch solved again from x0 = 0"}
-
-    # ---- roofline of the dominant kernel ----
-    names = ("expand", "spmv", "update") + (("project",) if mixed else ())
-    tot = {n: (prof["mean_ms"][n] or 0.0) * prof["samples"][n] for n in names}
-    dom = max(names, key=lambda n: tot[n])
-    phi_bytes = 8 if not mixed else (2 if args.phi == "bf16" else 4)
-    flops_dof, bytes_dof = kernel_work(dom, w.dim, w.k, phi_bytes, 4 if mixed else 8, mixed, B)
-    units = w.N * B
-    mean_s = prof["mean_ms"][dom] * 1e-3
-    hbm = peaks().get("hbm_gbs")
-    if mixed:  # FP32 arithmetic: the streaming kernels are HBM-bound by design
-        achieved = bytes_dof * units / mean_s / 1e9
-        roof = {"kernel": f"k_{dom}", "bound": "hbm", "achieved": achieved, "peak": hbm,
-                "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": profile_traffic(dom + "_mixed", w.name),
-                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
-    else:
-        achieved = flops_dof * units / mean_s / 1e12
-        roof = {"kernel": f"k_{dom}", "bound": "alu", "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": profile_traffic(dom, w.name),
-                "peak_source": "nominal FP64 of the profiling recipe (1.25 TFLOP/s; probe measured 1.20)"}
-    roof.update({
-            "algorithmic_flops_per_launch": flops_dof * units,
-            "algorithmic_bytes_per_launch": bytes_dof * units,
-            "hbm_gbs_at_algorithmic_bytes": bytes_dof * units / mean_s / 1e9,
-            "hbm_peak_gbs": hbm, "mean_launch_ms": prof["mean_ms"][dom],
-            "timed_launches": prof["samples"][dom],
-            "kernel_mean_ms": {n: prof["mean_ms"][n] for n in names + ("resid",)},
-            "units_per_launch": units})
-
-    cg = [sum(s["cg_iters"]) for s in stats]
-    outer = [s["outer_iters"] for s in stats]
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
-        "warmup": warm, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64" if mixed else "f64", "data": "synthetic",
-        "config": {"workload": w.name, "grid": [w.n] * w.dim, "k": w.k, "alpha": w.alpha,
-                   "instances_per_step": B * world, "batch_per_gpu": B,
-                   "path": ("mixed FP32/%s A-DEF2, FP64 x, reductions and residual replacement"
-                            % args.phi if mixed else "plain FP64 A-DEF2 per instance")
-                           + (", learned warm start" if learned else "")
-                           + " (primal active-set loop)",
-                   "modes": "closed-form sines on the GPU (Sec. 2.2.8)",
-                   "l2": "inputs larger than L2: Phi is %.2f GB, read twice per CG iteration"
-                         % (w.N * w.k * phi_bytes / 1e9),
-                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
-                   "autotuned_column_depth": tuned_zc},
-        "cg_iters_per_instance": float(np.mean(cg)), "outer_iters_per_instance": float(np.mean(outer)),
-        "statuses": sorted(set(s["status"] for s in stats)),
-        "roofline": roof, "clocks": clk.summary(), "e2e": e2e,
-        # the solver's launches plus the warm-start prediction's per step: per
-        # layer one weight conversion and one product, then input conversion,
-        # input scaling and the expansion
-        "gpu_launches": int(prof["launches"]) + (steps * (2 * 4 + 3) if model is not None else 0),
-    }
-    if model is not None:
-        line["learned"] = {"training": train_info, "same_batch_cold": cold_cmp}
-    if mixed and not args.no_plain:
-        # the metric compares against the plain per-instance FP64 path: one
-        # instance of the same workload after one warm-up solve
-        Gp, _ = make_problem(w, sdf, dev, sdf.F64)
-        op = sdf.default_opts(check_every=128)
-        one = inst_t[0][:1].contiguous()
-        Gp.solve(one, psi, op, want_lambda=False)
-        torch.cuda.synchronize()
-        ep0, ep1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ep0.record(stream)
-        rp = Gp.solve(inst_t[1][:1].contiguous(), psi, op, want_lambda=False)
-        ep1.record(stream)
-        torch.cuda.synchronize()
-        pv = 1e3 / ep0.elapsed_time(ep1)
-        line["plain_fp64_per_instance"] = {
-            "value": pv, "unit": UNIT, "instances_timed": 1,
-            "cg_iters": sum(rp["stats"][0]["cg_iters"]), "note": "same workload, same run"}
-        line["speedup_vs_plain"] = value / pv
-        del Gp
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        ts, ti, cores = cpu_sample(w, mine[0], 20)
-        per = np.mean(outer) * ts + np.mean(cg) * ti
-        line["cpu_baseline"] = {
-            "value": 1.0 / per, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": (f"oracle A-DEF2 at the full {w.n}^{w.dim} size on instance 0, one restricted "
-                       f"solve truncated at 20 CG iterations (set-up {ts:.2f} s, {ti * 1e3:.1f} ms "
-                       f"per iteration); instances/s = 1/(outer*t_setup + iters*t_iter) with this "
-                       f"run's mean outer={np.mean(outer):.2f}, iters={np.mean(cg):.0f}")}
-    if args.eig and rank == 0:
-        # the offline eigensolve, timed on its own (not part of the metric)
-        we = W.WORKLOADS[args.eig]
-        Ge = sdf.Problem(we.dim, we.n, alpha=we.alpha, kappa=W.kappa_field(we), yd_sigma=we.sigma,
-                         device=dev)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        _, ls, la, est = Ge.eig_modes(we.k, degree=args.eig_degree, max_iter=2000)
-        torch.cuda.synchronize()
-        line["eigensolve"] = {"workload": we.name, "k": we.k, "N": we.N,
-                              "seconds": time.perf_counter() - t0, "passes": est["iters"],
-                              "converged": est["converged"], "max_rel_resid": est["max_rel_resid"],
-                              "block_matvecs": est["matvecs"],
-                              "method": "Chebyshev-filtered subspace iteration on A, FP64"}
-        if args.eig_coarse >= 2:
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            phc, _, cst = Ge.coarse_modes(args.eig_coarse, we.k, degree=args.eig_degree,
-                                          max_iter=2000)
-            torch.cuda.synchronize()
-            line["eigensolve"]["coarse_grid"] = {
-                "factor": args.eig_coarse, "seconds": time.perf_counter() - t0,
-                "columns_kept": int(phc.shape[0]), "coarse_passes": cst["iters"],
-                "method": "eigenpairs on the grid coarsened by the factor, linear prolongation, QR"}
-        del Ge
+        line["e2e"] = {"value": ne * B * world / te, "unit": UNIT,
+                       "h2d_bytes_per_step": int(inst_h[0].numel() * 8 + psi_h.numel() * 8),
+                       "d2h_bytes_per_step": int(y_h.numel() * 8 + a_h.numel()), "steps": ne,
+                       "path": "sdf_solve_batch_learned_host (C ABI: host mu in, prediction "
+                               "and solve on the device, host y and A out)"}
     if not args.no_diag and rank == 0:
-        # Eq. delta / Eq. rho / the mode-weighted distance of the last timed
-        # batch's active sets from its first instance's (not part of the metric)
         ref = out["active"][0].clone()
         G.diag_active_sets(ref, out["active"], r=w.k)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         dg = G.diag_active_sets(ref, out["active"], r=w.k)
         td = time.perf_counter() - t0
-        line["diagnostics"] = {
-            "active_sets": B, "N": w.N, "r": w.k, "ms": 1e3 * td,
-            "mask_and_mode_gb_per_s": (B * w.N + w.N + w.N * w.k * phi_bytes * ((B + 7) // 8))
-                                      / td / 1e9,
-            "delta_max": float(dg["delta"].max()), "rho_mean": float(dg["rho"].mean()),
-            "note": "sdf_diag_active_sets, host round trip included"}
-    if args.spacetime and rank == 0:
-        line["spacetime"] = spacetime_leg(W.WORKLOADS[args.spacetime], sdf, dev)
-    if args.csr_n and rank == 0:
-        line["csr_path"] = csr_leg(args.csr_n, sdf, dev)
-    if args.diag_sweep and rank == 0:
-        line["diagnostics_sweep"] = diag_sweep_leg(args.diag_n, args.diag_sweep, sdf, dev)
-    if rank == 0:
-        print(json.dumps(line))
-    if world > 1:
-        dist.destroy_process_group()
+        line["diagnostics"] = {"active_sets": B, "N": w.N, "r": w.k, "ms": 1e3 * td,
+                               "delta_max": float(dg["delta"].max()),
+                               "rho_mean": float(dg["rho"].mean()),
+                               "note": "sdf_diag_active_sets, host round trip included"}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_leg(w, held[0], stats)
+    return line
 
 
 if __name__ == "__main__":

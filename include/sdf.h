@@ -157,7 +157,11 @@ typedef struct {
  *                mixed path stops on max(rtol, floor); 0: rtol only  [10]
  *   column_depth mixed 3D path: z planes per column item of the stencil
  *                kernels, 8, 16, 32 or 64 (0: the depth sdf_autotune chose
- *                for this batch size, else 32 for batches of 8 or more) [0] */
+ *                for this batch size, else 32 for batches of 8 or more) [0]
+ *   column_pairs mixed 3D path: 1 runs the stencil kernels on instance pairs
+ *                (two instances per block on the packed FP32 pipe), 2 one
+ *                instance per block, 0 what sdf_autotune chose for this
+ *                batch size (pairs for 2 or more instances when untuned) [0] */
 typedef struct {
   double rtol;
   double tau;
@@ -177,6 +181,7 @@ typedef struct {
   double tau_dep;
   double floor_c;
   int32_t column_depth;
+  int32_t column_pairs;
 } sdf_opts;
 
 /* Per-instance statistics (host struct filled at the end of a solve).
@@ -328,13 +333,17 @@ sdf_status sdf_solve_batch_rhs(sdf_problem *p, const double *inst_dev, const dou
 
 /* Autotuner of the batched mixed 3D path: for this batch size, time a short
  * capped solve (40 CG iterations) of these instances with each candidate
- * column depth of the stencil kernels (8, 16, 32, 64 planes per block) and
- * keep the fastest for later solves of this handle with the same batch size
- * (*choice receives it; 0 when nothing is tuned for this problem).  Outputs
- * y_dev / active_dev are scratch here.  No counterpart in the paper. */
+ * column depth of the stencil kernels (8, 16, 32, 64 planes per block), each
+ * with instance pairs and with one instance per block, and keep the fastest
+ * for later solves of this handle with the same batch size (*choice receives
+ * the depth; 0 when nothing is tuned for this problem).  Outputs y_dev /
+ * active_dev are scratch here.  sdf_autotune_choice returns the depth and the
+ * pairing (1 pairs, 0 single, -1 not tuned) kept for a batch size.  No
+ * counterpart in the paper. */
 sdf_status sdf_autotune(sdf_problem *p, const double *inst_dev, int batch, const double *psi_dev,
                         const sdf_opts *opts, void *ws, size_t ws_bytes, void *stream,
                         double *y_dev, uint8_t *active_dev, int *choice);
+sdf_status sdf_autotune_choice(const sdf_problem *p, int batch, int *depth, int *pairs);
 
 /* The same solve with every input and output in HOST memory: the instance
  * array and psi are copied to the device inside the call and y, lambda (if not
@@ -596,6 +605,7 @@ sdf_status sdf_diag_angles(sdf_problem *p, const uint8_t *active_dev, const doub
 #define SDF_MLP_MAX_LAYERS 8
 #define SDF_POD_MAX_R 64
 #define SDF_POD_MAX_SNAPSHOTS 512
+#define SDF_FIT_MAX_SNAPSHOTS 4096
 
 /* width[0] inputs, width[1..n_layers-1] hidden (GELU), width[n_layers]
  * outputs (identity); every width in 1..256. */
@@ -691,7 +701,12 @@ typedef struct {
  * psi), target scaling (cmean, cscale), then `epochs` full-batch Adam steps
  * (beta 0.9 / 0.999, eps 1e-8) with the learning rate decaying from lr0 to 0
  * on a cosine, starting from the caller's theta.  loss_host (epochs doubles,
- * may be NULL) receives the loss before each step.  m <= 512, epochs <= 4096. */
+ * may be NULL) receives the loss before each step.  2 <= m <=
+ * SDF_FIT_MAX_SNAPSHOTS, epochs <= 4096.  The POD basis comes from the first
+ * min(m, 384) states (the method of snapshots diagonalises their Gram matrix
+ * on the host); the MLP is fit to the coefficients of all m states on that
+ * basis, Psi^T (y_i - ybar) in FP64, so a large training set costs one
+ * projection, not a larger eigenproblem. */
 sdf_status sdf_warm_fit_workspace_size(const sdf_warm_model *M, int m, size_t *bytes);
 sdf_status sdf_warm_fit(sdf_warm_model *M, const double *Y_dev, const double *inst_dev, int m,
                         int epochs, float lr0, double *loss_host, void *ws, size_t ws_bytes,
@@ -709,6 +724,25 @@ sdf_status sdf_warm_predict(const sdf_warm_model *M, const double *inst_dev, int
 
 /* Error text of the last failing call above on this host thread. */
 const char *sdf_aux_last_error(void);
+
+/* The learned pipeline end to end from HOST buffers (no counterpart in the
+ * paper): the instances (batch x SDF_INSTANCE_DOUBLES) and psi (N) are copied
+ * to the device inside the call, x0 is predicted by the model M
+ * (sdf_warm_predict: MLP on the tensor cores, FP64 expansion), the batch is
+ * solved from x0 (sdf_solve_batch_x0), and y, lambda (if not NULL) and the
+ * active sets are copied back; every copy is on `stream`, and the call returns
+ * after the last one.  batch <= 256.  ws (device, 256-byte aligned): at least
+ * sdf_workspace_size(p, batch, opts) rounded up to 256 plus
+ * sdf_learned_host_io_bytes(p, M, batch) bytes.  Returns the solve's status
+ * (instance statuses in stats_host), or the prediction's error. */
+sdf_status sdf_learned_host_io_bytes(const sdf_problem *p, const sdf_warm_model *M, int batch,
+                                     size_t *bytes);
+sdf_status sdf_solve_batch_learned_host(sdf_problem *p, const sdf_warm_model *M,
+                                        const double *inst_host, int batch,
+                                        const double *psi_host, const sdf_opts *opts, void *ws,
+                                        size_t ws_bytes, void *stream, double *y_host,
+                                        double *lambda_host, uint8_t *active_host,
+                                        sdf_stats *stats_host);
 
 #ifdef __cplusplus
 }

@@ -86,6 +86,7 @@ struct Layout {
   int tce, kp;   // tensor-core expansion and the padded mode count of its node-major copy
   size_t phin;   // node-major BF16 copy of the modes (tensor-core expansion)
   int fb;        // FP64 path with the shared-Phi batch kernels (batch >= kFp64BatchMin)
+  int pairs;     // mixed 3D path: stencil kernels on instance pairs (packed FP32)
 };
 
 inline size_t al(size_t v) { return (v + 255) & ~size_t(255); }
@@ -1582,6 +1583,169 @@ __global__ void __launch_bounds__(NT, 3) k_update_v3c(OpParams P, const double *
                                         rtol2, max_cg);
 }
 
+// Instance-pair variants of k_spmv3c and k_update_v3c (col_S3_pair): block x
+// handles instances 2x and 2x + 1 (the second absent when B is odd).  An
+// instance that is not iterating in this pass keeps every vector: its stores
+// are skipped and its reduction is not entered (the half of the pair is
+// computed and dropped).
+struct ColSrcP2 {
+  const float *p0, *p1;
+  struct Raw { float a, b; };
+  __device__ __forceinline__ Raw fetch(int g) const { return Raw{p0[g], p1[g]}; }
+  __device__ __forceinline__ F2 value(const Raw &r) const { return F2{r.a, r.b}; }
+};
+struct ColOutQ2 {
+  const uint8_t *m0, *m1;
+  float *q0, *q1;
+  bool run0, run1;
+  KahanF2 sg;
+  struct Pre { uint8_t a, b; };
+  __device__ __forceinline__ Pre fetch(int g) const { return Pre{m0[g], m1[g]}; }
+  __device__ __forceinline__ void store(int g, F2 su, F2 uc, const Pre &pr) {
+    const F2 qv{pr.a ? 0.0f : su.x, pr.b ? 0.0f : su.y};
+    if (run0) q0[g] = qv.x;
+    if (run1) q1[g] = qv.y;
+    sg.add(mul2(uc, qv));
+  }
+};
+// u = z = D^-1 (r - alpha q) of both instances (shared D^-1: no convection)
+struct ColSrcZ2 {
+  const float *r0, *r1, *q0, *q1, *dinv;
+  F2 nalpha;  // -alpha of each instance
+  struct Raw { float r0, r1, q0, q1, d; };
+  __device__ __forceinline__ Raw fetch(int g) const { return Raw{r0[g], r1[g], q0[g], q1[g], dinv[g]}; }
+  __device__ __forceinline__ F2 value(const Raw &a) const {
+    return mul2(bc2(a.d), fma2(nalpha, F2{a.q0, a.q1}, F2{a.r0, a.r1}));
+  }
+};
+// FOLDANY: at least one instance is in its correction pass (folds x_lo into
+// the FP64 iterate); the other 99 of every 100 passes compile without FP64 code.
+template <bool FOLDANY> struct ColOutUpd2 {
+  const uint8_t *m0, *m1;
+  const float *r0, *r1, *q0, *q1, *p0, *p1;
+  float *rw0, *rw1, *v0, *v1, *xl0, *xl1;
+  double *x0, *x1;
+  F2 alpha, nalpha;
+  double a64_0, a64_1;
+  bool run0, run1, fold0, fold1;  // fold: correction pass, x_lo folded into x
+  KahanF2 rho, rr;
+  struct Pre { float r0, r1, q0, q1, p0, p1, l0, l1; uint8_t m0, m1; };
+  __device__ __forceinline__ Pre fetch(int g) const {
+    return Pre{r0[g], r1[g], q0[g], q1[g], p0[g], p1[g], xl0[g], xl1[g], m0[g], m1[g]};
+  }
+  __device__ __forceinline__ void store(int g, F2 su, F2 z, const Pre &a) {
+    // r, q, p and x_lo vanish on the active set, so only v needs the mask
+    const F2 rn = fma2(nalpha, F2{a.q0, a.q1}, F2{a.r0, a.r1});
+    F2 v = sub2(su, rn);
+    if (a.m0) v.x = 0.0f;
+    if (a.m1) v.y = 0.0f;
+    rho.add(mul2(rn, z));
+    rr.add(mul2(rn, rn));
+    const F2 xn = fma2(alpha, F2{a.p0, a.p1}, F2{a.l0, a.l1});
+    if (run0) {
+      rw0[g] = rn.x;
+      v0[g] = v.x;
+      if (FOLDANY && fold0) {
+        x0[g] = x0[g] + (double)a.l0 + a64_0 * (double)a.p0;
+        xl0[g] = 0.0f;
+      } else {
+        xl0[g] = xn.x;
+      }
+    }
+    if (run1) {
+      rw1[g] = rn.y;
+      v1[g] = v.y;
+      if (FOLDANY && fold1) {
+        x1[g] = x1[g] + (double)a.l1 + a64_1 * (double)a.p1;
+        xl1[g] = 0.0f;
+      } else {
+        xl1[g] = xn.y;
+      }
+    }
+  }
+};
+
+template <bool VARK>
+__global__ void __launch_bounds__(NT, 3) k_spmv3p(OpParams P, InstState *st, const uint8_t *mask,
+                                               const float *p, float *q, double *part, int *cnt,
+                                               Ctrl *ctrl, int GX, int zc, int B) {
+  __shared__ ColSmemPair sm;
+  __shared__ double red[NWARP], scratch[NT], tot1[1];
+  __shared__ int flag;
+  const int b0 = 2 * blockIdx.x, b1 = min(b0 + 1, B - 1);
+  const bool run0 = inst_running(st[b0]), run1 = b0 + 1 < B && inst_running(st[b1]);
+  if (!run0 && !run1) return;
+  const long long N = P.N;
+  const ColSrcP2 src{p + b0 * N, p + b1 * N};
+  ColOutQ2 out{mask + b0 * N, mask + b1 * N, q + b0 * N, q + b1 * N, run0, run1};
+  const long long items = col_items(P.nx, P.ny, P.nz, zc);
+  for (long long t = blockIdx.y; t < items; t += GX) {
+    int x0, y0, z0, z1;
+    col_origin(P, t, zc, x0, y0, z0, z1);
+    col_S3_pair<VARK>(P, x0, y0, z0, z1, sm, src, out);
+  }
+  if (run0) sigma_epilogue(st[b0], b0, out.sg.value0(), part, cnt, ctrl, GX, red, scratch, tot1, &flag);
+  if (run1) sigma_epilogue(st[b1], b1, out.sg.value1(), part, cnt, ctrl, GX, red, scratch, tot1, &flag);
+}
+
+template <bool VARK>
+__global__ void __launch_bounds__(NT, 2) k_update_v3p(OpParams P, InstState *st, const uint8_t *mask,
+                                                   const float *r_in, float *r_out, const float *q,
+                                                   const float *p, double *x, float *xlo,
+                                                   const float *dinv, float *v, double *part,
+                                                   int *cnt, Ctrl *ctrl, int GX, int zc,
+                                                   double rtol2, int max_cg, int B) {
+  __shared__ ColSmemPair sm;
+  __shared__ double red[NWARP], scratch[NT], tot2[2];
+  __shared__ int flag;
+  const int b0 = 2 * blockIdx.x, b1 = min(b0 + 1, B - 1);
+  InstState &S0 = st[b0], &S1 = st[b1];
+  const bool run0 = inst_running(S0), run1 = b0 + 1 < B && inst_running(S1);
+  if (!run0 && !run1) return;
+  const long long N = P.N;
+  const float al0 = (float)S0.alpha, al1 = (float)S1.alpha;
+  const ColSrcZ2 src{r_in + b0 * N, r_in + b1 * N, q + b0 * N, q + b1 * N, dinv, F2{-al0, -al1}};
+  const bool fold0 = run0 && S0.phase == 2, fold1 = run1 && S1.phase == 2;
+  const long long items = col_items(P.nx, P.ny, P.nz, zc);
+  double rho[2], rr[2];
+  auto run = [&](auto out) {
+    for (long long t = blockIdx.y; t < items; t += GX) {
+      int x0, y0, z0, z1;
+      col_origin(P, t, zc, x0, y0, z0, z1);
+      col_S3_pair<VARK>(P, x0, y0, z0, z1, sm, src, out);
+    }
+    rho[0] = out.rho.value0();
+    rho[1] = out.rho.value1();
+    rr[0] = out.rr.value0();
+    rr[1] = out.rr.value1();
+  };
+#define SDF_UPD2(F_)                                                                             \
+  ColOutUpd2<F_>{mask + b0 * N, mask + b1 * N, r_in + b0 * N, r_in + b1 * N, q + b0 * N,         \
+                 q + b1 * N, p + b0 * N, p + b1 * N, r_out + b0 * N, r_out + b1 * N,            \
+                 v + b0 * N, v + b1 * N, xlo + b0 * N, xlo + b1 * N, x + b0 * N, x + b1 * N,    \
+                 F2{al0, al1}, F2{-al0, -al1}, S0.alpha, S1.alpha, run0, run1, fold0, fold1}
+  if (fold0 || fold1)
+    run(SDF_UPD2(true));
+  else
+    run(SDF_UPD2(false));
+#undef SDF_UPD2
+  for (int h = 0; h < 2; ++h) {
+    if (!(h == 0 ? run0 : run1)) continue;
+    const int b = h == 0 ? b0 : b1;
+    const double rb = block_sum(rho[h], red);
+    const double rrb = block_sum(rr[h], red);
+    if (threadIdx.x == 0) {
+      part[((long long)b * GX + blockIdx.y) * 2 + 0] = rb;
+      part[((long long)b * GX + blockIdx.y) * 2 + 1] = rrb;
+    }
+    if (!last_block(cnt + b * NCNT + CNT_UPDATE, GX, &flag)) continue;
+    reduce_fields(part + (long long)b * GX * 2, GX, 2, 2, tot2, scratch);
+    if (threadIdx.x == 0)
+      update_epilogue(st[b], tot2[0], tot2[1], cnt + b * NCNT + CNT_UPDATE, ctrl, rtol2, max_cg);
+    __syncthreads();
+  }
+}
+
 // Projection GEMM: part[gblk][b][j] = sum over block gblk's node range of
 // Phi_j(g) v_b(g), for NB instances per block (NB = 1: threads split modes x
 // node lanes; NB >= 16: threads split modes x instances).  FP32 products and
@@ -2243,7 +2407,9 @@ struct sdf_problem {
   const double *x0 = nullptr;  // start of every inner solve (set for one call)
   // autotuned column depth of the 3D mixed kernels, keyed by batch size
   std::map<int, int> tuned_zc;
-  int force_zc = 0;  // set by sdf_autotune while it times one candidate
+  std::map<int, int> tuned_pairs;  // 1: instance pairs, 0: one instance per block
+  int force_zc = 0;     // set by sdf_autotune while it times one candidate
+  int force_pairs = 0;  // the same for the pairing (1 pairs, 2 single)
   // a problem created from its operator K (sdf_problem_create_csr): the
   // assembled S = mass I + wgt K^T K and its inverse diagonal, host copies
   bool csr = false;
@@ -2277,7 +2443,7 @@ sdf_status cuda_check(sdf_problem *p, cudaError_t e, const char *what) {
 int kmax_for(int k) { return k <= 16 ? 16 : k <= 32 ? 32 : k <= 64 ? 64 : 128; }
 
 Layout make_layout(const sdf_problem *p, int B, int max_blocks = 0, int mixed = 0,
-                   int column_depth = 0) {
+                   int column_depth = 0, int column_pairs = 0) {
   Layout L{};
   const long long N = p->P.N;
   const int k = std::max(p->k, 1), KM = kmax_for(k);
@@ -2326,6 +2492,12 @@ Layout make_layout(const sdf_problem *p, int B, int max_blocks = 0, int mixed = 
     if (it != p->tuned_zc.end()) L.zc = it->second;
     if (p->force_zc > 0) L.zc = p->force_zc;
     if (column_depth > 0) L.zc = column_depth;
+    L.pairs = B >= 2 ? 1 : 0;
+    auto ip = p->tuned_pairs.find(B);
+    if (ip != p->tuned_pairs.end()) L.pairs = ip->second;
+    const int fp = p->force_pairs > 0 ? p->force_pairs : column_pairs;
+    if (fp == 1) L.pairs = B >= 2 ? 1 : 0;
+    if (fp == 2) L.pairs = 0;
   }
   L.gxc = 1;
   int gxc_max = 1;  // the partial buffers fit every candidate depth (8 planes)
@@ -2803,7 +2975,7 @@ template <int DIM, int KMAX, class PhiT>
 sdf_status solve_mixed(sdf_problem *p, const double *inst, int B, const double *psi,
                        const sdf_opts &o, char *ws, cudaStream_t s, double *y, double *lam,
                        uint8_t *active, sdf_stats *stats) {
-  const Layout L = make_layout(p, B, o.max_blocks, 1, o.column_depth);
+  const Layout L = make_layout(p, B, o.max_blocks, 1, o.column_depth, o.column_pairs);
   const OpParams &P = p->P;
   const long long N = P.N;
   double *x = (double *)(ws + L.x), *b64 = (double *)(ws + L.b64);
@@ -2927,14 +3099,24 @@ sdf_status solve_mixed(sdf_problem *p, const double *inst, int B, const double *
                                                   dinv, P.convection, dir);
     if (timed) CK(cudaEventRecord(p->ev[1], s));
     if constexpr (DIM == 3) {
-      const dim3 gC(B, L.gxc);
       // the mixed path has no convection (rejected at entry): VARK only
-      auto spmv = P.fx ? k_spmv3c<true> : k_spmv3c<false>;
-      auto upd = P.fx ? k_update_v3c<true> : k_update_v3c<false>;
-      spmv<<<gC, NT, 0, s>>>(P, inst, st, mask, dir, q, part, cnt, ctrl, L.gxc, L.zc);
-      if (timed) CK(cudaEventRecord(p->ev[2], s));
-      upd<<<gC, NT, 0, s>>>(P, inst, st, mask, rbuf[par], rbuf[par ^ 1], q, dir, x, xlo, dinv, vv,
-                            part, cnt, ctrl, L.gxc, L.zc, rtol2, o.max_cg);
+      if (L.pairs) {  // instance pairs on the packed FP32 pipe
+        const dim3 gC2((B + 1) / 2, L.gxc);
+        auto spmv = P.fx ? k_spmv3p<true> : k_spmv3p<false>;
+        auto upd = P.fx ? k_update_v3p<true> : k_update_v3p<false>;
+        spmv<<<gC2, NT, 0, s>>>(P, st, mask, dir, q, part, cnt, ctrl, L.gxc, L.zc, B);
+        if (timed) CK(cudaEventRecord(p->ev[2], s));
+        upd<<<gC2, NT, 0, s>>>(P, st, mask, rbuf[par], rbuf[par ^ 1], q, dir, x, xlo, dinv, vv,
+                               part, cnt, ctrl, L.gxc, L.zc, rtol2, o.max_cg, B);
+      } else {
+        const dim3 gC(B, L.gxc);
+        auto spmv = P.fx ? k_spmv3c<true> : k_spmv3c<false>;
+        auto upd = P.fx ? k_update_v3c<true> : k_update_v3c<false>;
+        spmv<<<gC, NT, 0, s>>>(P, inst, st, mask, dir, q, part, cnt, ctrl, L.gxc, L.zc);
+        if (timed) CK(cudaEventRecord(p->ev[2], s));
+        upd<<<gC, NT, 0, s>>>(P, inst, st, mask, rbuf[par], rbuf[par ^ 1], q, dir, x, xlo, dinv,
+                              vv, part, cnt, ctrl, L.gxc, L.zc, rtol2, o.max_cg);
+      }
     } else {
       k_spmv<DIM, float><<<gT, NT, 0, s>>>(P, inst, st, mask, dir, q, part, cnt, ctrl, L.gx);
       if (timed) CK(cudaEventRecord(p->ev[2], s));
@@ -3194,6 +3376,7 @@ void sdf_default_opts(sdf_opts *o) {
   o->tau_dep = 1e-10;
   o->floor_c = 10.0;
   o->column_depth = 0;
+  o->column_pairs = 0;
 }
 
 sdf_status sdf_problem_create(const sdf_problem_desc *desc, const double *kappa_host,
@@ -3618,6 +3801,8 @@ static sdf_status check_solve_args(sdf_problem *p, int batch, const sdf_opts *op
     const int cd = opts->column_depth;
     if (cd != 0 && cd != 8 && cd != 16 && cd != 32 && cd != 64)
       return fail(p, SDF_ERR_INVALID_ARG, "column_depth must be 0, 8, 16, 32 or 64");
+    if (opts->column_pairs < 0 || opts->column_pairs > 2)
+      return fail(p, SDF_ERR_INVALID_ARG, "column_pairs must be 0, 1 or 2");
   }
   if (opts->precision == SDF_PREC_MIXED && p->P.N > 2147483647LL)
     return fail(p, SDF_ERR_UNSUPPORTED, "the mixed path indexes one instance with 32 bits");
@@ -3680,32 +3865,110 @@ sdf_status sdf_autotune(sdf_problem *p, const double *inst_dev, int batch, const
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    for (int zc : {8, 16, 32, 64}) {
-      p->force_zc = zc;
-      for (int rep = 0; rep < 2; ++rep) {  // the first run warms up
-        CK(cudaEventRecord(e0, s));
-        st = sdf_solve_batch(p, inst_dev, batch, psi_dev, &o, ws, ws_bytes, stream, y_dev,
-                             nullptr, active_dev, nullptr);
-        CK(cudaEventRecord(e1, s));
-        CK(cudaEventSynchronize(e1));
-        if (st != SDF_OK && st != SDF_ERR_CG_MAXIT) {
-          p->force_zc = 0;
-          return st;
+    o.column_depth = 0;
+    o.column_pairs = 0;
+    int best_pairs = 0;
+    for (int pr : {1, 2}) {  // instance pairs, then one instance per block
+      if (pr == 1 && batch < 2) continue;
+      for (int zc : {8, 16, 32, 64}) {
+        p->force_zc = zc;
+        p->force_pairs = pr;
+        for (int rep = 0; rep < 2; ++rep) {  // the first run warms up
+          CK(cudaEventRecord(e0, s));
+          st = sdf_solve_batch(p, inst_dev, batch, psi_dev, &o, ws, ws_bytes, stream, y_dev,
+                               nullptr, active_dev, nullptr);
+          CK(cudaEventRecord(e1, s));
+          CK(cudaEventSynchronize(e1));
+          if (st != SDF_OK && st != SDF_ERR_CG_MAXIT) {
+            p->force_zc = 0;
+            p->force_pairs = 0;
+            return st;
+          }
         }
-      }
-      float ms = 0.0f;
-      CK(cudaEventElapsedTime(&ms, e0, e1));
-      if (best == 0 || ms < best_ms) {
-        best = zc;
-        best_ms = ms;
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (best == 0 || ms < best_ms) {
+          best = zc;
+          best_pairs = pr == 1 ? 1 : 0;
+          best_ms = ms;
+        }
       }
     }
     p->force_zc = 0;
+    p->force_pairs = 0;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     p->tuned_zc[batch] = best;
+    p->tuned_pairs[batch] = best_pairs;
   }
   if (choice) *choice = best;
+  return SDF_OK;
+}
+
+sdf_status sdf_learned_host_io_bytes(const sdf_problem *p, const sdf_warm_model *M, int batch,
+                                     size_t *bytes) {
+  if (!p || !M || !bytes || batch < 1) return SDF_ERR_INVALID_ARG;
+  size_t io = 0, pw = 0;
+  if (sdf_host_io_bytes(p, batch, &io) != SDF_OK) return SDF_ERR_INVALID_ARG;
+  if (sdf_warm_predict_workspace_size(M, batch, &pw) != SDF_OK)
+    return fail((sdf_problem *)p, SDF_ERR_INVALID_ARG,
+                std::string("warm-start model: ") + sdf_aux_last_error());
+  *bytes = al(io) + al(sizeof(double) * (size_t)p->P.N * batch) + al(pw);
+  return SDF_OK;
+}
+
+sdf_status sdf_solve_batch_learned_host(sdf_problem *p, const sdf_warm_model *M,
+                                        const double *inst_host, int batch,
+                                        const double *psi_host, const sdf_opts *opts, void *ws,
+                                        size_t ws_bytes, void *stream, double *y_host,
+                                        double *lambda_host, uint8_t *active_host,
+                                        sdf_stats *stats_host) {
+  if (!p) return SDF_ERR_INVALID_ARG;
+  if (!M || !inst_host || !psi_host || !y_host || !active_host)
+    return fail(p, SDF_ERR_INVALID_ARG, "NULL model or host pointer");
+  if (M->n != p->P.N) return fail(p, SDF_ERR_INVALID_ARG, "warm-start model has another N");
+  size_t need = 0, extra = 0, io = 0;
+  if (batch < 1) return fail(p, SDF_ERR_INVALID_ARG, "batch out of range");
+  sdf_status st = sdf_workspace_size(p, batch, opts, &need);
+  if (st != SDF_OK) return st;
+  st = sdf_learned_host_io_bytes(p, M, batch, &extra);
+  if (st != SDF_OK) return st;
+  sdf_host_io_bytes(p, batch, &io);
+  if (ws_bytes < al(need) + extra) return fail(p, SDF_ERR_WORKSPACE, "workspace too small");
+  cudaStream_t s = (cudaStream_t)stream;
+  const long long N = p->P.N;
+  char *base = (char *)ws + al(need);
+  double *inst_d = (double *)base;
+  double *psi_d = (double *)(base + al(sizeof(double) * 7 * batch));
+  double *y_d = (double *)((char *)psi_d + al(sizeof(double) * N));
+  double *lam_d = (double *)((char *)y_d + al(sizeof(double) * N * batch));
+  uint8_t *act_d = (uint8_t *)((char *)lam_d + al(sizeof(double) * N * batch));
+  double *x0_d = (double *)(base + al(io));
+  char *pws = (char *)x0_d + al(sizeof(double) * (size_t)N * batch);
+  const size_t pws_bytes = ws_bytes - (size_t)(pws - (char *)ws);
+  CK(cudaMemcpyAsync(inst_d, inst_host, sizeof(double) * 7 * batch, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(psi_d, psi_host, sizeof(double) * N, cudaMemcpyHostToDevice, s));
+  st = sdf_warm_predict(M, inst_d, batch, x0_d, pws, pws_bytes, stream);
+  if (st != SDF_OK) return fail(p, st, std::string("warm-start prediction: ") + sdf_aux_last_error());
+  st = sdf_solve_batch_x0(p, inst_d, batch, psi_d, x0_d, opts, ws, need, stream, y_d,
+                          lambda_host ? lam_d : nullptr, act_d, stats_host);
+  if (st != SDF_OK && st != SDF_ERR_CG_MAXIT && st != SDF_ERR_OUTER_MAXIT &&
+      st != SDF_ERR_BREAKDOWN && st != SDF_ERR_NONFINITE)
+    return st;
+  CK(cudaMemcpyAsync(y_host, y_d, sizeof(double) * N * batch, cudaMemcpyDeviceToHost, s));
+  if (lambda_host)
+    CK(cudaMemcpyAsync(lambda_host, lam_d, sizeof(double) * N * batch, cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(active_host, act_d, (size_t)N * batch, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  return st;
+}
+
+sdf_status sdf_autotune_choice(const sdf_problem *p, int batch, int *depth, int *pairs) {
+  if (!p || !depth || !pairs) return SDF_ERR_INVALID_ARG;
+  auto iz = p->tuned_zc.find(batch);
+  auto ip = p->tuned_pairs.find(batch);
+  *depth = iz == p->tuned_zc.end() ? 0 : iz->second;
+  *pairs = ip == p->tuned_pairs.end() ? -1 : ip->second;
   return SDF_OK;
 }
 

@@ -623,6 +623,247 @@ __device__ __forceinline__ void col_S3(const OpParams &P, const double cb64[3], 
                              out);
 }
 
+// ---------------------------------------------------------------------------
+// Instance pairs: the same column stencil for two instances of a batch at
+// once.  Both share the grid, so every slot index, bound and shared-memory
+// offset is computed once for the pair; shared memory holds (instance 0,
+// instance 1) pairs, so one 8-byte access moves both; and the arithmetic runs
+// on packed FP32 pairs (add / sub / mul / fma .f32x2 of this part), each
+// instruction doing the work of two scalar ones.
+struct F2 {
+  float x, y;
+};
+__device__ __forceinline__ F2 bc2(float a) { return F2{a, a}; }
+__device__ __forceinline__ unsigned long long pk2(F2 a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+  return r;
+}
+__device__ __forceinline__ F2 upk2(unsigned long long r) {
+  F2 o;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(o.x), "=f"(o.y) : "l"(r));
+  return o;
+}
+__device__ __forceinline__ F2 add2(F2 a, F2 b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)));
+  return upk2(r);
+}
+__device__ __forceinline__ F2 sub2(F2 a, F2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)));
+  return upk2(r);
+}
+__device__ __forceinline__ F2 mul2(F2 a, F2 b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)));
+  return upk2(r);
+}
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) {  // a * b + c, one rounding
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(pk2(a)), "l"(pk2(b)), "l"(pk2(c)));
+  return upk2(r);
+}
+
+// Compensated FP32 sums of a pair, as KahanF per half.
+struct KahanF2 {
+  F2 s{0.0f, 0.0f}, c{0.0f, 0.0f};
+  __device__ __forceinline__ void add(F2 v) {
+    const F2 y = sub2(v, c);
+    const F2 t = add2(s, y);
+    c = sub2(sub2(t, s), y);
+    s = t;
+  }
+  __device__ __forceinline__ double value0() const { return (double)s.x - (double)c.x; }
+  __device__ __forceinline__ double value1() const { return (double)s.y - (double)c.y; }
+};
+
+struct ColSmemPair {
+  float2 u[5][CNU];
+  float2 w[3][CNW];
+};
+
+// One side of the two-level stencil at a ring node: the sum over the six faces
+// of f_face (c - nb), as two independent chains (lower and upper faces) added
+// at the end, which halves the dependent-FMA latency of the scalar order.
+__device__ __forceinline__ F2 flux6(F2 c, F2 xm, F2 xp, F2 ym, F2 yp, F2 zm, F2 zp, float fw,
+                                   float fe, float fs, float fn, float fb, float ft) {
+  F2 lo = mul2(bc2(fw), sub2(c, xm));
+  F2 hi = mul2(bc2(fe), sub2(c, xp));
+  lo = fma2(bc2(fs), sub2(c, ym), lo);
+  hi = fma2(bc2(fn), sub2(c, yp), hi);
+  lo = fma2(bc2(fb), sub2(c, zm), lo);
+  hi = fma2(bc2(ft), sub2(c, zp), hi);
+  return add2(lo, hi);
+}
+
+// Src: `Raw fetch(g)` issues the loads of both instances' u at node g and
+// `F2 value(const Raw &)` forms the pair; Out: `Pre fetch(g)` and
+// `store(g, Su, u_g, pre)` as in col_S3_impl, on pairs.  No convection (the
+// mixed path refuses it), so the upwind terms are absent.  PF: the output
+// operands are loaded one plane ahead (registers for latency); without it they
+// are loaded at the output step (fewer registers, more resident blocks).
+template <bool VARK, bool PF = true, class Src, class Out>
+__device__ __forceinline__ void col_S3_pair(const OpParams &P, int x0, int y0, int z0, int z1,
+                                            ColSmemPair &sm, const Src &src, Out &out) {
+  using Raw = typename Src::Raw;
+  using Pre = typename Out::Pre;
+  const float cd[3] = {P.cdf[0], P.cdf[1], P.cdf[2]};
+  const F2 mass = bc2(P.massf), wgt = bc2(P.wgtf);
+  const int nx = P.nx, ny = P.ny, nz = P.nz;
+  const int nxy = nx * ny, base = y0 * nx + x0;
+  int ue[CSU], uoff[CSU];
+  bool uok[CSU];
+#pragma unroll
+  for (int q = 0; q < CSU; ++q) {
+    const int e = threadIdx.x + q * NT;
+    const int lx = e % CUX - 2, ly = e / CUX - 2;
+    ue[q] = e < CNU ? e : -1;
+    uok[q] = e < CNU && x0 + lx >= 0 && x0 + lx < nx && y0 + ly >= 0 && y0 + ly < ny;
+    uoff[q] = ly * nx + lx;
+  }
+  int we[CSW], wuc[CSW];
+  bool wok[CSW];
+#pragma unroll
+  for (int q = 0; q < CSW; ++q) {
+    const int e = threadIdx.x + q * NT;
+    const int lx = e % CWX - 1, ly = e / CWX - 1;
+    we[q] = e < CNW ? e : -1;
+    wok[q] = e < CNW && x0 + lx >= 0 && x0 + lx < nx && y0 + ly >= 0 && y0 + ly < ny;
+    wuc[q] = (ly + 2) * CUX + (lx + 2);
+  }
+  int owc[CSO], ouc[CSO], ooff[CSO];
+  bool ook[CSO];
+#pragma unroll
+  for (int q = 0; q < CSO; ++q) {
+    const int e = threadIdx.x + q * NT;
+    const int lx = e % CX, ly = e / CX;
+    ook[q] = x0 + lx < nx && y0 + ly < ny;
+    owc[q] = (ly + 1) * CWX + (lx + 1);
+    ouc[q] = (ly + 2) * CUX + (lx + 2);
+    ooff[q] = ly * nx + lx;
+  }
+  auto ld2 = [](const float2 *a, int i) { const float2 v = a[i]; return F2{v.x, v.y}; };
+  auto fetch = [&](int z, Raw (&raw)[CSU]) {
+    const bool zin = z >= 0 && z < nz;
+    const int zb = z * nxy + base;
+#pragma unroll
+    for (int q = 0; q < CSU; ++q) raw[q] = (zin && uok[q]) ? src.fetch(zb + uoff[q]) : Raw{};
+  };
+  auto put = [&](int z, int slot, const Raw (&raw)[CSU]) {
+    const bool zin = z >= 0 && z < nz;
+    float2 *up = sm.u[slot];
+#pragma unroll
+    for (int q = 0; q < CSU; ++q)
+      if (ue[q] >= 0) {
+        const F2 v = (zin && uok[q]) ? src.value(raw[q]) : F2{0.0f, 0.0f};
+        up[ue[q]] = make_float2(v.x, v.y);
+      }
+  };
+  auto prefetch = [&](int z, Pre (&pr)[CSO]) {
+    const int zb = z * nxy + base;
+#pragma unroll
+    for (int q = 0; q < CSO; ++q) pr[q] = ook[q] ? out.fetch(zb + ooff[q]) : Pre{};
+  };
+  auto comp_w = [&](int z, int ws, int sm1, int s0, int sp1) {
+    float2 *wp = sm.w[ws];
+    const float2 *um = sm.u[sm1], *uc = sm.u[s0], *upl = sm.u[sp1];
+    const bool zin = z >= 0 && z < nz;
+#pragma unroll
+    for (int q = 0; q < CSW; ++q) {
+      if (we[q] < 0) continue;
+      F2 val{0.0f, 0.0f};
+      if (zin && wok[q]) {
+        const int c0 = wuc[q];
+        float fw, fe, fs, fn, fb, ft;
+        if (VARK) {
+          const int gx = x0 + we[q] % CWX - 1, gy = y0 + we[q] / CWX - 1;
+          fw = fx_T<float>(P, cd, gx, gy, z); fe = fx_T<float>(P, cd, gx + 1, gy, z);
+          fs = fy_T<float>(P, cd, gx, gy, z); fn = fy_T<float>(P, cd, gx, gy + 1, z);
+          fb = fz_T<float>(P, cd, gx, gy, z); ft = fz_T<float>(P, cd, gx, gy, z + 1);
+        } else {
+          fw = fe = cd[0]; fs = fn = cd[1]; fb = ft = cd[2];
+        }
+        val = flux6(ld2(uc, c0), ld2(uc, c0 - 1), ld2(uc, c0 + 1), ld2(uc, c0 - CUX),
+                    ld2(uc, c0 + CUX), ld2(um, c0), ld2(upl, c0), fw, fe, fs, fn, fb, ft);
+      }
+      wp[we[q]] = make_float2(val.x, val.y);
+    }
+  };
+  auto outputs = [&](int z, int wsm, int ws0, int wsp, int us0, const Pre (&pr)[CSO]) {
+    const float2 *wm = sm.w[wsm], *wc = sm.w[ws0], *wpl = sm.w[wsp], *uc = sm.u[us0];
+    const int zb = z * nxy + base;
+#pragma unroll
+    for (int q = 0; q < CSO; ++q) {
+      if (!ook[q]) continue;
+      const int o = owc[q];
+      float fw, fe, fs, fn, fb, ft;
+      if (VARK) {
+        const int e = threadIdx.x + q * NT;
+        const int gx = x0 + e % CX, gy = y0 + e / CX;
+        fw = fx_T<float>(P, cd, gx, gy, z); fe = fx_T<float>(P, cd, gx + 1, gy, z);
+        fs = fy_T<float>(P, cd, gx, gy, z); fn = fy_T<float>(P, cd, gx, gy + 1, z);
+        fb = fz_T<float>(P, cd, gx, gy, z); ft = fz_T<float>(P, cd, gx, gy, z + 1);
+      } else {
+        fw = fe = cd[0]; fs = fn = cd[1]; fb = ft = cd[2];
+      }
+      const F2 acc = flux6(ld2(wc, o), ld2(wc, o - 1), ld2(wc, o + 1), ld2(wc, o - CWX),
+                           ld2(wc, o + CWX), ld2(wm, o), ld2(wpl, o), fw, fe, fs, fn, fb, ft);
+      const F2 u0 = ld2(uc, ouc[q]);
+      if constexpr (PF) {
+        out.store(zb + ooff[q], fma2(wgt, acc, mul2(mass, u0)), u0, pr[q]);
+      } else {
+        const Pre now = out.fetch(zb + ooff[q]);
+        out.store(zb + ooff[q], fma2(wgt, acc, mul2(mass, u0)), u0, now);
+      }
+    }
+  };
+  int s0 = 0, s1 = 1, s2 = 2, s3 = 3, s4 = 4, t0 = 0, t1 = 1, t2 = 2;
+  {
+    Raw a[CSU], b[CSU], c[CSU], d[CSU];
+    fetch(z0 - 2, a);
+    fetch(z0 - 1, b);
+    fetch(z0, c);
+    fetch(z0 + 1, d);
+    put(z0 - 2, 0, a);
+    put(z0 - 1, 1, b);
+    put(z0, 2, c);
+    put(z0 + 1, 3, d);
+  }
+  Raw nxt[CSU];
+  Pre pc[PF ? CSO : 1], pn[PF ? CSO : 1];
+  fetch(z0 + 2, nxt);
+  if constexpr (PF) prefetch(z0, pc);
+  __syncthreads();
+  comp_w(z0 - 1, 0, 0, 1, 2);
+  comp_w(z0, 1, 1, 2, 3);
+  for (int z = z0; z < z1; ++z) {
+    put(z + 2, s4, nxt);
+    if (z + 1 < z1) {
+      fetch(z + 3, nxt);
+      if constexpr (PF) prefetch(z + 1, pn);
+    }
+    __syncthreads();
+    comp_w(z + 1, t2, s2, s3, s4);
+    __syncthreads();
+    if constexpr (PF) {
+      outputs(z, t0, t1, t2, s2, pc);
+    } else {
+      Pre none[CSO];
+      outputs(z, t0, t1, t2, s2, none);
+    }
+    const int s = s0;
+    s0 = s1; s1 = s2; s2 = s3; s3 = s4; s4 = s;
+    const int t = t0;
+    t0 = t1; t1 = t2; t2 = t;
+    if constexpr (PF) {
+#pragma unroll
+      for (int q = 0; q < CSO; ++q) pc[q] = pn[q];
+    }
+  }
+  __syncthreads();
+}
+
 // Column work items of a 3D grid: xy tiles x z-chunks of zc planes.
 __host__ __device__ inline long long col_items(int nx, int ny, int nz, int zc) {
   return (long long)((nx + CX - 1) / CX) * ((ny + CY - 1) / CY) * ((nz + zc - 1) / zc);

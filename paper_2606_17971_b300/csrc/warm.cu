@@ -457,6 +457,59 @@ __global__ void k_pod_flip(const int *sign, long long N, int r, __nv_bfloat16 *p
   }
 }
 
+// POD coefficients of snapshots onto a basis: part[blk][i][j] = sum over the
+// block's node range of psi_j(g) (y_i - ybar)(g), FP64, for snapshot groups of
+// 16 (grid y); 16 x 16 threads: thread (a, c) holds modes a, a + 16, ... of
+// snapshot c of the group.
+constexpr int CT = 32;
+__global__ void __launch_bounds__(256) k_pod_project(const double *Y, const double *ybar, int m,
+                                                     long long N, const double *psi_cm, int r,
+                                                     int nchunk, double *part) {
+  __shared__ double sp[CT][SDF_POD_MAX_R + 1], sy[CT][PT + 1];
+  const int a = threadIdx.x / PT, c = threadIdx.x % PT;
+  const int i0 = blockIdx.y * PT;
+  const long long per = (N + nchunk - 1) / nchunk;
+  const long long g0 = blockIdx.x * per, g1 = min(N, g0 + per);
+  constexpr int MT = SDF_POD_MAX_R / PT;
+  double acc[MT];
+#pragma unroll
+  for (int q = 0; q < MT; ++q) acc[q] = 0.0;
+  for (long long gb = g0; gb < g1; gb += CT) {
+    for (int e = threadIdx.x; e < CT * SDF_POD_MAX_R; e += 256) {
+      const int k = e % CT, j = e / CT;
+      const long long g = gb + k;
+      sp[k][j] = (g < g1 && j < r) ? psi_cm[(long long)j * N + g] : 0.0;
+    }
+    for (int e = threadIdx.x; e < CT * PT; e += 256) {
+      const int k = e % CT, q = e / CT;
+      const long long g = gb + k;
+      sy[k][q] = (g < g1 && i0 + q < m) ? Y[(long long)(i0 + q) * N + g] - ybar[g] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < CT; ++k) {
+      const double d = sy[k][c];
+#pragma unroll
+      for (int q = 0; q < MT; ++q) acc[q] = fma(sp[k][a + PT * q], d, acc[q]);
+    }
+    __syncthreads();
+  }
+  const int i = i0 + c;
+  if (i < m)
+#pragma unroll
+    for (int q = 0; q < MT; ++q)
+      if (a + PT * q < r) part[((long long)blockIdx.x * m + i) * r + a + PT * q] = acc[q];
+}
+
+// coef[i][j] = sum over blocks (in block order) of the projection partials
+__global__ void k_pod_project_reduce(const double *part, int nchunk, int m, int r, double *coef) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * r; e += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < nchunk; ++c) s += part[(long long)c * m * r + e];
+    coef[e] = s;
+  }
+}
+
 // standardised MLP outputs -> BF16 coefficients (instances x r, padded to 16
 // rows) for the expansion product
 __global__ void k_coef_bf16(const float *cstd, int B, int r, const float *cmean,
@@ -646,15 +699,23 @@ __global__ void k_targets(const double *coef, int m, int r, const float *cmean,
   }
 }
 
+// The fit's POD basis comes from the first kFitPodSnapshots snapshots (the
+// method of snapshots diagonalises their Gram matrix on the host); the MLP is
+// fit to the coefficients of every snapshot on that basis.
+constexpr int kFitPodSnapshots = 384;
+constexpr int kProjChunks = 148;
+
 struct FitLayout {
-  size_t pod_ws, psi_cm, coef, x, t, grad, am, av, loss, box, mlp_ws, total;
+  size_t pod_ws, psi_cm, coef, x, t, grad, am, av, loss, box, mlp_ws, ppart, total;
   size_t pod_bytes, mlp_bytes;
+  int m_pod;
 };
 
 bool fit_layout(const sdf_warm_model *M, int m, FitLayout &F) {
-  if (!M || m < 2) return false;
+  if (!M || m < 2 || m > SDF_FIT_MAX_SNAPSHOTS) return false;
   size_t pb = 0, mb = 0;
-  if (sdf_pod_workspace_size(M->n, m, &pb) != SDF_OK) return false;
+  F.m_pod = std::min(m, kFitPodSnapshots);
+  if (sdf_pod_workspace_size(M->n, F.m_pod, &pb) != SDF_OK) return false;
   if (sdf_mlp_workspace_size(&M->mlp, m, &mb) != SDF_OK) return false;
   const long long np = param_count(&M->mlp);
   size_t o = 0;
@@ -674,6 +735,7 @@ bool fit_layout(const sdf_warm_model *M, int m, FitLayout &F) {
   F.loss = take(sizeof(double) * 4096);
   F.box = take(sizeof(double) * 16);
   F.mlp_ws = take(mb);
+  F.ppart = take(sizeof(double) * (size_t)kProjChunks * m * M->r);
   F.total = o;
   F.pod_bytes = pb;
   F.mlp_bytes = mb;
@@ -900,11 +962,19 @@ sdf_status sdf_warm_fit(sdf_warm_model *M, const double *Y_dev, const double *in
   cudaStream_t s = (cudaStream_t)stream;
   char *w = (char *)ws;
   const int r = M->r, nin = M->mlp.width[0];
-  // 1. POD of the solved states
+  // 1. POD of the first m_pod solved states, then the coefficients of all m
+  //    states on that basis (FP64 projections)
   std::vector<double> sing(r), coef((size_t)m * r);
-  sdf_status st = sdf_pod(Y_dev, m, M->n, r, M->ybar, w + F.psi_cm, M->psi, sing.data(),
-                          coef.data(), w + F.pod_ws, F.pod_bytes, stream);
+  sdf_status st = sdf_pod(Y_dev, F.m_pod, M->n, r, M->ybar, w + F.psi_cm, M->psi, sing.data(),
+                          nullptr, w + F.pod_ws, F.pod_bytes, stream);
   if (st != SDF_OK) return st;
+  k_pod_project<<<dim3(kProjChunks, (m + PT - 1) / PT), 256, 0, s>>>(
+      Y_dev, M->ybar, m, M->n, M->psi, r, kProjChunks, (double *)(w + F.ppart));
+  k_pod_project_reduce<<<64, 256, 0, s>>>((const double *)(w + F.ppart), kProjChunks, m, r,
+                                          (double *)(w + F.coef));
+  WCK(cudaGetLastError());
+  WCK(cudaMemcpyAsync(coef.data(), w + F.coef, sizeof(double) * m * r, cudaMemcpyDeviceToHost, s));
+  WCK(cudaStreamSynchronize(s));
   // 2. targets: coefficients centred per coefficient and divided by one common
   //    scale (the largest coefficient standard deviation), so that the loss
   //    weighs each coefficient by its share of the state
@@ -924,7 +994,6 @@ sdf_status sdf_warm_fit(sdf_warm_model *M, const double *Y_dev, const double *in
   for (int j = 0; j < r; ++j) cs[j] = (float)(smax > 0.0 ? smax : 1.0);
   WCK(cudaMemcpyAsync(M->cmean, cm.data(), sizeof(float) * r, cudaMemcpyHostToDevice, s));
   WCK(cudaMemcpyAsync(M->cscale, cs.data(), sizeof(float) * r, cudaMemcpyHostToDevice, s));
-  WCK(cudaMemcpyAsync(w + F.coef, coef.data(), sizeof(double) * m * r, cudaMemcpyHostToDevice, s));
   double box[16];
   for (int i = 0; i < nin; ++i) {
     box[i] = M->in_lo[i];

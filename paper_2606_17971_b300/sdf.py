@@ -48,7 +48,7 @@ class Opts(ctypes.Structure):
                 ("max_launches", ctypes.c_int64), ("ritz_r", ctypes.c_int32),
                 ("safe_r", ctypes.c_int32), ("tau_safe", ctypes.c_double),
                 ("tau_dep", ctypes.c_double), ("floor_c", ctypes.c_double),
-                ("column_depth", ctypes.c_int32)]
+                ("column_depth", ctypes.c_int32), ("column_pairs", ctypes.c_int32)]
 
 
 SDF_NPROF = 9
@@ -128,6 +128,11 @@ _sigs = {
     "sdf_warm_fit": (_i32, [_vp, _vp, _vp, _i32, _i32, ctypes.c_float, _vp, _vp, _sz, _vp]),
     "sdf_warm_predict_workspace_size": (_i32, [_vp, _i32, ctypes.POINTER(_sz)]),
     "sdf_warm_predict": (_i32, [_vp, _vp, _i32, _vp, _vp, _sz, _vp]),
+    "sdf_learned_host_io_bytes": (_i32, [_vp, _vp, _i32, ctypes.POINTER(_sz)]),
+    "sdf_solve_batch_learned_host": (_i32, [_vp, _vp, _vp, _i32, _vp, ctypes.POINTER(Opts), _vp,
+                                            _sz, _vp, _vp, _vp, _vp, _vp]),
+    "sdf_autotune_choice": (_i32, [_vp, _i32, ctypes.POINTER(ctypes.c_int),
+                                   ctypes.POINTER(ctypes.c_int)]),
     "sdf_autotune": (_i32, [_vp, _vp, _i32, _vp, ctypes.POINTER(Opts), _vp, _sz, _vp, _vp, _vp,
                             ctypes.POINTER(_i32)]),
     "sdf_default_eig_opts": (None, [_vp]),
@@ -496,6 +501,13 @@ class Problem:
                                       ctypes.byref(ch)))
         return ch.value
 
+    def autotune_choice(self, batch):
+        """sdf_autotune_choice: (column depth, pairing) kept for a batch size
+        (depth 0 / pairing -1: not tuned)."""
+        d, pr = ctypes.c_int(0), ctypes.c_int(0)
+        self._check(_lib.sdf_autotune_choice(self._h, batch, ctypes.byref(d), ctypes.byref(pr)))
+        return d.value, pr.value
+
     def solve_x0(self, inst: torch.Tensor, psi: torch.Tensor, x0: torch.Tensor, opts=None,
                  want_lambda=False, out=None):
         """sdf_solve_batch_x0: every inner solve starts from x0 (B, N) float64
@@ -557,6 +569,34 @@ class Problem:
                                        ctypes.byref(opts), _ptr(ws), ws.numel(), _stream(),
                                        y.ctypes.data, None if lam is None else lam.ctypes.data,
                                        active.ctypes.data, stats)
+        if st not in (0, 5, 6, 7, 8):
+            self._check(st)
+        return dict(y=y, lam=lam, active=active, status=st, stats=[stats_dict(s) for s in stats])
+
+    def solve_learned_host(self, model, inst: np.ndarray, psi: np.ndarray, opts=None, y=None,
+                           lam=None, active=None):
+        """The learned pipeline from host buffers (sdf_solve_batch_learned_host):
+        numpy in, x0 predicted by `model` (a WarmModel) and the solve on the
+        device, numpy out."""
+        opts = opts or default_opts()
+        inst = np.ascontiguousarray(inst, dtype=np.float64)
+        psi = np.ascontiguousarray(psi, dtype=np.float64)
+        B = inst.shape[0]
+        nb, xb = _sz(), _sz()
+        self._check(_lib.sdf_workspace_size(self._h, B, ctypes.byref(opts), ctypes.byref(nb)))
+        self._check(_lib.sdf_learned_host_io_bytes(self._h, ctypes.byref(model.desc), B,
+                                                   ctypes.byref(xb)))
+        need = ((int(nb.value) + 255) // 256) * 256 + int(xb.value)
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.empty(need, dtype=torch.uint8, device=self.device)
+        ws = self._ws
+        y = np.empty((B, self.N)) if y is None else y
+        active = np.empty((B, self.N), np.uint8) if active is None else active
+        stats = (Stats * B)()
+        st = _lib.sdf_solve_batch_learned_host(
+            self._h, ctypes.byref(model.desc), inst.ctypes.data, B, psi.ctypes.data,
+            ctypes.byref(opts), _ptr(ws), ws.numel(), _stream(), y.ctypes.data,
+            None if lam is None else lam.ctypes.data, active.ctypes.data, stats)
         if st not in (0, 5, 6, 7, 8):
             self._check(st)
         return dict(y=y, lam=lam, active=active, status=st, stats=[stats_dict(s) for s in stats])

@@ -193,3 +193,50 @@ def test_fitted_model_gives_same_active_sets_with_fewer_iterations(sdf):
     # only with log(1 / error)
     assert iw < ic, (iw, ic, rel.item())
     assert rel.item() < 5e-2
+
+
+def test_fit_on_more_states_than_the_pod_takes(sdf):
+    # 600 training states: the basis is the POD of the first 384 (compared
+    # with the oracle's POD of those), the MLP is fit to the coefficients of
+    # all 600 on it, and the fitted model predicts held-out first solves
+    W, w, G, psi = _diff2d(sdf)
+    train = W.draw_instances(w, count=600, seed=w.seed + 300)
+    it = torch.as_tensor(W.instances_array(train), device="cuda")
+    Y = G.solve(it, psi, sdf.default_opts(max_outer=1), want_lambda=False)["y"]
+    widths = (3, 256, 256, 256, 32)
+    lo, hi = W.input_box(w)
+    model = sdf.WarmModel(widths, w.N, lo, hi, torch.from_numpy(W.mlp_init(widths)).cuda())
+    loss = model.fit(Y, it, epochs=1000, lr0=1e-3)
+    assert np.isfinite(loss).all() and loss[-1] < 1e-3 * loss[0]
+    yb, Psi, _, _ = WO.pod(Y[:384].cpu().numpy(), 32)
+    np.testing.assert_allclose(model.ybar.cpu().numpy(), yb, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(model.psi.cpu().numpy().T, Psi, rtol=0, atol=1e-8)
+    held = torch.as_tensor(W.instances_array(W.draw_instances(w, count=16, seed=w.seed + 400)),
+                           device="cuda")
+    first = G.solve(held, psi, sdf.default_opts(max_outer=1), want_lambda=False)["y"]
+    rel = ((model.predict(held) - first).norm() / first.norm()).item()
+    assert rel < 5e-2, rel
+
+
+def test_learned_host_entry_matches_the_device_pipeline(sdf):
+    # sdf_solve_batch_learned_host (host mu in, x0 predicted and the solve on
+    # the device, host y / lambda / A out) against predict + solve_x0 on
+    # device buffers: the same kernels in the same order, so bit for bit
+    W, w, G, psi = _diff2d(sdf)
+    train = W.draw_instances(w, count=128, seed=w.seed + 500)
+    it = torch.as_tensor(W.instances_array(train), device="cuda")
+    Y = G.solve(it, psi, sdf.default_opts(max_outer=1), want_lambda=False)["y"]
+    widths = (3, 256, 256, 256, 32)
+    lo, hi = W.input_box(w)
+    model = sdf.WarmModel(widths, w.N, lo, hi, torch.from_numpy(W.mlp_init(widths)).cuda())
+    model.fit(Y, it, epochs=300, lr0=1e-3)
+    held = W.instances_array(W.draw_instances(w, count=11, seed=w.seed + 600))
+    hd = torch.as_tensor(held, device="cuda")
+    dev = G.solve_x0(hd, psi, model.predict(hd))
+    lam = np.empty((11, w.N))
+    host = G.solve_learned_host(model, held, psi.cpu().numpy(), lam=lam)
+    assert host["status"] == 0
+    assert np.array_equal(host["y"], dev["y"].cpu().numpy())
+    assert np.array_equal(host["active"], dev["active"].cpu().numpy())
+    assert np.array_equal(lam, dev["lam"].cpu().numpy())
+    assert [s["cg_iters"] for s in host["stats"]] == [s["cg_iters"] for s in dev["stats"]]
