@@ -232,7 +232,7 @@ def test_learned_host_entry_matches_the_device_pipeline(sdf):
     model.fit(Y, it, epochs=300, lr0=1e-3)
     held = W.instances_array(W.draw_instances(w, count=11, seed=w.seed + 600))
     hd = torch.as_tensor(held, device="cuda")
-    dev = G.solve_x0(hd, psi, model.predict(hd))
+    dev = G.solve_x0(hd, psi, model.predict(hd), want_lambda=True)
     lam = np.empty((11, w.N))
     host = G.solve_learned_host(model, held, psi.cpu().numpy(), lam=lam)
     assert host["status"] == 0
