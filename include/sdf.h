@@ -66,8 +66,9 @@ typedef enum { SDF_F64 = 0, SDF_F32 = 1, SDF_BF16 = 2 } sdf_dtype;
  *                   convergence is declared only on that FP64 residual:
  *                   ||b - S_II x|| <= max(rtol ||b||, floor_c u || |S_II||x| ||)
  *                   (the second term, the attainable accuracy of an FP64
- *                   residual, is evaluated when the recurrence has met rtol
- *                   or the true residual has stopped falling; see sdf_stats).
+ *                   residual, is evaluated once per solve, when the
+ *                   recurrence has met rtol or the true residual has stopped
+ *                   falling; see sdf_stats).
  *                   Not available with per-instance convection
  *                   (SDF_ERR_UNSUPPORTED). */
 typedef enum { SDF_PREC_F64 = 0, SDF_PREC_MIXED = 1 } sdf_precision;

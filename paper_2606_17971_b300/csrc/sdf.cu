@@ -65,7 +65,7 @@ struct InstState {
   int32_t changes;     // active-set changes of the last update
   int32_t empty_I;     // every node active: nothing to solve
   int32_t await;       // mixed path: recurrence residual met rtol, waiting for the FP64 check
-  int32_t stall;       // mixed path: the true residual fell less than 2x at the last replacement
+  int32_t stall;       // mixed path: the true residual stalled at the last replacement
   double t[SDF_MAX_K]; // reduced projection Phi_I^T v
   sdf_stats stats;
 };
@@ -896,9 +896,10 @@ __device__ __forceinline__ double signed_abs(int gx, int gy, int gz, double v) {
 // residual, App. B.2's recurrence stop read for a method whose recurrence runs
 // in FP32), or arms the coarse correction pass (phase 2: w = Phi E_raw^-1
 // Phi_I^T r, alpha = 1) whose projection the GEMM computes from the new r.
-// The floor is evaluated (a second stencil pass on s o |x|) only when the
-// recurrence has met rtol or the true residual fell less than 2x at the last
-// replacement; otherwise the last value stands.  r is written in place: this
+// The floor is evaluated (a second stencil pass on s o |x|) once per solve:
+// at the first replacement where the recurrence has met rtol or the true
+// residual stalled (it fell less than 2x while the recurrence ran more than
+// 10x below it); near convergence x, and with it the floor, barely moves.  r is written in place: this
 // kernel reads x, not r.
 template <int DIM>
 __global__ void __launch_bounds__(NT) k_resid(OpParams P, const double *inst, InstState *st,
@@ -912,7 +913,8 @@ __global__ void __launch_bounds__(NT) k_resid(OpParams P, const double *inst, In
   const int b = blockIdx.x, gblk = blockIdx.y;
   InstState &S = st[b];
   if (S.outer_done || S.cg_done) return;
-  const bool need_floor = floor_cu > 0.0 && (S.await || S.stall);  // uniform in the block
+  // the floor is evaluated once per solve, when first needed (uniform in the block)
+  const bool need_floor = floor_cu > 0.0 && S.floor2 == 0.0 && (S.await || S.stall);
   const long long N = P.N;
   double cb[3];
   inst_cb(P, inst + 7 * b, cb);
@@ -959,6 +961,7 @@ __global__ void __launch_bounds__(NT) k_resid(OpParams P, const double *inst, In
   reduce_fields(part + (long long)b * GX * 2, GX, 2, 2, tot2, scratch);
   if (threadIdx.x == 0) {
     const double rn2 = tot2[0];
+    const double rec2 = S.rnorm2;  // the recurrence residual this replaces
     cnt[b * NCNT + CNT_UPDATE] = 0;
     S.rnorm2 = rn2;
     if (need_floor) S.floor2 = floor_cu * floor_cu * tot2[1];
@@ -970,7 +973,10 @@ __global__ void __launch_bounds__(NT) k_resid(OpParams P, const double *inst, In
       S.cg_done = 1;
       S.stats.floor_stop[S.outer] = rn2 > rtb ? 1 : 0;
     } else {
-      S.stall = rn2 > 0.25 * S.rt2_prev ? 1 : 0;
+      // stalled: the true residual fell less than 2x since the last
+      // replacement while the recurrence ran more than 10x below it (the
+      // drift of a residual at its attainable accuracy)
+      S.stall = (rn2 > 0.25 * S.rt2_prev && rec2 < 0.01 * rn2) ? 1 : 0;
       S.await = 0;
       S.phase = 2;
       S.gamma = 0.0;
@@ -1520,7 +1526,7 @@ __global__ void __launch_bounds__(NT, 3) k_spmv3c(OpParams P, const double *inst
   __shared__ int flag;
   const int b = blockIdx.x, gblk = blockIdx.y;
   InstState &S = st[b];
-  if (S.outer_done || S.cg_done || (S.await && S.phase == 0)) return;
+  if (!inst_running(S)) return;
   const long long N = P.N;
   double cb[3];
   inst_cb(P, inst + 7 * b, cb);
