@@ -469,7 +469,7 @@ def test_schur_from_operator_is_the_grid_assembly():
 # --------------------------------------------------------------------------
 # true residual and attainable-accuracy floor of an inner solve (App. B.2)
 
-def _restricted_dense(P, active):
+def _dense_S_and_inactive(P, active):
     S = P.dense_S()
     I = np.flatnonzero(~active)
     return S, I
@@ -491,7 +491,7 @@ def test_floor_uses_the_entrywise_absolute_value_of_S_II():
     assert r["status"] == 0 and r["outer_iters"] >= 2
     active = r["active"]
     # the last inner solve ran on the final active set (no change at exit)
-    S, I = _restricted_dense(P, active)
+    S, I = _dense_S_and_inactive(P, active)
     jj, ii = np.divmod(np.arange(P.N), n)
     d = np.where((ii + jj) % 2 == 0, 1.0, -1.0)
     SII = S[np.ix_(I, I)]
