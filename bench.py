@@ -608,6 +608,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1,
                     help="steps of the end-to-end (host-buffer) measurement")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-path comparison")
+    ap.add_argument("--no-deflate", action="store_true",
+                    help="plain Jacobi-PCG (no deflation) on the same workload and path")
     ap.add_argument("--plain-instances", type=int, default=8,
                     help="instances of the plain per-instance FP64 comparison")
     ap.add_argument("--no-learned", action="store_true",
@@ -710,7 +712,7 @@ def workload_run(args, w, mode, sdf, dev, world, rank):
                for i in range(steps + warm)]
     psi = torch.full((w.N,), w.psi, dtype=torch.float64, device=dev)
     opts = sdf.default_opts(check_every=128, precision=sdf.PREC_MIXED if mixed else sdf.PREC_F64,
-                            max_cg=1000000)
+                            max_cg=1000000, deflate=0 if args.no_deflate else 1)
     if args.max_cg:
         opts.max_cg = args.max_cg
     out = {"y": torch.empty((B, w.N), dtype=torch.float64, device=dev), "lam": None,
@@ -735,7 +737,8 @@ def workload_run(args, w, mode, sdf, dev, world, rank):
         "path": ("mixed FP32 / %s modes, FP64 x, reductions, coarse operator and residual "
                  "replacement" % mode.get("phi") if mixed else
                  ("FP64 A-DEF2, shared-Phi batch kernels" if fb else
-                  "FP64 A-DEF2, one instance per launch")) + " (primal active-set loop)",
+                  "FP64 A-DEF2, one instance per launch")) + " (primal active-set loop)"
+                + (", deflation off (plain Jacobi-PCG)" if args.no_deflate else ""),
         "modes": modes_info, "l2": "inputs larger than L2 (%.2f GB of vectors per batch)"
                                   % (8 * units * (4 if mixed else 8) / 1e9),
         "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}
@@ -891,29 +894,37 @@ def headline_run(args, w, mode, sdf, dev, world, rank):
     opts.profile = 0
     stats = [s for r in res for s in r["stats"]]
 
-    # ---- the remaining cold solves of held-out batches (untimed) ----
+    # ---- the other held-out batches, cold, on their first 32 instances
+    # (untimed; iteration counts per instance against the learned step's) ----
+    nsl = min(32, B)
+    cold_slices = {}
     for b in range(nb):
         if b not in cold:
-            cold[b] = timed_solve(lambda: G.solve(batches[b], psi, opts, out=out,
-                                                  want_lambda=False))
-    # learned ms and iterations per held-out batch (one timed step each)
+            cold_slices[b] = timed_solve(lambda: G.solve(batches[b][:nsl].contiguous(), psi, opts,
+                                                         want_lambda=False))
+    # learned against cold iterations and ms per held-out batch
     per_batch = []
     for b in range(nb):
         i = next((i for i in range(steps) if i % nb == b), None)
-        lrn_it = mean_stat(res[i]["stats"], lambda s: sum(s["cg_iters"])) if i is not None else None
-        lrn_ms = None
-        if i is None:
+        if i is not None:
+            lst = res[i]["stats"]
+            lrn_ms = ms / steps
+        else:
             lrn_ms, rl = timed_solve(lambda: learned_step(batches[b]))
-            lrn_it = mean_stat(rl["stats"], lambda s: sum(s["cg_iters"]))
-        cms, rc = cold[b]
-        lst = res[i]["stats"] if i is not None else rl["stats"]
+            lst = rl["stats"]
+        full = b in cold
+        cms, rc = cold[b] if full else cold_slices[b]
+        cst = rc["stats"]
+        lst = lst[:len(cst)]
         # the learned start changes the CG iterations only: the outer
         # iterations and the active-set sizes of every solve equal the cold ones
         same = all(a["outer_iters"] == c["outer_iters"] and a["n_active"] == c["n_active"]
-                   for a, c in zip(lst, rc["stats"]))
-        per_batch.append({"batch": b, "cold_ms": cms,
-                          "cold_cg_iters": mean_stat(rc["stats"], lambda s: sum(s["cg_iters"])),
-                          "learned_cg_iters": lrn_it, "learned_ms": lrn_ms,
+                   for a, c in zip(lst, cst))
+        per_batch.append({"batch": b, "instances_compared": len(cst),
+                          "cold_ms": cms if full else None,
+                          "learned_ms": lrn_ms if full else None,
+                          "cold_cg_iters": mean_stat(cst, lambda s: sum(s["cg_iters"])),
+                          "learned_cg_iters": mean_stat(lst, lambda s: sum(s["cg_iters"])),
                           "outer_and_active_sizes_equal": same})
     # relative error of the prediction against the first (unconstrained)
     # solve, on 16 held-out instances
@@ -939,6 +950,7 @@ def headline_run(args, w, mode, sdf, dev, world, rank):
         "autotuned": {"column_depth": tuned, "instance_pairs": G.autotune_choice(B)[1]}}
     cold_ms = float(np.mean([c[0] for c in cold.values()]))
     cold_it = float(np.mean([p["cold_cg_iters"] for p in per_batch]))
+    lrn_cmp = float(np.mean([p["learned_cg_iters"] for p in per_batch]))
     lrn_it = mean_stat(stats, lambda s: sum(s["cg_iters"]))
     line.update({
         "cg_iters_per_instance": lrn_it,
@@ -954,8 +966,11 @@ def headline_run(args, w, mode, sdf, dev, world, rank):
         "learned": {"training": train_info,
                     "cold": {"ms_per_batch": cold_ms, "cg_iters_per_instance": cold_it,
                              "instances_per_s": B / (cold_ms * 1e-3)},
-                    "learned_vs_cold": {"cg_iters": lrn_it / cold_it,
-                                        "ms": (ms / steps) / cold_ms},
+                    "learned_vs_cold": {"cg_iters": lrn_cmp / cold_it,
+                                        "ms": (ms / steps) / cold_ms,
+                                        "note": "iterations: the same instances, every held-out "
+                                                "batch; ms: the timed steps against the full "
+                                                "cold batches solved during warm-up"},
                     "prediction_rel_error_first_solve": pred_err,
                     "per_batch": per_batch}})
     if plain:
