@@ -616,7 +616,7 @@ def main():
                     help="the headline workload without the learned warm start")
     ap.add_argument("--train", type=int, default=0,
                     help="training instances of the learned warm start (default: the workload's)")
-    ap.add_argument("--train-rtol", type=float, default=1e-4,
+    ap.add_argument("--train-rtol", type=float, default=1e-3,
                     help="CG tolerance of the training solves")
     ap.add_argument("--held-out", type=int, default=0,
                     help="held-out instances cycled by the timed steps (default: the workload's)")
