@@ -162,7 +162,15 @@ typedef struct {
  *   column_pairs mixed 3D path: 1 runs the stencil kernels on instance pairs
  *                (two instances per block on the packed FP32 pipe), 2 one
  *                instance per block, 0 what sdf_autotune chose for this
- *                batch size (pairs for 2 or more instances when untuned) [0] */
+ *                batch size (pairs for 2 or more instances when untuned) [0]
+ *   graph        1: the launches between two host polls (check_every CG
+ *                iterations on the FP64 path; replace_every iterations, the
+ *                residual replacement and the correction pass on the mixed
+ *                path) are captured once per call into a CUDA graph on a
+ *                private stream and replayed on `stream`; 0: launched one by
+ *                one.  Passes timed with profile = 1 are launched one by one.
+ *                The call must not be made while `stream` is being captured
+ *                (it synchronises `stream` between chunks)             [1] */
 typedef struct {
   double rtol;
   double tau;
@@ -183,6 +191,7 @@ typedef struct {
   double floor_c;
   int32_t column_depth;
   int32_t column_pairs;
+  int32_t graph;
 } sdf_opts;
 
 /* Per-instance statistics (host struct filled at the end of a solve).

@@ -2468,6 +2468,7 @@ struct sdf_problem {
   // autotuned column depth of the 3D mixed kernels, keyed by batch size
   std::map<int, int> tuned_zc;
   std::map<int, int> tuned_pairs;  // 1: instance pairs, 0: one instance per block
+  cudaStream_t cap_stream = nullptr;  // private stream the CG chunks are captured on
   int force_zc = 0;     // set by sdf_autotune while it times one candidate
   int force_pairs = 0;  // the same for the pairing (1 pairs, 2 single)
   // a problem created from its operator K (sdf_problem_create_csr): the
@@ -2803,6 +2804,57 @@ sdf_status ritz_select(sdf_problem *p, int B, int k, int r, InstState *st_d, con
   return SDF_OK;
 }
 
+// A chunk of CG launches (the iterations between two host polls, and on the
+// mixed path the residual replacement and correction pass after them),
+// captured once per solve call into a CUDA graph on a private stream and
+// replayed on the caller's stream: one slot per starting parity of the
+// ping-pong residual buffers.  Capturing launches nothing, so the host-side
+// effects of the captured body (parity flips, launch counts) are undone and
+// then applied per replay.
+struct ChunkGraphs {
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  int flip[2] = {0, 0};
+  long long launches[2] = {0, 0};
+  ~ChunkGraphs() {
+    for (cudaGraphExec_t &e : exec)
+      if (e) cudaGraphExecDestroy(e);
+  }
+};
+
+// body(stream) enqueues one chunk on `stream`, advancing *par and the
+// problem's launch count.  use_graph = false launches it directly on s.
+template <class Body>
+sdf_status run_chunk(sdf_problem *p, ChunkGraphs &gr, bool use_graph, cudaStream_t s, int *par,
+                     Body body) {
+  if (!use_graph) return body(s);
+  const int slot = *par & 1;
+  if (!gr.exec[slot]) {
+    if (!p->cap_stream) CK(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+    const int par0 = *par;
+    const long long l0 = p->prof.launches;
+    CK(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const sdf_status e = body(p->cap_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(p->cap_stream, &g);
+    if (e != SDF_OK) {
+      if (g) cudaGraphDestroy(g);
+      return e;
+    }
+    CK(ce);
+    const cudaError_t ie = cudaGraphInstantiate(&gr.exec[slot], g, 0);
+    cudaGraphDestroy(g);
+    CK(ie);
+    gr.flip[slot] = (*par ^ par0) & 1;
+    gr.launches[slot] = p->prof.launches - l0;
+    *par = par0;
+    p->prof.launches = l0;
+  }
+  CK(cudaGraphLaunch(gr.exec[slot], s));
+  *par ^= gr.flip[slot];
+  p->prof.launches += gr.launches[slot];
+  return SDF_OK;
+}
+
 template <int DIM, int KMAX, class PhiT, class V>
 sdf_status solve_impl(sdf_problem *p, const double *inst, int B, const double *psi,
                       const sdf_opts &o, char *ws, cudaStream_t s, double *y, double *lam,
@@ -2844,15 +2896,17 @@ sdf_status solve_impl(sdf_problem *p, const double *inst, int B, const double *p
   CK(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), s));
   if (fb) CK(cudaMemsetAsync(cvec64, 0, sizeof(double) * B * KMAX, s));
 
+  cudaStream_t ls = s;  // stream of the CG launches (a capture stream while a chunk is captured)
+  ChunkGraphs graphs;
   // cvec64 <- csign E^-1 Phi_I^T src for every running instance (batch kernels)
   auto project64 = [&](const V *src) -> sdf_status {
     if constexpr (f64) {
       switch (L.nb) {
-        case 16: k_proj_gemm64<KMAX, 16><<<gPb, NT, 0, s>>>(Phi, ld, k, N, B, st, src, ppart64, L.bpad); break;
-        case 32: k_proj_gemm64<KMAX, 32><<<gPb, NT, 0, s>>>(Phi, ld, k, N, B, st, src, ppart64, L.bpad); break;
-        default: k_proj_gemm64<KMAX, 64><<<gPb, NT, 0, s>>>(Phi, ld, k, N, B, st, src, ppart64, L.bpad); break;
+        case 16: k_proj_gemm64<KMAX, 16><<<gPb, NT, 0, ls>>>(Phi, ld, k, N, B, st, src, ppart64, L.bpad); break;
+        case 32: k_proj_gemm64<KMAX, 32><<<gPb, NT, 0, ls>>>(Phi, ld, k, N, B, st, src, ppart64, L.bpad); break;
+        default: k_proj_gemm64<KMAX, 64><<<gPb, NT, 0, ls>>>(Phi, ld, k, N, B, st, src, ppart64, L.bpad); break;
       }
-      k_proj_reduce<KMAX, double><<<B, NT, 0, s>>>(ppart64, L.gxp, L.bpad, k, st, Einv, cvec64);
+      k_proj_reduce<KMAX, double><<<B, NT, 0, ls>>>(ppart64, L.gxp, L.bpad, k, st, Einv, cvec64);
       p->prof.launches += 2;
     }
     return SDF_OK;
@@ -2873,18 +2927,18 @@ sdf_status solve_impl(sdf_problem *p, const double *inst, int B, const double *p
     bool expanded = false;
     if constexpr (f64) {
       if (fb) {
-        k_expand64_b<KMAX, kExpandGroup><<<gEb, NT, 0, s>>>(Phi, ld, k, N, B, st, cvec64, mask,
+        k_expand64_b<KMAX, kExpandGroup><<<gEb, NT, 0, ls>>>(Phi, ld, k, N, B, st, cvec64, mask,
                                                             rbuf[par], dinv, P.convection, dir);
         expanded = true;
       }
     }
     if (!expanded)
-      k_expand<KMAX, PhiT, V><<<gA, NT, 0, s>>>(Phi, ld, k, N, st, Einv, mask, rbuf[par], dinv,
+      k_expand<KMAX, PhiT, V><<<gA, NT, 0, ls>>>(Phi, ld, k, N, st, Einv, mask, rbuf[par], dinv,
                                                 P.convection, dir, L.gxa);
     if (timed) CK(cudaEventRecord(p->ev[1], s));
-    k_spmv<DIM, V><<<gT, NT, 0, s>>>(P, inst, st, mask, dir, q, part, cnt, ctrl, L.gx);
+    k_spmv<DIM, V><<<gT, NT, 0, ls>>>(P, inst, st, mask, dir, q, part, cnt, ctrl, L.gx);
     if (timed) CK(cudaEventRecord(p->ev[2], s));
-    k_update<DIM, KMAX, PhiT, V><<<gT, NT, 0, s>>>(P, inst, Phi, ld, k, st, mask, rbuf[par],
+    k_update<DIM, KMAX, PhiT, V><<<gT, NT, 0, ls>>>(P, inst, Phi, ld, k, st, mask, rbuf[par],
                                                    rbuf[par ^ 1], q, dir, x, dinv, part, cnt,
                                                    ctrl, L.gx, rtol2, o.max_cg, mixed,
                                                    fb ? vv : nullptr);
@@ -2960,10 +3014,20 @@ sdf_status solve_impl(sdf_problem *p, const double *inst, int B, const double *p
     }
     for (int it = 0;; ++it) {
       const bool timed = o.profile && p->ev_ready;
-      for (int rep = 0; rep < chunk; ++rep) {
-        sdf_status e = triple(pp, timed && rep == 0);
-        if (e != SDF_OK) return e;
-      }
+      sdf_status e = run_chunk(p, graphs, o.graph != 0 && !timed, s, &par,
+                               [&](cudaStream_t cs) -> sdf_status {
+                                 ls = cs;
+                                 for (int rep = 0; rep < chunk; ++rep) {
+                                   const sdf_status e2 = triple(pp, timed && rep == 0);
+                                   if (e2 != SDF_OK) {
+                                     ls = s;
+                                     return e2;
+                                   }
+                                 }
+                                 ls = s;
+                                 return SDF_OK;
+                               });
+      if (e != SDF_OK) return e;
       CKL("cg iteration");
       launches += chunk;
       CK(cudaMemcpyAsync(p->pinned, &ctrl->running, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -3106,32 +3170,34 @@ sdf_status solve_mixed(sdf_problem *p, const double *inst, int B, const double *
       CK(e);
     }
   }
+  cudaStream_t ls = s;  // stream of the CG launches (a capture stream while a chunk is captured)
+  ChunkGraphs graphs;
   auto project = [&](const float *src) -> sdf_status {  // cvec <- csign E^-1 Phi_I^T src
     if (!defl) return SDF_OK;
     if constexpr (std::is_same<PhiT, __nv_bfloat16>::value) {
       if (L.tcp) {
         const size_t sm = (size_t)tc::GM * tc::GK * 2 + 3 * (size_t)L.nbp * tc::GK * 2;
         switch (L.nbp) {
-          case 16: k_proj_tc<16><<<L.gxp, tc::GTH, sm, s>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad, KMAX); break;
-          case 32: k_proj_tc<32><<<L.gxp, tc::GTH, sm, s>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad, KMAX); break;
-          case 64: k_proj_tc<64><<<L.gxp, tc::GTH, sm, s>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad, KMAX); break;
-          case 128: k_proj_tc<128><<<L.gxp, tc::GTH, sm, s>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad, KMAX); break;
-          default: k_proj_tc<256><<<L.gxp, tc::GTH, sm, s>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad, KMAX); break;
+          case 16: k_proj_tc<16><<<L.gxp, tc::GTH, sm, ls>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad, KMAX); break;
+          case 32: k_proj_tc<32><<<L.gxp, tc::GTH, sm, ls>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad, KMAX); break;
+          case 64: k_proj_tc<64><<<L.gxp, tc::GTH, sm, ls>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad, KMAX); break;
+          case 128: k_proj_tc<128><<<L.gxp, tc::GTH, sm, ls>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad, KMAX); break;
+          default: k_proj_tc<256><<<L.gxp, tc::GTH, sm, ls>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad, KMAX); break;
         }
-        k_proj_reduce<KMAX><<<B, NT, 0, s>>>(ppart, L.gxp, L.bpad, k, st, Einv, cvec);
+        k_proj_reduce<KMAX><<<B, NT, 0, ls>>>(ppart, L.gxp, L.bpad, k, st, Einv, cvec);
         p->prof.launches += 2;
         return SDF_OK;
       }
     }
     if (L.nb == 1)
-      k_proj_gemm<KMAX, 1, PhiT><<<gP, NT, 0, s>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad);
+      k_proj_gemm<KMAX, 1, PhiT><<<gP, NT, 0, ls>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad);
     else if (L.nb == 16)
-      k_proj_gemm<KMAX, 16, PhiT><<<gP, NT, 0, s>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad);
+      k_proj_gemm<KMAX, 16, PhiT><<<gP, NT, 0, ls>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad);
     else if (L.nb == 32)
-      k_proj_gemm<KMAX, 32, PhiT><<<gP, NT, 0, s>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad);
+      k_proj_gemm<KMAX, 32, PhiT><<<gP, NT, 0, ls>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad);
     else
-      k_proj_gemm<KMAX, 64, PhiT><<<gP, NT, 0, s>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad);
-    k_proj_reduce<KMAX><<<B, NT, 0, s>>>(ppart, L.gxp, L.bpad, k, st, Einv, cvec);
+      k_proj_gemm<KMAX, 64, PhiT><<<gP, NT, 0, ls>>>(Phi, ld, k, N, B, st, src, ppart, L.bpad);
+    k_proj_reduce<KMAX><<<B, NT, 0, ls>>>(ppart, L.gxp, L.bpad, k, st, Einv, cvec);
     p->prof.launches += 2;
     return SDF_OK;
   };
@@ -3141,7 +3207,7 @@ sdf_status solve_mixed(sdf_problem *p, const double *inst, int B, const double *
     if constexpr (std::is_same<PhiT, __nv_bfloat16>::value) {
       if (L.tce && defl) {
 #define SDF_EXPAND_TC(NB_)                                                                        \
-  k_expand_tc<NB_><<<gxt, tc::GTH, xsm, s>>>(phin, L.kp, N, B, st, cvec, KMAX, mask, rbuf[par], \
+  k_expand_tc<NB_><<<gxt, tc::GTH, xsm, ls>>>(phin, L.kp, N, B, st, cvec, KMAX, mask, rbuf[par], \
                                              dinv, P.convection, dir)
         switch (L.nbp) {
           case 16: SDF_EXPAND_TC(16); break;
@@ -3155,7 +3221,7 @@ sdf_status solve_mixed(sdf_problem *p, const double *inst, int B, const double *
       }
     }
     if (!expanded)
-      k_expand_b<KMAX, PhiT><<<gxe, NT, esm, s>>>(Phi, ld, k, N, B, st, cvec, mask, rbuf[par],
+      k_expand_b<KMAX, PhiT><<<gxe, NT, esm, ls>>>(Phi, ld, k, N, B, st, cvec, mask, rbuf[par],
                                                   dinv, P.convection, dir);
     if (timed) CK(cudaEventRecord(p->ev[1], s));
     if constexpr (DIM == 3) {
@@ -3164,23 +3230,23 @@ sdf_status solve_mixed(sdf_problem *p, const double *inst, int B, const double *
         const dim3 gC2((B + 1) / 2, L.gxc);
         auto spmv = P.fx ? k_spmv3p<true> : k_spmv3p<false>;
         auto upd = P.fx ? k_update_v3p<true> : k_update_v3p<false>;
-        spmv<<<gC2, NT, 0, s>>>(P, st, mask, dir, q, part, cnt, ctrl, L.gxc, L.zc, B);
+        spmv<<<gC2, NT, 0, ls>>>(P, st, mask, dir, q, part, cnt, ctrl, L.gxc, L.zc, B);
         if (timed) CK(cudaEventRecord(p->ev[2], s));
-        upd<<<gC2, NT, 0, s>>>(P, st, mask, rbuf[par], rbuf[par ^ 1], q, dir, x, xlo, dinv, vv,
+        upd<<<gC2, NT, 0, ls>>>(P, st, mask, rbuf[par], rbuf[par ^ 1], q, dir, x, xlo, dinv, vv,
                                part, cnt, ctrl, L.gxc, L.zc, rtol2, o.max_cg, B);
       } else {
         const dim3 gC(B, L.gxc);
         auto spmv = P.fx ? k_spmv3c<true> : k_spmv3c<false>;
         auto upd = P.fx ? k_update_v3c<true> : k_update_v3c<false>;
-        spmv<<<gC, NT, 0, s>>>(P, inst, st, mask, dir, q, part, cnt, ctrl, L.gxc, L.zc);
+        spmv<<<gC, NT, 0, ls>>>(P, inst, st, mask, dir, q, part, cnt, ctrl, L.gxc, L.zc);
         if (timed) CK(cudaEventRecord(p->ev[2], s));
-        upd<<<gC, NT, 0, s>>>(P, inst, st, mask, rbuf[par], rbuf[par ^ 1], q, dir, x, xlo, dinv,
+        upd<<<gC, NT, 0, ls>>>(P, inst, st, mask, rbuf[par], rbuf[par ^ 1], q, dir, x, xlo, dinv,
                               vv, part, cnt, ctrl, L.gxc, L.zc, rtol2, o.max_cg);
       }
     } else {
-      k_spmv<DIM, float><<<gT, NT, 0, s>>>(P, inst, st, mask, dir, q, part, cnt, ctrl, L.gx);
+      k_spmv<DIM, float><<<gT, NT, 0, ls>>>(P, inst, st, mask, dir, q, part, cnt, ctrl, L.gx);
       if (timed) CK(cudaEventRecord(p->ev[2], s));
-      k_update_v<DIM><<<gT, NT, 0, s>>>(P, inst, st, mask, rbuf[par], rbuf[par ^ 1], q, dir, x,
+      k_update_v<DIM><<<gT, NT, 0, ls>>>(P, inst, st, mask, rbuf[par], rbuf[par ^ 1], q, dir, x,
                                         xlo, dinv, vv, part, cnt, ctrl, L.gx, rtol2, o.max_cg);
     }
     if (timed) CK(cudaEventRecord(p->ev[3], s));
@@ -3244,25 +3310,33 @@ sdf_status solve_mixed(sdf_problem *p, const double *inst, int B, const double *
     }
     for (;;) {
       const bool timed = o.profile && p->ev_ready;
-      for (int rep = 0; rep < chunk; ++rep) {
-        sdf_status e = triple(pp, timed && rep == 0);
-        if (e != SDF_OK) return e;
-      }
-      if (timed) CK(cudaEventRecord(p->ev[5], s));
-      if constexpr (DIM == 3)
-        k_resid<DIM><<<dim3(B, L.gxc), NT, 0, s>>>(P, inst, st, mask, b64, x, xlo, rbuf[par], part,
-                                                   cnt, ctrl, L.gxc, rtol2, floor_cu, L.zc);
-      else
-        k_resid<DIM><<<gT, NT, 0, s>>>(P, inst, st, mask, b64, x, xlo, rbuf[par], part, cnt,
-                                       ctrl, L.gx, rtol2, floor_cu, L.zc);
-      if (timed) CK(cudaEventRecord(p->ev[6], s));
-      p->prof.launches += 1;
-      {
+      // one chunk: `chunk` CG iterations, the FP64 residual replacement and
+      // the correction pass
+      sdf_status ec = run_chunk(p, graphs, o.graph != 0 && !timed, s, &par,
+                                [&](cudaStream_t cs) -> sdf_status {
+        ls = cs;
+        for (int rep = 0; rep < chunk; ++rep) {
+          sdf_status e = triple(pp, timed && rep == 0);
+          if (e != SDF_OK) {
+            ls = s;
+            return e;
+          }
+        }
+        if (timed) CK(cudaEventRecord(p->ev[5], s));
+        if constexpr (DIM == 3)
+          k_resid<DIM><<<dim3(B, L.gxc), NT, 0, ls>>>(P, inst, st, mask, b64, x, xlo, rbuf[par],
+                                                      part, cnt, ctrl, L.gxc, rtol2, floor_cu, L.zc);
+        else
+          k_resid<DIM><<<gT, NT, 0, ls>>>(P, inst, st, mask, b64, x, xlo, rbuf[par], part, cnt,
+                                          ctrl, L.gx, rtol2, floor_cu, L.zc);
+        if (timed) CK(cudaEventRecord(p->ev[6], s));
+        p->prof.launches += 1;
         sdf_status e = project(rbuf[par]);  // correction pass: c = -E^-1 Phi_I^T r
-        if (e != SDF_OK) return e;
-        e = triple(wv, false);
-        if (e != SDF_OK) return e;
-      }
+        if (e == SDF_OK) e = triple(wv, false);
+        ls = s;
+        return e;
+      });
+      if (ec != SDF_OK) return ec;
       CKL("cg iteration");
       launches += chunk;
       CK(cudaMemcpyAsync(p->pinned, &ctrl->running, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -3441,6 +3515,7 @@ void sdf_default_opts(sdf_opts *o) {
   o->floor_c = 10.0;
   o->column_depth = 0;
   o->column_pairs = 0;
+  o->graph = 1;
 }
 
 sdf_status sdf_problem_create(const sdf_problem_desc *desc, const double *kappa_host,
@@ -4280,6 +4355,7 @@ void sdf_problem_destroy(sdf_problem *p) {
   if (p->pinned) cudaFreeHost(p->pinned);
   for (int i = 0; i < 8; ++i)
     if (p->ev[i]) cudaEventDestroy(p->ev[i]);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   delete p;
 }
 

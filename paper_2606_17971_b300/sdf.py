@@ -48,7 +48,8 @@ class Opts(ctypes.Structure):
                 ("max_launches", ctypes.c_int64), ("ritz_r", ctypes.c_int32),
                 ("safe_r", ctypes.c_int32), ("tau_safe", ctypes.c_double),
                 ("tau_dep", ctypes.c_double), ("floor_c", ctypes.c_double),
-                ("column_depth", ctypes.c_int32), ("column_pairs", ctypes.c_int32)]
+                ("column_depth", ctypes.c_int32), ("column_pairs", ctypes.c_int32),
+                ("graph", ctypes.c_int32)]
 
 
 SDF_NPROF = 9

@@ -551,3 +551,34 @@ def test_mixed_3d_column_depth_64_with_active_sets():
     out = G3.solve(t64(W.instances_array(insts)), t64(psi),
                    sdf.default_opts(precision=sdf.PREC_MIXED, column_depth=64))
     compare_mixed(out, orc, P=P3, rhs=rhs)
+
+
+@pytest.mark.parametrize("case", ["fp64_batch", "fp64_single", "mixed_3d"])
+def test_graph_replay_matches_direct_launches(case):
+    # the chunks of CG launches replayed from CUDA graphs run the same kernels
+    # in the same order as launching them one by one: bit for bit
+    if case == "mixed_3d":
+        n, dim = (14, 12, 10), 3
+        w = W.scaled(W.WORKLOADS["diff3d_128"], 12, instances=5)
+        G = sdf.Problem(3, n, alpha=1e-4, yd_sigma=w.sigma)
+        phi, _ = G.analytic_modes(10, sdf.F32)
+        insts = W.draw_instances(w, count=5)
+        insts[2].a = 4.2
+        kw = dict(precision=sdf.PREC_MIXED, replace_every=9)
+        N = int(np.prod(n))
+    else:
+        w = W.WORKLOADS["diff2d_32"]
+        G = sdf.Problem(2, w.n, alpha=w.alpha, yd_sigma=w.sigma)
+        phi, _ = G.analytic_modes(w.k)
+        insts = W.draw_instances(w, count=20 if case == "fp64_batch" else 3)
+        insts[0].a = 3.2
+        kw = dict(check_every=7)
+        N = w.N
+    G.set_modes(phi)
+    inst, psi = t64(W.instances_array(insts)), t64(np.ones(N))
+    a = G.solve(inst, psi, sdf.default_opts(graph=1, **kw))
+    b = G.solve(inst, psi, sdf.default_opts(graph=0, **kw))
+    assert a["status"] == 0 and b["status"] == 0
+    assert torch.equal(a["y"], b["y"]) and torch.equal(a["active"], b["active"])
+    assert torch.equal(a["lam"], b["lam"])
+    assert [s["cg_iters"] for s in a["stats"]] == [s["cg_iters"] for s in b["stats"]]
