@@ -67,14 +67,16 @@ def kernel_work(name, dim, k, phi_bytes, vec_bytes=8, mixed=False, batch=1):
 
     Mixed path (FP32 vectors; Phi shared by the batch, so its bytes are
     divided by the batch size):
-      update  k_update_v: r, q, p, mask, x_lo read; r_out, v, x_lo written
+      update  k_update_v: r, q, p, x_lo (4 B each) and mask (1 B) read;
+              r_out, v, x_lo written (the FP64 x fold, once per replacement
+              period, is not counted)
       expand  k_expand_b: mask, r, p read, p written, Phi (shared)
       spmv    k_spmv:     p read, q written
       project k_proj_gemm: v read, Phi (shared)
     FP64 path: see the per-kernel comments below."""
     if mixed:
         if name == "update":
-            return stencil_flops(dim) + 9, 4 * 4 + 1 + 8 + 4 + 4
+            return stencil_flops(dim) + 9, 4 * 4 + 1 + 3 * 4
         if name == "expand":
             return 2 * k + 4, 1 + 4 + 8 + k * phi_bytes / batch
         if name == "spmv":

@@ -1481,10 +1481,10 @@ __global__ void __launch_bounds__(NT) k_update_v(OpParams P, const double *inst,
 
 // 3D column variants (2.5D z-marching) of k_spmv and k_update_v for the mixed
 // path; same arithmetic and reductions, different traversal.
+// gblk: the block's slot among the GX blocks of instance b.
 __device__ __forceinline__ void sigma_epilogue(InstState &S, int b, double sg, double *part, int *cnt,
-                                               Ctrl *ctrl, int GX, double *red, double *scratch,
-                                               double *tot1, int *flag) {
-  const int gblk = blockIdx.y;
+                                               Ctrl *ctrl, int GX, int gblk, double *red,
+                                               double *scratch, double *tot1, int *flag) {
   sg = block_sum(sg, red);
   if (threadIdx.x == 0) part[(long long)b * GX + gblk] = sg;
   if (!last_block(cnt + b * NCNT + CNT_SIGMA, GX, flag)) return;
@@ -1592,7 +1592,7 @@ __global__ void __launch_bounds__(NT, 3) k_spmv3c(OpParams P, const double *inst
     col_origin(P, t, zc, x0, y0, z0, z1);
     col_S3<float, VARK, false>(P, cb, x0, y0, z0, z1, sm, src, out);
   }
-  sigma_epilogue(S, b, out.sg.value(), part, cnt, ctrl, GX, red, scratch, tot1, &flag);
+  sigma_epilogue(S, b, out.sg.value(), part, cnt, ctrl, GX, blockIdx.y, red, scratch, tot1, &flag);
 }
 
 template <bool VARK>
@@ -1732,20 +1732,24 @@ __global__ void __launch_bounds__(NT, 3) k_spmv3p(OpParams P, InstState *st, con
   __shared__ ColSmemPair sm;
   __shared__ double red[NWARP], scratch[NT], tot1[1];
   __shared__ int flag;
-  const int b0 = 2 * blockIdx.x, b1 = min(b0 + 1, B - 1);
+  const int b0 = 2 * blockIdx.y, b1 = min(b0 + 1, B - 1);
   const bool run0 = inst_running(st[b0]), run1 = b0 + 1 < B && inst_running(st[b1]);
   if (!run0 && !run1) return;
   const long long N = P.N;
   const ColSrcP2 src{p + b0 * N, p + b1 * N};
   ColOutQ2 out{mask + b0 * N, mask + b1 * N, q + b0 * N, q + b1 * N, run0, run1};
   const long long items = col_items(P.nx, P.ny, P.nz, zc);
-  for (long long t = blockIdx.y; t < items; t += GX) {
+  for (long long t = blockIdx.x; t < items; t += GX) {
     int x0, y0, z0, z1;
     col_origin(P, t, zc, x0, y0, z0, z1);
     col_S3_pair<VARK>(P, x0, y0, z0, z1, sm, src, out);
   }
-  if (run0) sigma_epilogue(st[b0], b0, out.sg.value0(), part, cnt, ctrl, GX, red, scratch, tot1, &flag);
-  if (run1) sigma_epilogue(st[b1], b1, out.sg.value1(), part, cnt, ctrl, GX, red, scratch, tot1, &flag);
+  if (run0)
+    sigma_epilogue(st[b0], b0, out.sg.value0(), part, cnt, ctrl, GX, blockIdx.x, red, scratch, tot1,
+                   &flag);
+  if (run1)
+    sigma_epilogue(st[b1], b1, out.sg.value1(), part, cnt, ctrl, GX, blockIdx.x, red, scratch, tot1,
+                   &flag);
 }
 
 template <bool VARK>
@@ -1758,7 +1762,7 @@ __global__ void __launch_bounds__(NT, 2) k_update_v3p(OpParams P, InstState *st,
   __shared__ ColSmemPair sm;
   __shared__ double red[NWARP], scratch[NT], tot2[2];
   __shared__ int flag;
-  const int b0 = 2 * blockIdx.x, b1 = min(b0 + 1, B - 1);
+  const int b0 = 2 * blockIdx.y, b1 = min(b0 + 1, B - 1);
   InstState &S0 = st[b0], &S1 = st[b1];
   const bool run0 = inst_running(S0), run1 = b0 + 1 < B && inst_running(S1);
   if (!run0 && !run1) return;
@@ -1769,7 +1773,7 @@ __global__ void __launch_bounds__(NT, 2) k_update_v3p(OpParams P, InstState *st,
   const long long items = col_items(P.nx, P.ny, P.nz, zc);
   double rho[2], rr[2];
   auto run = [&](auto out) {
-    for (long long t = blockIdx.y; t < items; t += GX) {
+    for (long long t = blockIdx.x; t < items; t += GX) {
       int x0, y0, z0, z1;
       col_origin(P, t, zc, x0, y0, z0, z1);
       col_S3_pair<VARK>(P, x0, y0, z0, z1, sm, src, out);
@@ -1795,8 +1799,8 @@ __global__ void __launch_bounds__(NT, 2) k_update_v3p(OpParams P, InstState *st,
     const double rb = block_sum(rho[h], red);
     const double rrb = block_sum(rr[h], red);
     if (threadIdx.x == 0) {
-      part[((long long)b * GX + blockIdx.y) * 2 + 0] = rb;
-      part[((long long)b * GX + blockIdx.y) * 2 + 1] = rrb;
+      part[((long long)b * GX + blockIdx.x) * 2 + 0] = rb;
+      part[((long long)b * GX + blockIdx.x) * 2 + 1] = rrb;
     }
     if (!last_block(cnt + b * NCNT + CNT_UPDATE, GX, &flag)) continue;
     reduce_fields(part + (long long)b * GX * 2, GX, 2, 2, tot2, scratch);
@@ -3227,7 +3231,10 @@ sdf_status solve_mixed(sdf_problem *p, const double *inst, int B, const double *
     if constexpr (DIM == 3) {
       // the mixed path has no convection (rejected at entry): VARK only
       if (L.pairs) {  // instance pairs on the packed FP32 pipe
-        const dim3 gC2((B + 1) / 2, L.gxc);
+        // column items fastest: the blocks resident at one time hold every
+        // item of a few pairs, so neighbouring tiles read each other's halo
+        // sectors from L2 while both march the same planes
+        const dim3 gC2(L.gxc, (B + 1) / 2);
         auto spmv = P.fx ? k_spmv3p<true> : k_spmv3p<false>;
         auto upd = P.fx ? k_update_v3p<true> : k_update_v3p<false>;
         spmv<<<gC2, NT, 0, ls>>>(P, st, mask, dir, q, part, cnt, ctrl, L.gxc, L.zc, B);
