@@ -596,7 +596,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="diff3d_128", choices=sorted(MODES))
-    ap.add_argument("--n", type=int, default=0, help="grid override (profiling captures only)")
+    ap.add_argument("--n", type=int, default=0,
+                    help="grid override (profiling captures and reduced-size runs)")
     ap.add_argument("--max-cg", type=int, default=0, help="CG cap (profiling captures only)")
     ap.add_argument("--path", default="", choices=["", "plain", "mixed"],
                     help="plain: FP64 A-DEF2; mixed: FP32/BF16 with FP64 refinement "

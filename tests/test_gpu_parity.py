@@ -358,6 +358,28 @@ def test_mixed_32x32_workload_matches_fp64_oracle(phi_dtype, max_blocks, replace
     compare_mixed(out, orc, P=P, rhs=rhs)
 
 
+@pytest.mark.parametrize("phi_dtype", ["f32", "bf16"])
+def test_mixed_k128_lognormal_matches_fp64_oracle(phi_dtype):
+    # k = 128 modes (the precision configuration's count; the widest mode
+    # tiles of the mixed kernels: two 64-wide K blocks on the tensor cores,
+    # eight 16-mode register tiles in the FP32 projection) on the lognormal
+    # law at 40 x 40, three instances, each with an active set (psi = 0.5)
+    w = W.scaled(W.WORKLOADS["lognormal2d_2048"], 40)
+    kap = W.kappa_field(w)
+    P = O.Problem(2, w.n, kappa=kap, alpha=w.alpha)
+    Phi = O.dense_modes(P, 128)[0]
+    insts = W.draw_instances(w, count=3)
+    psi = np.full(w.N, 0.5)
+    rhs = [P.desired_state(i.a, i.c[:2], w.sigma)[1] for i in insts]
+    orc = _orc_solves(P, rhs, psi, Phi)
+    assert all(max(r["n_active"]) > 0 for r in orc)
+    G = sdf.Problem(2, w.n, alpha=w.alpha, kappa=kap, yd_sigma=w.sigma)
+    G.set_modes(modes_tensor_as(Phi, torch.float32 if phi_dtype == "f32" else torch.bfloat16))
+    out = G.solve(t64(W.instances_array(insts)), t64(psi),
+                  sdf.default_opts(precision=sdf.PREC_MIXED))
+    compare_mixed(out, orc, P=P, rhs=rhs)
+
+
 def test_mixed_ragged_block_kappa_and_3d_and_no_convection():
     # ragged 2D with 100x contrast, BF16 modes
     w = W.scaled(W.WORKLOADS["block2d_1024"], 70)
