@@ -1,0 +1,68 @@
+"""Host-side arithmetic of bench.py's roofline objects (no GPU).
+
+The algorithmic bytes per dof and instance that bench.py divides by each
+kernel's CUDA-event time are checked against the DRAM traffic ncu measured
+for the same kernels at full size (the one-pass capture summarised in
+profiles/traffic_mixed_diff3d_128.md): a count that included bytes a kernel
+does not move, or left out a vector it does, shows up as a ratio away from 1.
+The traffic lookup is checked to follow the kernel-source hash."""
+import os
+import re
+
+import pytest
+
+import bench
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+TRAFFIC = os.path.join(ROOT, "profiles", "traffic_mixed_diff3d_128.md")
+
+
+def _measured_bytes_per_unit():
+    """kernel -> DRAM read + write per dof and instance, from the summary."""
+    out = {}
+    for line in open(TRAFFIC):
+        m = re.match(r"\| `(k_\w+)<[^`]*>` \| ([0-9.]+) \| ([0-9.]+) \|", line)
+        if m and m.group(1) not in out:  # the first table: read | write | ...
+            out[m.group(1)] = float(m.group(2)) + float(m.group(3))
+    return out
+
+
+def test_mixed_algorithmic_bytes_match_the_measured_full_size_traffic():
+    meas = _measured_bytes_per_unit()
+    # the headline configuration: 3D, k = 60 BF16 modes shared by 128 instances
+    k, phi_bytes, B = 60, 2, 128
+    names = {"update": "k_update_v3p", "spmv": "k_spmv3p", "expand": "k_expand_tc",
+             "project": "k_proj_tc"}
+    assert set(names.values()) <= set(meas), meas
+    for name, kern in names.items():
+        _, byts = bench.kernel_work(name, 3, k, phi_bytes, 4, True, B)
+        ratio = meas[kern] / byts
+        # traffic may exceed the count a little (halo sectors at tile edges),
+        # never fall short of it at this size (every vector is 1.07 GB)
+        assert 0.99 <= ratio <= 1.05, (name, byts, meas[kern], ratio)
+
+
+def test_loop_floor_is_below_the_sum_of_the_kernels():
+    # the per-iteration floor of one fused pass (bench.loop_roofline) against
+    # what the four launches move: the split re-reads p, r, the mask and v
+    prof = {"mean_ms": {"expand": 1.0, "spmv": 1.0, "update": 1.0, "project": 1.0,
+                        "resid": 10.0}}
+    w = type("Wk", (), {"dim": 3})()
+    loop = bench.loop_roofline(prof, w, 60, True, 2, 128, 1)
+    kernels = sum(bench.kernel_work(n, 3, 60, 2, 4, True, 128)[1]
+                  for n in ("update", "spmv", "expand", "project"))
+    assert loop["bytes_per_unit"] < kernels
+    assert loop["ms_per_iter"] == pytest.approx(4.0 + 10.0 / 100)
+
+
+def test_profile_traffic_follows_the_kernel_source_hash(monkeypatch):
+    path = os.path.join(ROOT, "profiles", "k_update_mixed_diff3d_128.md")
+    txt = open(path).read()
+    h = re.search(r"source_hash:\s*([0-9a-f]+)", txt).group(1)
+    t = float(re.search(r"traffic_bytes_per_launch_full_size:\s*([0-9.eE+]+)", txt).group(1))
+    monkeypatch.setattr(bench, "source_hash", lambda: h)
+    assert bench.profile_traffic("update_mixed", "diff3d_128") == t
+    monkeypatch.setattr(bench, "source_hash", lambda: "0" * 16)
+    assert bench.profile_traffic("update_mixed", "diff3d_128") is None
+    assert bench.profile_traffic("update_mixed", "no_such_workload") is None
