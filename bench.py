@@ -507,8 +507,9 @@ def kernel_work_fp64(name, dim, k, batched, B):
         f = stencil_flops(dim) + 9 + (0 if batched else 2 * k)
         b = 7 * 8 + 1 + (8 if batched else k * 8)
         return f, b
-    if name == "expand":   # r, p read; p written; mask; modes
-        return 2 * k + 4, 3 * 8 + 1 + k * 8 / share
+    if name == "expand":   # r, p read; p written; mask; modes (once per group of 32)
+        groups = -(-B // 32) if batched else 1
+        return 2 * k + 4, 3 * 8 + 1 + k * 8 * groups / share
     if name == "spmv":     # p read, q written, mask
         return stencil_flops(dim) + 2, 2 * 8 + 1
     if name == "project":  # v read; modes shared by the batch

@@ -66,3 +66,14 @@ def test_profile_traffic_follows_the_kernel_source_hash(monkeypatch):
     monkeypatch.setattr(bench, "source_hash", lambda: "0" * 16)
     assert bench.profile_traffic("update_mixed", "diff3d_128") is None
     assert bench.profile_traffic("update_mixed", "no_such_workload") is None
+
+
+def test_fp64_batch_projection_bytes_match_its_capture():
+    # k_proj_gemm64 on the convection-diffusion law at 384^2, batch 64, k = 48
+    # (profiles/k_project_fp64_convdiff2d_512.md): v of every instance and the
+    # modes once per launch
+    txt = open(os.path.join(ROOT, "profiles", "k_project_fp64_convdiff2d_512.md")).read()
+    read_mb = float(re.search(r"\| DRAM read \+ write \| ([0-9.]+) \+", txt).group(1))
+    _, byts = bench.kernel_work_fp64("project", 2, 48, True, 64)
+    units = 384 * 384 * 64
+    assert read_mb * 1e6 / (byts * units) == pytest.approx(1.0, abs=0.03)
