@@ -2,9 +2,9 @@
 
 The algorithmic bytes per dof and instance that bench.py divides by each
 kernel's CUDA-event time are checked against the DRAM traffic ncu measured
-for the same kernels at full size (the one-pass capture summarised in
-profiles/traffic_mixed_diff3d_128.md): a count that included bytes a kernel
-does not move, or left out a vector it does, shows up as a ratio away from 1.
+for the same kernels at full size (the committed summary of the one-pass
+capture under profiles/): a count that included bytes a kernel does not
+move, or left out a vector it does, shows up as a ratio away from 1.
 The traffic lookup is checked to follow the kernel-source hash."""
 import os
 import re
@@ -70,7 +70,7 @@ def test_profile_traffic_follows_the_kernel_source_hash(monkeypatch):
 
 def test_fp64_batch_projection_bytes_match_its_capture():
     # k_proj_gemm64 on the convection-diffusion law at 384^2, batch 64, k = 48
-    # (profiles/k_project_fp64_convdiff2d_512.md): v of every instance and the
+    # (its small-case capture under profiles/): v of every instance and the
     # modes once per launch
     txt = open(os.path.join(ROOT, "profiles", "k_project_fp64_convdiff2d_512.md")).read()
     read_mb = float(re.search(r"\| DRAM read \+ write \| ([0-9.]+) \+", txt).group(1))
