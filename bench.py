@@ -376,7 +376,49 @@ def oracle_counts(name):
             float(np.mean([sum(i["cg_iters"]) for i in inst])))
 
 
-def run_reference(args, w):
+def resolve_mode(args):
+    """The workload's benchmark mode (MODES) with the command line's overrides."""
+    mode = dict(MODES[args.workload])
+    if args.path:
+        mode["path"] = args.path
+    if args.phi:
+        mode["phi"] = args.phi
+    if args.modes:
+        mode["modes"] = args.modes
+    if args.batch:
+        mode["batch"] = args.batch
+    if args.no_learned:
+        mode["learned"] = False
+    if mode["path"] == "plain":
+        mode["learned"] = False
+    return mode
+
+
+def workload_config(w, mode, world, args):
+    """The `config` object of a line: the workload measured (grid, modes,
+    instances per step, held-out set) and how its inputs relate to L2.  Both
+    arms print this same object; how each arm computes (GPU path, CPU oracle)
+    is in the line's `path` key."""
+    mixed = mode["path"] == "mixed"
+    B = mode["batch"]
+    units = w.N * B
+    cfg = {"workload": w.name, "grid": [w.n] * w.dim, "k": w.k, "alpha": w.alpha,
+           "instances_per_step": B * world, "batch_per_gpu": B}
+    if mode.get("learned"):
+        phi_bytes = 2 if mode.get("phi") == "bf16" else 4
+        n_held = args.held_out or w.extra.get("held_out", 1024)
+        cfg["held_out"] = n_held  # per rank: shard() deals n_held * world instances
+        cfg["held_out_batches"] = max(1, n_held // B)
+        cfg["l2"] = ("inputs larger than L2: Phi is %.2f GB and each vector %.2f GB"
+                     % (w.N * w.k * phi_bytes / 1e9, units * 4 / 1e9))
+    else:
+        cfg["l2"] = ("inputs larger than L2 (%.2f GB of vectors per batch)"
+                     % (8 * units * (4 if mixed else 8) / 1e9))
+    cfg["parallelism"] = f"replicas x{world}" if world > 1 else "1 GPU"
+    return cfg
+
+
+def run_reference(args, w, mode, world):
     from paper_2606_17971_b300 import workloads as W
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -405,7 +447,8 @@ def run_reference(args, w):
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": w.name, "path": "CPU oracle (plain C, FP64)"},
+        "data": "synthetic", "config": workload_config(w, mode, world, args),
+        "path": "CPU oracle (plain C, FP64)",
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
@@ -643,14 +686,15 @@ def main():
     w = W.WORKLOADS[args.workload]
     if args.n:
         w = W.scaled(w, args.n)
+    mode = resolve_mode(args)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
-        return run_reference(args, w)
+        return run_reference(args, w, mode, world)
 
     import torch
     import torch.distributed as dist
     from paper_2606_17971_b300 import sdf
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
@@ -658,19 +702,6 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    mode = dict(MODES[args.workload])
-    if args.path:
-        mode["path"] = args.path
-    if args.phi:
-        mode["phi"] = args.phi
-    if args.modes:
-        mode["modes"] = args.modes
-    if args.batch:
-        mode["batch"] = args.batch
-    if args.no_learned:
-        mode["learned"] = False
-    if mode["path"] == "plain":
-        mode["learned"] = False
     if mode.get("learned"):
         line = headline_run(args, w, mode, sdf, dev, world, rank)
     else:
@@ -735,20 +766,15 @@ def workload_run(args, w, mode, sdf, dev, world, rank):
     fb = (not mixed) and B >= 8
     roof = dominant_roofline(prof, w, w.k, mixed, phi_bytes, B, units, fb)
     roof["loop"] = loop_roofline(prof, w, w.k, mixed, phi_bytes, B, units)
-    line["config"] = {
-        "workload": w.name, "grid": [w.n] * w.dim, "k": w.k, "alpha": w.alpha,
-        "instances_per_step": B * world, "batch_per_gpu": B,
-        "path": ("mixed FP32 / %s modes, FP64 x, reductions, coarse operator and residual "
-                 "replacement" % mode.get("phi") if mixed else
-                 ("FP64 A-DEF2, shared-Phi batch kernels" if fb else
-                  "FP64 A-DEF2, one instance per launch")) + " (primal active-set loop)"
-                + (", deflation off (plain Jacobi-PCG)" if args.no_deflate else ""),
-        "modes": modes_info, "l2": "inputs larger than L2 (%.2f GB of vectors per batch)"
-                                  % (8 * units * (4 if mixed else 8) / 1e9),
-        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}
+    line["config"] = workload_config(w, mode, world, args)
+    line["path"] = (("mixed FP32 / %s modes, FP64 x, reductions, coarse operator and residual "
+                     "replacement" % mode.get("phi") if mixed else
+                     ("FP64 A-DEF2, shared-Phi batch kernels" if fb else
+                      "FP64 A-DEF2, one instance per launch")) + " (primal active-set loop)"
+                    + (", deflation off (plain Jacobi-PCG)" if args.no_deflate else ""))
+    line["modes"] = modes_info
     if tuned:
-        line["config"]["autotuned"] = {"column_depth": tuned,
-                                       "instance_pairs": G.autotune_choice(B)[1]}
+        line["autotuned"] = {"column_depth": tuned, "instance_pairs": G.autotune_choice(B)[1]}
     line.update({
         "cg_iters_per_instance": mean_stat(stats, lambda s: sum(s["cg_iters"])),
         "outer_iters_per_instance": mean_stat(stats, lambda s: s["outer_iters"]),
@@ -941,17 +967,11 @@ def headline_run(args, w, mode, sdf, dev, world, rank):
     units = w.N * B
     roof = dominant_roofline(prof, w, w.k, True, phi_bytes, B, units, False)
     roof["loop"] = loop_roofline(prof, w, w.k, True, phi_bytes, B, units)
-    line["config"] = {
-        "workload": w.name, "grid": [w.n] * w.dim, "k": w.k, "alpha": w.alpha,
-        "instances_per_step": B * world, "batch_per_gpu": B, "held_out": len(held),
-        "held_out_batches": nb,
-        "path": "mixed FP32 / %s modes, FP64 x, reductions, coarse operator and residual "
-                "replacement, learned warm start (primal active-set loop)" % mode.get("phi"),
-        "modes": modes_info,
-        "l2": "inputs larger than L2: Phi is %.2f GB and each vector %.2f GB"
-              % (w.N * w.k * phi_bytes / 1e9, units * 4 / 1e9),
-        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
-        "autotuned": {"column_depth": tuned, "instance_pairs": G.autotune_choice(B)[1]}}
+    line["config"] = workload_config(w, mode, world, args)
+    line["path"] = ("mixed FP32 / %s modes, FP64 x, reductions, coarse operator and residual "
+                    "replacement, learned warm start (primal active-set loop)" % mode.get("phi"))
+    line["modes"] = modes_info
+    line["autotuned"] = {"column_depth": tuned, "instance_pairs": G.autotune_choice(B)[1]}
     cold_ms = float(np.mean([c[0] for c in cold.values()]))
     cold_it = float(np.mean([p["cold_cg_iters"] for p in per_batch]))
     lrn_cmp = float(np.mean([p["learned_cg_iters"] for p in per_batch]))

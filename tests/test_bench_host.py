@@ -77,3 +77,47 @@ def test_fp64_batch_projection_bytes_match_its_capture():
     _, byts = bench.kernel_work_fp64("project", 2, 48, True, 64)
     units = 384 * 384 * 64
     assert read_mb * 1e6 / (byts * units) == pytest.approx(1.0, abs=0.03)
+
+
+def _reference_line(monkeypatch, capsys, argv):
+    # the oracle sample is replaced by fixed timings: only the line's shape
+    # is under test here
+    monkeypatch.setattr(bench, "cpu_sample", lambda w, inst, m=20: (2.0, 0.5, 4))
+    monkeypatch.setattr("sys.argv", ["bench.py", "--impl", "reference"] + argv)
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    monkeypatch.delenv("RANK", raising=False)
+    bench.main()
+    import json
+    return json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+
+
+def test_reference_arm_prints_the_headline_workload_config(monkeypatch, capsys):
+    line = _reference_line(monkeypatch, capsys, ["--steps", "2", "--warmup", "1"])
+    cfg = line["config"]
+    # the headline: 128^3, k = 60 BF16 modes, 1024 held-out instances in 8
+    # batches of 128; vectors of a batch are 1.07 GB, the modes 0.25 GB
+    assert cfg == {"workload": "diff3d_128", "grid": [128, 128, 128], "k": 60, "alpha": 1e-4,
+                   "instances_per_step": 128, "batch_per_gpu": 128, "held_out": 1024,
+                   "held_out_batches": 8,
+                   "l2": "inputs larger than L2: Phi is 0.25 GB and each vector 1.07 GB",
+                   "parallelism": "1 GPU"}
+    assert line["impl"] == "reference" and line["path"].startswith("CPU oracle")
+    assert line["steps"] == 2 and line["warmup"] == 1
+    # one outer set-up plus the golden CG count at 0.5 s per iteration
+    assert line["value"] == pytest.approx(1.0 / (2.0 * 1.0 + 0.5 * 5542), rel=1e-2)
+
+
+def test_both_arms_share_the_config_of_an_overridden_mode(monkeypatch, capsys):
+    # the same overrides give the same config object on both arms: the GPU
+    # arm's line and the reference arm's come from workload_config
+    line = _reference_line(monkeypatch, capsys, ["--steps", "1", "--warmup", "0",
+                                                 "--path", "plain", "--batch", "16"])
+    import argparse
+    args = argparse.Namespace(workload="diff3d_128", path="plain", phi="", modes="", batch=16,
+                              no_learned=False, held_out=0)
+    mode = bench.resolve_mode(args)
+    assert not mode["learned"]
+    from paper_2606_17971_b300 import workloads as W
+    assert line["config"] == bench.workload_config(W.WORKLOADS["diff3d_128"], mode, 1, args)
+    assert line["config"]["l2"] == "inputs larger than L2 (2.15 GB of vectors per batch)"
+    assert "held_out" not in line["config"]
