@@ -121,3 +121,27 @@ def test_both_arms_share_the_config_of_an_overridden_mode(monkeypatch, capsys):
     assert line["config"] == bench.workload_config(W.WORKLOADS["diff3d_128"], mode, 1, args)
     assert line["config"]["l2"] == "inputs larger than L2 (2.15 GB of vectors per batch)"
     assert "held_out" not in line["config"]
+
+
+def test_clock_summary_parses_the_sampled_lines():
+    # nvidia-smi --format=csv,noheader,nounits lines as the sampler reads
+    # them: index, SM clock, max SM clock, power, active mask, then the four
+    # throttle reasons of the query
+    c = bench.ClockSampler(0)
+    c.lines = [
+        "0, 2032, 2032, 850.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 2010, 2032, 1098.7, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 345, 2032, 120.0, 0x0000000000000001, Not Active, Not Active, Not Active, Not Active",
+        "0, [N/A], 2032, 100.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "garbage",
+    ]
+    s = c.summary()
+    # the idle sample (345 MHz, below half the maximum) is not under load;
+    # the unreadable and short lines are skipped
+    assert s["samples"] == 3 and s["sm_max_mhz"] == 2032.0
+    assert s["sm_mhz"] == pytest.approx(2021.0)
+    assert s["reasons"] == ["sw_power_cap"]
+    c.lines = ["0, 1500, 2032, 900, 0x8, Not Active, Active, Not Active, Not Active"]
+    assert bench.ClockSampler.summary(c)["reasons"] == ["hw_thermal_slowdown"]
+    c.lines = []
+    assert c.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
