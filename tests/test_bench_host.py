@@ -145,3 +145,22 @@ def test_clock_summary_parses_the_sampled_lines():
     assert bench.ClockSampler.summary(c)["reasons"] == ["hw_thermal_slowdown"]
     c.lines = []
     assert c.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+
+def test_reference_arm_runs_on_rank_0_only(monkeypatch, capsys):
+    # under torchrun the oracle runs once: rank 0 prints the line for the
+    # whole job's config, the other ranks exit without work
+    calls = []
+    monkeypatch.setattr(bench, "cpu_sample", lambda w, inst, m=20: calls.append(m) or (2.0, 0.5, 4))
+    monkeypatch.setattr("sys.argv", ["bench.py", "--impl", "reference", "--gpus", "2",
+                                     "--steps", "1", "--warmup", "0"])
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("RANK", "1")
+    bench.main()
+    assert capsys.readouterr().out.strip() == "" and not calls
+    monkeypatch.setenv("RANK", "0")
+    bench.main()
+    import json
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["n_gpus"] == 2 and line["config"]["instances_per_step"] == 256
+    assert line["config"]["parallelism"] == "replicas x2" and calls == [10]
