@@ -164,3 +164,26 @@ def test_reference_arm_runs_on_rank_0_only(monkeypatch, capsys):
     line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
     assert line["n_gpus"] == 2 and line["config"]["instances_per_step"] == 256
     assert line["config"]["parallelism"] == "replicas x2" and calls == [10]
+
+
+def test_roofline_peak_comes_from_the_measured_file_else_the_labelled_fallback(monkeypatch):
+    prof = {"mean_ms": {"expand": 1.3, "spmv": 1.2, "update": 2.2, "project": 0.7,
+                        "resid": 19.0},
+            "samples": {"expand": 10, "spmv": 10, "update": 10, "project": 10, "resid": 1}}
+    w = type("Wk", (), {"dim": 3, "name": "diff3d_128"})()
+    units = 128**3 * 128
+    monkeypatch.setattr(bench, "peaks", lambda: {"hbm_gbs": 6480.8})
+    dom = bench.dominant_roofline(prof, w, 60, True, 2, 128, units, False)
+    assert dom["kernel"] == "k_update" and dom["peak"] == 6480.8
+    assert dom["peak_source"].startswith("measured")
+    # 29 B per unit moved in 2.2 ms
+    assert dom["achieved"] == pytest.approx(29 * units / 2.2e-3 / 1e9)
+    assert dom["frac"] == pytest.approx(dom["achieved"] / 6480.8)
+    loop = bench.loop_roofline(prof, w, 60, True, 2, 128, units)
+    assert loop["peak"] == 6480.8 and loop["ms_per_iter"] == pytest.approx(5.4 + 0.19)
+    monkeypatch.setattr(bench, "peaks", lambda: {})
+    dom = bench.dominant_roofline(prof, w, 60, True, 2, 128, units, False)
+    loop = bench.loop_roofline(prof, w, 60, True, 2, 128, units)
+    for r in (dom, loop):
+        assert r["peak"] == bench.HBM_FALLBACK_GBS and r["peak_source"].startswith("fallback")
+        assert r["frac"] == pytest.approx(r["achieved"] / bench.HBM_FALLBACK_GBS)
